@@ -1,0 +1,218 @@
+"""CPU oracle of the multi-morphology HH + Hines stepper (FP64).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by the smoke check and by
+the CPU-baseline leg of ``bench.py``; never by the library.  It shares no code
+with the CUDA path.  ``mm_oracle.c`` holds the arithmetic (see its header for
+the step order and the readings of the paper); this module builds it with gcc
+and wraps it with ctypes.  ``mlp.py`` holds the FP64 oracle of the cost-model
+network.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile mm_oracle.c (gcc, -O2, no FMA contraction, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+               "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [(k, C.c_double) for k in
+                ("gNa", "gK", "gL", "ENa", "EK", "EL", "Cm", "Ra", "v_init", "threshold", "tau_syn", "e_syn")]
+
+
+def params_from(d: dict) -> Params:
+    return Params(*[float(d[k]) for k in
+                    ("gNa", "gK", "gL", "ENa", "EK", "EL", "Cm", "Ra", "v_init", "threshold", "tau_syn", "e_syn")])
+
+
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_I64 = C.POINTER(C.c_int64)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB)
+            L.orc_area_cm2.restype = C.c_double
+            L.orc_area_cm2.argtypes = [C.c_double, C.c_double]
+            L.orc_rhalf_Mohm.restype = C.c_double
+            L.orc_rhalf_Mohm.argtypes = [C.c_double, C.c_double, C.c_double]
+            L.orc_exprelr.restype = C.c_double
+            L.orc_exprelr.argtypes = [C.c_double]
+            L.orc_rates.restype = None
+            L.orc_rates.argtypes = [C.c_double, _D]
+            L.orc_gates_inf.restype = None
+            L.orc_gates_inf.argtypes = [C.c_double, _D, _D, _D]
+            L.orc_gate_step.restype = None
+            L.orc_gate_step.argtypes = [C.c_double, C.c_double, _D, _D, _D]
+            L.orc_hines_solve.restype = None
+            L.orc_hines_solve.argtypes = [_D, _D, _D, _D, _I32, C.c_int32, _I64]
+            L.orc_geometry.restype = None
+            L.orc_geometry.argtypes = [C.c_int32, _I64, _I32, _D, _D, C.POINTER(Params), _D, _D, _D]
+            L.orc_assemble.restype = None
+            L.orc_assemble.argtypes = [C.c_int32, _I32, _D, _D, _D, _D, _D, _D, _D, _D, C.c_double,
+                                       C.POINTER(Params), C.c_double, _D, _D, _D, _D]
+            L.orc_simulate.restype = C.c_int
+            L.orc_simulate.argtypes = [C.c_int32, _I64, _I32, _D, _D, _D,
+                                       C.c_int64, _I32, _I32, _I32, _D, _D,
+                                       C.POINTER(Params), C.c_double, C.c_int64, _D,
+                                       _D, _D, _D, _D, _D, _D, _I32, _D, C.c_int64, _I64, C.c_int]
+            _lib = L
+    return _lib
+
+
+def _p(a, ct):
+    if a is None:
+        return None
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _i64(a):
+    return np.ascontiguousarray(a, dtype=np.int64)
+
+
+# ------------------------------------------------------------------ pieces
+
+def exprelr(x: float) -> float:
+    return lib().orc_exprelr(float(x))
+
+
+def rates(V: float) -> np.ndarray:
+    """[alpha_m, beta_m, alpha_h, beta_h, alpha_n, beta_n] at V (1/ms)."""
+    r = np.zeros(6)
+    lib().orc_rates(float(V), _p(r, C.c_double))
+    return r
+
+
+def gates_inf(V: float):
+    m, h, n = C.c_double(), C.c_double(), C.c_double()
+    lib().orc_gates_inf(float(V), C.byref(m), C.byref(h), C.byref(n))
+    return m.value, h.value, n.value
+
+
+def gate_step(V: float, dt: float, m: float, h: float, n: float):
+    cm, ch, cn = C.c_double(m), C.c_double(h), C.c_double(n)
+    lib().orc_gate_step(float(V), float(dt), C.byref(cm), C.byref(ch), C.byref(cn))
+    return cm.value, ch.value, cn.value
+
+
+def hines_solve(a, b, c, rhs, parent, count_ops: bool = False):
+    """Algorithm 1 on one tree; returns the solution (and the op count)."""
+    a, b, c, rhs = _f64(a).copy(), _f64(b).copy(), _f64(c).copy(), _f64(rhs).copy()
+    parent = _i32(parent)
+    ops = np.zeros(1, np.int64)
+    lib().orc_hines_solve(_p(a, C.c_double), _p(b, C.c_double), _p(c, C.c_double),
+                          _p(rhs, C.c_double), _p(parent, C.c_int32), len(rhs), _p(ops, C.c_int64))
+    return (rhs, int(ops[0])) if count_ops else rhs
+
+
+def geometry(comp_offset, parent, length_um, diam_um, params: dict):
+    """(area_cm2, C_nF, gax_uS) per compartment."""
+    off = _i64(comp_offset)
+    parent = _i32(parent)
+    L, d = _f64(length_um), _f64(diam_um)
+    n = int(off[-1])
+    area, Cn, gax = np.zeros(n), np.zeros(n), np.zeros(n)
+    pr = params_from(params)
+    lib().orc_geometry(len(off) - 1, _p(off, C.c_int64), _p(parent, C.c_int32), _p(L, C.c_double),
+                       _p(d, C.c_double), C.byref(pr), _p(area, C.c_double), _p(Cn, C.c_double),
+                       _p(gax, C.c_double))
+    return area, Cn, gax
+
+
+def assemble(parent, V, m, h, n, gsyn, area, Cn, gax, stim_nA, params: dict, dt: float):
+    """Hines system (a, b, c, rhs) of one neuron for dV."""
+    k = len(V)
+    parent = _i32(parent)
+    arrs = [_f64(x) for x in (V, m, h, n, gsyn, area, Cn, gax)]
+    a, b, c, rhs = np.zeros(k), np.zeros(k), np.zeros(k), np.zeros(k)
+    pr = params_from(params)
+    lib().orc_assemble(k, _p(parent, C.c_int32), *[_p(x, C.c_double) for x in arrs], float(stim_nA),
+                       C.byref(pr), float(dt), _p(a, C.c_double), _p(b, C.c_double), _p(c, C.c_double),
+                       _p(rhs, C.c_double))
+    return a, b, c, rhs
+
+
+# --------------------------------------------------------------- simulation
+
+class Result:
+    def __init__(self, V, m, h, n, g, soma_trace, spk_neuron, spk_t, n_spikes):
+        self.V, self.m, self.h, self.n, self.g = V, m, h, n, g
+        self.soma_trace = soma_trace
+        self.spk_neuron = spk_neuron
+        self.spk_t = spk_t
+        self.n_spikes = n_spikes
+
+    def spikes_sorted(self):
+        """(neuron, t) ordered by (t, neuron)."""
+        o = np.lexsort((self.spk_neuron, self.spk_t))
+        return self.spk_neuron[o], self.spk_t[o]
+
+
+def simulate(net, n_steps: int, dt: float = None, params: dict = None, V_init=None,
+             record_soma: bool = False, spike_cap: int = None, threads: int = 0) -> Result:
+    """Run the oracle on a ``netgen.Network`` for n_steps steps."""
+    dt = net.dt if dt is None else dt
+    params = net.params if params is None else params
+    pr = params_from(params)
+    off = _i64(net.comp_offset)
+    parent = _i32(net.parent)
+    L, d, stim = _f64(net.length_um), _f64(net.diam_um), _f64(net.stim_nA)
+    src, dst, comp = _i32(net.syn_src), _i32(net.syn_dst), _i32(net.syn_comp)
+    w, dl = _f64(net.syn_w), _f64(net.syn_delay_ms)
+    N = len(off) - 1
+    Cc = int(off[-1])
+    V, m, h, n, g = np.zeros(Cc), np.zeros(Cc), np.zeros(Cc), np.zeros(Cc), np.zeros(Cc)
+    trace = np.zeros((N, n_steps + 1)) if record_soma else None
+    cap = spike_cap if spike_cap is not None else max(1024, N * (n_steps // 40 + 2))
+    spn = np.zeros(cap, np.int32)
+    spt = np.zeros(cap, np.float64)
+    nsp = np.zeros(1, np.int64)
+    vi = None if V_init is None else _f64(V_init)
+    rc = lib().orc_simulate(N, _p(off, C.c_int64), _p(parent, C.c_int32), _p(L, C.c_double),
+                            _p(d, C.c_double), _p(stim, C.c_double), len(src), _p(src, C.c_int32),
+                            _p(dst, C.c_int32), _p(comp, C.c_int32), _p(w, C.c_double), _p(dl, C.c_double),
+                            C.byref(pr), float(dt), int(n_steps), _p(vi, C.c_double),
+                            _p(V, C.c_double), _p(m, C.c_double), _p(h, C.c_double), _p(n, C.c_double),
+                            _p(g, C.c_double), _p(trace, C.c_double), _p(spn, C.c_int32), _p(spt, C.c_double), cap,
+                            _p(nsp, C.c_int64), int(threads))
+    if rc == -1:
+        raise ValueError("oracle: invalid network")
+    if rc == -2:
+        raise MemoryError("oracle: allocation failed")
+    if rc == -3:
+        raise OverflowError("oracle: spike capacity exceeded")
+    k = int(nsp[0])
+    return Result(V, m, h, n, g, trace, spn[:k].copy(), spt[:k].copy(), k)

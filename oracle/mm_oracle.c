@@ -1,0 +1,414 @@
+/*
+ * mm_oracle.c -- plain, slow FP64 CPU oracle of the multi-morphology
+ * Hodgkin-Huxley + Hines time stepper.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check and the CPU
+ * baseline leg of bench.py may load this.  It shares no code, header or
+ * constant table with the CUDA library; both read the same seeded inputs.
+ *
+ * Units: um (lengths), cm^2 (areas), mV, ms, nA, uS, nF.
+ *
+ * What it computes, per time step n -> n+1 (t_n = n*dt), in this order:
+ *   1. event delivery: every event whose arrival step is n adds its weight
+ *      to the merged synaptic conductance of its target compartment,
+ *      ascending by synapse id (local/global buffers, Sec. 2);
+ *   2. currents at (V^n, gates^n, g_syn^n): Hodgkin-Huxley Na, K, leak,
+ *      synaptic, and the soma stimulus (the current I of Eq. 1);
+ *   3. assembly of the Hines system for dV = V^{n+1} - V^n, backward Euler
+ *      with the membrane conductance implicit (Eq. 2, in the symmetric
+ *      finite-volume reading, see below);
+ *   4. the Hines solve (Algorithm 1, backward sweep from the leaves to the
+ *      root over parent[], then forward substitution), V += dV;
+ *   5. exponential-Euler gate update at V^{n+1};
+ *   6. synaptic decay g_syn *= exp(-dt/tau);
+ *   7. soma threshold test: an upward crossing of theta between V^n and
+ *      V^{n+1} is a spike at the linearly interpolated time; each outgoing
+ *      synapse s then arrives at step n + 1 + round(delay_s/dt).
+ *
+ * Readings of the paper (Sec. 2) taken here:
+ *   - Eq. 2 prints the same g_{i+1/2} for both off-diagonals and a
+ *     half-explicit rhs; on a tree the link between i and p(i) carries one
+ *     conductance g_{i,p(i)}, so the matrix is symmetric (the Hines
+ *     property stated in Sec. 2): a_i = c_i = -g_{i,p(i)}, and
+ *     d_i = C_i/dt + G_i + sum_j g_ij,  rhs_i = -I_i + sum_j g_ij (V_j - V_i).
+ *   - Algorithm 1's backward loop is printed from n-1 down to 0; the root has
+ *     no parent, so it runs down to 1 and the root is finished by
+ *     rhs[0] /= b[0].
+ *   - Compartment indices are 0-based with parent[0] = -1, parent[i] < i.
+ *   - Capacitance is constant (Cm * area).
+ *   - The spike test is at the soma, threshold theta, upward crossing only.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+typedef struct {
+    double gNa, gK, gL;      /* mS/cm^2 */
+    double ENa, EK, EL;      /* mV */
+    double Cm;               /* uF/cm^2 */
+    double Ra;               /* ohm*cm */
+    double v_init;           /* mV */
+    double threshold;        /* mV */
+    double tau_syn;          /* ms */
+    double e_syn;            /* mV */
+} orc_params;
+
+/* ---------------------------------------------------------------- geometry */
+
+/* Lateral area of a cylinder, cm^2 (1 um^2 = 1e-8 cm^2). */
+double orc_area_cm2(double L_um, double d_um) { return ORC_PI * d_um * L_um * 1e-8; }
+
+/* Axial resistance of half a cylinder, MOhm. */
+double orc_rhalf_Mohm(double Ra, double L_um, double d_um)
+{
+    double len_cm = 0.5 * L_um * 1e-4;
+    double rad_cm = 0.5 * d_um * 1e-4;
+    double xsec_cm2 = ORC_PI * rad_cm * rad_cm;
+    return Ra * len_cm / xsec_cm2 * 1e-6;
+}
+
+/* Per-compartment constants of all neurons:
+ *   area_cm2[i], C_nF[i] = Cm * area * 1e3 (uF -> nF),
+ *   gax_uS[i] = 1 / (Rhalf_i + Rhalf_{p(i)}) for i != soma, 0 at the soma.
+ */
+void orc_geometry(int32_t n_neurons, const int64_t *off, const int32_t *parent,
+                  const double *L, const double *d, const orc_params *p,
+                  double *area_cm2, double *C_nF, double *gax_uS)
+{
+    for (int32_t k = 0; k < n_neurons; ++k) {
+        int64_t base = off[k];
+        int64_t n = off[k + 1] - off[k];
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t g = base + i;
+            area_cm2[g] = orc_area_cm2(L[g], d[g]);
+            C_nF[g] = p->Cm * area_cm2[g] * 1e3;
+            if (i == 0) {
+                gax_uS[g] = 0.0;
+            } else {
+                int64_t q = base + parent[g];
+                gax_uS[g] = 1.0 / (orc_rhalf_Mohm(p->Ra, L[g], d[g]) + orc_rhalf_Mohm(p->Ra, L[q], d[q]));
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------- HH kinetics */
+
+/* x / (exp(x) - 1), with its limit 1 - x/2 near x = 0 (expm1 keeps the
+ * quotient accurate close to the removable singularity). */
+double orc_exprelr(double x)
+{
+    if (fabs(x) < 1e-6) return 1.0 - 0.5 * x;
+    return x / expm1(x);
+}
+
+/* Hodgkin-Huxley rate functions (1/ms) at V (mV), rest at -65 mV, q10 = 1:
+ * r = {alpha_m, beta_m, alpha_h, beta_h, alpha_n, beta_n}. */
+void orc_rates(double V, double *r)
+{
+    r[0] = orc_exprelr(-(V + 40.0) / 10.0);
+    r[1] = 4.0 * exp(-(V + 65.0) / 18.0);
+    r[2] = 0.07 * exp(-(V + 65.0) / 20.0);
+    r[3] = 1.0 / (1.0 + exp(-(V + 35.0) / 10.0));
+    r[4] = 0.1 * orc_exprelr(-(V + 55.0) / 10.0);
+    r[5] = 0.125 * exp(-(V + 65.0) / 80.0);
+}
+
+/* Steady-state gates alpha / (alpha + beta) at V. */
+void orc_gates_inf(double V, double *m, double *h, double *n)
+{
+    double r[6];
+    orc_rates(V, r);
+    *m = r[0] / (r[0] + r[1]);
+    *h = r[2] / (r[2] + r[3]);
+    *n = r[4] / (r[4] + r[5]);
+}
+
+/* Exponential Euler for one gate with frozen V: exact solution of
+ * dx/dt = alpha (1 - x) - beta x over dt. */
+static double gate_exp_euler(double x, double alpha, double beta, double dt)
+{
+    double xinf = alpha / (alpha + beta);
+    return xinf + (x - xinf) * exp(-dt * (alpha + beta));
+}
+
+void orc_gate_step(double V, double dt, double *m, double *h, double *n)
+{
+    double r[6];
+    orc_rates(V, r);
+    *m = gate_exp_euler(*m, r[0], r[1], dt);
+    *h = gate_exp_euler(*h, r[2], r[3], dt);
+    *n = gate_exp_euler(*n, r[4], r[5], dt);
+}
+
+/* ------------------------------------------------------------- Hines solve */
+
+/* Algorithm 1 (Sec. 2): a = upper, b = diagonal, c = lower, p = parent.
+ * Row i holds b[i] on the diagonal and c[i] at column p[i]; row p[i] holds
+ * a[i] at column i.  On return rhs holds the solution; b is overwritten.
+ * If ops != NULL it is incremented by the floating-point operations done
+ * (the paper counts 8 per compartment). */
+void orc_hines_solve(double *a, double *b, double *c, double *rhs,
+                     const int32_t *p, int32_t n, int64_t *ops)
+{
+    int64_t cnt = 0;
+    /* backward sweep, leaves to root */
+    for (int32_t i = n - 1; i >= 1; --i) {
+        double factor = a[i] / b[i];
+        b[p[i]] -= factor * c[i];
+        rhs[p[i]] -= factor * rhs[i];
+        cnt += 5;
+    }
+    rhs[0] /= b[0];
+    cnt += 1;
+    /* forward sweep, root to leaves */
+    for (int32_t i = 1; i <= n - 1; ++i) {
+        rhs[i] -= c[i] * rhs[p[i]];
+        rhs[i] /= b[i];
+        cnt += 3;
+    }
+    if (ops) *ops += cnt;
+}
+
+/* ---------------------------------------------------------------- assembly */
+
+/* Membrane conductance G (uS) and current I (nA, outward positive) of one
+ * compartment at V with the given gates and merged synaptic conductance. */
+static void membrane(const orc_params *p, double area, double V, double m, double h,
+                     double n, double gsyn, double *G, double *I)
+{
+    double s = area * 1e3;                     /* mS/cm^2 * cm^2 -> uS */
+    double gna = p->gNa * s * m * m * m * h;
+    double gk = p->gK * s * n * n * n * n;
+    double gl = p->gL * s;
+    *G = gna + gk + gl + gsyn;
+    *I = gna * (V - p->ENa) + gk * (V - p->EK) + gl * (V - p->EL) + gsyn * (V - p->e_syn);
+}
+
+/* Hines system of one neuron for dV (Eq. 2, symmetric reading):
+ *   b_i   = C_i/dt + G_i + sum_{j~i} g_ij
+ *   a_i = c_i = -g_{i,p(i)}                       (i >= 1)
+ *   rhs_i = -I_i + sum_{j~i} g_ij (V_j - V_i)  (+ stim at the soma)
+ * All arrays are local to the neuron (length n). */
+void orc_assemble(int32_t n, const int32_t *parent, const double *V, const double *m,
+                  const double *h, const double *nn, const double *gsyn,
+                  const double *area, const double *C, const double *gax,
+                  double stim_nA, const orc_params *p, double dt,
+                  double *a, double *b, double *c, double *rhs)
+{
+    for (int32_t i = 0; i < n; ++i) {
+        double G, I;
+        membrane(p, area[i], V[i], m[i], h[i], nn[i], gsyn[i], &G, &I);
+        b[i] = C[i] / dt + G;
+        rhs[i] = -I;
+        a[i] = 0.0;
+        c[i] = 0.0;
+    }
+    rhs[0] += stim_nA;
+    for (int32_t i = 1; i < n; ++i) {
+        int32_t q = parent[i];
+        double g = gax[i];
+        a[i] = -g;
+        c[i] = -g;
+        b[i] += g;
+        b[q] += g;
+        rhs[i] += g * (V[q] - V[i]);
+        rhs[q] += g * (V[i] - V[q]);
+    }
+}
+
+/* ----------------------------------------------------------- the network */
+
+typedef struct {
+    int64_t *ids;
+    int64_t len, cap;
+} idlist;
+
+static int idlist_push(idlist *l, int64_t v)
+{
+    if (l->len == l->cap) {
+        int64_t nc = l->cap ? 2 * l->cap : 64;
+        int64_t *ni = (int64_t *)realloc(l->ids, (size_t)nc * sizeof(int64_t));
+        if (!ni) return -1;
+        l->ids = ni;
+        l->cap = nc;
+    }
+    l->ids[l->len++] = v;
+    return 0;
+}
+
+static int cmp_i64(const void *x, const void *y)
+{
+    int64_t a = *(const int64_t *)x, b = *(const int64_t *)y;
+    return (a > b) - (a < b);
+}
+
+/* Simulate n_steps steps of the whole network from rest (or from the given
+ * initial V; gates start at their steady state for that V, g_syn at 0).
+ *
+ * Outputs (any may be NULL):
+ *   V_out, m_out, h_out, n_out, g_out [n_comp] state after the last step
+ *                                             (g_out: merged synaptic conductance)
+ *   soma_trace [n_neurons * (n_steps + 1)]    soma V at t_0 .. t_nsteps
+ *   spk_neuron, spk_t [spk_cap]               spikes in detection order
+ * Returns 0, -1 on bad input, -2 on allocation failure, -3 if more than
+ * spk_cap spikes were detected (n_spk still counts all of them). */
+int orc_simulate(int32_t n_neurons, const int64_t *off, const int32_t *parent,
+                 const double *L, const double *diam, const double *stim_nA,
+                 int64_t n_syn, const int32_t *syn_src, const int32_t *syn_dst,
+                 const int32_t *syn_comp, const double *syn_w, const double *syn_delay_ms,
+                 const orc_params *p, double dt, int64_t n_steps, const double *V_init,
+                 double *V_out, double *m_out, double *h_out, double *n_out,
+                 double *g_out, double *soma_trace, int32_t *spk_neuron, double *spk_t, int64_t spk_cap,
+                 int64_t *n_spk, int n_threads)
+{
+    int64_t C = off[n_neurons];
+    int rc = 0;
+    if (dt <= 0.0 || n_neurons < 0) return -1;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+    double *area = malloc((size_t)C * sizeof(double));
+    double *Cn = malloc((size_t)C * sizeof(double));
+    double *gax = malloc((size_t)C * sizeof(double));
+    double *V = malloc((size_t)C * sizeof(double));
+    double *m = malloc((size_t)C * sizeof(double));
+    double *h = malloc((size_t)C * sizeof(double));
+    double *nn = malloc((size_t)C * sizeof(double));
+    double *gs = calloc((size_t)C, sizeof(double));
+    double *wa = malloc((size_t)C * sizeof(double));
+    double *wb = malloc((size_t)C * sizeof(double));
+    double *wc = malloc((size_t)C * sizeof(double));
+    double *wr = malloc((size_t)C * sizeof(double));
+    unsigned char *fired = calloc((size_t)(n_neurons > 0 ? n_neurons : 1), 1);
+    double *tfire = malloc((size_t)(n_neurons > 0 ? n_neurons : 1) * sizeof(double));
+    int64_t *out_start = calloc((size_t)n_neurons + 1, sizeof(int64_t));
+    int64_t *out_syn = malloc((size_t)(n_syn > 0 ? n_syn : 1) * sizeof(int64_t));
+    int64_t *dsteps = malloc((size_t)(n_syn > 0 ? n_syn : 1) * sizeof(int64_t));
+    idlist *ring = NULL;
+    int64_t R = 2;
+    if (!area || !Cn || !gax || !V || !m || !h || !nn || !gs || !wa || !wb || !wc || !wr ||
+        !fired || !tfire || !out_start || !out_syn || !dsteps) {
+        rc = -2;
+        goto done;
+    }
+
+    /* validate */
+    for (int32_t k = 0; k < n_neurons; ++k) {
+        int64_t n = off[k + 1] - off[k];
+        if (n < 1 || parent[off[k]] != -1) { rc = -1; goto done; }
+        for (int64_t i = 1; i < n; ++i)
+            if (parent[off[k] + i] < 0 || parent[off[k] + i] >= i) { rc = -1; goto done; }
+    }
+    for (int64_t s = 0; s < n_syn; ++s) {
+        if (syn_src[s] < 0 || syn_src[s] >= n_neurons || syn_dst[s] < 0 || syn_dst[s] >= n_neurons ||
+            syn_comp[s] < 0 || syn_comp[s] >= off[syn_dst[s] + 1] - off[syn_dst[s]]) { rc = -1; goto done; }
+        dsteps[s] = (int64_t)llround(syn_delay_ms[s] / dt);
+        if (dsteps[s] < 1) { rc = -1; goto done; }
+        if (dsteps[s] + 2 > R) R = dsteps[s] + 2;
+    }
+
+    orc_geometry(n_neurons, off, parent, L, diam, p, area, Cn, gax);
+
+    /* outgoing synapses of each source, ascending synapse id */
+    for (int64_t s = 0; s < n_syn; ++s) out_start[syn_src[s] + 1]++;
+    for (int32_t k = 0; k < n_neurons; ++k) out_start[k + 1] += out_start[k];
+    {
+        int64_t *fill = calloc((size_t)n_neurons + 1, sizeof(int64_t));
+        if (!fill) { rc = -2; goto done; }
+        for (int64_t s = 0; s < n_syn; ++s) {
+            int32_t src = syn_src[s];
+            out_syn[out_start[src] + fill[src]++] = s;
+        }
+        free(fill);
+    }
+    ring = calloc((size_t)R, sizeof(idlist));
+    if (!ring) { rc = -2; goto done; }
+
+    /* initial state */
+    for (int64_t i = 0; i < C; ++i) {
+        V[i] = V_init ? V_init[i] : p->v_init;
+        orc_gates_inf(V[i], &m[i], &h[i], &nn[i]);
+    }
+    if (soma_trace)
+        for (int32_t k = 0; k < n_neurons; ++k) soma_trace[(int64_t)k * (n_steps + 1)] = V[off[k]];
+
+    const double decay = exp(-dt / p->tau_syn);
+    int64_t nsp = 0;
+    for (int64_t step = 0; step < n_steps; ++step) {
+        /* 1. deliver events due at this step, ascending synapse id */
+        idlist *due = &ring[step % R];
+        if (due->len > 1) qsort(due->ids, (size_t)due->len, sizeof(int64_t), cmp_i64);
+        for (int64_t e = 0; e < due->len; ++e) {
+            int64_t s = due->ids[e];
+            gs[off[syn_dst[s]] + syn_comp[s]] += syn_w[s];
+        }
+        due->len = 0;
+
+        /* 2-7. every neuron independently */
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int32_t k = 0; k < n_neurons; ++k) {
+            int64_t b0 = off[k];
+            int32_t n = (int32_t)(off[k + 1] - off[k]);
+            double v0 = V[b0];
+            orc_assemble(n, parent + b0, V + b0, m + b0, h + b0, nn + b0, gs + b0,
+                         area + b0, Cn + b0, gax + b0, stim_nA[k], p, dt,
+                         wa + b0, wb + b0, wc + b0, wr + b0);
+            orc_hines_solve(wa + b0, wb + b0, wc + b0, wr + b0, parent + b0, n, NULL);
+            for (int32_t i = 0; i < n; ++i) {
+                V[b0 + i] += wr[b0 + i];
+                orc_gate_step(V[b0 + i], dt, &m[b0 + i], &h[b0 + i], &nn[b0 + i]);
+                gs[b0 + i] *= decay;
+            }
+            double v1 = V[b0];
+            fired[k] = 0;
+            if (v0 < p->threshold && v1 >= p->threshold) {
+                fired[k] = 1;
+                tfire[k] = (double)step * dt + dt * (p->threshold - v0) / (v1 - v0);
+            }
+        }
+        /* spikes in neuron order; schedule their events */
+        for (int32_t k = 0; k < n_neurons; ++k) {
+            if (!fired[k]) continue;
+            if (nsp < spk_cap) {
+                if (spk_neuron) spk_neuron[nsp] = k;
+                if (spk_t) spk_t[nsp] = tfire[k];
+            } else {
+                rc = -3;
+            }
+            nsp++;
+            for (int64_t o = out_start[k]; o < out_start[k + 1]; ++o) {
+                int64_t s = out_syn[o];
+                int64_t arrival = step + 1 + dsteps[s];
+                if (idlist_push(&ring[arrival % R], s)) { rc = -2; goto done; }
+            }
+        }
+        if (soma_trace)
+            for (int32_t k = 0; k < n_neurons; ++k)
+                soma_trace[(int64_t)k * (n_steps + 1) + step + 1] = V[off[k]];
+    }
+    if (n_spk) *n_spk = nsp;
+    if (V_out) memcpy(V_out, V, (size_t)C * sizeof(double));
+    if (m_out) memcpy(m_out, m, (size_t)C * sizeof(double));
+    if (h_out) memcpy(h_out, h, (size_t)C * sizeof(double));
+    if (n_out) memcpy(n_out, nn, (size_t)C * sizeof(double));
+    if (g_out) memcpy(g_out, gs, (size_t)C * sizeof(double));
+
+done:
+    if (ring) {
+        for (int64_t r = 0; r < R; ++r) free(ring[r].ids);
+        free(ring);
+    }
+    free(area); free(Cn); free(gax); free(V); free(m); free(h); free(nn); free(gs);
+    free(wa); free(wb); free(wc); free(wr); free(fired); free(tfire);
+    free(out_start); free(out_syn); free(dsteps);
+    return rc;
+}
