@@ -1,0 +1,279 @@
+#!/usr/bin/env python3
+"""Benchmark of the multi-morphology HH + Hines stepper on one GB300 (or N).
+
+A "step" is one time step dt of the whole network: spike delivery plus the
+fused gates + currents + assembly + Hines solve + spike-detection kernel.
+The metric is compartment-updates per second (compartments x steps / time).
+
+Default workload: the 10,000-neuron multi-morphology network (compartment
+counts log-uniform in [50, 5000], branch probability U[0.02, 0.2], 100
+synapses per neuron, dt = 0.025 ms), FP64, in the launch configuration of
+the library's defaults (CUDA graphs of 40 steps).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config multi10k] [--precision fp64|fp32c]
+
+Under torchrun (N > 1) every rank runs its own replica of the workload
+(weak scaling) and rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2005_06332_gb300 import netgen  # noqa: E402
+
+METRIC = "compartment-updates/sec (HH+Hines per dt) on 1 GB300, % HBM roofline, vs plain FP64"
+UNIT = "compartment-updates/s"
+L2_BYTES = 129 * 1024 * 1024
+
+# Algorithmic bytes per compartment-update of the fused step kernel:
+# FP64 state V, m, h, n read + written (64 B) and the constants area, g_axial
+# read (16 B); per synaptic site g_syn read + written and its index (20 B).
+BYTES_PER_UPDATE = {"fp64": (80.0, 20.0)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            if self.thread is not None:
+                self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(net, seconds_hint: float = 15.0):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    rng = np.random.default_rng(0)
+    k = min(net.n_neurons, 1000)
+    pick = np.sort(rng.choice(net.n_neurons, k, replace=False))
+    sub = net.subset(pick, keep_synapses=True)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.simulate(sub, 4, threads=cores)
+    probe = max(1e-3, time.perf_counter() - t0)
+    steps = int(max(8, min(400, 4 * seconds_hint / probe)))
+    t0 = time.perf_counter()
+    oracle.simulate(sub, steps, threads=cores)
+    el = time.perf_counter() - t0
+    return {"value": sub.n_comp * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{k} of {net.n_neurons} neurons ({sub.n_comp} compartments, synapses among them), "
+                      f"{steps} steps from rest, FP64 C oracle with OpenMP over neurons"}
+
+
+def run_reference(args, net):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    rng = np.random.default_rng(0)
+    k = min(net.n_neurons, 1000)
+    pick = np.sort(rng.choice(net.n_neurons, k, replace=False))
+    sub = net.subset(pick, keep_synapses=True)
+    cores = os.cpu_count() or 1
+    oracle.simulate(sub, max(1, args.warmup), threads=cores)
+    t0 = time.perf_counter()
+    oracle.simulate(sub, args.steps, threads=cores)
+    el = time.perf_counter() - t0
+    v = sub.n_comp * args.steps / el
+    sample = (f"{k} of {net.n_neurons} neurons ({sub.n_comp} compartments, synapses among them), "
+              f"{args.steps} steps after {args.warmup} warm-up steps")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": net.name, "n_neurons": net.n_neurons, "n_comp": net.n_comp, "sampled": sample},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="multi10k")
+    ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32c"])
+    ap.add_argument("--graph-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    net = netgen.make_config(args.config)
+    precision = args.precision or net.params.get("precision", "fp64")
+    if args.impl == "reference":
+        run_reference(args, net)
+        return
+
+    import torch
+    from paper_2005_06332_gb300 import mm
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    mm.load()
+    stream = torch.cuda.Stream(device=local)
+    g = mm.Network(net, precision=precision, graph_steps=args.graph_steps, device=local, stream=stream.cuda_stream)
+
+    # warm-up (also captures the CUDA graph)
+    g.step(args.warmup)
+    g.synchronize()
+
+    # timed region: K steps, CUDA events on the launching stream; the state
+    # (> 500 MB for the default workload) is larger than L2.
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        g.step(args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    G = args.graph_steps
+    K = args.steps
+    launches = (K // G) * (2 * G + 1) + ((K % G > 0) * (2 * (K % G) + 1)) if G > 0 else 2 * K + 1
+    updates = net.n_comp * K * ws
+    value = updates / (ms * 1e-3)
+
+    # per-kernel times (events around each launch, direct launches)
+    kt_steps = max(10, K // 4)
+    g.set_kernel_timing(True)
+    g.step(kt_steps)
+    kt = g.read_kernel_timing(reset=True)
+    g.set_kernel_timing(False)
+    step_ms = kt["step_kernel_ms"] / max(1, kt["step_kernel_launches"])
+    deliver_ms = kt["deliver_kernel_ms"] / max(1, kt["deliver_kernel_launches"])
+
+    # end to end through the public API with host buffers: per step the soma
+    # stimulus goes host -> device and the soma voltages and spikes come back.
+    stim = np.ascontiguousarray(net.stim_nA, np.float64)
+    soma = np.empty(net.n_neurons, np.float64)
+    ke = args.e2e_steps
+    n_spk = 0
+    g.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        g.set_stimulus(stim)
+        g.step(1)
+        g.read_soma(soma)
+        sn, _st = g.read_spikes(allow_overflow=True)
+        n_spk += len(sn)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": net.n_comp * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * net.n_neurons,
+           "d2h_bytes_per_step": int(8 * net.n_neurons + round(12 * n_spk / ke)), "steps": ke,
+           "calls_per_step": "mm_set_stimulus, mm_step(1), mm_read_soma_voltages, mm_read_spikes"}
+
+    peak, peak_kind = _peaks()
+    b0, bsite = BYTES_PER_UPDATE.get(precision, (80.0, 20.0))
+    nsite = int(np.unique(net.syn_comp.astype(np.int64) + net.comp_offset[net.syn_dst]).size)
+    bytes_per_launch = b0 * net.n_comp + bsite * nsite
+    achieved = bytes_per_launch / (step_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_kind": peak_kind, "kernel": f"step_{precision}",
+                "kernel_ms": step_ms, "deliver_kernel_ms": deliver_ms,
+                "bytes_per_launch": bytes_per_launch,
+                "bytes_per_update": f"{b0:g} B per compartment + {bsite:g} B per synaptic site"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+           "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if precision == "fp64" else "f32", "data": "synthetic",
+           "config": {"workload": net.name, "precision": precision, "n_neurons": net.n_neurons,
+                      "n_comp": net.n_comp, "n_syn": net.n_syn, "dt_ms": net.dt, "graph_steps": G,
+                      "l2": f"inputs larger than L2 (state + constants {(48 * net.n_comp) / 1e6:.0f} MB)",
+                      "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(net)
+    g.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

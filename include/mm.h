@@ -1,0 +1,221 @@
+/*
+ * mm.h -- C-ABI of the GB300 multi-morphology neuron stepper.
+ *
+ * The library advances many neurons of different shapes and sizes at once.
+ * Each neuron is a tree of cylinder compartments; every time step it
+ * updates the membrane voltage of every compartment: Hodgkin-Huxley gating
+ * and currents, assembly of the neuron's Hines matrix, the Hines tree solve,
+ * synaptic currents, soma spike detection and delayed spike delivery.  The
+ * calls follow the paper's statement of the problem (Sec. 2): a network is
+ * created from morphologies (compartment trees given by parent arrays),
+ * channel parameters and synapses, stepped in time, and its voltages and
+ * spikes are read back.
+ *
+ * Units: um, mV, ms, nA, uS, nF; channel densities in mS/cm^2, membrane
+ * capacitance in uF/cm^2, axial resistivity in ohm*cm.
+ *
+ * Conventions shared by every call:
+ *   - Pointers to inputs are HOST pointers, owned by the caller and only
+ *     read during the call (the library copies what it keeps).
+ *   - Device memory is owned by the library: allocated at create through
+ *     the allocator in mm_options (or cudaMalloc when none is given) and
+ *     released by mm_destroy.
+ *   - Every call returns an mm_status and never throws.  After a CUDA error
+ *     or a failed kernel check the network is poisoned: every later call
+ *     except mm_last_error / mm_destroy returns MM_ESTATE.
+ *   - mm_step is asynchronous on the network's stream; errors raised by its
+ *     kernels surface at the next synchronising call (the mm_read_* calls,
+ *     mm_save_state, mm_synchronize).
+ *   - A network is used from one host thread at a time.
+ */
+#ifndef MM_H_
+#define MM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mm_net mm_net; /* opaque, library-owned */
+
+typedef enum {
+    MM_OK = 0,
+    MM_EINVAL = 1,     /* an argument or an input array is invalid */
+    MM_ENOMEM = 2,     /* a device or host allocation failed */
+    MM_ECUDA = 3,      /* a CUDA call failed */
+    MM_ETIMEOUT = 4,   /* a bounded device wait gave up */
+    MM_ENUMERIC = 5,   /* a soma voltage became NaN or infinite */
+    MM_EOVERFLOW = 6,  /* more spikes than the spike buffer holds were detected */
+    MM_ESTATE = 7,     /* the network is poisoned by an earlier error */
+    MM_ENOTSUP = 8     /* valid request this build does not support */
+} mm_status;
+
+/* Arithmetic of the time step. */
+enum {
+    MM_FP64 = 0,   /* everything in FP64 */
+    MM_FP32C = 1   /* FP32 gates, currents and solve with compensated (TwoSum)
+                      elimination and voltage updates; FP64 soma voltage and
+                      spike-crossing time */
+};
+
+/* Order in which the per-step kernel takes its work items. */
+enum {
+    MM_SCHED_SIZE_SORTED = 0,  /* neurons sorted by compartment count, largest first */
+    MM_SCHED_COST = 1          /* neurons sorted by mm_options.cost, largest first */
+};
+
+/* What mm_read_state reads. */
+enum {
+    MM_STATE_V = 0,      /* membrane voltage, mV */
+    MM_STATE_M = 1,      /* Na activation gate */
+    MM_STATE_H = 2,      /* Na inactivation gate */
+    MM_STATE_N = 3,      /* K activation gate */
+    MM_STATE_GSYN = 4    /* merged synaptic conductance, uS (0 where no synapse) */
+};
+
+/* Neuron morphologies (Sec. 2: compartments joined into an acyclic tree,
+ * numbered so that every parent precedes its children).
+ *   comp_offset [n_neurons+1]: neuron k owns compartments
+ *                comp_offset[k] .. comp_offset[k+1]-1 (user numbering);
+ *                comp_offset[0] = 0, strictly increasing.
+ *   parent      [comp_offset[n]]: LOCAL parent index within the neuron;
+ *                -1 at local index 0 (the soma) and 0 <= parent[i] < i elsewhere.
+ *   length_um, diam_um [comp_offset[n]]: cylinder of each compartment, > 0. */
+typedef struct {
+    int32_t n_neurons;
+    const int64_t *comp_offset;
+    const int32_t *parent;
+    const double *length_um;
+    const double *diam_um;
+} mm_morphologies;
+
+/* Hodgkin-Huxley channels (the current I of Eq. 1) and cable constants. */
+typedef struct {
+    double gNa, gK, gL;     /* mS/cm^2 */
+    double ENa, EK, EL;     /* mV */
+    double Cm;              /* uF/cm^2 */
+    double Ra;              /* ohm*cm */
+    double v_init;          /* initial voltage, mV; gates start at steady state */
+    double threshold_mV;    /* soma spike threshold (upward crossing) */
+} mm_channel_params;
+
+/* Exponential synapses.  Synapse s makes a spike of neuron src_neuron[s]
+ * raise the conductance of compartment dst_comp[s] (LOCAL index) of neuron
+ * dst_neuron[s] by weight_uS[s], round(delay_ms[s]/dt) + 1 steps after the
+ * step in which the spike was detected; conductances decay with tau_ms and
+ * drive the current g (V - e_rev_mV).  Arrays have n entries (n may be 0). */
+typedef struct {
+    int64_t n;
+    const int32_t *src_neuron;
+    const int32_t *dst_neuron;
+    const int32_t *dst_comp;
+    const double *weight_uS;   /* >= 0 */
+    const double *delay_ms;    /* round(delay/dt) >= 1 */
+    double tau_ms;             /* > 0 */
+    double e_rev_mV;
+} mm_synapses;
+
+/* Device-memory allocator: alloc returns a device pointer (256-byte aligned)
+ * or NULL; release frees it.  Used for every device buffer of a network. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*release)(void *ptr, void *ctx);
+    void *ctx;
+} mm_allocator;
+
+typedef struct {
+    int32_t precision;          /* MM_FP64 | MM_FP32C */
+    int32_t schedule;           /* MM_SCHED_SIZE_SORTED | MM_SCHED_COST */
+    int32_t graph_steps;        /* steps per captured CUDA graph; 0 = no graphs */
+    int32_t block_threads;      /* threads per work item's block; 0 = automatic */
+    int32_t group_comps;        /* compartment budget of one work item; 0 = automatic */
+    int32_t device;             /* CUDA device ordinal */
+    double dt_ms;               /* time step of the network, > 0 */
+    int64_t spike_capacity;     /* spikes held between two mm_read_spikes; 0 = automatic */
+    void *cuda_stream;          /* cudaStream_t to run on; NULL = a library-owned stream */
+    const float *cost;          /* [n_neurons] per-neuron cost for MM_SCHED_COST, or NULL */
+    mm_allocator allocator;     /* alloc == NULL: cudaMalloc / cudaFree */
+} mm_options;
+
+/* Fill *opt with defaults: FP64, size-sorted, graphs of 40 steps, dt 0.025 ms. */
+void mm_default_options(mm_options *opt);
+
+/* Build a network (Sec. 2: morphologies, parent arrays, channel parameters,
+ * synapses) and its device state at rest.  stim_nA [n_neurons]: constant
+ * current injected into each soma from t = 0 (may be NULL: no stimulus).
+ * On success *out owns the network; on failure *out is NULL.
+ * Errors: MM_EINVAL (bad sizes, parent[i] >= i, non-positive geometry,
+ * dst_comp out of range, delay < dt, dt <= 0), MM_ENOMEM, MM_ECUDA, MM_ENOTSUP. */
+mm_status mm_create_network(const mm_morphologies *morph, const mm_channel_params *chan,
+                            const mm_synapses *syn, const double *stim_nA,
+                            const mm_options *opt, mm_net **out);
+
+/* Advance n_steps >= 0 time steps of dt_ms, which must equal the network's
+ * dt.  Asynchronous on the network's stream. */
+mm_status mm_step(mm_net *net, int64_t n_steps, double dt_ms);
+
+/* Wait for the network's stream and report any error its kernels raised. */
+mm_status mm_synchronize(mm_net *net);
+
+/* Copy the voltage of every compartment, in user numbering, into the host
+ * array out [cap >= total compartments].  Synchronises. */
+mm_status mm_read_voltages(mm_net *net, double *out, int64_t cap);
+
+/* Like mm_read_voltages for any MM_STATE_* quantity. */
+mm_status mm_read_state(mm_net *net, int32_t which, double *out, int64_t cap);
+
+/* Soma voltage of every neuron, in user neuron order, into out [cap >= n_neurons]. */
+mm_status mm_read_soma_voltages(mm_net *net, double *out, int64_t cap);
+
+/* Drain the spikes detected since the last call: neuron (user id) and
+ * crossing time t_ms, ordered by (t, neuron).  Writes min(cap, count)
+ * records and the count to *n_out.  MM_EOVERFLOW if the device buffer
+ * overflowed (the records it held are still returned).  Synchronises. */
+mm_status mm_read_spikes(mm_net *net, int32_t *neuron, double *t_ms, int64_t cap, int64_t *n_out);
+
+/* Replace the soma stimulus of every neuron (host array [n], n = n_neurons). */
+mm_status mm_set_stimulus(mm_net *net, const double *stim_nA, int64_t n);
+
+/* Steps taken so far. */
+mm_status mm_get_step(const mm_net *net, int64_t *step);
+
+/* Checkpoint: the whole dynamic state (voltages, gates, synaptic
+ * conductances, in-flight spikes, step counter).  mm_save_state with
+ * buf == NULL stores the needed size in *len.  mm_load_state restores a
+ * state saved from a network created with identical inputs and options;
+ * the continued run is bitwise identical to an uninterrupted one. */
+mm_status mm_save_state(mm_net *net, void *buf, size_t cap, size_t *len);
+mm_status mm_load_state(mm_net *net, const void *buf, size_t len);
+
+/* Per-kernel device time, measured with CUDA events recorded on the
+ * network's stream around each launch while timing is enabled. */
+typedef struct {
+    double step_kernel_ms;          /* fused per-step kernel, summed */
+    int64_t step_kernel_launches;
+    double deliver_kernel_ms;       /* spike-delivery kernel, summed */
+    int64_t deliver_kernel_launches;
+} mm_kernel_times;
+
+/* While enabled (enable != 0), mm_step launches every kernel directly (no
+ * CUDA graph) with a start/stop event pair around it. */
+mm_status mm_set_kernel_timing(mm_net *net, int32_t enable);
+
+/* Synchronise and report the time accumulated since the last reset;
+ * reset != 0 clears the totals afterwards. */
+mm_status mm_read_kernel_timing(mm_net *net, mm_kernel_times *out, int32_t reset);
+
+/* Message of the last error on this network ("" if none); never NULL. */
+const char *mm_last_error(const mm_net *net);
+
+/* Static name of a status code. */
+const char *mm_status_string(mm_status s);
+
+/* Release the network and all its device memory (NULL is ignored). */
+void mm_destroy(mm_net *net);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MM_H_ */

@@ -1,0 +1,758 @@
+// mm_api.cpp -- the C-ABI of include/mm.h: network lifetime, device memory,
+// step launches (direct and CUDA-graph), reads, stimulus and checkpoints.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mm.h"
+#include "mm_internal.h"
+#include "mm_layout.h"
+
+namespace {
+
+constexpr int kStepThreads = 256;
+constexpr int kDefaultGroupComps = 4096;
+constexpr int kMaxGroupComps = 8192;
+constexpr size_t kMaxSmem = 227 * 1024;
+
+}  // namespace
+
+struct mm_net {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;
+    mm_allocator alloc{};
+    std::vector<void *> blocks;
+    std::string err;
+    bool poisoned = false;
+
+    int precision = MM_FP64;
+    double dt = 0.025;
+    int32_t N = 0;
+    int64_t C = 0, nsite = 0, S = 0;
+    int32_t R = 2;
+    int64_t spk_cap = 0;
+    int64_t steps_done = 0;
+
+    mmk::StepArgs sa{};
+    mmk::DeliverArgs da{};
+    int step_blocks = 1, step_threads = kStepThreads, deliver_blocks = 1;
+    int graph_steps = 40;
+    cudaGraphExec_t gexec = nullptr;
+
+    // device arrays
+    double *V = nullptr, *m = nullptr, *h = nullptr, *n = nullptr;
+    double *area = nullptr, *gax = nullptr, *stim = nullptr, *gsyn = nullptr;
+    double *spk_t = nullptr, *scratch = nullptr;
+    int32_t *spk_nrn = nullptr, *ring_nrn = nullptr, *ring_cnt = nullptr, *user_id = nullptr;
+    int64_t *user2int = nullptr, *soma_of_user = nullptr, *site_internal = nullptr;
+    mmk::DevCtl *ctl = nullptr;
+
+    // kernel timing (events around each launch while enabled)
+    bool timing = false;
+    struct Pending { cudaEvent_t a, b; int kind; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    mm_kernel_times times{};
+
+    std::vector<int32_t> order;          // internal -> user
+    std::vector<int32_t> internal_of;    // user -> internal
+    double f_syn = 0.0;
+};
+
+namespace {
+
+mm_status fail(mm_net *net, mm_status s, const std::string &m)
+{
+    if (net) {
+        if (net->err.empty() || s != MM_OK) net->err = m;
+        if (s == MM_ECUDA || s == MM_ENUMERIC || s == MM_ETIMEOUT) net->poisoned = true;
+    }
+    return s;
+}
+
+mm_status cuda_fail(mm_net *net, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(net, MM_ECUDA, m);
+}
+
+#define MM_CK(net, call)                                         \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail((net), e_, #call); \
+    } while (0)
+
+#define MM_CKI(net, call)                                                        \
+    do {                                                                         \
+        int e_ = (call);                                                         \
+        if (e_ != 0) return cuda_fail((net), (cudaError_t)e_, #call);            \
+    } while (0)
+
+void *dev_alloc(mm_net *net, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (net->alloc.alloc) {
+        p = net->alloc.alloc(bytes, net->alloc.ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) net->blocks.push_back(p);
+    return p;
+}
+
+template <class T>
+mm_status upload(mm_net *net, T **dst, const T *src, size_t count)
+{
+    *dst = (T *)dev_alloc(net, count * sizeof(T));
+    if (!*dst) return fail(net, MM_ENOMEM, "device allocation failed");
+    if (count && src) MM_CK(net, cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, net->stream));
+    return MM_OK;
+}
+
+template <class T>
+mm_status zeros(mm_net *net, T **dst, size_t count)
+{
+    *dst = (T *)dev_alloc(net, count * sizeof(T));
+    if (!*dst) return fail(net, MM_ENOMEM, "device allocation failed");
+    MM_CK(net, cudaMemsetAsync(*dst, 0, count * sizeof(T), net->stream));
+    return MM_OK;
+}
+
+mm_status guard(mm_net *net)
+{
+    if (!net) return MM_EINVAL;
+    if (net->poisoned) return MM_ESTATE;
+    if (cudaSetDevice(net->device) != cudaSuccess) return cuda_fail(net, cudaGetLastError(), "cudaSetDevice");
+    return MM_OK;
+}
+
+// Device error word -> status (synchronising).
+mm_status check_device(mm_net *net)
+{
+    MM_CK(net, cudaStreamSynchronize(net->stream));
+    mmk::DevCtl c;
+    MM_CK(net, cudaMemcpy(&c, net->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+    if (c.err & mmk::MMK_ERR_NUMERIC) return fail(net, MM_ENUMERIC, "a soma voltage became NaN or infinite");
+    return MM_OK;
+}
+
+cudaError_t take_event(mm_net *net, cudaEvent_t *e)
+{
+    if (!net->event_pool.empty()) {
+        *e = net->event_pool.back();
+        net->event_pool.pop_back();
+        return cudaSuccess;
+    }
+    return cudaEventCreate(e);
+}
+
+mm_status collect_timing(mm_net *net)
+{
+    for (auto &p : net->pending) {
+        MM_CK(net, cudaEventSynchronize(p.b));
+        float ms = 0.f;
+        MM_CK(net, cudaEventElapsedTime(&ms, p.a, p.b));
+        if (p.kind == 0) {
+            net->times.deliver_kernel_ms += ms;
+            net->times.deliver_kernel_launches++;
+        } else {
+            net->times.step_kernel_ms += ms;
+            net->times.step_kernel_launches++;
+        }
+        net->event_pool.push_back(p.a);
+        net->event_pool.push_back(p.b);
+    }
+    net->pending.clear();
+    return MM_OK;
+}
+
+mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
+{
+    const bool timed = net->timing && s == net->stream;
+    for (int j = 0; j < count; ++j) {
+        for (int kind = 0; kind < 2; ++kind) {
+            mm_net::Pending p{nullptr, nullptr, kind};
+            if (timed) {
+                MM_CK(net, take_event(net, &p.a));
+                MM_CK(net, take_event(net, &p.b));
+                MM_CK(net, cudaEventRecord(p.a, s));
+            }
+            if (kind == 0) {
+                mmk::DeliverArgs da = net->da;
+                da.step_offset = j;
+                MM_CKI(net, mmk_launch_deliver(da, net->deliver_blocks, s));
+            } else {
+                mmk::StepArgs sa = net->sa;
+                sa.step_offset = j;
+                MM_CKI(net, mmk_launch_step_fp64(sa, net->step_blocks, net->step_threads, s));
+            }
+            if (timed) {
+                MM_CK(net, cudaEventRecord(p.b, s));
+                net->pending.push_back(p);
+            }
+        }
+        if (timed && net->pending.size() > 4096) {
+            mm_status st = collect_timing(net);
+            if (st != MM_OK) return st;
+        }
+    }
+    MM_CKI(net, mmk_launch_advance(net->ctl, count, s));
+    return MM_OK;
+}
+
+mm_status ensure_graph(mm_net *net)
+{
+    if (net->gexec || net->graph_steps <= 0) return MM_OK;
+    cudaGraph_t graph = nullptr;
+    MM_CK(net, cudaStreamBeginCapture(net->cap_stream, cudaStreamCaptureModeThreadLocal));
+    mm_status st = launch_steps(net, net->cap_stream, net->graph_steps);
+    cudaError_t e = cudaStreamEndCapture(net->cap_stream, &graph);
+    if (st != MM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(net, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&net->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        net->gexec = nullptr;
+        return cuda_fail(net, e, "cudaGraphInstantiate");
+    }
+    return MM_OK;
+}
+
+void release_all(mm_net *net)
+{
+    if (net->gexec) cudaGraphExecDestroy(net->gexec);
+    net->gexec = nullptr;
+    if (net->stream) cudaStreamSynchronize(net->stream);
+    for (auto &p : net->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    net->pending.clear();
+    for (cudaEvent_t e : net->event_pool) cudaEventDestroy(e);
+    net->event_pool.clear();
+    for (void *p : net->blocks) {
+        if (net->alloc.alloc) {
+            if (net->alloc.release) net->alloc.release(p, net->alloc.ctx);
+        } else {
+            cudaFree(p);
+        }
+    }
+    net->blocks.clear();
+    if (net->cap_stream) cudaStreamDestroy(net->cap_stream);
+    if (net->own_stream && net->stream) cudaStreamDestroy(net->stream);
+    net->cap_stream = nullptr;
+    net->stream = nullptr;
+}
+
+mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_params *chan, const mm_synapses *syn,
+                const double *stim_nA, const mm_options *opt)
+{
+    net->precision = opt->precision;
+    net->dt = opt->dt_ms;
+    net->graph_steps = std::max(0, opt->graph_steps);
+    net->device = opt->device;
+    net->alloc = opt->allocator;
+    if (opt->precision != MM_FP64) return fail(net, MM_ENOTSUP, "only MM_FP64 is available in this build");
+    if (opt->schedule != MM_SCHED_SIZE_SORTED && opt->schedule != MM_SCHED_COST)
+        return fail(net, MM_EINVAL, "unknown schedule");
+    if (opt->schedule == MM_SCHED_COST && !opt->cost) return fail(net, MM_EINVAL, "MM_SCHED_COST needs mm_options.cost");
+    if (syn && !(syn->tau_ms > 0.0)) return fail(net, MM_EINVAL, "tau_ms must be > 0");
+    if (!chan) return fail(net, MM_EINVAL, "channel parameters must not be NULL");
+
+    MM_CK(net, cudaSetDevice(net->device));
+    if (opt->cuda_stream) {
+        net->stream = (cudaStream_t)opt->cuda_stream;
+    } else {
+        MM_CK(net, cudaStreamCreateWithFlags(&net->stream, cudaStreamNonBlocking));
+        net->own_stream = true;
+    }
+    MM_CK(net, cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
+
+    // layout
+    mmh::LayoutInput li{};
+    li.N = morph->n_neurons;
+    li.comp_offset = morph->comp_offset;
+    li.parent = morph->parent;
+    li.length_um = morph->length_um;
+    li.diam_um = morph->diam_um;
+    li.S = syn ? syn->n : 0;
+    li.src = syn ? syn->src_neuron : nullptr;
+    li.dst = syn ? syn->dst_neuron : nullptr;
+    li.dcomp = syn ? syn->dst_comp : nullptr;
+    li.w = syn ? syn->weight_uS : nullptr;
+    li.delay_ms = syn ? syn->delay_ms : nullptr;
+    li.stim = stim_nA;
+    li.cost = opt->schedule == MM_SCHED_COST ? opt->cost : nullptr;
+    li.dt = opt->dt_ms;
+    li.group_comps = opt->group_comps > 0 ? opt->group_comps : kDefaultGroupComps;
+    li.max_group_comps = kMaxGroupComps;
+    mmh::Layout L;
+    bool invalid = false;
+    std::string m;
+    try {
+        m = mmh::build_layout(li, L, &invalid);
+    } catch (const std::bad_alloc &) {
+        return fail(net, MM_ENOMEM, "host allocation failed while building the layout");
+    }
+    if (!m.empty()) return fail(net, invalid ? MM_EINVAL : MM_ENOTSUP, m);
+    if (L.dclass.size() > 1024) return fail(net, MM_ENOTSUP, "more than 1024 distinct delays");
+
+    net->N = L.N;
+    net->C = L.C;
+    net->nsite = (int64_t)L.site_comp.size();
+    net->S = li.S;
+    net->R = L.R;
+    net->order = L.order;
+    net->internal_of = L.internal_of;
+    net->f_syn = L.f_syn;
+    net->spk_cap = opt->spike_capacity > 0 ? opt->spike_capacity : std::max<int64_t>(1 << 16, (int64_t)L.N * 64);
+
+    const size_t C = (size_t)L.C, N = (size_t)L.N;
+    mm_status st;
+#define UP(dst, src, cnt) if ((st = upload(net, &(dst), (src), (cnt))) != MM_OK) return st
+#define ZR(dst, cnt) if ((st = zeros(net, &(dst), (cnt))) != MM_OK) return st
+    double *dL = nullptr, *dD = nullptr;
+    int32_t *dpd = nullptr;
+    UP(dL, L.L.data(), C);
+    UP(dD, L.D.data(), C);
+    UP(dpd, L.pdist.data(), C);
+    ZR(net->V, C);
+    ZR(net->m, C);
+    ZR(net->h, C);
+    ZR(net->n, C);
+    ZR(net->area, C);
+    ZR(net->gax, C);
+    ZR(net->scratch, 2 * std::max(C, N));
+    UP(net->stim, L.stim.data(), N);
+    ZR(net->gsyn, (size_t)std::max<int64_t>(net->nsite, 1));
+    UP(net->user_id, L.order.data(), N);
+    UP(net->user2int, L.user2int.data(), C);
+    UP(net->soma_of_user, L.soma_of_user.data(), N);
+    UP(net->site_internal, L.site_internal.data(), (size_t)net->nsite);
+    ZR(net->ring_nrn, (size_t)net->R * N);
+    ZR(net->ring_cnt, (size_t)net->R);
+    ZR(net->spk_nrn, (size_t)net->spk_cap);
+    ZR(net->spk_t, (size_t)net->spk_cap);
+    ZR(net->ctl, 1);
+    mmk::GroupRec *dgroups = nullptr;
+    mmk::SegRec *dsegs = nullptr;
+    int32_t *dchild = nullptr, *dwave = nullptr, *dsite = nullptr;
+    UP(dgroups, L.groups.data(), L.groups.size());
+    UP(dsegs, L.segs.data(), L.segs.size());
+    UP(dchild, L.seg_child.data(), std::max<size_t>(L.seg_child.size(), 1));
+    UP(dwave, L.wave_off.data(), L.wave_off.size());
+    UP(dsite, L.site_comp.data(), std::max<size_t>(L.site_comp.size(), 1));
+    int64_t *dout_off = nullptr;
+    int32_t *dout_site = nullptr, *dout_ds = nullptr, *ddclass = nullptr;
+    double *dout_w = nullptr;
+    UP(dout_off, L.out_off.data(), L.out_off.size());
+    UP(dout_site, L.out_site.data(), std::max<size_t>(L.out_site.size(), 1));
+    UP(dout_ds, L.out_dsteps.data(), std::max<size_t>(L.out_dsteps.size(), 1));
+    UP(dout_w, L.out_w.data(), std::max<size_t>(L.out_w.size(), 1));
+    UP(ddclass, L.dclass.data(), std::max<size_t>(L.dclass.size(), 1));
+#undef UP
+#undef ZR
+
+    // geometry and the resting state on the device
+    mmk::InitArgs ia{};
+    ia.L = dL;
+    ia.diam = dD;
+    ia.parent_dist = dpd;
+    ia.C = L.C;
+    ia.area = net->area;
+    ia.gax = net->gax;
+    ia.V = net->V;
+    ia.m = net->m;
+    ia.h = net->h;
+    ia.n = net->n;
+    ia.Ra = chan->Ra;
+    ia.v_init = chan->v_init;
+    MM_CKI(net, mmk_launch_init(ia, net->stream));
+
+    // kernel arguments
+    mmk::StepArgs &a = net->sa;
+    a.V = net->V;
+    a.m = net->m;
+    a.h = net->h;
+    a.n = net->n;
+    a.area = net->area;
+    a.gax = net->gax;
+    a.stim = net->stim;
+    a.user_id = net->user_id;
+    a.groups = dgroups;
+    a.n_groups = (int32_t)L.groups.size();
+    a.segs = dsegs;
+    a.seg_child = dchild;
+    a.wave_off = dwave;
+    a.site_comp = dsite;
+    a.gsyn = net->gsyn;
+    a.ring_nrn = net->ring_nrn;
+    a.ring_cnt = net->ring_cnt;
+    a.R = net->R;
+    a.N = net->N;
+    a.spk_nrn = net->spk_nrn;
+    a.spk_t = net->spk_t;
+    a.spk_cap = net->spk_cap;
+    a.ctl = net->ctl;
+    a.smem_comps = std::max(L.max_comps, 1);
+    a.smem_segs = std::max(L.max_segs, 1);
+    a.gNa = chan->gNa;
+    a.gK = chan->gK;
+    a.gL = chan->gL;
+    a.ENa = chan->ENa;
+    a.EK = chan->EK;
+    a.EL = chan->EL;
+    a.cm_dt = chan->Cm * 1e3 / opt->dt_ms;
+    a.e_syn = syn ? syn->e_rev_mV : 0.0;
+    a.threshold = chan->threshold_mV;
+    a.dt = opt->dt_ms;
+    a.decay = syn ? std::exp(-opt->dt_ms / syn->tau_ms) : 1.0;
+
+    mmk::DeliverArgs &d = net->da;
+    d.ring_nrn = net->ring_nrn;
+    d.ring_cnt = net->ring_cnt;
+    d.R = net->R;
+    d.N = net->N;
+    d.out_off = dout_off;
+    d.out_site = dout_site;
+    d.out_w = dout_w;
+    d.out_dsteps = dout_ds;
+    d.dclass = ddclass;
+    d.n_dclass = (int32_t)L.dclass.size();
+    d.gsyn = net->gsyn;
+    d.ctl = net->ctl;
+
+    const size_t smem = (size_t)(2 * a.smem_comps + 2 * a.smem_segs) * sizeof(double);
+    if (smem > kMaxSmem) return fail(net, MM_ENOTSUP, "a work item needs more shared memory than a block has");
+    int threads = opt->block_threads > 0 ? opt->block_threads : kStepThreads;
+    if (threads != 128 && threads != 256 && threads != 512) return fail(net, MM_EINVAL, "block_threads must be 128, 256 or 512");
+    net->step_threads = threads;
+    int per_sm = 0;
+    MM_CKI(net, mmk_step_fp64_blocks_per_sm(threads, (int)smem, &per_sm));
+    if (per_sm < 1) return fail(net, MM_ENOTSUP, "the step kernel does not fit on an SM");
+    int sms = 0;
+    MM_CK(net, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device));
+    net->step_blocks = std::max(1, std::min(a.n_groups, per_sm * sms));
+    net->deliver_blocks = std::max(1, 2 * sms);
+    MM_CK(net, cudaStreamSynchronize(net->stream));
+    return MM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mm_default_options(mm_options *opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = MM_FP64;
+    opt->schedule = MM_SCHED_SIZE_SORTED;
+    opt->graph_steps = 40;
+    opt->dt_ms = 0.025;
+}
+
+mm_status mm_create_network(const mm_morphologies *morph, const mm_channel_params *chan, const mm_synapses *syn,
+                            const double *stim_nA, const mm_options *opt, mm_net **out)
+{
+    if (!out) return MM_EINVAL;
+    *out = nullptr;
+    if (!morph || !chan) return MM_EINVAL;
+    mm_options defaults;
+    mm_default_options(&defaults);
+    if (!opt) opt = &defaults;
+    mm_net *net = new (std::nothrow) mm_net();
+    if (!net) return MM_ENOMEM;
+    mm_status st = build(net, morph, chan, syn, stim_nA, opt);
+    if (st != MM_OK) {
+        release_all(net);
+        delete net;
+        return st;
+    }
+    *out = net;
+    return MM_OK;
+}
+
+mm_status mm_step(mm_net *net, int64_t n_steps, double dt_ms)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    if (n_steps < 0) return fail(net, MM_EINVAL, "n_steps must be >= 0");
+    if (!(dt_ms == net->dt)) return fail(net, MM_EINVAL, "dt differs from the network's dt");
+    while (!net->timing && net->graph_steps > 0 && n_steps >= net->graph_steps) {
+        if ((st = ensure_graph(net)) != MM_OK) return st;
+        MM_CK(net, cudaGraphLaunch(net->gexec, net->stream));
+        n_steps -= net->graph_steps;
+        net->steps_done += net->graph_steps;
+    }
+    while (n_steps > 0) {
+        const int k = (int)std::min<int64_t>(n_steps, 1 << 20);
+        if ((st = launch_steps(net, net->stream, k)) != MM_OK) return st;
+        n_steps -= k;
+        net->steps_done += k;
+    }
+    return MM_OK;
+}
+
+mm_status mm_synchronize(mm_net *net)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    return check_device(net);
+}
+
+mm_status mm_read_state(mm_net *net, int32_t which, double *out, int64_t cap)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    if (!out || cap < net->C) return fail(net, MM_EINVAL, "output buffer too small");
+    const double *src = nullptr;
+    switch (which) {
+    case MM_STATE_V: src = net->V; break;
+    case MM_STATE_M: src = net->m; break;
+    case MM_STATE_H: src = net->h; break;
+    case MM_STATE_N: src = net->n; break;
+    case MM_STATE_GSYN: {
+        // merged conductances live per synaptic site: scatter them into a
+        // dense internal array (second half of the scratch) and gather that
+        double *dense = net->scratch + std::max<int64_t>(net->C, net->N);
+        MM_CKI(net, mmk_launch_fill_f64(dense, 0.0, net->C, net->stream));
+        MM_CKI(net, mmk_launch_scatter_site_gsyn(net->gsyn, net->site_internal, dense, net->nsite, net->stream));
+        src = dense;
+        break;
+    }
+    default:
+        return fail(net, MM_EINVAL, "unknown state quantity");
+    }
+    MM_CKI(net, mmk_launch_gather_f64(src, net->user2int, net->scratch, net->C, net->stream));
+    MM_CK(net, cudaMemcpyAsync(out, net->scratch, (size_t)net->C * sizeof(double), cudaMemcpyDeviceToHost, net->stream));
+    return check_device(net);
+}
+
+mm_status mm_read_voltages(mm_net *net, double *out, int64_t cap) { return mm_read_state(net, MM_STATE_V, out, cap); }
+
+mm_status mm_read_soma_voltages(mm_net *net, double *out, int64_t cap)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    if (!out || cap < net->N) return fail(net, MM_EINVAL, "output buffer too small");
+    MM_CKI(net, mmk_launch_gather_f64(net->V, net->soma_of_user, net->scratch, net->N, net->stream));
+    MM_CK(net, cudaMemcpyAsync(out, net->scratch, (size_t)net->N * sizeof(double), cudaMemcpyDeviceToHost, net->stream));
+    return check_device(net);
+}
+
+mm_status mm_read_spikes(mm_net *net, int32_t *neuron, double *t_ms, int64_t cap, int64_t *n_out)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    if (!n_out || cap < 0 || (cap > 0 && (!neuron || !t_ms))) return fail(net, MM_EINVAL, "bad spike output arguments");
+    if ((st = check_device(net)) != MM_OK) return st;
+    mmk::DevCtl c;
+    MM_CK(net, cudaMemcpy(&c, net->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+    const int64_t held = std::min<int64_t>((int64_t)c.spk_count, net->spk_cap);
+    std::vector<int32_t> nr((size_t)held);
+    std::vector<double> tt((size_t)held);
+    if (held) {
+        MM_CK(net, cudaMemcpy(nr.data(), net->spk_nrn, (size_t)held * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        MM_CK(net, cudaMemcpy(tt.data(), net->spk_t, (size_t)held * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    std::vector<int64_t> idx((size_t)held);
+    for (int64_t i = 0; i < held; ++i) idx[(size_t)i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
+        if (tt[(size_t)a] != tt[(size_t)b]) return tt[(size_t)a] < tt[(size_t)b];
+        return nr[(size_t)a] < nr[(size_t)b];
+    });
+    const int64_t w = std::min<int64_t>(held, cap);
+    for (int64_t i = 0; i < w; ++i) {
+        neuron[i] = nr[(size_t)idx[(size_t)i]];
+        t_ms[i] = tt[(size_t)idx[(size_t)i]];
+    }
+    *n_out = held;
+    const bool overflow = (c.err & mmk::MMK_ERR_OVERFLOW) != 0 || (int64_t)c.spk_count > net->spk_cap;
+    // drain: reset the count and the overflow bit
+    c.spk_count = 0;
+    c.err &= ~mmk::MMK_ERR_OVERFLOW;
+    MM_CK(net, cudaMemcpy(&net->ctl->spk_count, &c.spk_count, sizeof(c.spk_count), cudaMemcpyHostToDevice));
+    MM_CK(net, cudaMemcpy(&net->ctl->err, &c.err, sizeof(c.err), cudaMemcpyHostToDevice));
+    if (overflow) return fail(net, MM_EOVERFLOW, "spike buffer overflowed; raise mm_options.spike_capacity or read more often");
+    if (w < held) return fail(net, MM_EOVERFLOW, "caller's spike arrays are smaller than the spike count");
+    return MM_OK;
+}
+
+mm_status mm_set_stimulus(mm_net *net, const double *stim_nA, int64_t n)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    if (!stim_nA || n != net->N) return fail(net, MM_EINVAL, "stimulus must have n_neurons entries");
+    std::vector<double> s((size_t)net->N);
+    for (int32_t k = 0; k < net->N; ++k) {
+        if (!std::isfinite(stim_nA[net->order[(size_t)k]])) return fail(net, MM_EINVAL, "stimulus must be finite");
+        s[(size_t)k] = stim_nA[net->order[(size_t)k]];
+    }
+    MM_CK(net, cudaMemcpyAsync(net->stim, s.data(), s.size() * sizeof(double), cudaMemcpyHostToDevice, net->stream));
+    MM_CK(net, cudaStreamSynchronize(net->stream));
+    return MM_OK;
+}
+
+mm_status mm_get_step(const mm_net *net, int64_t *step)
+{
+    if (!net || !step) return MM_EINVAL;
+    *step = net->steps_done;
+    return MM_OK;
+}
+
+// Checkpoint blob: header, then V, m, h, n [C], gsyn [nsite], stim [N],
+// ring_cnt [R], ring_nrn [R*N], the DevCtl and the undrained spikes.
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int64_t C, nsite, N, R, spk_cap, steps_done;
+    int32_t precision, pad;
+};
+size_t ckpt_size(const mm_net *net)
+{
+    return sizeof(CkptHeader) + (size_t)(4 * net->C + net->nsite + net->N) * sizeof(double) +
+           (size_t)(net->R + (int64_t)net->R * net->N) * sizeof(int32_t) + sizeof(mmk::DevCtl) +
+           (size_t)net->spk_cap * (sizeof(int32_t) + sizeof(double));
+}
+}  // namespace
+
+mm_status mm_save_state(mm_net *net, void *buf, size_t cap, size_t *len)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    if (!len) return fail(net, MM_EINVAL, "len must not be NULL");
+    const size_t need = ckpt_size(net);
+    *len = need;
+    if (!buf) return MM_OK;
+    if (cap < need) return fail(net, MM_EINVAL, "checkpoint buffer too small");
+    if ((st = check_device(net)) != MM_OK) return st;
+    char *p = (char *)buf;
+    CkptHeader h{};
+    std::memcpy(h.magic, "MMCKPT01", 8);
+    h.C = net->C;
+    h.nsite = net->nsite;
+    h.N = net->N;
+    h.R = net->R;
+    h.spk_cap = net->spk_cap;
+    h.steps_done = net->steps_done;
+    h.precision = net->precision;
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    auto d2h = [&](const void *src, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMemcpy(p, src, bytes, cudaMemcpyDeviceToHost);
+        p += bytes;
+        return e;
+    };
+    const size_t C8 = (size_t)net->C * sizeof(double);
+    MM_CK(net, d2h(net->V, C8));
+    MM_CK(net, d2h(net->m, C8));
+    MM_CK(net, d2h(net->h, C8));
+    MM_CK(net, d2h(net->n, C8));
+    MM_CK(net, d2h(net->gsyn, (size_t)net->nsite * sizeof(double)));
+    MM_CK(net, d2h(net->stim, (size_t)net->N * sizeof(double)));
+    MM_CK(net, d2h(net->ring_cnt, (size_t)net->R * sizeof(int32_t)));
+    MM_CK(net, d2h(net->ring_nrn, (size_t)net->R * net->N * sizeof(int32_t)));
+    MM_CK(net, d2h(net->ctl, sizeof(mmk::DevCtl)));
+    MM_CK(net, d2h(net->spk_nrn, (size_t)net->spk_cap * sizeof(int32_t)));
+    MM_CK(net, d2h(net->spk_t, (size_t)net->spk_cap * sizeof(double)));
+    return MM_OK;
+}
+
+mm_status mm_load_state(mm_net *net, const void *buf, size_t len)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    if (!buf || len != ckpt_size(net)) return fail(net, MM_EINVAL, "checkpoint size does not match this network");
+    const char *p = (const char *)buf;
+    CkptHeader h;
+    std::memcpy(&h, p, sizeof(h));
+    if (std::memcmp(h.magic, "MMCKPT01", 8) != 0 || h.C != net->C || h.nsite != net->nsite || h.N != net->N ||
+        h.R != net->R || h.spk_cap != net->spk_cap || h.precision != net->precision)
+        return fail(net, MM_EINVAL, "checkpoint was saved from a different network");
+    p += sizeof(h);
+    MM_CK(net, cudaStreamSynchronize(net->stream));
+    auto h2d = [&](void *dst, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMemcpy(dst, p, bytes, cudaMemcpyHostToDevice);
+        p += bytes;
+        return e;
+    };
+    const size_t C8 = (size_t)net->C * sizeof(double);
+    MM_CK(net, h2d(net->V, C8));
+    MM_CK(net, h2d(net->m, C8));
+    MM_CK(net, h2d(net->h, C8));
+    MM_CK(net, h2d(net->n, C8));
+    MM_CK(net, h2d(net->gsyn, (size_t)net->nsite * sizeof(double)));
+    MM_CK(net, h2d(net->stim, (size_t)net->N * sizeof(double)));
+    MM_CK(net, h2d(net->ring_cnt, (size_t)net->R * sizeof(int32_t)));
+    MM_CK(net, h2d(net->ring_nrn, (size_t)net->R * net->N * sizeof(int32_t)));
+    MM_CK(net, h2d(net->ctl, sizeof(mmk::DevCtl)));
+    MM_CK(net, h2d(net->spk_nrn, (size_t)net->spk_cap * sizeof(int32_t)));
+    MM_CK(net, h2d(net->spk_t, (size_t)net->spk_cap * sizeof(double)));
+    net->steps_done = h.steps_done;
+    return MM_OK;
+}
+
+mm_status mm_set_kernel_timing(mm_net *net, int32_t enable)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    net->timing = enable != 0;
+    return MM_OK;
+}
+
+mm_status mm_read_kernel_timing(mm_net *net, mm_kernel_times *out, int32_t reset)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    if (!out) return fail(net, MM_EINVAL, "out must not be NULL");
+    if ((st = collect_timing(net)) != MM_OK) return st;
+    *out = net->times;
+    if (reset) net->times = mm_kernel_times{};
+    return MM_OK;
+}
+
+const char *mm_last_error(const mm_net *net)
+{
+    if (!net) return "";
+    return net->err.c_str();
+}
+
+const char *mm_status_string(mm_status s)
+{
+    switch (s) {
+    case MM_OK: return "MM_OK";
+    case MM_EINVAL: return "MM_EINVAL";
+    case MM_ENOMEM: return "MM_ENOMEM";
+    case MM_ECUDA: return "MM_ECUDA";
+    case MM_ETIMEOUT: return "MM_ETIMEOUT";
+    case MM_ENUMERIC: return "MM_ENUMERIC";
+    case MM_EOVERFLOW: return "MM_EOVERFLOW";
+    case MM_ESTATE: return "MM_ESTATE";
+    case MM_ENOTSUP: return "MM_ENOTSUP";
+    }
+    return "MM_UNKNOWN";
+}
+
+void mm_destroy(mm_net *net)
+{
+    if (!net) return;
+    cudaSetDevice(net->device);
+    release_all(net);
+    delete net;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// mm_internal.h -- records and kernel arguments shared by the host runtime
+// and the CUDA kernels of the multi-morphology stepper.
+//
+// Device layout (all per-compartment arrays in INTERNAL order):
+//   * neurons are re-ordered by the schedule (largest cost first);
+//   * inside a neuron, compartments are renumbered in depth-first preorder so
+//     that every unbranched run of the tree (a "segment": a path whose inner
+//     nodes have exactly one child) occupies consecutive indices and its
+//     child segments hang off its last (bottom) compartment;
+//   * consecutive neurons are packed into work items ("groups") whose
+//     compartments are contiguous; one thread block solves one group at a
+//     time, with the group's Hines diagonal and right-hand side in shared
+//     memory;
+//   * the segments of a group are sorted by height (0 = no child segment),
+//     so that all segments of one height ("wave") can be eliminated in
+//     parallel once the lower waves are done (the leaves-to-root sweep of
+//     Algorithm 1), and substituted in the reverse order (root-to-leaves).
+#pragma once
+#include <stdint.h>
+
+namespace mmk {
+
+// One segment of a group: compartments top .. top+len-1 (group-local), a
+// path from top down to the bottom compartment top+len-1.
+struct SegRec {
+    int32_t top;      // group-local index of the first compartment
+    int32_t len;      // >= 1
+    int32_t parent;   // group-local index of top's parent; -1 for a soma segment
+    int32_t child0;   // first entry of this segment's children in seg_child[]
+    int32_t nchild;   // number of child segments (all hang off the bottom)
+    int32_t neuron;   // soma segment: group-local neuron index; else -1
+};
+
+// One work item: a run of whole neurons.
+struct GroupRec {
+    int64_t comp0;    // internal index of the first compartment
+    int32_t ncomp;
+    int32_t seg0;     // first segment (index into segs[])
+    int32_t nseg;
+    int32_t wave0;    // first entry in wave_off[] (nwave + 1 entries, group-local seg indices)
+    int32_t nwave;
+    int32_t site0;    // first synaptic site (index into site_comp[] / gsyn[])
+    int32_t nsite;
+    int32_t neuron0;  // internal id of the first neuron
+    int32_t nneuron;
+    int32_t pad;
+};
+
+// Small device-side control block.
+struct DevCtl {
+    unsigned long long step_base;   // steps completed before the current launch batch
+    unsigned long long spk_count;   // spikes appended to the output buffer
+    unsigned int queue_head;        // next work item of the current step
+    int err;                        // MMK_ERR_* bits
+};
+
+enum { MMK_ERR_OVERFLOW = 1, MMK_ERR_NUMERIC = 2 };
+
+// Arguments of the FP64 step kernel.
+struct StepArgs {
+    double *V, *m, *h, *n;            // state [C]
+    const double *area;               // membrane area, cm^2 [C]
+    const double *gax;                // axial conductance to the parent, uS [C] (0 at a soma)
+    const double *stim;               // soma current per internal neuron, nA [N]
+    const int32_t *user_id;           // internal neuron -> user id [N]
+    const GroupRec *groups;
+    int32_t n_groups;
+    int32_t step_offset;              // step index = ctl->step_base + step_offset
+    const SegRec *segs;
+    const int32_t *seg_child;
+    const int32_t *wave_off;
+    const int32_t *site_comp;         // group-local compartment of each synaptic site
+    double *gsyn;                     // merged synaptic conductance per site, uS
+    int32_t *ring_nrn;                // [R * N] internal ids of neurons that spiked, per step slot
+    int32_t *ring_cnt;                // [R]
+    int32_t R, N;
+    int32_t *spk_nrn;                 // output spikes (user ids) [spk_cap]
+    double *spk_t;
+    long long spk_cap;
+    DevCtl *ctl;
+    int32_t smem_comps, smem_segs;    // shared-memory capacity of one block
+    double gNa, gK, gL, ENa, EK, EL;
+    double cm_dt;                     // Cm * 1e3 / dt: C_i/dt = area_i * cm_dt (nF/ms = uS)
+    double e_syn, threshold, dt, decay;
+};
+
+struct DeliverArgs {
+    const int32_t *ring_nrn;
+    int32_t *ring_cnt;
+    int32_t R, N;
+    const int64_t *out_off;           // [N+1] outgoing synapses of each internal source
+    const int32_t *out_site;          // target synaptic site
+    const double *out_w;              // weight, uS
+    const int32_t *out_dsteps;        // round(delay/dt), ascending within a source
+    const int32_t *dclass;            // distinct delays (steps), ascending
+    int32_t n_dclass;
+    int32_t step_offset;
+    double *gsyn;
+    DevCtl *ctl;
+};
+
+struct InitArgs {
+    const double *L, *diam;           // internal order
+    const int32_t *parent_dist;       // i - parent(i) (>= 1), 0 at a soma
+    int64_t C;
+    double *area, *gax;
+    double *V, *m, *h, *n;
+    double Ra, v_init;
+};
+
+}  // namespace mmk
+
+// Launch wrappers (defined in the .cu files; return a cudaError_t as int).
+extern "C++" {
+int mmk_launch_init(const mmk::InitArgs &a, void *stream);
+int mmk_launch_deliver(const mmk::DeliverArgs &a, int blocks, void *stream);
+int mmk_launch_step_fp64(const mmk::StepArgs &a, int blocks, int threads, void *stream);
+int mmk_step_fp64_blocks_per_sm(int threads, int smem_bytes, int *blocks);
+int mmk_launch_advance(mmk::DevCtl *ctl, int steps, void *stream);
+int mmk_launch_gather_f64(const double *src, const int64_t *idx, double *dst, int64_t n, void *stream);
+int mmk_launch_scatter_site_gsyn(const double *gsyn, const int64_t *site_internal_comp, double *dst,
+                                 int64_t nsite, void *stream);
+int mmk_launch_fill_f64(double *dst, double v, int64_t n, void *stream);
+}

@@ -1,0 +1,412 @@
+// mm_kernels.cu -- FP64 kernels of the multi-morphology stepper (sm_103a).
+//
+// One time step n -> n+1 is two launches:
+//   deliver_kernel: spikes detected round(delay/dt) + 1 steps ago raise the
+//                   synaptic conductance of their target sites (the local /
+//                   global spike buffers of Sec. 2 become a device ring of
+//                   per-step spike lists, expanded through an outgoing CSR);
+//   step_fp64:      per work item (a run of whole neurons): HH currents,
+//                   assembly of the Hines system for dV (Eq. 2), the Hines
+//                   solve (Algorithm 1) as segment waves in shared memory,
+//                   V += dV, exponential-Euler gates, synaptic decay and the
+//                   soma threshold test.
+// The model is the oracle's (units um, mV, ms, nA, uS, nF); the arithmetic
+// here is written independently of it.
+#include <cuda_runtime.h>
+
+#include "mm_internal.h"
+
+using namespace mmk;
+
+namespace {
+
+constexpr double kPi = 3.141592653589793;
+
+// x / (e^x - 1) and its limit near 0.
+__device__ __forceinline__ double xexpm1_ratio(double x)
+{
+    return fabs(x) < 1e-6 ? 1.0 - 0.5 * x : x / expm1(x);
+}
+
+// HH rate constants (1/ms) at v (mV), rest -65 mV.
+struct Rates {
+    double am, bm, ah, bh, an, bn;
+};
+
+__device__ __forceinline__ Rates hh_rates(double v)
+{
+    Rates r;
+    r.am = xexpm1_ratio(-(v + 40.0) * 0.1);
+    r.bm = 4.0 * exp(-(v + 65.0) * (1.0 / 18.0));
+    r.ah = 0.07 * exp(-(v + 65.0) * 0.05);
+    r.bh = 1.0 / (1.0 + exp(-(v + 35.0) * 0.1));
+    r.an = 0.1 * xexpm1_ratio(-(v + 55.0) * 0.1);
+    r.bn = 0.125 * exp(-(v + 65.0) * 0.0125);
+    return r;
+}
+
+// Exact relaxation of one gate over dt with frozen rates.
+__device__ __forceinline__ double relax(double x, double a, double b, double dt)
+{
+    double s = a + b;
+    double xinf = a / s;
+    return xinf + (x - xinf) * exp(-dt * s);
+}
+
+__device__ __forceinline__ double half_cyl_resistance(double Ra, double L_um, double d_um)
+{
+    // MOhm: Ra * (L/2) / (pi d^2 / 4), lengths converted um -> cm
+    double rad = 0.5e-4 * d_um;
+    return Ra * (0.5e-4 * L_um) / (kPi * rad * rad) * 1e-6;
+}
+
+// ------------------------------------------------------------------ init
+
+__global__ void init_kernel(InitArgs a)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.C;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double L = a.L[i], d = a.diam[i];
+        a.area[i] = kPi * d * L * 1e-8;
+        const int32_t pd = a.parent_dist[i];
+        double g = 0.0;
+        if (pd > 0) {
+            const int64_t q = i - pd;
+            g = 1.0 / (half_cyl_resistance(a.Ra, L, d) + half_cyl_resistance(a.Ra, a.L[q], a.diam[q]));
+        }
+        a.gax[i] = g;
+        double v = a.v_init;
+        Rates r = hh_rates(v);
+        a.V[i] = v;
+        a.m[i] = r.am / (r.am + r.bm);
+        a.h[i] = r.ah / (r.ah + r.bh);
+        a.n[i] = r.an / (r.an + r.bn);
+    }
+}
+
+// --------------------------------------------------------------- delivery
+
+constexpr int kMaxDClass = 1024;
+
+__global__ void __launch_bounds__(256) deliver_kernel(DeliverArgs a)
+{
+    __shared__ int s_pref[kMaxDClass + 1];
+    __shared__ int s_slot[kMaxDClass];
+    const long long n = (long long)a.ctl->step_base + a.step_offset;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->queue_head = 0u;
+        a.ring_cnt[n % a.R] = 0;
+    }
+    for (int k = threadIdx.x; k < a.n_dclass; k += blockDim.x) {
+        long long src_step = n - 1 - a.dclass[k];
+        int cnt = 0, slot = 0;
+        if (src_step >= 0) {
+            slot = (int)(src_step % a.R);
+            cnt = a.ring_cnt[slot];
+        }
+        s_slot[k] = slot;
+        s_pref[k + 1] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_pref[0] = 0;
+        for (int k = 1; k <= a.n_dclass; ++k) s_pref[k] += s_pref[k - 1];
+    }
+    __syncthreads();
+    const int total = s_pref[a.n_dclass];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < total; u += nwarps) {
+        int lo = 0, hi = a.n_dclass;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (s_pref[mid] <= u) lo = mid; else hi = mid;
+        }
+        const int src = a.ring_nrn[(long long)s_slot[lo] * a.N + (u - s_pref[lo])];
+        long long b = a.out_off[src], e = a.out_off[src + 1];
+        if (a.n_dclass > 1) {
+            const int D = a.dclass[lo];
+            long long l = b, r = e;            // first entry with dsteps >= D
+            while (l < r) { long long m = (l + r) >> 1; if (a.out_dsteps[m] < D) l = m + 1; else r = m; }
+            long long l2 = l, r2 = e;          // first entry with dsteps > D
+            while (l2 < r2) { long long m = (l2 + r2) >> 1; if (a.out_dsteps[m] <= D) l2 = m + 1; else r2 = m; }
+            b = l; e = l2;
+        }
+        for (long long q = b + lane; q < e; q += 32) atomicAdd(&a.gsyn[a.out_site[q]], a.out_w[q]);
+    }
+}
+
+// ------------------------------------------------------------ FP64 step
+
+template <int NT>
+__global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
+{
+    extern __shared__ double smem[];
+    double *sd = smem;                       // diagonal; after elimination: its reciprocal
+    double *sr = smem + a.smem_comps;        // rhs; after substitution: dV
+    double *scd = sr + a.smem_comps;         // per-segment contribution to its parent's diagonal
+    double *scr = scd + a.smem_segs;         // ... and to its parent's rhs
+    __shared__ int s_item;
+
+    const long long n = (long long)a.ctl->step_base + a.step_offset;
+    const int tid = threadIdx.x;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = (int)atomicAdd(&a.ctl->queue_head, 1u);
+        __syncthreads();
+        const int gi = s_item;
+        if (gi >= a.n_groups) break;
+        const GroupRec G = a.groups[gi];
+        const int64_t c0 = G.comp0;
+        const double *V = a.V + c0;
+        const double *gax = a.gax + c0;
+
+        // A. membrane conductance and current at (V^n, gates^n): the
+        //    compartment's own part of the diagonal and right-hand side.
+        for (int i = tid; i < G.ncomp; i += NT) {
+            const double v = V[i], mm = a.m[c0 + i], hh = a.h[c0 + i], nn = a.n[c0 + i];
+            const double ar = a.area[c0 + i];
+            const double s = ar * 1e3;
+            const double gna = a.gNa * s * (mm * mm * mm * hh);
+            const double n2 = nn * nn;
+            const double gk = a.gK * s * (n2 * n2);
+            const double gl = a.gL * s;
+            sd[i] = ar * a.cm_dt + gna + gk + gl;
+            sr[i] = -(gna * (v - a.ENa) + gk * (v - a.EK) + gl * (v - a.EL));
+        }
+        __syncthreads();
+
+        // S. synaptic sites: conductance into the system, then decay.
+        for (int t = tid; t < G.nsite; t += NT) {
+            const int st = G.site0 + t;
+            const int c = a.site_comp[st];
+            const double g = a.gsyn[st];
+            sd[c] += g;
+            sr[c] -= g * (V[c] - a.e_syn);
+            a.gsyn[st] = g * a.decay;
+        }
+        __syncthreads();
+
+        // B. leaves-to-root elimination, one segment per thread, wave by wave.
+        //    The axial terms of each link (i, p(i)) are folded in as the sweep
+        //    reaches i: d_i += g, rhs_i += g (V_p - V_i) and, for the parent,
+        //    d_p += g, rhs_p += g (V_i - V_p), next to the elimination update
+        //    d_p -= (a_i/d_i) c_i, rhs_p -= (a_i/d_i) rhs_i with a_i = c_i = -g.
+        const SegRec *segs = a.segs + G.seg0;
+        const int *woff = a.wave_off + G.wave0;
+        for (int w = 0; w < G.nwave; ++w) {
+            const int sb = woff[w], se = woff[w + 1];
+            for (int si = sb + tid; si < se; si += NT) {
+                const SegRec S = segs[si];
+                const int bot = S.top + S.len - 1;
+                double db = sd[bot], rb = sr[bot];
+                for (int c = 0; c < S.nchild; ++c) {
+                    const int cs = a.seg_child[S.child0 + c];
+                    db += scd[cs];
+                    rb += scr[cs];
+                }
+                for (int j = bot; j > S.top; --j) {
+                    const double g = gax[j];
+                    const double vj = V[j], vp = V[j - 1];
+                    db += g;
+                    rb += g * (vp - vj);
+                    const double inv = 1.0 / db;
+                    sd[j] = inv;
+                    sr[j] = rb;
+                    const double f = g * inv;
+                    db = sd[j - 1] + g - f * g;
+                    rb = sr[j - 1] + g * (vj - vp) + f * rb;
+                }
+                const int t = S.top;
+                if (S.parent >= 0) {
+                    const double g = gax[t];
+                    const double vt = V[t], vp = V[S.parent];
+                    db += g;
+                    rb += g * (vp - vt);
+                    const double inv = 1.0 / db;
+                    sd[t] = inv;
+                    sr[t] = rb;
+                    const double f = g * inv;
+                    scd[si] = g - f * g;
+                    scr[si] = g * (vt - vp) + f * rb;
+                } else {
+                    rb += a.stim[G.neuron0 + S.neuron];
+                    const double inv = 1.0 / db;
+                    sd[t] = inv;
+                    sr[t] = rb * inv;     // dV at the soma
+                }
+            }
+            __syncthreads();
+        }
+
+        // F. root-to-leaves substitution in the reverse wave order; the soma
+        //    segment also runs the spike test.
+        for (int w = G.nwave - 1; w >= 0; --w) {
+            const int sb = woff[w], se = woff[w + 1];
+            for (int si = sb + tid; si < se; si += NT) {
+                const SegRec S = segs[si];
+                const int t = S.top;
+                double x;
+                if (S.parent >= 0) {
+                    x = (sr[t] + gax[t] * sr[S.parent]) * sd[t];
+                    sr[t] = x;
+                } else {
+                    x = sr[t];
+                    const double v0 = V[t], v1 = v0 + x;
+                    const int nrn = G.neuron0 + S.neuron;
+                    if (!isfinite(v1)) atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
+                    if (v0 < a.threshold && v1 >= a.threshold) {
+                        const double ts = (double)n * a.dt + a.dt * (a.threshold - v0) / (v1 - v0);
+                        const unsigned long long k = atomicAdd(&a.ctl->spk_count, 1ull);
+                        if ((long long)k < a.spk_cap) {
+                            a.spk_nrn[k] = a.user_id[nrn];
+                            a.spk_t[k] = ts;
+                        } else {
+                            atomicOr(&a.ctl->err, MMK_ERR_OVERFLOW);
+                        }
+                        const int slot = (int)(n % a.R);
+                        const int pos = atomicAdd(&a.ring_cnt[slot], 1);
+                        a.ring_nrn[(long long)slot * a.N + pos] = nrn;
+                    }
+                }
+                for (int j = t + 1; j < t + S.len; ++j) {
+                    x = (sr[j] + gax[j] * x) * sd[j];
+                    sr[j] = x;
+                }
+            }
+            __syncthreads();
+        }
+
+        // C. V^{n+1} = V^n + dV, then exponential-Euler gates at V^{n+1}.
+        for (int i = tid; i < G.ncomp; i += NT) {
+            const double v = V[i] + sr[i];
+            a.V[c0 + i] = v;
+            const Rates r = hh_rates(v);
+            a.m[c0 + i] = relax(a.m[c0 + i], r.am, r.bm, a.dt);
+            a.h[c0 + i] = relax(a.h[c0 + i], r.ah, r.bh, a.dt);
+            a.n[c0 + i] = relax(a.n[c0 + i], r.an, r.bn, a.dt);
+        }
+    }
+}
+
+__global__ void advance_kernel(DevCtl *ctl, int steps) { ctl->step_base += (unsigned long long)steps; }
+
+__global__ void gather_f64_kernel(const double *src, const int64_t *idx, double *dst, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[idx[i]];
+}
+
+__global__ void scatter_f64_kernel(const double *src, const int64_t *idx, double *dst, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[idx[i]] = src[i];
+}
+
+__global__ void fill_f64_kernel(double *dst, double v, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = v;
+}
+
+int grid_for(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 8) b = 152 * 8;
+    return (int)b;
+}
+
+}  // namespace
+
+int mmk_launch_init(const InitArgs &a, void *stream)
+{
+    init_kernel<<<grid_for(a.C, 256), 256, 0, (cudaStream_t)stream>>>(a);
+    return (int)cudaGetLastError();
+}
+
+int mmk_launch_deliver(const DeliverArgs &a, int blocks, void *stream)
+{
+    if (a.n_dclass > kMaxDClass) return (int)cudaErrorInvalidValue;
+    deliver_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
+    return (int)cudaGetLastError();
+}
+
+static size_t step_smem_bytes(const StepArgs &a)
+{
+    return (size_t)(2 * a.smem_comps + 2 * a.smem_segs) * sizeof(double);
+}
+
+int mmk_launch_step_fp64(const StepArgs &a, int blocks, int threads, void *stream)
+{
+    const size_t smem = step_smem_bytes(a);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (threads) {
+    case 128:
+        step_fp64_kernel<128><<<blocks, 128, smem, s>>>(a);
+        break;
+    case 256:
+        step_fp64_kernel<256><<<blocks, 256, smem, s>>>(a);
+        break;
+    case 512:
+        step_fp64_kernel<512><<<blocks, 512, smem, s>>>(a);
+        break;
+    default:
+        return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
+}
+
+int mmk_step_fp64_blocks_per_sm(int threads, int smem_bytes, int *blocks)
+{
+    cudaError_t e = cudaSuccess;
+    switch (threads) {
+    case 128:
+        e = cudaFuncSetAttribute(step_fp64_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, step_fp64_kernel<128>, 128, smem_bytes);
+        break;
+    case 256:
+        e = cudaFuncSetAttribute(step_fp64_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, step_fp64_kernel<256>, 256, smem_bytes);
+        break;
+    case 512:
+        e = cudaFuncSetAttribute(step_fp64_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, step_fp64_kernel<512>, 512, smem_bytes);
+        break;
+    default:
+        return (int)cudaErrorInvalidValue;
+    }
+    return (int)e;
+}
+
+int mmk_launch_advance(DevCtl *ctl, int steps, void *stream)
+{
+    advance_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(ctl, steps);
+    return (int)cudaGetLastError();
+}
+
+int mmk_launch_gather_f64(const double *src, const int64_t *idx, double *dst, int64_t n, void *stream)
+{
+    if (n <= 0) return 0;
+    gather_f64_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(src, idx, dst, n);
+    return (int)cudaGetLastError();
+}
+
+int mmk_launch_scatter_site_gsyn(const double *gsyn, const int64_t *site_internal_comp, double *dst,
+                                 int64_t nsite, void *stream)
+{
+    if (nsite <= 0) return 0;
+    scatter_f64_kernel<<<grid_for(nsite, 256), 256, 0, (cudaStream_t)stream>>>(gsyn, site_internal_comp, dst, nsite);
+    return (int)cudaGetLastError();
+}
+
+int mmk_launch_fill_f64(double *dst, double v, int64_t n, void *stream)
+{
+    if (n <= 0) return 0;
+    fill_f64_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(dst, v, n);
+    return (int)cudaGetLastError();
+}

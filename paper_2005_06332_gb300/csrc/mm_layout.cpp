@@ -1,0 +1,345 @@
+// mm_layout.cpp -- validation and device layout of a network (host side).
+//
+// The paper stores each neuron as parent-indexed arrays and solves it with
+// Algorithm 1, neuron after neuron, one OpenMP task per neuron; it balances
+// multi-morphology runs by sorting neurons by size before the simulation
+// (Sec. 4).  Here the same pre-processing feeds a GPU layout instead:
+//   1. neurons are ordered by cost (compartment count or a supplied
+//      prediction), largest first, so that the work queue hands the longest
+//      items out first;
+//   2. each tree is renumbered in depth-first preorder, which keeps
+//      parent < child (the numbering Algorithm 1 needs) and makes every
+//      unbranched segment a contiguous index range;
+//   3. consecutive neurons are packed into work items of about
+//      `group_comps` compartments, each with its segments sorted into
+//      height waves for the parallel leaves-to-root / root-to-leaves sweeps;
+//   4. synapse targets are merged into synaptic sites (one conductance per
+//      compartment that receives synapses) and outgoing synapses are stored
+//      per source neuron, sorted by delay, for delivery.
+#include "mm_layout.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <sstream>
+
+namespace mmh {
+
+namespace {
+
+std::string msg(const std::ostringstream &o) { return o.str(); }
+
+struct NeuronScratch {
+    std::vector<int32_t> ccount, cstart, clist, newl, oldof, pnew, nch, stack;
+    std::vector<int32_t> seg_top, seg_len, seg_par, seg_height, seg_of_bottom;
+};
+
+}  // namespace
+
+std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
+{
+    *invalid = true;
+    std::ostringstream e;
+    const int32_t N = in.N;
+    if (N < 1) { e << "n_neurons must be >= 1"; return msg(e); }
+    if (!in.comp_offset || !in.parent || !in.length_um || !in.diam_um) { e << "morphology arrays must not be NULL"; return msg(e); }
+    if (!(in.dt > 0.0) || !std::isfinite(in.dt)) { e << "dt must be > 0"; return msg(e); }
+    if (in.comp_offset[0] != 0) { e << "comp_offset[0] must be 0"; return msg(e); }
+    for (int32_t k = 0; k < N; ++k) {
+        int64_t n = in.comp_offset[k + 1] - in.comp_offset[k];
+        if (n < 1) { e << "neuron " << k << " has no compartments"; return msg(e); }
+        if (n > (int64_t)INT32_MAX / 2) { e << "neuron " << k << " is too large"; return msg(e); }
+    }
+    const int64_t C = in.comp_offset[N];
+    for (int32_t k = 0; k < N; ++k) {
+        const int64_t b = in.comp_offset[k], n = in.comp_offset[k + 1] - b;
+        if (in.parent[b] != -1) { e << "neuron " << k << ": parent[0] must be -1"; return msg(e); }
+        for (int64_t i = 1; i < n; ++i) {
+            const int32_t p = in.parent[b + i];
+            if (p < 0 || p >= i) { e << "neuron " << k << ": parent[" << i << "] = " << p << " is not in [0, " << i << ")"; return msg(e); }
+        }
+    }
+    for (int64_t i = 0; i < C; ++i) {
+        if (!(in.length_um[i] > 0.0) || !(in.diam_um[i] > 0.0) || !std::isfinite(in.length_um[i]) ||
+            !std::isfinite(in.diam_um[i])) { e << "compartment " << i << ": length and diameter must be positive and finite"; return msg(e); }
+    }
+    if (in.S < 0) { e << "negative synapse count"; return msg(e); }
+    if (in.S > 0 && (!in.src || !in.dst || !in.dcomp || !in.w || !in.delay_ms)) { e << "synapse arrays must not be NULL"; return msg(e); }
+    int64_t max_ds = 0;
+    std::vector<int32_t> dsteps((size_t)in.S);
+    for (int64_t s = 0; s < in.S; ++s) {
+        const int32_t a = in.src[s], b = in.dst[s];
+        if (a < 0 || a >= N || b < 0 || b >= N) { e << "synapse " << s << ": neuron id out of range"; return msg(e); }
+        const int64_t nb = in.comp_offset[b + 1] - in.comp_offset[b];
+        if (in.dcomp[s] < 0 || in.dcomp[s] >= nb) { e << "synapse " << s << ": dst_comp out of range"; return msg(e); }
+        if (!(in.w[s] >= 0.0) || !std::isfinite(in.w[s])) { e << "synapse " << s << ": weight must be finite and >= 0"; return msg(e); }
+        const double q = in.delay_ms[s] / in.dt;
+        if (!std::isfinite(q)) { e << "synapse " << s << ": delay must be finite"; return msg(e); }
+        const long long d = std::llround(q);
+        if (d < 1) { e << "synapse " << s << ": delay is shorter than dt"; return msg(e); }
+        if (d > 1000000) { *invalid = false; e << "synapse " << s << ": delay of more than 1e6 steps"; return msg(e); }
+        dsteps[(size_t)s] = (int32_t)d;
+        max_ds = std::max<int64_t>(max_ds, d);
+    }
+    if (in.stim) {
+        for (int32_t k = 0; k < N; ++k)
+            if (!std::isfinite(in.stim[k])) { e << "stim of neuron " << k << " is not finite"; return msg(e); }
+    }
+    if (in.cost) {
+        for (int32_t k = 0; k < N; ++k)
+            if (!std::isfinite(in.cost[k])) { e << "cost of neuron " << k << " is not finite"; return msg(e); }
+    }
+    *invalid = false;
+    for (int32_t k = 0; k < N; ++k) {
+        const int64_t n = in.comp_offset[k + 1] - in.comp_offset[k];
+        if (n > in.max_group_comps) {
+            e << "neuron " << k << " has " << n << " compartments; this build holds at most " << in.max_group_comps
+              << " per neuron";
+            return msg(e);
+        }
+    }
+
+    Layout &L = out;
+    L.N = N;
+    L.C = C;
+
+    // 1. order: largest cost first, ties by user id
+    L.order.resize((size_t)N);
+    std::iota(L.order.begin(), L.order.end(), 0);
+    auto size_of = [&](int32_t u) { return in.comp_offset[u + 1] - in.comp_offset[u]; };
+    if (in.cost) {
+        std::stable_sort(L.order.begin(), L.order.end(), [&](int32_t a, int32_t b) { return in.cost[a] > in.cost[b]; });
+    } else {
+        std::stable_sort(L.order.begin(), L.order.end(), [&](int32_t a, int32_t b) { return size_of(a) > size_of(b); });
+    }
+    L.internal_of.assign((size_t)N, 0);
+    for (int32_t k = 0; k < N; ++k) L.internal_of[(size_t)L.order[(size_t)k]] = k;
+    L.noff.assign((size_t)N + 1, 0);
+    for (int32_t k = 0; k < N; ++k) L.noff[(size_t)k + 1] = L.noff[(size_t)k] + size_of(L.order[(size_t)k]);
+
+    L.L.resize((size_t)C);
+    L.D.resize((size_t)C);
+    L.pdist.resize((size_t)C);
+    L.user2int.resize((size_t)C);
+    L.soma_of_user.resize((size_t)N);
+    L.stim.assign((size_t)N, 0.0);
+    for (int32_t k = 0; k < N; ++k) {
+        const int32_t u = L.order[(size_t)k];
+        L.soma_of_user[(size_t)u] = L.noff[(size_t)k];
+        if (in.stim) L.stim[(size_t)k] = in.stim[u];
+    }
+
+    // 3a. group boundaries
+    std::vector<int32_t> gstart;
+    {
+        int64_t cur = 0;
+        for (int32_t k = 0; k < N; ++k) {
+            const int64_t n = L.noff[(size_t)k + 1] - L.noff[(size_t)k];
+            if (k == 0 || cur + n > in.group_comps) {
+                gstart.push_back(k);
+                cur = 0;
+            }
+            cur += n;
+        }
+        gstart.push_back(N);
+    }
+    const int32_t G = (int32_t)gstart.size() - 1;
+    L.groups.resize((size_t)G);
+
+    // 2 + 3b. per group: renumber its neurons, cut segments, sort into waves
+    NeuronScratch ws;
+    std::vector<mmk::SegRec> gsegs;
+    std::vector<std::vector<int32_t>> gkids;
+    std::vector<int32_t> gheight, perm, newidx;
+    L.max_comps = 0;
+    L.max_segs = 0;
+    L.max_waves = 0;
+    for (int32_t g = 0; g < G; ++g) {
+        const int32_t k0 = gstart[(size_t)g], k1 = gstart[(size_t)g + 1];
+        const int64_t comp0 = L.noff[(size_t)k0];
+        gsegs.clear();
+        gkids.clear();
+        gheight.clear();
+        for (int32_t k = k0; k < k1; ++k) {
+            const int32_t u = L.order[(size_t)k];
+            const int64_t ub = in.comp_offset[u];
+            const int32_t n = (int32_t)size_of(u);
+            const int64_t ib = L.noff[(size_t)k];
+            const int32_t lb = (int32_t)(ib - comp0);
+            const int32_t *par = in.parent + ub;
+            // children lists (ascending old index)
+            ws.ccount.assign((size_t)n, 0);
+            for (int32_t i = 1; i < n; ++i) ws.ccount[(size_t)par[i]]++;
+            ws.cstart.assign((size_t)n + 1, 0);
+            for (int32_t i = 0; i < n; ++i) ws.cstart[(size_t)i + 1] = ws.cstart[(size_t)i] + ws.ccount[(size_t)i];
+            ws.clist.resize((size_t)std::max(n - 1, 1));
+            {
+                std::vector<int32_t> &fill = ws.nch;
+                fill.assign((size_t)n, 0);
+                for (int32_t i = 1; i < n; ++i) {
+                    const int32_t p = par[i];
+                    ws.clist[(size_t)(ws.cstart[(size_t)p] + fill[(size_t)p]++)] = i;
+                }
+            }
+            // depth-first preorder; the smallest-index child is visited first
+            ws.newl.resize((size_t)n);
+            ws.oldof.resize((size_t)n);
+            ws.stack.clear();
+            ws.stack.push_back(0);
+            int32_t next = 0;
+            while (!ws.stack.empty()) {
+                const int32_t x = ws.stack.back();
+                ws.stack.pop_back();
+                ws.newl[(size_t)x] = next;
+                ws.oldof[(size_t)next] = x;
+                ++next;
+                for (int32_t c = ws.cstart[(size_t)x + 1] - 1; c >= ws.cstart[(size_t)x]; --c)
+                    ws.stack.push_back(ws.clist[(size_t)c]);
+            }
+            ws.pnew.resize((size_t)n);
+            ws.nch.assign((size_t)n, 0);
+            for (int32_t j = 0; j < n; ++j) {
+                const int32_t x = ws.oldof[(size_t)j];
+                const int32_t pj = (j == 0) ? -1 : ws.newl[(size_t)par[x]];
+                ws.pnew[(size_t)j] = pj;
+                if (pj >= 0) ws.nch[(size_t)pj]++;
+                L.L[(size_t)(ib + j)] = in.length_um[ub + x];
+                L.D[(size_t)(ib + j)] = in.diam_um[ub + x];
+                L.pdist[(size_t)(ib + j)] = (j == 0) ? 0 : (j - pj);
+                L.user2int[(size_t)(ub + x)] = ib + j;
+            }
+            // segments: j starts one unless it is the only child of j-1
+            const size_t s_first = gsegs.size();
+            ws.seg_of_bottom.assign((size_t)n, -1);
+            for (int32_t j = 0; j < n; ++j) {
+                const bool cont = (j > 0 && ws.pnew[(size_t)j] == j - 1 && ws.nch[(size_t)(j - 1)] == 1);
+                if (!cont) {
+                    mmk::SegRec s;
+                    s.top = lb + j;
+                    s.len = 1;
+                    s.parent = (j == 0) ? -1 : lb + ws.pnew[(size_t)j];
+                    s.child0 = 0;
+                    s.nchild = 0;
+                    s.neuron = (j == 0) ? (k - k0) : -1;
+                    gsegs.push_back(s);
+                    gkids.emplace_back();
+                    gheight.push_back(0);
+                } else {
+                    gsegs.back().len++;
+                }
+            }
+            for (size_t s = s_first; s < gsegs.size(); ++s) {
+                const int32_t bottom = gsegs[s].top + gsegs[s].len - 1 - lb;
+                ws.seg_of_bottom[(size_t)bottom] = (int32_t)s;
+            }
+            // children and heights (child segments have larger tops than their parents)
+            for (size_t s = gsegs.size(); s-- > s_first + 1;) {
+                const int32_t pb = gsegs[s].parent - lb;
+                const int32_t ps = ws.seg_of_bottom[(size_t)pb];
+                if (ps < 0) { e << "internal: segment parent is not a segment bottom"; return msg(e); }
+                gkids[(size_t)ps].push_back((int32_t)s);
+                gheight[(size_t)ps] = std::max(gheight[(size_t)ps], gheight[s] + 1);
+            }
+        }
+        // sort by (height, longest first, top)
+        const int32_t ns = (int32_t)gsegs.size();
+        perm.resize((size_t)ns);
+        std::iota(perm.begin(), perm.end(), 0);
+        std::sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) {
+            if (gheight[(size_t)a] != gheight[(size_t)b]) return gheight[(size_t)a] < gheight[(size_t)b];
+            if (gsegs[(size_t)a].len != gsegs[(size_t)b].len) return gsegs[(size_t)a].len > gsegs[(size_t)b].len;
+            return gsegs[(size_t)a].top < gsegs[(size_t)b].top;
+        });
+        newidx.resize((size_t)ns);
+        for (int32_t i = 0; i < ns; ++i) newidx[(size_t)perm[(size_t)i]] = i;
+        mmk::GroupRec &gr = L.groups[(size_t)g];
+        gr.comp0 = comp0;
+        gr.ncomp = (int32_t)(L.noff[(size_t)k1] - comp0);
+        gr.seg0 = (int32_t)L.segs.size();
+        gr.nseg = ns;
+        gr.neuron0 = k0;
+        gr.nneuron = k1 - k0;
+        gr.pad = 0;
+        int32_t maxh = 0;
+        for (int32_t i = 0; i < ns; ++i) {
+            const int32_t s = perm[(size_t)i];
+            mmk::SegRec r = gsegs[(size_t)s];
+            r.child0 = (int32_t)L.seg_child.size();
+            r.nchild = (int32_t)gkids[(size_t)s].size();
+            for (int32_t c : gkids[(size_t)s]) L.seg_child.push_back(newidx[(size_t)c]);
+            L.segs.push_back(r);
+            maxh = std::max(maxh, gheight[(size_t)s]);
+        }
+        gr.wave0 = (int32_t)L.wave_off.size();
+        gr.nwave = maxh + 1;
+        {
+            int32_t i = 0;
+            for (int32_t h = 0; h <= maxh; ++h) {
+                while (i < ns && gheight[(size_t)perm[(size_t)i]] < h) ++i;
+                L.wave_off.push_back(i);
+            }
+            L.wave_off.push_back(ns);
+        }
+        L.max_comps = std::max(L.max_comps, gr.ncomp);
+        L.max_segs = std::max(L.max_segs, ns);
+        L.max_waves = std::max(L.max_waves, gr.nwave);
+    }
+
+    // 4a. synaptic sites: one per compartment that receives a synapse
+    std::vector<int32_t> site_of((size_t)C, -1);
+    for (int64_t s = 0; s < in.S; ++s) {
+        const int64_t ic = L.user2int[(size_t)(in.comp_offset[in.dst[s]] + in.dcomp[s])];
+        site_of[(size_t)ic] = 0;
+    }
+    {
+        int32_t ns = 0;
+        int32_t g = 0;
+        for (auto &gr : L.groups) { gr.site0 = 0; gr.nsite = 0; }
+        for (int64_t i = 0; i < C; ++i) {
+            if (site_of[(size_t)i] < 0) continue;
+            while (i >= L.groups[(size_t)g].comp0 + L.groups[(size_t)g].ncomp) ++g;
+            if (L.groups[(size_t)g].nsite == 0) L.groups[(size_t)g].site0 = ns;
+            L.groups[(size_t)g].nsite++;
+            site_of[(size_t)i] = ns++;
+            L.site_comp.push_back((int32_t)(i - L.groups[(size_t)g].comp0));
+            L.site_internal.push_back(i);
+        }
+        for (auto &gr : L.groups) if (gr.nsite == 0) gr.site0 = ns;
+        L.f_syn = C > 0 ? (double)ns / (double)C : 0.0;
+    }
+
+    // 4b. delays and the outgoing synapses of each source, sorted by delay
+    {
+        std::vector<char> seen((size_t)max_ds + 1, 0);
+        for (int64_t s = 0; s < in.S; ++s) seen[(size_t)dsteps[(size_t)s]] = 1;
+        L.dclass.clear();
+        for (int64_t d = 1; d <= max_ds; ++d) if (seen[(size_t)d]) L.dclass.push_back((int32_t)d);
+        L.R = (int32_t)(max_ds + 2);
+    }
+    L.out_off.assign((size_t)N + 1, 0);
+    for (int64_t s = 0; s < in.S; ++s) L.out_off[(size_t)L.internal_of[(size_t)in.src[s]] + 1]++;
+    for (int32_t k = 0; k < N; ++k) L.out_off[(size_t)k + 1] += L.out_off[(size_t)k];
+    std::vector<int64_t> order_s((size_t)in.S);
+    {
+        std::vector<int64_t> fill(L.out_off.begin(), L.out_off.end() - 1);
+        for (int64_t s = 0; s < in.S; ++s) order_s[(size_t)fill[(size_t)L.internal_of[(size_t)in.src[s]]]++] = s;
+    }
+    if (L.dclass.size() > 1) {
+        for (int32_t k = 0; k < N; ++k)
+            std::stable_sort(order_s.begin() + L.out_off[(size_t)k], order_s.begin() + L.out_off[(size_t)k + 1],
+                             [&](int64_t a, int64_t b) { return dsteps[(size_t)a] < dsteps[(size_t)b]; });
+    }
+    L.out_site.resize((size_t)in.S);
+    L.out_dsteps.resize((size_t)in.S);
+    L.out_w.resize((size_t)in.S);
+    for (int64_t q = 0; q < in.S; ++q) {
+        const int64_t s = order_s[(size_t)q];
+        const int64_t ic = L.user2int[(size_t)(in.comp_offset[in.dst[s]] + in.dcomp[s])];
+        L.out_site[(size_t)q] = site_of[(size_t)ic];
+        L.out_dsteps[(size_t)q] = dsteps[(size_t)s];
+        L.out_w[(size_t)q] = in.w[s];
+    }
+    return "";
+}
+
+}  // namespace mmh

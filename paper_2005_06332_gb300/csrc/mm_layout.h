@@ -1,0 +1,58 @@
+// mm_layout.h -- host-side construction of the device layout of a network.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "mm_internal.h"
+
+namespace mmh {
+
+struct LayoutInput {
+    int32_t N;
+    const int64_t *comp_offset;
+    const int32_t *parent;
+    const double *length_um, *diam_um;
+    int64_t S;
+    const int32_t *src, *dst, *dcomp;
+    const double *w, *delay_ms;
+    const double *stim;           // may be NULL
+    const float *cost;            // may be NULL (size order)
+    double dt;
+    int32_t group_comps;          // compartment budget of a work item
+    int32_t max_group_comps;      // largest work item a block can hold
+};
+
+struct Layout {
+    int32_t N = 0;
+    int64_t C = 0;
+    std::vector<int32_t> order;         // internal neuron -> user neuron
+    std::vector<int32_t> internal_of;   // user neuron -> internal neuron
+    std::vector<int64_t> noff;          // internal compartment offset of each internal neuron [N+1]
+    std::vector<int64_t> user2int;      // user compartment -> internal compartment [C]
+    std::vector<int64_t> soma_of_user;  // internal soma compartment of each user neuron [N]
+    std::vector<double> L, D;           // cylinders, internal order
+    std::vector<int32_t> pdist;         // i - parent(i) in internal order, 0 at somata
+    std::vector<double> stim;           // internal order
+    std::vector<mmk::GroupRec> groups;
+    std::vector<mmk::SegRec> segs;
+    std::vector<int32_t> seg_child;
+    std::vector<int32_t> wave_off;
+    int32_t max_comps = 0, max_segs = 0;
+    int32_t max_waves = 0;
+    std::vector<int32_t> site_comp;     // group-local compartment of each site
+    std::vector<int64_t> site_internal; // internal compartment of each site
+    std::vector<int64_t> out_off;       // outgoing synapses per internal source [N+1]
+    std::vector<int32_t> out_site, out_dsteps;
+    std::vector<double> out_w;
+    std::vector<int32_t> dclass;        // distinct delays in steps, ascending
+    int32_t R = 2;                      // spike ring depth (steps)
+    double f_syn = 0.0;                 // fraction of compartments with a synapse
+};
+
+// Validates the inputs and builds the layout.  Returns "" on success, else
+// a message; *invalid tells whether the inputs were invalid (vs. unsupported).
+std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid);
+
+}  // namespace mmh

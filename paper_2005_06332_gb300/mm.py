@@ -1,0 +1,297 @@
+"""ctypes binding of the C-ABI in include/mm.h (argument marshalling only).
+
+Every step of the simulation runs in the CUDA library; this module converts
+NumPy inputs to the C structs, hands PyTorch's caching allocator to the
+library for device memory, and turns status codes into exceptions.  There is
+no fallback: if the library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ETIMEOUT, MM_ENUMERIC, MM_EOVERFLOW, MM_ESTATE, MM_ENOTSUP = range(9)
+MM_FP64, MM_FP32C = 0, 1
+MM_SCHED_SIZE_SORTED, MM_SCHED_COST = 0, 1
+STATE = {"V": 0, "m": 1, "h": 2, "n": 3, "gsyn": 4}
+PRECISION = {"fp64": MM_FP64, "fp32c": MM_FP32C}
+
+
+class MMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_status_name(status)}: {message}")
+        self.status = status
+
+
+class Morphologies(C.Structure):
+    _fields_ = [("n_neurons", C.c_int32), ("comp_offset", C.POINTER(C.c_int64)), ("parent", C.POINTER(C.c_int32)),
+                ("length_um", C.POINTER(C.c_double)), ("diam_um", C.POINTER(C.c_double))]
+
+
+class ChannelParams(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("gNa", "gK", "gL", "ENa", "EK", "EL", "Cm", "Ra", "v_init", "threshold_mV")]
+
+
+class Synapses(C.Structure):
+    _fields_ = [("n", C.c_int64), ("src_neuron", C.POINTER(C.c_int32)), ("dst_neuron", C.POINTER(C.c_int32)),
+                ("dst_comp", C.POINTER(C.c_int32)), ("weight_uS", C.POINTER(C.c_double)),
+                ("delay_ms", C.POINTER(C.c_double)), ("tau_ms", C.c_double), ("e_rev_mV", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("release", RELEASE_FN), ("ctx", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("schedule", C.c_int32), ("graph_steps", C.c_int32),
+                ("block_threads", C.c_int32), ("group_comps", C.c_int32), ("device", C.c_int32),
+                ("dt_ms", C.c_double), ("spike_capacity", C.c_int64), ("cuda_stream", C.c_void_p),
+                ("cost", C.POINTER(C.c_float)), ("allocator", Allocator)]
+
+
+class KernelTimes(C.Structure):
+    _fields_ = [("step_kernel_ms", C.c_double), ("step_kernel_launches", C.c_int64),
+                ("deliver_kernel_ms", C.c_double), ("deliver_kernel_launches", C.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load the CUDA library (raises if it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise ImportError(f"CUDA library {path} is not built; run __graft_entry__.build()")
+            _build.build()
+        L = C.CDLL(path)
+        P = C.POINTER
+        net_p = C.c_void_p
+        L.mm_default_options.argtypes = [P(Options)]
+        L.mm_default_options.restype = None
+        L.mm_create_network.argtypes = [P(Morphologies), P(ChannelParams), P(Synapses), P(C.c_double), P(Options),
+                                        P(net_p)]
+        L.mm_step.argtypes = [net_p, C.c_int64, C.c_double]
+        L.mm_synchronize.argtypes = [net_p]
+        L.mm_read_voltages.argtypes = [net_p, P(C.c_double), C.c_int64]
+        L.mm_read_state.argtypes = [net_p, C.c_int32, P(C.c_double), C.c_int64]
+        L.mm_read_soma_voltages.argtypes = [net_p, P(C.c_double), C.c_int64]
+        L.mm_read_spikes.argtypes = [net_p, P(C.c_int32), P(C.c_double), C.c_int64, P(C.c_int64)]
+        L.mm_set_stimulus.argtypes = [net_p, P(C.c_double), C.c_int64]
+        L.mm_get_step.argtypes = [net_p, P(C.c_int64)]
+        L.mm_save_state.argtypes = [net_p, C.c_void_p, C.c_size_t, P(C.c_size_t)]
+        L.mm_load_state.argtypes = [net_p, C.c_void_p, C.c_size_t]
+        L.mm_set_kernel_timing.argtypes = [net_p, C.c_int32]
+        L.mm_read_kernel_timing.argtypes = [net_p, P(KernelTimes), C.c_int32]
+        L.mm_last_error.argtypes = [net_p]
+        L.mm_last_error.restype = C.c_char_p
+        L.mm_status_string.argtypes = [C.c_int]
+        L.mm_status_string.restype = C.c_char_p
+        L.mm_destroy.argtypes = [net_p]
+        L.mm_destroy.restype = None
+        for name in ("mm_create_network", "mm_step", "mm_synchronize", "mm_read_voltages", "mm_read_state",
+                     "mm_read_soma_voltages", "mm_read_spikes", "mm_set_stimulus", "mm_get_step", "mm_save_state",
+                     "mm_load_state", "mm_set_kernel_timing", "mm_read_kernel_timing"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def _status_name(s: int) -> str:
+    names = ["MM_OK", "MM_EINVAL", "MM_ENOMEM", "MM_ECUDA", "MM_ETIMEOUT", "MM_ENUMERIC", "MM_EOVERFLOW",
+             "MM_ESTATE", "MM_ENOTSUP"]
+    return names[s] if 0 <= s < len(names) else f"status {s}"
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+class TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator."""
+
+    def __init__(self, device: int):
+        import torch
+        self._torch = torch
+        self.device = torch.device("cuda", device)
+        self.blocks = {}
+        self._alloc = ALLOC_FN(self._do_alloc)
+        self._release = RELEASE_FN(self._do_release)
+
+    def _do_alloc(self, nbytes, ctx):
+        try:
+            t = self._torch.empty(int(nbytes), dtype=self._torch.uint8, device=self.device)
+        except Exception:
+            return None
+        p = t.data_ptr()
+        self.blocks[p] = t
+        return p
+
+    def _do_release(self, ptr, ctx):
+        self.blocks.pop(ptr, None)
+
+    def struct(self) -> Allocator:
+        return Allocator(self._alloc, self._release, None)
+
+    def bytes_held(self) -> int:
+        return sum(t.numel() for t in self.blocks.values())
+
+
+class Network:
+    """A network living on one GPU; see include/mm.h for the semantics."""
+
+    def __init__(self, net, precision: str = "fp64", cost: Optional[np.ndarray] = None, graph_steps: int = 40,
+                 block_threads: int = 0, group_comps: int = 0, spike_capacity: int = 0, device: int = 0,
+                 stream=None, torch_alloc: bool = True):
+        L = load()
+        self._L = L
+        self._h = C.c_void_p()
+        self.n_neurons = net.n_neurons
+        self.n_comp = net.n_comp
+        self.dt = float(net.dt)
+        # keep the NumPy inputs alive for the duration of the create call
+        self._in = dict(
+            off=np.ascontiguousarray(net.comp_offset, np.int64), parent=np.ascontiguousarray(net.parent, np.int32),
+            L=np.ascontiguousarray(net.length_um, np.float64), D=np.ascontiguousarray(net.diam_um, np.float64),
+            src=np.ascontiguousarray(net.syn_src, np.int32), dst=np.ascontiguousarray(net.syn_dst, np.int32),
+            comp=np.ascontiguousarray(net.syn_comp, np.int32), w=np.ascontiguousarray(net.syn_w, np.float64),
+            dl=np.ascontiguousarray(net.syn_delay_ms, np.float64),
+            stim=np.ascontiguousarray(net.stim_nA, np.float64))
+        a = self._in
+        morph = Morphologies(net.n_neurons, _ptr(a["off"], C.c_int64), _ptr(a["parent"], C.c_int32),
+                             _ptr(a["L"], C.c_double), _ptr(a["D"], C.c_double))
+        p = net.params
+        chan = ChannelParams(p["gNa"], p["gK"], p["gL"], p["ENa"], p["EK"], p["EL"], p["Cm"], p["Ra"], p["v_init"],
+                             p["threshold"])
+        syn = Synapses(len(a["src"]), _ptr(a["src"], C.c_int32), _ptr(a["dst"], C.c_int32), _ptr(a["comp"], C.c_int32),
+                       _ptr(a["w"], C.c_double), _ptr(a["dl"], C.c_double), p["tau_syn"], p["e_syn"])
+        opt = Options()
+        L.mm_default_options(C.byref(opt))
+        opt.precision = PRECISION[precision]
+        opt.graph_steps = graph_steps
+        opt.block_threads = block_threads
+        opt.group_comps = group_comps
+        opt.device = device
+        opt.dt_ms = self.dt
+        opt.spike_capacity = spike_capacity
+        self._cost = None
+        if cost is not None:
+            self._cost = np.ascontiguousarray(cost, np.float32)
+            opt.schedule = MM_SCHED_COST
+            opt.cost = _ptr(self._cost, C.c_float)
+        if stream is not None:
+            opt.cuda_stream = C.c_void_p(int(stream))
+        self._alloc = TorchAllocator(device) if torch_alloc else None
+        if self._alloc is not None:
+            opt.allocator = self._alloc.struct()
+        st = L.mm_create_network(C.byref(morph), C.byref(chan), C.byref(syn), _ptr(a["stim"], C.c_double),
+                                 C.byref(opt), C.byref(self._h))
+        if st != MM_OK:
+            raise MMError(st, "mm_create_network failed")
+        self._in = None
+
+    # ---------------------------------------------------------------- helpers
+    def _check(self, st: int, what: str):
+        if st != MM_OK:
+            raise MMError(st, f"{what}: {self._L.mm_last_error(self._h).decode()}")
+
+    def close(self):
+        if self._h:
+            self._L.mm_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------ calls
+    def step(self, n_steps: int):
+        self._check(self._L.mm_step(self._h, int(n_steps), self.dt), "mm_step")
+
+    def synchronize(self):
+        self._check(self._L.mm_synchronize(self._h), "mm_synchronize")
+
+    @property
+    def steps(self) -> int:
+        s = C.c_int64()
+        self._check(self._L.mm_get_step(self._h, C.byref(s)), "mm_get_step")
+        return s.value
+
+    def read_voltages(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        return self.read_state("V", out)
+
+    def read_state(self, which: str, out: Optional[np.ndarray] = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.n_comp, np.float64)
+        self._check(self._L.mm_read_state(self._h, STATE[which], _ptr(out, C.c_double), out.size), "mm_read_state")
+        return out
+
+    def read_soma(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.n_neurons, np.float64)
+        self._check(self._L.mm_read_soma_voltages(self._h, _ptr(out, C.c_double), out.size), "mm_read_soma_voltages")
+        return out
+
+    def read_spikes(self, cap: Optional[int] = None, allow_overflow: bool = False):
+        """(neuron, t_ms) drained since the last call, ordered by (t, neuron)."""
+        if cap is None:
+            cap = max(1 << 16, self.n_neurons * 64)
+        nr = np.empty(cap, np.int32)
+        tt = np.empty(cap, np.float64)
+        n = C.c_int64()
+        st = self._L.mm_read_spikes(self._h, _ptr(nr, C.c_int32), _ptr(tt, C.c_double), cap, C.byref(n))
+        if st == MM_EOVERFLOW and allow_overflow:
+            k = min(cap, n.value)
+            return nr[:k].copy(), tt[:k].copy()
+        self._check(st, "mm_read_spikes")
+        return nr[:n.value].copy(), tt[:n.value].copy()
+
+    def set_stimulus(self, stim_nA: np.ndarray):
+        s = np.ascontiguousarray(stim_nA, np.float64)
+        self._check(self._L.mm_set_stimulus(self._h, _ptr(s, C.c_double), s.size), "mm_set_stimulus")
+
+    def save_state(self) -> bytes:
+        n = C.c_size_t()
+        self._check(self._L.mm_save_state(self._h, None, 0, C.byref(n)), "mm_save_state")
+        buf = C.create_string_buffer(n.value)
+        self._check(self._L.mm_save_state(self._h, buf, n.value, C.byref(n)), "mm_save_state")
+        return buf.raw
+
+    def set_kernel_timing(self, enable: bool):
+        self._check(self._L.mm_set_kernel_timing(self._h, 1 if enable else 0), "mm_set_kernel_timing")
+
+    def read_kernel_timing(self, reset: bool = True) -> dict:
+        t = KernelTimes()
+        self._check(self._L.mm_read_kernel_timing(self._h, C.byref(t), 1 if reset else 0), "mm_read_kernel_timing")
+        return {k: getattr(t, k) for k, _ in KernelTimes._fields_}
+
+    def load_state(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check(self._L.mm_load_state(self._h, buf, len(blob)), "mm_load_state")

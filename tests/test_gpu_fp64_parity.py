@@ -1,0 +1,146 @@
+"""FP64 CUDA path vs the FP64 CPU oracle, element by element, through the C-ABI.
+
+Tolerance: |dV| <= 1e-9 mV on every compartment (the FP64 acceptance bar),
+gates within 1e-12, identical spike trains (same neurons, same steps, times
+within 1e-9 ms).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_06332_gb300 import mm, netgen
+
+pytestmark = pytest.mark.gpu
+
+TOL_V = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    mm.load(build_if_missing=True)
+
+
+def _run_gpu(net, steps, **kw):
+    with mm.Network(net, **kw) as g:
+        g.step(steps)
+        V = g.read_voltages()
+        st = {k: g.read_state(k) for k in ("m", "h", "n", "gsyn")}
+        spk = g.read_spikes()
+    return V, st, spk
+
+
+def _compare(net, steps, tol_v=TOL_V, **kw):
+    ref = oracle.simulate(net, steps)
+    V, st, (sn, stt) = _run_gpu(net, steps, **kw)
+    dv = np.max(np.abs(V - ref.V)) if net.n_comp else 0.0
+    assert dv <= tol_v, f"max |dV| = {dv:.3e} mV"
+    for k, r in (("m", ref.m), ("h", ref.h), ("n", ref.n)):
+        assert np.max(np.abs(st[k] - r)) <= 1e-11, k
+    assert np.max(np.abs(st["gsyn"] - ref.g)) <= 1e-12
+    rn, rt = ref.spikes_sorted()
+    assert len(sn) == len(rn), (len(sn), len(rn))
+    # same neurons in the same steps; times within rounding
+    np.testing.assert_array_equal(np.floor(stt / net.dt + 1e-9), np.floor(rt / net.dt + 1e-9))
+    order_g = np.lexsort((sn, np.round(stt, 6)))
+    order_r = np.lexsort((rn, np.round(rt, 6)))
+    np.testing.assert_array_equal(sn[order_g], rn[order_r])
+    assert np.max(np.abs(stt[order_g] - rt[order_r]), initial=0.0) <= 1e-9
+    return dv, len(rn)
+
+
+def _chain(n, stim=0.3):
+    off = np.array([0, n], dtype=np.int64)
+    return netgen.Network(
+        comp_offset=off, parent=np.arange(-1, n - 1, dtype=np.int32),
+        length_um=np.linspace(5, 20, n), diam_um=np.linspace(2, 0.5, n), stim_nA=np.array([stim]),
+        syn_src=np.zeros(0, np.int32), syn_dst=np.zeros(0, np.int32), syn_comp=np.zeros(0, np.int32),
+        syn_w=np.zeros(0), syn_delay_ms=np.zeros(0), params=dict(netgen.DEFAULT_PARAMS), dt=0.025)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 33, 300])
+def test_single_chain_one_step(n):
+    _compare(_chain(n), 1)
+
+
+def test_single_chain_many_steps():
+    _compare(_chain(120, stim=0.6), 800)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_small_random_network(seed):
+    net = netgen.make_network(30, size_dist=("loguniform", 2, 300), p_branch=("uniform", 0.02, 0.3),
+                              syn_per_neuron=10, seed=seed, stim_nA=(0.2, 0.8), weight_uS=(0.0, 0.05))
+    dv, nsp = _compare(net, 600)
+    assert nsp > 0
+
+
+def test_many_groups_and_waves():
+    """Work items far smaller than a neuron group: many blocks, ragged tails."""
+    net = netgen.make_network(60, size_dist=("loguniform", 5, 700), p_branch=("uniform", 0.05, 0.5),
+                              syn_per_neuron=8, seed=9, stim_nA=(0.2, 0.8))
+    _compare(net, 300, group_comps=256, block_threads=128)
+
+
+def test_graph_and_direct_launches_agree():
+    net = netgen.make_network(20, size_dist=("loguniform", 20, 200), p_branch=0.1, syn_per_neuron=5, seed=4,
+                              stim_nA=(0.3, 0.8))
+    a, _, sa = _run_gpu(net, 123, graph_steps=40)
+    b, _, sb = _run_gpu(net, 123, graph_steps=0)
+    assert np.max(np.abs(a - b)) <= 1e-12
+    assert len(sa[0]) == len(sb[0])
+
+
+def test_mono64_full_duration():
+    """The 64 x 255-compartment mono-morphology workload over 100 ms."""
+    net = netgen.make_config("mono64")
+    dv, nsp = _compare(net, net.n_steps)
+    assert nsp > 100
+
+
+def test_multi10k_full_size_first_window_sampled():
+    """The 10,000-neuron multi-morphology network at full size, in the launch
+    configuration the benchmark times: for the first min-delay window no
+    event can arrive, so each sampled neuron must follow the oracle's run of
+    that neuron alone."""
+    net = netgen.make_config("multi10k")
+    steps = int(round(1.0 / net.dt)) + 1
+    with mm.Network(net) as g:
+        g.step(steps)
+        V = g.read_voltages()
+    rng = np.random.default_rng(0)
+    sizes = net.sizes()
+    pick = np.unique(np.concatenate([rng.choice(net.n_neurons, 40, replace=False), [int(np.argmax(sizes))],
+                                     [int(np.argmin(sizes))]]))
+    sub = net.subset(pick, keep_synapses=False)
+    ref = oracle.simulate(sub, steps)
+    idx = np.concatenate([np.arange(net.comp_offset[k], net.comp_offset[k + 1]) for k in pick])
+    assert np.max(np.abs(V[idx] - ref.V)) <= TOL_V
+
+
+def test_checkpoint_resume_matches_uninterrupted_run():
+    net = netgen.make_network(25, size_dist=("loguniform", 10, 300), p_branch=0.1, syn_per_neuron=6, seed=12,
+                              stim_nA=(0.3, 0.9))
+    with mm.Network(net) as g:
+        g.step(90)
+        blob = g.save_state()
+        g.step(150)
+        ref = g.read_voltages()
+    with mm.Network(net) as g2:
+        g2.load_state(blob)
+        assert g2.steps == 90
+        g2.step(150)
+        got = g2.read_voltages()
+    assert np.max(np.abs(got - ref)) <= 1e-12
+
+
+def test_invalid_inputs_are_rejected():
+    bad = _chain(4)
+    bad.parent = bad.parent.copy()
+    bad.parent[2] = 3  # parent after child
+    with pytest.raises(mm.MMError) as e:
+        mm.Network(bad)
+    assert e.value.status == mm.MM_EINVAL
+    net = _chain(4)
+    with mm.Network(net) as g:
+        with pytest.raises(mm.MMError):
+            g._check(g._L.mm_step(g._h, 1, 0.05), "mm_step")
