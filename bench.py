@@ -41,7 +41,10 @@ L2_BYTES = 129 * 1024 * 1024
 # Algorithmic bytes per compartment-update of the fused step kernel:
 # FP64 state V, m, h, n read + written (64 B) and the constants area, g_axial
 # read (16 B); per synaptic site g_syn read + written and its index (20 B).
-BYTES_PER_UPDATE = {"fp64": (80.0, 20.0)}
+BYTES_PER_UPDATE = {"fp64": (80.0, 20.0),
+                    # FP32c: int32 V and three uint32 gates read + written (32 B),
+                    # FP32 area and g_axial read (8 B); per site FP32 g_syn r/w + index
+                    "fp32c": (40.0, 12.0)}
 
 
 def _peaks():

@@ -18,6 +18,7 @@ namespace {
 constexpr int kStepThreads = 256;
 constexpr int kDefaultGroupComps = 4096;
 constexpr int kMaxGroupComps = 8192;
+constexpr int kMaxGroupComps32 = 24576;
 constexpr size_t kMaxSmem = 227 * 1024;
 
 }  // namespace
@@ -46,9 +47,19 @@ struct mm_net {
     int graph_steps = 40;
     cudaGraphExec_t gexec = nullptr;
 
-    // device arrays
+    mmk::StepArgs32 sa32{};
+
+    // device arrays (FP64 path)
     double *V = nullptr, *m = nullptr, *h = nullptr, *n = nullptr;
-    double *area = nullptr, *gax = nullptr, *stim = nullptr, *gsyn = nullptr;
+    double *area = nullptr, *gax = nullptr, *gsyn = nullptr;
+    // device arrays (FP32c path)
+    int32_t *Vq = nullptr;
+    uint32_t *mq = nullptr, *hq = nullptr, *nq = nullptr;
+    double *Vsoma = nullptr;
+    float *area32 = nullptr, *gax32 = nullptr, *gsyn32 = nullptr;
+    int64_t *soma_internal = nullptr, *internal_of64 = nullptr;
+    // both
+    double *stim = nullptr;
     double *spk_t = nullptr, *scratch = nullptr;
     int32_t *spk_nrn = nullptr, *ring_nrn = nullptr, *ring_cnt = nullptr, *user_id = nullptr;
     int64_t *user2int = nullptr, *soma_of_user = nullptr, *site_internal = nullptr;
@@ -190,11 +201,16 @@ mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
             if (kind == 0) {
                 mmk::DeliverArgs da = net->da;
                 da.step_offset = j;
-                MM_CKI(net, mmk_launch_deliver(da, net->deliver_blocks, s));
-            } else {
+                if (net->precision == MM_FP64) MM_CKI(net, mmk_launch_deliver(da, net->deliver_blocks, s));
+                else MM_CKI(net, mmk_launch_deliver_fp32c(da, net->deliver_blocks, s));
+            } else if (net->precision == MM_FP64) {
                 mmk::StepArgs sa = net->sa;
                 sa.step_offset = j;
                 MM_CKI(net, mmk_launch_step_fp64(sa, net->step_blocks, net->step_threads, s));
+            } else {
+                mmk::StepArgs32 sa = net->sa32;
+                sa.step_offset = j;
+                MM_CKI(net, mmk_launch_step_fp32c(sa, net->step_blocks, net->step_threads, s));
             }
             if (timed) {
                 MM_CK(net, cudaEventRecord(p.b, s));
@@ -265,7 +281,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     net->graph_steps = std::max(0, opt->graph_steps);
     net->device = opt->device;
     net->alloc = opt->allocator;
-    if (opt->precision != MM_FP64) return fail(net, MM_ENOTSUP, "only MM_FP64 is available in this build");
+    if (opt->precision != MM_FP64 && opt->precision != MM_FP32C) return fail(net, MM_EINVAL, "unknown precision");
     if (opt->schedule != MM_SCHED_SIZE_SORTED && opt->schedule != MM_SCHED_COST)
         return fail(net, MM_EINVAL, "unknown schedule");
     if (opt->schedule == MM_SCHED_COST && !opt->cost) return fail(net, MM_EINVAL, "MM_SCHED_COST needs mm_options.cost");
@@ -298,7 +314,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     li.cost = opt->schedule == MM_SCHED_COST ? opt->cost : nullptr;
     li.dt = opt->dt_ms;
     li.group_comps = opt->group_comps > 0 ? opt->group_comps : kDefaultGroupComps;
-    li.max_group_comps = kMaxGroupComps;
+    li.max_group_comps = opt->precision == MM_FP64 ? kMaxGroupComps : kMaxGroupComps32;
     mmh::Layout L;
     bool invalid = false;
     std::string m;
@@ -324,20 +340,37 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     mm_status st;
 #define UP(dst, src, cnt) if ((st = upload(net, &(dst), (src), (cnt))) != MM_OK) return st
 #define ZR(dst, cnt) if ((st = zeros(net, &(dst), (cnt))) != MM_OK) return st
+    const bool f64 = opt->precision == MM_FP64;
     double *dL = nullptr, *dD = nullptr;
     int32_t *dpd = nullptr;
     UP(dL, L.L.data(), C);
     UP(dD, L.D.data(), C);
     UP(dpd, L.pdist.data(), C);
-    ZR(net->V, C);
-    ZR(net->m, C);
-    ZR(net->h, C);
-    ZR(net->n, C);
-    ZR(net->area, C);
-    ZR(net->gax, C);
+    if (f64) {
+        ZR(net->V, C);
+        ZR(net->m, C);
+        ZR(net->h, C);
+        ZR(net->n, C);
+        ZR(net->area, C);
+        ZR(net->gax, C);
+        ZR(net->gsyn, (size_t)std::max<int64_t>(net->nsite, 1));
+    } else {
+        ZR(net->Vq, C);
+        ZR(net->mq, C);
+        ZR(net->hq, C);
+        ZR(net->nq, C);
+        ZR(net->area32, C);
+        ZR(net->gax32, C);
+        ZR(net->Vsoma, N);
+        ZR(net->gsyn32, (size_t)std::max<int64_t>(net->nsite, 1));
+        std::vector<int64_t> soma_int(N), int_of(N);
+        for (size_t k = 0; k < N; ++k) soma_int[k] = L.noff[k];
+        for (size_t u = 0; u < N; ++u) int_of[u] = L.internal_of[u];
+        UP(net->soma_internal, soma_int.data(), N);
+        UP(net->internal_of64, int_of.data(), N);
+    }
     ZR(net->scratch, 2 * std::max(C, N));
     UP(net->stim, L.stim.data(), N);
-    ZR(net->gsyn, (size_t)std::max<int64_t>(net->nsite, 1));
     UP(net->user_id, L.order.data(), N);
     UP(net->user2int, L.user2int.data(), C);
     UP(net->soma_of_user, L.soma_of_user.data(), N);
@@ -358,10 +391,16 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     int64_t *dout_off = nullptr;
     int32_t *dout_site = nullptr, *dout_ds = nullptr, *ddclass = nullptr;
     double *dout_w = nullptr;
+    float *dout_w32 = nullptr;
     UP(dout_off, L.out_off.data(), L.out_off.size());
     UP(dout_site, L.out_site.data(), std::max<size_t>(L.out_site.size(), 1));
     UP(dout_ds, L.out_dsteps.data(), std::max<size_t>(L.out_dsteps.size(), 1));
-    UP(dout_w, L.out_w.data(), std::max<size_t>(L.out_w.size(), 1));
+    if (f64) {
+        UP(dout_w, L.out_w.data(), std::max<size_t>(L.out_w.size(), 1));
+    } else {
+        std::vector<float> w32(L.out_w.begin(), L.out_w.end());
+        UP(dout_w32, w32.data(), std::max<size_t>(w32.size(), 1));
+    }
     UP(ddclass, L.dclass.data(), std::max<size_t>(L.dclass.size(), 1));
 #undef UP
 #undef ZR
@@ -372,54 +411,117 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     ia.diam = dD;
     ia.parent_dist = dpd;
     ia.C = L.C;
-    ia.area = net->area;
-    ia.gax = net->gax;
-    ia.V = net->V;
-    ia.m = net->m;
-    ia.h = net->h;
-    ia.n = net->n;
     ia.Ra = chan->Ra;
     ia.v_init = chan->v_init;
-    MM_CKI(net, mmk_launch_init(ia, net->stream));
+    if (f64) {
+        ia.area = net->area;
+        ia.gax = net->gax;
+        ia.V = net->V;
+        ia.m = net->m;
+        ia.h = net->h;
+        ia.n = net->n;
+        MM_CKI(net, mmk_launch_init(ia, net->stream));
+    } else {
+        ia.Vq = net->Vq;
+        ia.mq = net->mq;
+        ia.hq = net->hq;
+        ia.nq = net->nq;
+        ia.area32 = net->area32;
+        ia.gax32 = net->gax32;
+        MM_CKI(net, mmk_launch_init_fp32c(ia, net->stream));
+        MM_CKI(net, mmk_launch_fill_f64(net->Vsoma, chan->v_init, (int64_t)N, net->stream));
+    }
 
-    // kernel arguments
-    mmk::StepArgs &a = net->sa;
-    a.V = net->V;
-    a.m = net->m;
-    a.h = net->h;
-    a.n = net->n;
-    a.area = net->area;
-    a.gax = net->gax;
-    a.stim = net->stim;
-    a.user_id = net->user_id;
-    a.groups = dgroups;
-    a.n_groups = (int32_t)L.groups.size();
-    a.segs = dsegs;
-    a.seg_child = dchild;
-    a.wave_off = dwave;
-    a.site_comp = dsite;
-    a.gsyn = net->gsyn;
-    a.ring_nrn = net->ring_nrn;
-    a.ring_cnt = net->ring_cnt;
-    a.R = net->R;
-    a.N = net->N;
-    a.spk_nrn = net->spk_nrn;
-    a.spk_t = net->spk_t;
-    a.spk_cap = net->spk_cap;
-    a.ctl = net->ctl;
-    a.smem_comps = std::max(L.max_comps, 1);
-    a.smem_segs = std::max(L.max_segs, 1);
-    a.gNa = chan->gNa;
-    a.gK = chan->gK;
-    a.gL = chan->gL;
-    a.ENa = chan->ENa;
-    a.EK = chan->EK;
-    a.EL = chan->EL;
-    a.cm_dt = chan->Cm * 1e3 / opt->dt_ms;
-    a.e_syn = syn ? syn->e_rev_mV : 0.0;
-    a.threshold = chan->threshold_mV;
-    a.dt = opt->dt_ms;
-    a.decay = syn ? std::exp(-opt->dt_ms / syn->tau_ms) : 1.0;
+    const int32_t smem_comps = std::max(L.max_comps, 1), smem_segs = std::max(L.max_segs, 1);
+    const double decay = syn ? std::exp(-opt->dt_ms / syn->tau_ms) : 1.0;
+    if (f64) {
+        mmk::StepArgs &a = net->sa;
+        a.V = net->V;
+        a.m = net->m;
+        a.h = net->h;
+        a.n = net->n;
+        a.area = net->area;
+        a.gax = net->gax;
+        a.stim = net->stim;
+        a.user_id = net->user_id;
+        a.groups = dgroups;
+        a.n_groups = (int32_t)L.groups.size();
+        a.segs = dsegs;
+        a.seg_child = dchild;
+        a.wave_off = dwave;
+        a.site_comp = dsite;
+        a.gsyn = net->gsyn;
+        a.ring_nrn = net->ring_nrn;
+        a.ring_cnt = net->ring_cnt;
+        a.R = net->R;
+        a.N = net->N;
+        a.spk_nrn = net->spk_nrn;
+        a.spk_t = net->spk_t;
+        a.spk_cap = net->spk_cap;
+        a.ctl = net->ctl;
+        a.smem_comps = smem_comps;
+        a.smem_segs = smem_segs;
+        a.gNa = chan->gNa;
+        a.gK = chan->gK;
+        a.gL = chan->gL;
+        a.ENa = chan->ENa;
+        a.EK = chan->EK;
+        a.EL = chan->EL;
+        a.cm_dt = chan->Cm * 1e3 / opt->dt_ms;
+        a.e_syn = syn ? syn->e_rev_mV : 0.0;
+        a.threshold = chan->threshold_mV;
+        a.dt = opt->dt_ms;
+        a.decay = decay;
+    } else {
+        auto pot = [](double E) {
+            mmk::FxPot p;
+            const double q = std::nearbyint(E * mmk::kVScaleD);
+            p.q = (int32_t)q;
+            p.res = (float)(E - q / mmk::kVScaleD);
+            return p;
+        };
+        for (double E : {chan->ENa, chan->EK, chan->EL, chan->v_init, syn ? syn->e_rev_mV : 0.0})
+            if (!(std::fabs(E) < 250.0)) return fail(net, MM_EINVAL, "potentials must lie within +-250 mV for MM_FP32C");
+        mmk::StepArgs32 &a = net->sa32;
+        a.Vq = net->Vq;
+        a.mq = net->mq;
+        a.hq = net->hq;
+        a.nq = net->nq;
+        a.Vsoma = net->Vsoma;
+        a.area = net->area32;
+        a.gax = net->gax32;
+        a.stim = net->stim;
+        a.user_id = net->user_id;
+        a.groups = dgroups;
+        a.n_groups = (int32_t)L.groups.size();
+        a.segs = dsegs;
+        a.seg_child = dchild;
+        a.wave_off = dwave;
+        a.site_comp = dsite;
+        a.gsyn = net->gsyn32;
+        a.ring_nrn = net->ring_nrn;
+        a.ring_cnt = net->ring_cnt;
+        a.R = net->R;
+        a.N = net->N;
+        a.spk_nrn = net->spk_nrn;
+        a.spk_t = net->spk_t;
+        a.spk_cap = net->spk_cap;
+        a.ctl = net->ctl;
+        a.smem_comps = smem_comps;
+        a.smem_segs = smem_segs;
+        a.gNa = (float)chan->gNa;
+        a.gK = (float)chan->gK;
+        a.gL = (float)chan->gL;
+        a.ENa = pot(chan->ENa);
+        a.EK = pot(chan->EK);
+        a.EL = pot(chan->EL);
+        a.Esyn = pot(syn ? syn->e_rev_mV : 0.0);
+        a.cm_dt = (float)(chan->Cm * 1e3 / opt->dt_ms);
+        a.dt = (float)opt->dt_ms;
+        a.decay = (float)decay;
+        a.threshold = chan->threshold_mV;
+        a.dt64 = opt->dt_ms;
+    }
 
     mmk::DeliverArgs &d = net->da;
     d.ring_nrn = net->ring_nrn;
@@ -434,18 +536,21 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     d.n_dclass = (int32_t)L.dclass.size();
     d.gsyn = net->gsyn;
     d.ctl = net->ctl;
+    d.gsyn32 = net->gsyn32;
+    d.out_w32 = dout_w32;
 
-    const size_t smem = (size_t)(2 * a.smem_comps + 2 * a.smem_segs) * sizeof(double);
+    const size_t smem = (size_t)(2 * smem_comps + 2 * smem_segs) * (f64 ? sizeof(double) : sizeof(float));
     if (smem > kMaxSmem) return fail(net, MM_ENOTSUP, "a work item needs more shared memory than a block has");
     int threads = opt->block_threads > 0 ? opt->block_threads : kStepThreads;
     if (threads != 128 && threads != 256 && threads != 512) return fail(net, MM_EINVAL, "block_threads must be 128, 256 or 512");
     net->step_threads = threads;
     int per_sm = 0;
-    MM_CKI(net, mmk_step_fp64_blocks_per_sm(threads, (int)smem, &per_sm));
+    if (f64) MM_CKI(net, mmk_step_fp64_blocks_per_sm(threads, (int)smem, &per_sm));
+    else MM_CKI(net, mmk_step_fp32c_blocks_per_sm(threads, (int)smem, &per_sm));
     if (per_sm < 1) return fail(net, MM_ENOTSUP, "the step kernel does not fit on an SM");
     int sms = 0;
     MM_CK(net, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device));
-    net->step_blocks = std::max(1, std::min(a.n_groups, per_sm * sms));
+    net->step_blocks = std::max(1, std::min((int)L.groups.size(), per_sm * sms));
     net->deliver_blocks = std::max(1, 2 * sms);
     MM_CK(net, cudaStreamSynchronize(net->stream));
     return MM_OK;
@@ -519,23 +624,37 @@ mm_status mm_read_state(mm_net *net, int32_t which, double *out, int64_t cap)
     mm_status st = guard(net);
     if (st != MM_OK) return st;
     if (!out || cap < net->C) return fail(net, MM_EINVAL, "output buffer too small");
+    if (which < MM_STATE_V || which > MM_STATE_GSYN) return fail(net, MM_EINVAL, "unknown state quantity");
+    // dense internal-order values in the second half of the scratch, then a
+    // gather into user order in its first half
+    double *dense = net->scratch + std::max<int64_t>(net->C, net->N);
     const double *src = nullptr;
-    switch (which) {
-    case MM_STATE_V: src = net->V; break;
-    case MM_STATE_M: src = net->m; break;
-    case MM_STATE_H: src = net->h; break;
-    case MM_STATE_N: src = net->n; break;
-    case MM_STATE_GSYN: {
-        // merged conductances live per synaptic site: scatter them into a
-        // dense internal array (second half of the scratch) and gather that
-        double *dense = net->scratch + std::max<int64_t>(net->C, net->N);
-        MM_CKI(net, mmk_launch_fill_f64(dense, 0.0, net->C, net->stream));
-        MM_CKI(net, mmk_launch_scatter_site_gsyn(net->gsyn, net->site_internal, dense, net->nsite, net->stream));
+    if (net->precision == MM_FP64) {
+        switch (which) {
+        case MM_STATE_V: src = net->V; break;
+        case MM_STATE_M: src = net->m; break;
+        case MM_STATE_H: src = net->h; break;
+        case MM_STATE_N: src = net->n; break;
+        default:
+            MM_CKI(net, mmk_launch_fill_f64(dense, 0.0, net->C, net->stream));
+            MM_CKI(net, mmk_launch_scatter_f64(net->gsyn, net->site_internal, dense, net->nsite, net->stream));
+            src = dense;
+        }
+    } else {
+        switch (which) {
+        case MM_STATE_V:
+            MM_CKI(net, mmk_launch_vq_to_f64(net->Vq, dense, net->C, net->stream));
+            // somata carry their FP64 accumulator
+            MM_CKI(net, mmk_launch_scatter_f64(net->Vsoma, net->soma_internal, dense, net->N, net->stream));
+            break;
+        case MM_STATE_M: MM_CKI(net, mmk_launch_gq_to_f64(net->mq, dense, net->C, net->stream)); break;
+        case MM_STATE_H: MM_CKI(net, mmk_launch_gq_to_f64(net->hq, dense, net->C, net->stream)); break;
+        case MM_STATE_N: MM_CKI(net, mmk_launch_gq_to_f64(net->nq, dense, net->C, net->stream)); break;
+        default:
+            MM_CKI(net, mmk_launch_fill_f64(dense, 0.0, net->C, net->stream));
+            MM_CKI(net, mmk_launch_scatter_f32_to_f64(net->gsyn32, net->site_internal, dense, net->nsite, net->stream));
+        }
         src = dense;
-        break;
-    }
-    default:
-        return fail(net, MM_EINVAL, "unknown state quantity");
     }
     MM_CKI(net, mmk_launch_gather_f64(src, net->user2int, net->scratch, net->C, net->stream));
     MM_CK(net, cudaMemcpyAsync(out, net->scratch, (size_t)net->C * sizeof(double), cudaMemcpyDeviceToHost, net->stream));
@@ -549,7 +668,10 @@ mm_status mm_read_soma_voltages(mm_net *net, double *out, int64_t cap)
     mm_status st = guard(net);
     if (st != MM_OK) return st;
     if (!out || cap < net->N) return fail(net, MM_EINVAL, "output buffer too small");
-    MM_CKI(net, mmk_launch_gather_f64(net->V, net->soma_of_user, net->scratch, net->N, net->stream));
+    if (net->precision == MM_FP64)
+        MM_CKI(net, mmk_launch_gather_f64(net->V, net->soma_of_user, net->scratch, net->N, net->stream));
+    else
+        MM_CKI(net, mmk_launch_gather_f64(net->Vsoma, net->internal_of64, net->scratch, net->N, net->stream));
     MM_CK(net, cudaMemcpyAsync(out, net->scratch, (size_t)net->N * sizeof(double), cudaMemcpyDeviceToHost, net->stream));
     return check_device(net);
 }
@@ -614,19 +736,48 @@ mm_status mm_get_step(const mm_net *net, int64_t *step)
     return MM_OK;
 }
 
-// Checkpoint blob: header, then V, m, h, n [C], gsyn [nsite], stim [N],
-// ring_cnt [R], ring_nrn [R*N], the DevCtl and the undrained spikes.
+// Checkpoint blob: a header, then every dynamic device array of the
+// network's precision, the stimulus, the spike ring, the control block and
+// the undrained spikes, in a fixed order.
 namespace {
 struct CkptHeader {
     char magic[8];
     int64_t C, nsite, N, R, spk_cap, steps_done;
     int32_t precision, pad;
 };
-size_t ckpt_size(const mm_net *net)
+
+std::vector<std::pair<void *, size_t>> ckpt_regions(mm_net *net)
 {
-    return sizeof(CkptHeader) + (size_t)(4 * net->C + net->nsite + net->N) * sizeof(double) +
-           (size_t)(net->R + (int64_t)net->R * net->N) * sizeof(int32_t) + sizeof(mmk::DevCtl) +
-           (size_t)net->spk_cap * (sizeof(int32_t) + sizeof(double));
+    std::vector<std::pair<void *, size_t>> r;
+    const size_t C = (size_t)net->C, N = (size_t)net->N, ns = (size_t)net->nsite;
+    if (net->precision == MM_FP64) {
+        r.push_back({net->V, C * sizeof(double)});
+        r.push_back({net->m, C * sizeof(double)});
+        r.push_back({net->h, C * sizeof(double)});
+        r.push_back({net->n, C * sizeof(double)});
+        r.push_back({net->gsyn, ns * sizeof(double)});
+    } else {
+        r.push_back({net->Vq, C * sizeof(int32_t)});
+        r.push_back({net->mq, C * sizeof(uint32_t)});
+        r.push_back({net->hq, C * sizeof(uint32_t)});
+        r.push_back({net->nq, C * sizeof(uint32_t)});
+        r.push_back({net->Vsoma, N * sizeof(double)});
+        r.push_back({net->gsyn32, ns * sizeof(float)});
+    }
+    r.push_back({net->stim, N * sizeof(double)});
+    r.push_back({net->ring_cnt, (size_t)net->R * sizeof(int32_t)});
+    r.push_back({net->ring_nrn, (size_t)net->R * N * sizeof(int32_t)});
+    r.push_back({net->ctl, sizeof(mmk::DevCtl)});
+    r.push_back({net->spk_nrn, (size_t)net->spk_cap * sizeof(int32_t)});
+    r.push_back({net->spk_t, (size_t)net->spk_cap * sizeof(double)});
+    return r;
+}
+
+size_t ckpt_size(mm_net *net)
+{
+    size_t s = sizeof(CkptHeader);
+    for (auto &r : ckpt_regions(net)) s += r.second;
+    return s;
 }
 }  // namespace
 
@@ -642,7 +793,7 @@ mm_status mm_save_state(mm_net *net, void *buf, size_t cap, size_t *len)
     if ((st = check_device(net)) != MM_OK) return st;
     char *p = (char *)buf;
     CkptHeader h{};
-    std::memcpy(h.magic, "MMCKPT01", 8);
+    std::memcpy(h.magic, "MMCKPT02", 8);
     h.C = net->C;
     h.nsite = net->nsite;
     h.N = net->N;
@@ -652,23 +803,10 @@ mm_status mm_save_state(mm_net *net, void *buf, size_t cap, size_t *len)
     h.precision = net->precision;
     std::memcpy(p, &h, sizeof(h));
     p += sizeof(h);
-    auto d2h = [&](const void *src, size_t bytes) -> cudaError_t {
-        cudaError_t e = cudaMemcpy(p, src, bytes, cudaMemcpyDeviceToHost);
-        p += bytes;
-        return e;
-    };
-    const size_t C8 = (size_t)net->C * sizeof(double);
-    MM_CK(net, d2h(net->V, C8));
-    MM_CK(net, d2h(net->m, C8));
-    MM_CK(net, d2h(net->h, C8));
-    MM_CK(net, d2h(net->n, C8));
-    MM_CK(net, d2h(net->gsyn, (size_t)net->nsite * sizeof(double)));
-    MM_CK(net, d2h(net->stim, (size_t)net->N * sizeof(double)));
-    MM_CK(net, d2h(net->ring_cnt, (size_t)net->R * sizeof(int32_t)));
-    MM_CK(net, d2h(net->ring_nrn, (size_t)net->R * net->N * sizeof(int32_t)));
-    MM_CK(net, d2h(net->ctl, sizeof(mmk::DevCtl)));
-    MM_CK(net, d2h(net->spk_nrn, (size_t)net->spk_cap * sizeof(int32_t)));
-    MM_CK(net, d2h(net->spk_t, (size_t)net->spk_cap * sizeof(double)));
+    for (auto &r : ckpt_regions(net)) {
+        MM_CK(net, cudaMemcpy(p, r.first, r.second, cudaMemcpyDeviceToHost));
+        p += r.second;
+    }
     return MM_OK;
 }
 
@@ -680,28 +818,15 @@ mm_status mm_load_state(mm_net *net, const void *buf, size_t len)
     const char *p = (const char *)buf;
     CkptHeader h;
     std::memcpy(&h, p, sizeof(h));
-    if (std::memcmp(h.magic, "MMCKPT01", 8) != 0 || h.C != net->C || h.nsite != net->nsite || h.N != net->N ||
+    if (std::memcmp(h.magic, "MMCKPT02", 8) != 0 || h.C != net->C || h.nsite != net->nsite || h.N != net->N ||
         h.R != net->R || h.spk_cap != net->spk_cap || h.precision != net->precision)
         return fail(net, MM_EINVAL, "checkpoint was saved from a different network");
     p += sizeof(h);
     MM_CK(net, cudaStreamSynchronize(net->stream));
-    auto h2d = [&](void *dst, size_t bytes) -> cudaError_t {
-        cudaError_t e = cudaMemcpy(dst, p, bytes, cudaMemcpyHostToDevice);
-        p += bytes;
-        return e;
-    };
-    const size_t C8 = (size_t)net->C * sizeof(double);
-    MM_CK(net, h2d(net->V, C8));
-    MM_CK(net, h2d(net->m, C8));
-    MM_CK(net, h2d(net->h, C8));
-    MM_CK(net, h2d(net->n, C8));
-    MM_CK(net, h2d(net->gsyn, (size_t)net->nsite * sizeof(double)));
-    MM_CK(net, h2d(net->stim, (size_t)net->N * sizeof(double)));
-    MM_CK(net, h2d(net->ring_cnt, (size_t)net->R * sizeof(int32_t)));
-    MM_CK(net, h2d(net->ring_nrn, (size_t)net->R * net->N * sizeof(int32_t)));
-    MM_CK(net, h2d(net->ctl, sizeof(mmk::DevCtl)));
-    MM_CK(net, h2d(net->spk_nrn, (size_t)net->spk_cap * sizeof(int32_t)));
-    MM_CK(net, h2d(net->spk_t, (size_t)net->spk_cap * sizeof(double)));
+    for (auto &r : ckpt_regions(net)) {
+        MM_CK(net, cudaMemcpy(r.first, p, r.second, cudaMemcpyHostToDevice));
+        p += r.second;
+    }
     net->steps_done = h.steps_done;
     return MM_OK;
 }

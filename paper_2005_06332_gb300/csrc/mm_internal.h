@@ -84,6 +84,55 @@ struct StepArgs {
     double e_syn, threshold, dt, decay;
 };
 
+// Fixed-point state of the FP32c path: V = Vq * 2^-23 mV (int32, +-256 mV),
+// gates x = q * 2^-32 (uint32).  FP32 increments are rounded once and added
+// exactly, so the state itself never accumulates rounding.
+constexpr float kVScale = 8388608.0f;          // 2^23 per mV
+constexpr float kVInv = 1.0f / 8388608.0f;
+constexpr double kVScaleD = 8388608.0;
+constexpr float kGScale = 4294967296.0f;       // 2^32
+constexpr float kGInv = 1.0f / 4294967296.0f;
+constexpr double kGScaleD = 4294967296.0;
+
+// A reversal (or any fixed) potential split into its nearest fixed-point
+// value and an FP32 residual: E = q * 2^-23 + res.
+struct FxPot {
+    int32_t q;
+    float res;
+};
+
+// Arguments of the FP32c step kernel.
+struct StepArgs32 {
+    int32_t *Vq;                      // [C]
+    uint32_t *mq, *hq, *nq;           // [C]
+    double *Vsoma;                    // [N] FP64 soma voltage accumulator
+    const float *area;                // cm^2 [C]
+    const float *gax;                 // uS [C]
+    const double *stim;               // nA [N]
+    const int32_t *user_id;
+    const GroupRec *groups;
+    int32_t n_groups;
+    int32_t step_offset;
+    const SegRec *segs;
+    const int32_t *seg_child;
+    const int32_t *wave_off;
+    const int32_t *site_comp;
+    float *gsyn;                      // per site, uS
+    int32_t *ring_nrn;
+    int32_t *ring_cnt;
+    int32_t R, N;
+    int32_t *spk_nrn;
+    double *spk_t;
+    long long spk_cap;
+    DevCtl *ctl;
+    int32_t smem_comps, smem_segs;
+    float gNa, gK, gL;
+    FxPot ENa, EK, EL, Esyn;
+    float cm_dt;                      // Cm * 1e3 / dt
+    float dt, decay;
+    double threshold, dt64;
+};
+
 struct DeliverArgs {
     const int32_t *ring_nrn;
     int32_t *ring_cnt;
@@ -97,6 +146,8 @@ struct DeliverArgs {
     int32_t step_offset;
     double *gsyn;
     DevCtl *ctl;
+    float *gsyn32;                    // FP32c: per-site conductance (gsyn unused)
+    const float *out_w32;             // FP32c: weights
 };
 
 struct InitArgs {
@@ -106,6 +157,10 @@ struct InitArgs {
     double *area, *gax;
     double *V, *m, *h, *n;
     double Ra, v_init;
+    // FP32c outputs (used when Vq != nullptr; the FP64 pointers are then unused)
+    int32_t *Vq;
+    uint32_t *mq, *hq, *nq;
+    float *area32, *gax32;
 };
 
 }  // namespace mmk
@@ -116,9 +171,15 @@ int mmk_launch_init(const mmk::InitArgs &a, void *stream);
 int mmk_launch_deliver(const mmk::DeliverArgs &a, int blocks, void *stream);
 int mmk_launch_step_fp64(const mmk::StepArgs &a, int blocks, int threads, void *stream);
 int mmk_step_fp64_blocks_per_sm(int threads, int smem_bytes, int *blocks);
+int mmk_launch_step_fp32c(const mmk::StepArgs32 &a, int blocks, int threads, void *stream);
+int mmk_step_fp32c_blocks_per_sm(int threads, int smem_bytes, int *blocks);
+int mmk_launch_init_fp32c(const mmk::InitArgs &a, void *stream);
+int mmk_launch_deliver_fp32c(const mmk::DeliverArgs &a, int blocks, void *stream);
+int mmk_launch_vq_to_f64(const int32_t *vq, double *dst, int64_t n, void *stream);
+int mmk_launch_gq_to_f64(const uint32_t *q, double *dst, int64_t n, void *stream);
+int mmk_launch_scatter_f32_to_f64(const float *src, const int64_t *idx, double *dst, int64_t n, void *stream);
 int mmk_launch_advance(mmk::DevCtl *ctl, int steps, void *stream);
 int mmk_launch_gather_f64(const double *src, const int64_t *idx, double *dst, int64_t n, void *stream);
-int mmk_launch_scatter_site_gsyn(const double *gsyn, const int64_t *site_internal_comp, double *dst,
-                                 int64_t nsite, void *stream);
+int mmk_launch_scatter_f64(const double *src, const int64_t *idx, double *dst, int64_t n, void *stream);
 int mmk_launch_fill_f64(double *dst, double v, int64_t n, void *stream);
 }

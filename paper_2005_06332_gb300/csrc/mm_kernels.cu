@@ -396,11 +396,10 @@ int mmk_launch_gather_f64(const double *src, const int64_t *idx, double *dst, in
     return (int)cudaGetLastError();
 }
 
-int mmk_launch_scatter_site_gsyn(const double *gsyn, const int64_t *site_internal_comp, double *dst,
-                                 int64_t nsite, void *stream)
+int mmk_launch_scatter_f64(const double *src, const int64_t *idx, double *dst, int64_t n, void *stream)
 {
-    if (nsite <= 0) return 0;
-    scatter_f64_kernel<<<grid_for(nsite, 256), 256, 0, (cudaStream_t)stream>>>(gsyn, site_internal_comp, dst, nsite);
+    if (n <= 0) return 0;
+    scatter_f64_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(src, idx, dst, n);
     return (int)cudaGetLastError();
 }
 
