@@ -45,6 +45,10 @@ BYTES_PER_UPDATE = {"fp64": (80.0, 20.0),
                     # FP32c: int32 V and three uint32 gates read + written (32 B),
                     # FP32 area and g_axial read (8 B); per site FP32 g_syn r/w + index
                     "fp32c": (40.0, 12.0)}
+# FP32c splits the step over two kernels; their own algorithmic bytes:
+#   step (currents, tree solve, V): V r/w 8 + gates read 12 + area, g_axial 8 = 28 B (+12 B per site)
+#   gates (rates and gate update):  V read 4 + gates r/w 24 = 28 B
+KERNEL_BYTES_FP32C = {"step": (28.0, 12.0), "gates": (28.0, 0.0)}
 
 
 def _peaks():
@@ -172,6 +176,8 @@ def main():
     ap.add_argument("--graph-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--block-threads", type=int, default=0)
+    ap.add_argument("--group-comps", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -191,8 +197,10 @@ def main():
     torch.cuda.set_device(local)
     mm.load()
     stream = torch.cuda.Stream(device=local)
-    g = mm.Network(net, precision=precision, graph_steps=args.graph_steps, device=local, stream=stream.cuda_stream)
+    g = mm.Network(net, precision=precision, graph_steps=args.graph_steps, device=local, stream=stream.cuda_stream,
+                   block_threads=args.block_threads, group_comps=args.group_comps)
 
+    launch = g.launch_info()
     # warm-up (also captures the CUDA graph)
     g.step(args.warmup)
     g.synchronize()
@@ -218,7 +226,8 @@ def main():
         dist.barrier()
     G = args.graph_steps
     K = args.steps
-    launches = (K // G) * (2 * G + 1) + ((K % G > 0) * (2 * (K % G) + 1)) if G > 0 else 2 * K + 1
+    kps = 2 if precision == "fp64" else 3  # kernels per step (delivery, step[, gates])
+    launches = (K // G) * (kps * G + 1) + ((K % G > 0) * (kps * (K % G) + 1)) if G > 0 else kps * K + 1
     updates = net.n_comp * K * ws
     value = updates / (ms * 1e-3)
 
@@ -253,22 +262,32 @@ def main():
     peak, peak_kind = _peaks()
     b0, bsite = BYTES_PER_UPDATE.get(precision, (80.0, 20.0))
     nsite = int(np.unique(net.syn_comp.astype(np.int64) + net.comp_offset[net.syn_dst]).size)
-    bytes_per_launch = b0 * net.n_comp + bsite * nsite
-    achieved = bytes_per_launch / (step_ms * 1e-3) / 1e9
+    kernels = {"step": (step_ms, (b0 * net.n_comp + bsite * nsite) if precision == "fp64" else
+                        KERNEL_BYTES_FP32C["step"][0] * net.n_comp + KERNEL_BYTES_FP32C["step"][1] * nsite),
+               "deliver": (deliver_ms, None)}
+    if precision != "fp64":
+        gates_ms = kt["gates_kernel_ms"] / max(1, kt["gates_kernel_launches"])
+        kernels["gates"] = (gates_ms, KERNEL_BYTES_FP32C["gates"][0] * net.n_comp)
+    dom = max((k for k in kernels if kernels[k][1] is not None), key=lambda k: kernels[k][0])
+    dom_ms, dom_bytes = kernels[dom]
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_kind": peak_kind, "kernel": f"step_{precision}",
-                "kernel_ms": step_ms, "deliver_kernel_ms": deliver_ms,
-                "bytes_per_launch": bytes_per_launch,
-                "bytes_per_update": f"{b0:g} B per compartment + {bsite:g} B per synaptic site"}
+                "traffic": None, "peak_kind": peak_kind, "kernel": f"{dom}_{precision}",
+                "kernel_ms": dom_ms, "bytes_per_launch": dom_bytes,
+                "kernels_ms": {k: v[0] for k, v in kernels.items()},
+                "step_bytes_per_update": f"{b0:g} B per compartment + {bsite:g} B per synaptic site",
+                "step_achieved_gbs": (b0 * net.n_comp + bsite * nsite) / (ms / K * 1e-3) / 1e9}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if precision == "fp64" else "f32", "data": "synthetic",
            "config": {"workload": net.name, "precision": precision, "n_neurons": net.n_neurons,
+                      "block_threads": args.block_threads, "group_comps": args.group_comps,
                       "n_comp": net.n_comp, "n_syn": net.n_syn, "dt_ms": net.dt, "graph_steps": G,
                       "l2": f"inputs larger than L2 (state + constants {(48 * net.n_comp) / 1e6:.0f} MB)",
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
+           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+           "launch": launch}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(net)
     g.close()

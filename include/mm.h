@@ -192,10 +192,14 @@ mm_status mm_load_state(mm_net *net, const void *buf, size_t len);
 /* Per-kernel device time, measured with CUDA events recorded on the
  * network's stream around each launch while timing is enabled. */
 typedef struct {
-    double step_kernel_ms;          /* fused per-step kernel, summed */
+    double step_kernel_ms;          /* per-step kernel (FP64: everything; FP32c: currents, tree solve, V), summed */
     int64_t step_kernel_launches;
     double deliver_kernel_ms;       /* spike-delivery kernel, summed */
     int64_t deliver_kernel_launches;
+    double gates_kernel_ms;         /* FP32c gate-update kernel, summed (0 for FP64) */
+    int64_t gates_kernel_launches;
+    double giant_kernel_ms;         /* FP32c giant-neuron solve kernel, summed */
+    int64_t giant_kernel_launches;
 } mm_kernel_times;
 
 /* While enabled (enable != 0), mm_step launches every kernel directly (no
@@ -205,6 +209,21 @@ mm_status mm_set_kernel_timing(mm_net *net, int32_t enable);
 /* Synchronise and report the time accumulated since the last reset;
  * reset != 0 clears the totals afterwards. */
 mm_status mm_read_kernel_timing(mm_net *net, mm_kernel_times *out, int32_t reset);
+
+/* Launch configuration chosen for the per-step kernel. */
+typedef struct {
+    int32_t work_items;        /* neuron groups handed out by the device queue */
+    int32_t blocks;            /* persistent blocks launched */
+    int32_t threads;           /* threads per block */
+    int32_t blocks_per_sm;     /* resident blocks per SM at this shared-memory size */
+    int32_t smem_bytes;        /* dynamic shared memory per block */
+    int32_t max_item_comps;    /* compartments of the largest work item */
+    int32_t max_item_segments; /* unbranched segments of the largest work item */
+    int32_t max_item_waves;    /* height waves of the deepest work item */
+    int32_t giant_items;       /* FP32c work items solved from global memory (too big for shared memory) */
+} mm_launch_info;
+
+mm_status mm_get_launch_info(const mm_net *net, mm_launch_info *out);
 
 /* Message of the last error on this network ("" if none); never NULL. */
 const char *mm_last_error(const mm_net *net);

@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mm.h"
+#include "mm.h"
 #include "mm_internal.h"
 #include "mm_layout.h"
 
@@ -18,7 +18,8 @@ namespace {
 constexpr int kStepThreads = 256;
 constexpr int kDefaultGroupComps = 4096;
 constexpr int kMaxGroupComps = 8192;
-constexpr int kMaxGroupComps32 = 24576;
+constexpr int kMaxGroupComps32 = 1 << 30;
+constexpr int kGiantSmemLimit = 110 * 1024;  // FP32c items above this use the giant kernel
 constexpr size_t kMaxSmem = 227 * 1024;
 
 }  // namespace
@@ -43,7 +44,8 @@ struct mm_net {
 
     mmk::StepArgs sa{};
     mmk::DeliverArgs da{};
-    int step_blocks = 1, step_threads = kStepThreads, deliver_blocks = 1;
+    int step_blocks = 1, step_threads = kStepThreads, deliver_blocks = 1, gates_blocks = 1, giant_blocks = 1;
+    int32_t n_giant = 0;
     int graph_steps = 40;
     cudaGraphExec_t gexec = nullptr;
 
@@ -57,6 +59,7 @@ struct mm_net {
     uint32_t *mq = nullptr, *hq = nullptr, *nq = nullptr;
     double *Vsoma = nullptr;
     float *area32 = nullptr, *gax32 = nullptr, *gsyn32 = nullptr;
+    float2 *dr = nullptr;
     int64_t *soma_internal = nullptr, *internal_of64 = nullptr;
     // both
     double *stim = nullptr;
@@ -71,6 +74,8 @@ struct mm_net {
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> event_pool;
     mm_kernel_times times{};
+
+    mm_launch_info info{};
 
     std::vector<int32_t> order;          // internal -> user
     std::vector<int32_t> internal_of;    // user -> internal
@@ -176,9 +181,15 @@ mm_status collect_timing(mm_net *net)
         if (p.kind == 0) {
             net->times.deliver_kernel_ms += ms;
             net->times.deliver_kernel_launches++;
-        } else {
+        } else if (p.kind == 3) {
+            net->times.giant_kernel_ms += ms;
+            net->times.giant_kernel_launches++;
+        } else if (p.kind == 1) {
             net->times.step_kernel_ms += ms;
             net->times.step_kernel_launches++;
+        } else {
+            net->times.gates_kernel_ms += ms;
+            net->times.gates_kernel_launches++;
         }
         net->event_pool.push_back(p.a);
         net->event_pool.push_back(p.b);
@@ -190,8 +201,9 @@ mm_status collect_timing(mm_net *net)
 mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
 {
     const bool timed = net->timing && s == net->stream;
+    const int kinds = net->precision == MM_FP64 ? 2 : (net->n_giant > 0 ? 4 : 3);
     for (int j = 0; j < count; ++j) {
-        for (int kind = 0; kind < 2; ++kind) {
+        for (int kind = 0; kind < kinds; ++kind) {
             mm_net::Pending p{nullptr, nullptr, kind};
             if (timed) {
                 MM_CK(net, take_event(net, &p.a));
@@ -207,10 +219,17 @@ mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
                 mmk::StepArgs sa = net->sa;
                 sa.step_offset = j;
                 MM_CKI(net, mmk_launch_step_fp64(sa, net->step_blocks, net->step_threads, s));
-            } else {
+            } else if (kind == 1) {
                 mmk::StepArgs32 sa = net->sa32;
                 sa.step_offset = j;
-                MM_CKI(net, mmk_launch_step_fp32c(sa, net->step_blocks, net->step_threads, s));
+                if (net->sa32.n_small > 0)
+                    MM_CKI(net, mmk_launch_step_fp32c(sa, net->step_blocks, net->step_threads, s));
+            } else if (kind == 3) {
+                mmk::StepArgs32 sa = net->sa32;
+                sa.step_offset = j;
+                MM_CKI(net, mmk_launch_giant_fp32c(sa, net->giant_blocks, s));
+            } else {
+                MM_CKI(net, mmk_launch_gates_fp32c(net->sa32, net->gates_blocks, s));
             }
             if (timed) {
                 MM_CK(net, cudaEventRecord(p.b, s));
@@ -315,6 +334,9 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     li.dt = opt->dt_ms;
     li.group_comps = opt->group_comps > 0 ? opt->group_comps : kDefaultGroupComps;
     li.max_group_comps = opt->precision == MM_FP64 ? kMaxGroupComps : kMaxGroupComps32;
+    li.smem_per_comp = opt->precision == MM_FP64 ? 16 : 12;
+    li.smem_per_seg = opt->precision == MM_FP64 ? 0 : 8;
+    li.giant_smem_limit = opt->precision == MM_FP64 ? 0 : kGiantSmemLimit;
     mmh::Layout L;
     bool invalid = false;
     std::string m;
@@ -363,6 +385,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         ZR(net->gax32, C);
         ZR(net->Vsoma, N);
         ZR(net->gsyn32, (size_t)std::max<int64_t>(net->nsite, 1));
+        ZR(net->dr, (size_t)std::max<int64_t>(L.giant_comps, 1));
         std::vector<int64_t> soma_int(N), int_of(N);
         for (size_t k = 0; k < N; ++k) soma_int[k] = L.noff[k];
         for (size_t u = 0; u < N; ++u) int_of[u] = L.internal_of[u];
@@ -381,12 +404,10 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     ZR(net->spk_t, (size_t)net->spk_cap);
     ZR(net->ctl, 1);
     mmk::GroupRec *dgroups = nullptr;
-    mmk::SegRec *dsegs = nullptr;
-    int32_t *dchild = nullptr, *dwave = nullptr, *dsite = nullptr;
+    unsigned char *dmeta = nullptr;
+    int32_t *dsite = nullptr;
     UP(dgroups, L.groups.data(), L.groups.size());
-    UP(dsegs, L.segs.data(), L.segs.size());
-    UP(dchild, L.seg_child.data(), std::max<size_t>(L.seg_child.size(), 1));
-    UP(dwave, L.wave_off.data(), L.wave_off.size());
+    UP(dmeta, L.meta.data(), L.meta.size());
     UP(dsite, L.site_comp.data(), std::max<size_t>(L.site_comp.size(), 1));
     int64_t *dout_off = nullptr;
     int32_t *dout_site = nullptr, *dout_ds = nullptr, *ddclass = nullptr;
@@ -446,9 +467,8 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.user_id = net->user_id;
         a.groups = dgroups;
         a.n_groups = (int32_t)L.groups.size();
-        a.segs = dsegs;
-        a.seg_child = dchild;
-        a.wave_off = dwave;
+        a.meta = dmeta;
+        a.smem_meta = L.max_meta;
         a.site_comp = dsite;
         a.gsyn = net->gsyn;
         a.ring_nrn = net->ring_nrn;
@@ -481,7 +501,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
             return p;
         };
         for (double E : {chan->ENa, chan->EK, chan->EL, chan->v_init, syn ? syn->e_rev_mV : 0.0})
-            if (!(std::fabs(E) < 250.0)) return fail(net, MM_EINVAL, "potentials must lie within +-250 mV for MM_FP32C");
+            if (!(std::fabs(E) < 120.0)) return fail(net, MM_EINVAL, "potentials must lie within +-120 mV for MM_FP32C");
         mmk::StepArgs32 &a = net->sa32;
         a.Vq = net->Vq;
         a.mq = net->mq;
@@ -490,13 +510,14 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.Vsoma = net->Vsoma;
         a.area = net->area32;
         a.gax = net->gax32;
+        a.dr = net->dr;
         a.stim = net->stim;
         a.user_id = net->user_id;
         a.groups = dgroups;
         a.n_groups = (int32_t)L.groups.size();
-        a.segs = dsegs;
-        a.seg_child = dchild;
-        a.wave_off = dwave;
+        a.n_small = L.n_small;
+        a.meta = dmeta;
+        a.smem_meta = L.max_meta;
         a.site_comp = dsite;
         a.gsyn = net->gsyn32;
         a.ring_nrn = net->ring_nrn;
@@ -518,9 +539,11 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.Esyn = pot(syn ? syn->e_rev_mV : 0.0);
         a.cm_dt = (float)(chan->Cm * 1e3 / opt->dt_ms);
         a.dt = (float)opt->dt_ms;
+        a.dt_lo = (float)(opt->dt_ms - (double)a.dt);
         a.decay = (float)decay;
         a.threshold = chan->threshold_mV;
         a.dt64 = opt->dt_ms;
+        a.C = L.C;
     }
 
     mmk::DeliverArgs &d = net->da;
@@ -539,10 +562,12 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     d.gsyn32 = net->gsyn32;
     d.out_w32 = dout_w32;
 
-    const size_t smem = (size_t)(2 * smem_comps + 2 * smem_segs) * (f64 ? sizeof(double) : sizeof(float));
+    const size_t smem = f64 ? mmk_step_fp64_smem(smem_comps, smem_segs, L.max_meta)
+                            : mmk_step_fp32c_smem(smem_comps, smem_segs, L.max_meta);
     if (smem > kMaxSmem) return fail(net, MM_ENOTSUP, "a work item needs more shared memory than a block has");
-    int threads = opt->block_threads > 0 ? opt->block_threads : kStepThreads;
-    if (threads != 128 && threads != 256 && threads != 512) return fail(net, MM_EINVAL, "block_threads must be 128, 256 or 512");
+    int threads = opt->block_threads > 0 ? opt->block_threads : (f64 ? kStepThreads : 512);
+    if (threads != 128 && threads != 256 && threads != 512 && (f64 || threads != 1024))
+        return fail(net, MM_EINVAL, "block_threads must be 128, 256 or 512 (or 1024 for MM_FP32C)");
     net->step_threads = threads;
     int per_sm = 0;
     if (f64) MM_CKI(net, mmk_step_fp64_blocks_per_sm(threads, (int)smem, &per_sm));
@@ -550,8 +575,20 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     if (per_sm < 1) return fail(net, MM_ENOTSUP, "the step kernel does not fit on an SM");
     int sms = 0;
     MM_CK(net, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device));
-    net->step_blocks = std::max(1, std::min((int)L.groups.size(), per_sm * sms));
+    net->step_blocks = std::max(1, std::min(std::max(L.n_small, 1), per_sm * sms));
+    net->n_giant = (int32_t)L.groups.size() - L.n_small;
+    net->giant_blocks = std::max(1, std::min(net->n_giant, 4 * sms));
+    net->info.work_items = (int32_t)L.groups.size();
+    net->info.blocks = net->step_blocks;
+    net->info.threads = threads;
+    net->info.blocks_per_sm = per_sm;
+    net->info.smem_bytes = (int32_t)smem;
+    net->info.max_item_comps = L.max_comps;
+    net->info.max_item_segments = L.max_segs;
+    net->info.max_item_waves = L.max_waves;
+    net->info.giant_items = net->n_giant;
     net->deliver_blocks = std::max(1, 2 * sms);
+    net->gates_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((L.C + 255) / 256, (int64_t)sms * 8));
     MM_CK(net, cudaStreamSynchronize(net->stream));
     return MM_OK;
 }
@@ -847,6 +884,13 @@ mm_status mm_read_kernel_timing(mm_net *net, mm_kernel_times *out, int32_t reset
     if ((st = collect_timing(net)) != MM_OK) return st;
     *out = net->times;
     if (reset) net->times = mm_kernel_times{};
+    return MM_OK;
+}
+
+mm_status mm_get_launch_info(const mm_net *net, mm_launch_info *out)
+{
+    if (!net || !out) return MM_EINVAL;
+    *out = net->info;
     return MM_OK;
 }
 

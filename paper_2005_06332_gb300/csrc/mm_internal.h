@@ -17,6 +17,7 @@
 //     Algorithm 1), and substituted in the reverse order (root-to-leaves).
 #pragma once
 #include <stdint.h>
+#include <vector_types.h>
 
 namespace mmk {
 
@@ -31,13 +32,30 @@ struct SegRec {
     int32_t neuron;   // soma segment: group-local neuron index; else -1
 };
 
-// One work item: a run of whole neurons.
+// Packed form of a segment inside a work item's tree blob (12 bytes;
+// group-local indices fit 15 bits because a work item holds at most 32767
+// compartments and segments).
+struct SegP {
+    int16_t top;      // group-local index of the first compartment
+    int16_t len;      // >= 1
+    int16_t parent;   // group-local index of top's parent; -1 for a soma segment
+    int16_t nchild;   // number of child segments
+    int16_t child0;   // first entry of this segment's children in the blob's child list
+    int16_t neuron;   // soma segment: group-local neuron index; else -1
+};
+
+// One work item: a run of whole neurons.  Its tree is one contiguous,
+// 16-byte aligned blob in global memory, staged into shared memory with a
+// single bulk copy: SegP[nseg] | int16 child[nchild] | int16 wave_off[nwave+1]
+// (wave w holds segments wave_off[w] .. wave_off[w+1]-1), padded to 16 bytes.
 struct GroupRec {
     int64_t comp0;    // internal index of the first compartment
+    int64_t scratch0; // giant items: first entry in the global Hines scratch
+    int64_t meta_off; // byte offset of the tree blob
+    int32_t meta_bytes;
     int32_t ncomp;
-    int32_t seg0;     // first segment (index into segs[])
     int32_t nseg;
-    int32_t wave0;    // first entry in wave_off[] (nwave + 1 entries, group-local seg indices)
+    int32_t nchild;
     int32_t nwave;
     int32_t site0;    // first synaptic site (index into site_comp[] / gsyn[])
     int32_t nsite;
@@ -52,9 +70,11 @@ struct DevCtl {
     unsigned long long spk_count;   // spikes appended to the output buffer
     unsigned int queue_head;        // next work item of the current step
     int err;                        // MMK_ERR_* bits
+    unsigned int giant_head;        // next giant work item of the current step
+    unsigned int pad;
 };
 
-enum { MMK_ERR_OVERFLOW = 1, MMK_ERR_NUMERIC = 2 };
+enum { MMK_ERR_OVERFLOW = 1, MMK_ERR_NUMERIC = 2, MMK_ERR_TIMEOUT = 4 };
 
 // Arguments of the FP64 step kernel.
 struct StepArgs {
@@ -66,9 +86,8 @@ struct StepArgs {
     const GroupRec *groups;
     int32_t n_groups;
     int32_t step_offset;              // step index = ctl->step_base + step_offset
-    const SegRec *segs;
-    const int32_t *seg_child;
-    const int32_t *wave_off;
+    const unsigned char *meta;        // tree blobs of all work items
+    int32_t smem_meta;                // bytes reserved for the largest blob
     const int32_t *site_comp;         // group-local compartment of each synaptic site
     double *gsyn;                     // merged synaptic conductance per site, uS
     int32_t *ring_nrn;                // [R * N] internal ids of neurons that spiked, per step slot
@@ -107,15 +126,16 @@ struct StepArgs32 {
     uint32_t *mq, *hq, *nq;           // [C]
     double *Vsoma;                    // [N] FP64 soma voltage accumulator
     const float *area;                // cm^2 [C]
-    const float *gax;                 // uS [C]
+    const float *gax;                 // uS [C], sign bit set at segment tops and somata
+    float2 *dr;                       // scratch for giant items: Hines diagonal and rhs
     const double *stim;               // nA [N]
     const int32_t *user_id;
     const GroupRec *groups;
     int32_t n_groups;
     int32_t step_offset;
-    const SegRec *segs;
-    const int32_t *seg_child;
-    const int32_t *wave_off;
+    const unsigned char *meta;
+    int32_t smem_meta;
+    int32_t n_small;                  // items [0, n_small) fit shared memory; the rest are giants
     const int32_t *site_comp;
     float *gsyn;                      // per site, uS
     int32_t *ring_nrn;
@@ -129,7 +149,8 @@ struct StepArgs32 {
     float gNa, gK, gL;
     FxPot ENa, EK, EL, Esyn;
     float cm_dt;                      // Cm * 1e3 / dt
-    float dt, decay;
+    float dt, dt_lo, decay;           // dt as a float pair (dt + dt_lo)
+    int64_t C;                        // compartments (gate kernel)
     double threshold, dt64;
 };
 
@@ -152,7 +173,7 @@ struct DeliverArgs {
 
 struct InitArgs {
     const double *L, *diam;           // internal order
-    const int32_t *parent_dist;       // i - parent(i) (>= 1), 0 at a soma
+    const int32_t *parent_dist;       // i - parent(i), negated at segment tops, 0 at a soma
     int64_t C;
     double *area, *gax;
     double *V, *m, *h, *n;
@@ -173,7 +194,11 @@ int mmk_launch_step_fp64(const mmk::StepArgs &a, int blocks, int threads, void *
 int mmk_step_fp64_blocks_per_sm(int threads, int smem_bytes, int *blocks);
 int mmk_launch_step_fp32c(const mmk::StepArgs32 &a, int blocks, int threads, void *stream);
 int mmk_step_fp32c_blocks_per_sm(int threads, int smem_bytes, int *blocks);
+size_t mmk_step_fp32c_smem(int comps, int segs, int meta_bytes);
+size_t mmk_step_fp64_smem(int comps, int segs, int meta_bytes);
 int mmk_launch_init_fp32c(const mmk::InitArgs &a, void *stream);
+int mmk_launch_gates_fp32c(const mmk::StepArgs32 &a, int blocks, void *stream);
+int mmk_launch_giant_fp32c(const mmk::StepArgs32 &a, int blocks, void *stream);
 int mmk_launch_deliver_fp32c(const mmk::DeliverArgs &a, int blocks, void *stream);
 int mmk_launch_vq_to_f64(const int32_t *vq, double *dst, int64_t n, void *stream);
 int mmk_launch_gq_to_f64(const uint32_t *q, double *dst, int64_t n, void *stream);

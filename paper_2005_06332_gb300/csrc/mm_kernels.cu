@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "mm_internal.h"
+#include "mm_tma.h"
 
 using namespace mmk;
 
@@ -68,7 +69,7 @@ __global__ void init_kernel(InitArgs a)
          i += (int64_t)gridDim.x * blockDim.x) {
         double L = a.L[i], d = a.diam[i];
         a.area[i] = kPi * d * L * 1e-8;
-        const int32_t pd = a.parent_dist[i];
+        const int32_t pd = abs(a.parent_dist[i]);
         double g = 0.0;
         if (pd > 0) {
             const int64_t q = i - pd;
@@ -95,6 +96,7 @@ __global__ void __launch_bounds__(256) deliver_kernel(DeliverArgs a)
     const long long n = (long long)a.ctl->step_base + a.step_offset;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctl->queue_head = 0u;
+        a.ctl->giant_head = 0u;
         a.ring_cnt[n % a.R] = 0;
     }
     for (int k = threadIdx.x; k < a.n_dclass; k += blockDim.x) {
@@ -141,19 +143,38 @@ __global__ void __launch_bounds__(256) deliver_kernel(DeliverArgs a)
 template <int NT>
 __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
 {
-    extern __shared__ double smem[];
-    double *sd = smem;                       // diagonal; after elimination: its reciprocal
-    double *sr = smem + a.smem_comps;        // rhs; after substitution: dV
-    double *scd = sr + a.smem_comps;         // per-segment contribution to its parent's diagonal
-    double *scr = scd + a.smem_segs;         // ... and to its parent's rhs
-    __shared__ int s_item;
+    // Shared memory: the work item's tree blob (one bulk copy), then the
+    // diagonal (after elimination: its reciprocal) and rhs (after
+    // substitution: dV) of every compartment.
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *smeta = smem_raw;
+    double *sd = (double *)(smem_raw + a.smem_meta);
+    double *sr = sd + a.smem_comps;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_item, s_abort;
 
     const long long n = (long long)a.ctl->step_base + a.step_offset;
     const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    uint32_t parity = 0;
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_item = (int)atomicAdd(&a.ctl->queue_head, 1u);
+        if (tid == 0) {
+            const int item = (int)atomicAdd(&a.ctl->queue_head, 1u);
+            s_item = item;
+            s_abort = 0;
+            if (item < a.n_groups) {
+                const GroupRec *gp = a.groups + item;
+                const uint32_t bytes = (uint32_t)gp->meta_bytes;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bar, bytes);
+                bulk_copy_g2s(smeta, a.meta + gp->meta_off, bytes, &bar);
+            }
+        }
         __syncthreads();
         const int gi = s_item;
         if (gi >= a.n_groups) break;
@@ -175,7 +196,16 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
             sd[i] = ar * a.cm_dt + gna + gk + gl;
             sr[i] = -(gna * (v - a.ENa) + gk * (v - a.EK) + gl * (v - a.EL));
         }
+        if (!mbar_wait_bounded(&bar, parity)) s_abort = 1;
+        parity ^= 1u;
         __syncthreads();
+        if (s_abort) {
+            if (tid == 0) atomicOr(&a.ctl->err, MMK_ERR_TIMEOUT);
+            break;
+        }
+        const SegP *segs = (const SegP *)smeta;
+        const int16_t *kids = (const int16_t *)(segs + G.nseg);
+        const int16_t *woff = kids + G.nchild;
 
         // S. synaptic sites: conductance into the system, then decay.
         for (int t = tid; t < G.nsite; t += NT) {
@@ -193,18 +223,21 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
         //    reaches i: d_i += g, rhs_i += g (V_p - V_i) and, for the parent,
         //    d_p += g, rhs_p += g (V_i - V_p), next to the elimination update
         //    d_p -= (a_i/d_i) c_i, rhs_p -= (a_i/d_i) rhs_i with a_i = c_i = -g.
-        const SegRec *segs = a.segs + G.seg0;
-        const int *woff = a.wave_off + G.wave0;
         for (int w = 0; w < G.nwave; ++w) {
             const int sb = woff[w], se = woff[w + 1];
             for (int si = sb + tid; si < se; si += NT) {
-                const SegRec S = segs[si];
+                const SegP S = segs[si];
                 const int bot = S.top + S.len - 1;
                 double db = sd[bot], rb = sr[bot];
+                // each child segment hangs off the bottom: from its top's
+                // stored 1/d and rhs, its link terms (+g, +g (V_t - V_b)) and
+                // its elimination (-g^2/d_t, +g rhs_t/d_t)
                 for (int c = 0; c < S.nchild; ++c) {
-                    const int cs = a.seg_child[S.child0 + c];
-                    db += scd[cs];
-                    rb += scr[cs];
+                    const int t = segs[kids[S.child0 + c]].top;
+                    const double g = gax[t];
+                    const double f = g * sd[t];
+                    db += g - f * g;
+                    rb += g * (V[t] - V[bot]) + f * sr[t];
                 }
                 for (int j = bot; j > S.top; --j) {
                     const double g = gax[j];
@@ -221,15 +254,10 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
                 const int t = S.top;
                 if (S.parent >= 0) {
                     const double g = gax[t];
-                    const double vt = V[t], vp = V[S.parent];
                     db += g;
-                    rb += g * (vp - vt);
-                    const double inv = 1.0 / db;
-                    sd[t] = inv;
+                    rb += g * (V[S.parent] - V[t]);
+                    sd[t] = 1.0 / db;
                     sr[t] = rb;
-                    const double f = g * inv;
-                    scd[si] = g - f * g;
-                    scr[si] = g * (vt - vp) + f * rb;
                 } else {
                     rb += a.stim[G.neuron0 + S.neuron];
                     const double inv = 1.0 / db;
@@ -245,7 +273,7 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
         for (int w = G.nwave - 1; w >= 0; --w) {
             const int sb = woff[w], se = woff[w + 1];
             for (int si = sb + tid; si < se; si += NT) {
-                const SegRec S = segs[si];
+                const SegP S = segs[si];
                 const int t = S.top;
                 double x;
                 if (S.parent >= 0) {
@@ -333,10 +361,13 @@ int mmk_launch_deliver(const DeliverArgs &a, int blocks, void *stream)
     return (int)cudaGetLastError();
 }
 
-static size_t step_smem_bytes(const StepArgs &a)
+size_t mmk_step_fp64_smem(int comps, int segs, int meta_bytes)
 {
-    return (size_t)(2 * a.smem_comps + 2 * a.smem_segs) * sizeof(double);
+    (void)segs;
+    return (size_t)meta_bytes + (size_t)(2 * comps) * sizeof(double);
 }
+
+static size_t step_smem_bytes(const StepArgs &a) { return mmk_step_fp64_smem(a.smem_comps, a.smem_segs, a.smem_meta); }
 
 int mmk_launch_step_fp64(const StepArgs &a, int blocks, int threads, void *stream)
 {

@@ -9,13 +9,16 @@
 //     once, so rounding never accumulates in the state itself;
 //   * differences of potentials (V - E, V_parent - V_child, V + c in the rate
 //     arguments) are taken exactly in integers before the single rounding;
-//   * exponential arguments are carried as an unevaluated float pair
-//     (hi + lo) and exp(hi + lo) = exp(hi) (1 + lo);
+//   * the rate functions, steady states and relaxation factors are computed
+//     as float pairs (mm_fp32c_math.h: an FMA-only exponential, three per
+//     compartment, shared by the six rates);
 //   * the soma voltage is also accumulated in FP64 and the spike crossing
 //     time is computed in FP64.
 #include <cuda_runtime.h>
 
+#include "mm_fp32c_math.h"
 #include "mm_internal.h"
+#include "mm_tma.h"
 
 using namespace mmk;
 
@@ -23,96 +26,7 @@ namespace {
 
 constexpr double kPiD = 3.141592653589793;
 
-struct F2 {
-    float hi, lo;
-};
-
-// (a - b) * 2^-23, one rounding.
-__device__ __forceinline__ float vdiff(int32_t a, int32_t b)
-{
-    return (float)((long long)a - (long long)b) * kVInv;
-}
-
-__device__ __forceinline__ float vminus(int32_t vq, FxPot E) { return vdiff(vq, E.q) - E.res; }
-
-// (a - b) * c as a float pair, where c = ch + cl.
-__device__ __forceinline__ F2 scaled_diff(int32_t a, int32_t b, float ch, float cl)
-{
-    const long long d = (long long)a - (long long)b;
-    const float dh = (float)d;
-    const float dl = (float)(d - (long long)dh);
-    const float xh = dh * ch;
-    const float xl = fmaf(dh, ch, -xh) + fmaf(dh, cl, dl * ch);
-    return {xh, xl};
-}
-
-__device__ __forceinline__ float exp_pair(F2 x)
-{
-    const float e = expf(x.hi);
-    return fmaf(e, x.lo, e);
-}
-
-// x / (e^x - 1) for x = hi + lo.
-__device__ __forceinline__ float xexpm1_ratio_pair(F2 x)
-{
-    if (fabsf(x.hi) < 1e-4f) {
-        const float v = x.hi + x.lo;
-        return fmaf(v, fmaf(v, 1.0f / 12.0f, -0.5f), 1.0f);
-    }
-    const float E = expm1f(x.hi);
-    const float den = fmaf(x.lo, E + 1.0f, E);
-    return __fdiv_rn(x.hi + x.lo, den);
-}
-
-// Fixed-point potentials of the rate-function shifts (exact: integer mV).
-constexpr int32_t kQm40 = -40 * 8388608;
-constexpr int32_t kQm65 = -65 * 8388608;
-constexpr int32_t kQm35 = -35 * 8388608;
-constexpr int32_t kQm55 = -55 * 8388608;
-
-// 2^-23 / k split into a float pair.
-#define MMK_SPLIT(name, k)                                               \
-    constexpr double name##_d = 1.0 / ((double)(k) * 8388608.0);         \
-    constexpr float name##_h = (float)name##_d;                          \
-    constexpr float name##_l = (float)(name##_d - (double)name##_h);
-MMK_SPLIT(kC10, 10)
-MMK_SPLIT(kC18, 18)
-MMK_SPLIT(kC20, 20)
-MMK_SPLIT(kC80, 80)
-#undef MMK_SPLIT
-
-struct Rates32 {
-    float am, bm, ah, bh, an, bn;
-};
-
-// HH rates (1/ms) at V = vq * 2^-23 mV; every argument -(V + c)/k is formed
-// as (Q_{-c} - vq) * 2^-23 / k exactly before rounding.
-__device__ __forceinline__ Rates32 hh_rates32(int32_t vq)
-{
-    Rates32 r;
-    r.am = xexpm1_ratio_pair(scaled_diff(kQm40, vq, kC10_h, kC10_l));
-    r.bm = 4.0f * exp_pair(scaled_diff(kQm65, vq, kC18_h, kC18_l));
-    r.ah = 0.07f * exp_pair(scaled_diff(kQm65, vq, kC20_h, kC20_l));
-    r.bh = __frcp_rn(1.0f + exp_pair(scaled_diff(kQm35, vq, kC10_h, kC10_l)));
-    r.an = 0.1f * xexpm1_ratio_pair(scaled_diff(kQm55, vq, kC10_h, kC10_l));
-    r.bn = 0.125f * exp_pair(scaled_diff(kQm65, vq, kC80_h, kC80_l));
-    return r;
-}
-
-// Exponential-Euler relaxation of a fixed-point gate: dx = (xinf - x)(1 - e^{-dt s}).
-__device__ __forceinline__ uint32_t gate_step32(uint32_t q, float a, float b, float dt)
-{
-    const float s = a + b;
-    const float xinf = __fdiv_rn(a, s);
-    const float E = expm1f(-dt * s);
-    const float qh = __uint2float_rn(q);
-    const float ql = (float)((long long)q - (long long)qh);
-    const float d = (xinf - qh * kGInv) - ql * kGInv;
-    const long long nq = (long long)q + __float2ll_rn(-E * d * kGScale);
-    return (uint32_t)(nq < 0 ? 0 : (nq > 4294967295LL ? 4294967295LL : nq));
-}
-
-__device__ __forceinline__ float gate_value(uint32_t q) { return __uint2float_rn(q) * kGInv; }
+__device__ __forceinline__ float vminus(int32_t vq, FxPot E) { return mmf::vdiff(vq, E.q) - E.res; }
 
 // ------------------------------------------------------------------ init
 
@@ -131,12 +45,15 @@ __global__ void init_fp32c_kernel(InitArgs a)
         const double L = a.L[i], d = a.diam[i];
         a.area32[i] = (float)(kPiD * d * L * 1e-8);
         const int32_t pd = a.parent_dist[i];
+        const int32_t pa = abs(pd);
         double g = 0.0;
-        if (pd > 0) {
-            const int64_t q = i - pd;
+        if (pa > 0) {
+            const int64_t q = i - pa;
             g = 1.0 / (half_cyl_resistance_d(a.Ra, L, d) + half_cyl_resistance_d(a.Ra, a.L[q], a.diam[q]));
         }
-        a.gax32[i] = (float)g;
+        // segment tops (and somata) carry the sign bit: phase A assembles
+        // only the links inside segments, the sweep the links of the tops
+        a.gax32[i] = pd > 0 ? (float)g : -(float)g;
         const double v = a.v_init;
         a.Vq[i] = (int32_t)llrint(v * kVScaleD);
         const double am = xexpm1_d(-(v + 40.0) * 0.1), bm = 4.0 * exp(-(v + 65.0) / 18.0);
@@ -163,6 +80,7 @@ __global__ void __launch_bounds__(256) deliver_fp32c_kernel(DeliverArgs a)
     const long long n = (long long)a.ctl->step_base + a.step_offset;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctl->queue_head = 0u;
+        a.ctl->giant_head = 0u;
         a.ring_cnt[n % a.R] = 0;
     }
     for (int k = threadIdx.x; k < a.n_dclass; k += blockDim.x) {
@@ -207,46 +125,113 @@ __global__ void __launch_bounds__(256) deliver_fp32c_kernel(DeliverArgs a)
 
 // ------------------------------------------------------------ FP32c step
 
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Pull the cache lines of [p, p + bytes) into L1 ahead of a serial walk.
+__device__ __forceinline__ void prefetch_l1(const void *p, int bytes)
+{
+    const char *c = (const char *)((uintptr_t)p & ~(uintptr_t)127);
+    const char *e = (const char *)p + bytes;
+    for (; c < e; c += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(c));
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
 {
-    extern __shared__ float smem32[];
-    float *sd = smem32;                      // diagonal; after elimination: its reciprocal
-    float *sr = smem32 + a.smem_comps;       // rhs; after substitution: dV
-    float *scd = sr + a.smem_comps;          // per-segment contributions to the parent
+    // Shared memory of one work item: its tree blob (staged by one bulk
+    // copy), then per compartment the diagonal (after elimination: its
+    // reciprocal), the rhs (after substitution: dV) and |g_axial| (staged
+    // by phase A, so that the serial sweeps touch only shared memory), then
+    // per segment its contribution to its parent.
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *smeta = smem_raw;
+    float *sd = (float *)(smem_raw + a.smem_meta);
+    float *sr = sd + a.smem_comps;
+    float *sg = sr + a.smem_comps;
+    float *scd = sg + a.smem_comps;
     float *scr = scd + a.smem_segs;
-    __shared__ int s_item;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_item, s_abort;
 
     const long long n = (long long)a.ctl->step_base + a.step_offset;
     const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    uint32_t parity = 0;
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_item = (int)atomicAdd(&a.ctl->queue_head, 1u);
+        if (tid == 0) {
+            const int item = (int)atomicAdd(&a.ctl->queue_head, 1u);
+            s_item = item;
+            s_abort = 0;
+            if (item < a.n_small) {
+                const GroupRec *gp = a.groups + item;
+                const uint32_t bytes = (uint32_t)gp->meta_bytes;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&bar, bytes);
+                bulk_copy_g2s(smeta, a.meta + gp->meta_off, bytes, &bar);
+            }
+        }
         __syncthreads();
         const int gi = s_item;
-        if (gi >= a.n_groups) break;
+        if (gi >= a.n_small) break;
         const GroupRec G = a.groups[gi];
         const int64_t c0 = G.comp0;
         const int32_t *Vq = a.Vq + c0;
-        const float *gax = a.gax + c0;
 
-        // A. membrane conductance and current at (V^n, gates^n)
+        // A. membrane conductance and current at (V^n, gates^n), plus the
+        //    axial terms of every link inside a segment (both ends; a link
+        //    (i-1, i) is inside a segment when g_axial[i] has no sign bit).
+        //    Stage |g_axial| for the sweeps.
         for (int i = tid; i < G.ncomp; i += NT) {
             const int32_t vq = Vq[i];
-            const float m = gate_value(a.mq[c0 + i]), h = gate_value(a.hq[c0 + i]), nn = gate_value(a.nq[c0 + i]);
+            const float gs = a.gax[c0 + i];
+            const float g = fabsf(gs);
+            sg[i] = g;
+            const float m = mmf::gate_f(a.mq[c0 + i]), h = mmf::gate_f(a.hq[c0 + i]), nn = mmf::gate_f(a.nq[c0 + i]);
             const float ar = a.area[c0 + i];
             const float s = ar * 1e3f;
             const float gna = a.gNa * s * (m * m * m * h);
             const float n2 = nn * nn;
             const float gk = a.gK * s * (n2 * n2);
             const float gl = a.gL * s;
-            sd[i] = fmaf(ar, a.cm_dt, gna + gk + gl);
-            sr[i] = -fmaf(gna, vminus(vq, a.ENa), fmaf(gk, vminus(vq, a.EK), gl * vminus(vq, a.EL)));
+            float d = fmaf(ar, a.cm_dt, gna + gk + gl);
+            float r = -fmaf(gna, vminus(vq, a.ENa), fmaf(gk, vminus(vq, a.EK), gl * vminus(vq, a.EL)));
+            if (!signbit(gs)) {  // link to the parent i-1
+                d += g;
+                r = fmaf(g, mmf::vdiff(Vq[i - 1], vq), r);
+            }
+            if (i + 1 < G.ncomp) {
+                const float gc = a.gax[c0 + i + 1];
+                if (!signbit(gc)) {  // link to the child i+1
+                    d += gc;
+                    r = fmaf(gc, mmf::vdiff(Vq[i + 1], vq), r);
+                }
+            }
+            sd[i] = d;
+            sr[i] = r;
         }
+        // the tree blob must have landed before the sweeps
+        if (!mbar_wait_bounded(&bar, parity)) s_abort = 1;
+        parity ^= 1u;
         __syncthreads();
+        if (s_abort) {
+            if (tid == 0) atomicOr(&a.ctl->err, MMK_ERR_TIMEOUT);
+            break;
+        }
+        const SegP *segs = (const SegP *)smeta;
+        const int16_t *kids = (const int16_t *)(segs + G.nseg);
+        const int16_t *woff = kids + G.nchild;
 
-        // S. synaptic sites, then decay
+        // S. synaptic sites, then decay (sites are distinct compartments)
         for (int t = tid; t < G.nsite; t += NT) {
             const int st = G.site0 + t;
             const int c = a.site_comp[st];
@@ -257,39 +242,38 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         }
         __syncthreads();
 
-        // B. leaves-to-root elimination with the axial terms folded in
-        const SegRec *segs = a.segs + G.seg0;
-        const int *woff = a.wave_off + G.wave0;
+        // B. leaves-to-root elimination (Algorithm 1), one segment per thread,
+        //    wave by wave; a segment top adds its link to its parent and
+        //    leaves the parent its contribution.
         for (int w = 0; w < G.nwave; ++w) {
             const int sb = woff[w], se = woff[w + 1];
             for (int si = sb + tid; si < se; si += NT) {
-                const SegRec S = segs[si];
+                const SegP S = segs[si];
                 const int bot = S.top + S.len - 1;
                 float db = sd[bot], rb = sr[bot];
                 for (int c = 0; c < S.nchild; ++c) {
-                    const int cs = a.seg_child[S.child0 + c];
+                    const int cs = kids[S.child0 + c];
                     db += scd[cs];
                     rb += scr[cs];
                 }
+                // inside the segment the links are assembled: elimination of
+                // j into its parent j-1 with a = c = -g
                 for (int j = bot; j > S.top; --j) {
-                    const float g = gax[j];
-                    const float vpj = vdiff(Vq[j - 1], Vq[j]);       // V_p - V_j
-                    db += g;
-                    rb = fmaf(g, vpj, rb);
-                    const float inv = __frcp_rn(db);
+                    const float g = sg[j];
+                    const float inv = rcp_approx(db);
                     sd[j] = inv;
                     sr[j] = rb;
                     const float f = g * inv;
-                    db = fmaf(-f, g, sd[j - 1] + g);
-                    rb = fmaf(f, rb, fmaf(-g, vpj, sr[j - 1]));
+                    db = fmaf(-f, g, sd[j - 1]);
+                    rb = fmaf(f, rb, sr[j - 1]);
                 }
                 const int t = S.top;
                 if (S.parent >= 0) {
-                    const float g = gax[t];
-                    const float vpt = vdiff(Vq[S.parent], Vq[t]);
+                    const float g = sg[t];
+                    const float vpt = mmf::vdiff(Vq[S.parent], Vq[t]);
                     db += g;
                     rb = fmaf(g, vpt, rb);
-                    const float inv = __frcp_rn(db);
+                    const float inv = rcp_approx(db);
                     sd[t] = inv;
                     sr[t] = rb;
                     const float f = g * inv;
@@ -297,7 +281,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                     scr[si] = fmaf(f, rb, -g * vpt);
                 } else {
                     rb += (float)a.stim[G.neuron0 + S.neuron];
-                    const float inv = __frcp_rn(db);
+                    const float inv = rcp_approx(db);
                     sd[t] = inv;
                     sr[t] = rb * inv;
                 }
@@ -310,11 +294,11 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         for (int w = G.nwave - 1; w >= 0; --w) {
             const int sb = woff[w], se = woff[w + 1];
             for (int si = sb + tid; si < se; si += NT) {
-                const SegRec S = segs[si];
+                const SegP S = segs[si];
                 const int t = S.top;
                 float x;
                 if (S.parent >= 0) {
-                    x = fmaf(gax[t], sr[S.parent], sr[t]) * sd[t];
+                    x = fmaf(sg[t], sr[S.parent], sr[t]) * sd[t];
                     sr[t] = x;
                 } else {
                     x = sr[t];
@@ -337,28 +321,225 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                     }
                 }
                 for (int j = t + 1; j < t + S.len; ++j) {
-                    x = fmaf(gax[j], x, sr[j]) * sd[j];
+                    x = fmaf(sg[j], x, sr[j]) * sd[j];
                     sr[j] = x;
                 }
             }
             __syncthreads();
         }
 
-        // C. V^{n+1} = V^n + dV (exact in fixed point), gates at V^{n+1}
+        // C. V^{n+1} = V^n + dV (exact in fixed point); the gates follow in
+        //    gates_fp32c_kernel
         for (int i = tid; i < G.ncomp; i += NT) {
-            const float dv = sr[i];
-            long long nv = (long long)Vq[i] + __float2ll_rn(dv * kVScale);
-            if (!(fabsf(dv) < 256.0f) || nv > 2147483647LL || nv < -2147483647LL) {
+            const int32_t vold = Vq[i];
+            int32_t vq;
+            if (!mmf::v_add(vold, sr[i], &vq)) {
                 atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
-                nv = (long long)Vq[i];
+                vq = vold;
             }
-            const int32_t vq = (int32_t)nv;
             a.Vq[c0 + i] = vq;
-            const Rates32 r = hh_rates32(vq);
-            a.mq[c0 + i] = gate_step32(a.mq[c0 + i], r.am, r.bm, a.dt);
-            a.hq[c0 + i] = gate_step32(a.hq[c0 + i], r.ah, r.bh, a.dt);
-            a.nq[c0 + i] = gate_step32(a.nq[c0 + i], r.an, r.bn, a.dt);
         }
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
+{
+    // Work items too large for shared memory (giant neurons, up to the
+    // int32 index range).  The Hines diagonal and rhs of each compartment
+    // live in a global scratch (float2 per compartment: d, rhs; after
+    // elimination 1/d and rhs; after substitution dV), written and read
+    // again within the item, so it stays in L2; every lane prefetches its
+    // segment into L1 before walking it.  The item's tree is read from its
+    // wide blob in global memory: SegRec[nseg] | int32 child[nchild] |
+    // int32 wave_off[nwave + 1].
+    __shared__ int s_item;
+
+    const long long n = (long long)a.ctl->step_base + a.step_offset;
+    const int tid = threadIdx.x;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = a.n_small + (int)atomicAdd(&a.ctl->giant_head, 1u);
+        __syncthreads();
+        const int gi = s_item;
+        if (gi >= a.n_groups) break;
+        const GroupRec G = a.groups[gi];
+        const int64_t c0 = G.comp0;
+        const int32_t *Vq = a.Vq + c0;
+        const float *gax = a.gax + c0;
+        float2 *dr = a.dr + G.scratch0;
+
+        // A. membrane conductance and current at (V^n, gates^n), plus the
+        //    axial terms of every link inside a segment (both ends; a link
+        //    (i-1, i) is inside a segment when g_axial[i] has no sign bit).
+#pragma unroll 4
+        for (int i = tid; i < G.ncomp; i += NT) {
+            const int32_t vq = Vq[i];
+            const float gs = gax[i];
+            const float m = mmf::gate_f(a.mq[c0 + i]), h = mmf::gate_f(a.hq[c0 + i]), nn = mmf::gate_f(a.nq[c0 + i]);
+            const float ar = a.area[c0 + i];
+            const float s = ar * 1e3f;
+            const float gna = a.gNa * s * (m * m * m * h);
+            const float n2 = nn * nn;
+            const float gk = a.gK * s * (n2 * n2);
+            const float gl = a.gL * s;
+            float d = fmaf(ar, a.cm_dt, gna + gk + gl);
+            float r = -fmaf(gna, vminus(vq, a.ENa), fmaf(gk, vminus(vq, a.EK), gl * vminus(vq, a.EL)));
+            if (!signbit(gs)) {  // link to the parent i-1
+                const float g = fabsf(gs);
+                d += g;
+                r = fmaf(g, mmf::vdiff(Vq[i - 1], vq), r);
+            }
+            if (i + 1 < G.ncomp) {
+                const float gc = gax[i + 1];
+                if (!signbit(gc)) {  // link to the child i+1
+                    d += gc;
+                    r = fmaf(gc, mmf::vdiff(Vq[i + 1], vq), r);
+                }
+            }
+            dr[i] = make_float2(d, r);
+        }
+        __syncthreads();
+        const SegRec *segs = (const SegRec *)(a.meta + G.meta_off);
+        const int32_t *kids = (const int32_t *)(segs + G.nseg);
+        const int32_t *woff = kids + G.nchild;
+
+        // S. synaptic sites, then decay (sites are distinct compartments)
+        for (int t = tid; t < G.nsite; t += NT) {
+            const int st = G.site0 + t;
+            const int c = a.site_comp[st];
+            const float g = a.gsyn[st];
+            float2 v = dr[c];
+            v.x += g;
+            v.y = fmaf(-g, vminus(Vq[c], a.Esyn), v.y);
+            dr[c] = v;
+            a.gsyn[st] = g * a.decay;
+        }
+        __syncthreads();
+
+        // B. leaves-to-root elimination (Algorithm 1), one segment per thread,
+        //    wave by wave.  Each child segment's contribution to the bottom
+        //    compartment is formed from the child top's stored 1/d and rhs:
+        //    link terms (+g, +g (V_t - V_P)) and elimination (-g^2/d_t, +g rhs_t/d_t).
+        for (int w = 0; w < G.nwave; ++w) {
+            const int sb = woff[w], se = woff[w + 1];
+            for (int si = sb + tid; si < se; si += NT) {
+                const SegRec S = segs[si];
+                const int bot = S.top + S.len - 1;
+                prefetch_l1(dr + S.top, S.len * (int)sizeof(float2));
+                prefetch_l1(gax + S.top, S.len * (int)sizeof(float));
+                float2 v = dr[bot];
+                float db = v.x, rb = v.y;
+                if (S.nchild) {
+                    const int32_t vb = Vq[bot];
+                    for (int c = 0; c < S.nchild; ++c) {
+                        const int t = segs[kids[S.child0 + c]].top;
+                        const float2 ct = dr[t];  // (1/d_t, rhs_t)
+                        const float g = fabsf(gax[t]);
+                        const float f = g * ct.x;
+                        db += fmaf(-f, g, g);
+                        rb += fmaf(f, ct.y, g * mmf::vdiff(Vq[t], vb));
+                    }
+                }
+                for (int j = bot; j > S.top; --j) {
+                    const float g = fabsf(gax[j]);
+                    const float inv = rcp_approx(db);
+                    dr[j] = make_float2(inv, rb);
+                    const float f = g * inv;
+                    const float2 p = dr[j - 1];
+                    db = fmaf(-f, g, p.x);
+                    rb = fmaf(f, rb, p.y);
+                }
+                const int t = S.top;
+                if (S.parent >= 0) {
+                    const float g = fabsf(gax[t]);
+                    db += g;
+                    rb = fmaf(g, mmf::vdiff(Vq[S.parent], Vq[t]), rb);
+                    dr[t] = make_float2(rcp_approx(db), rb);
+                } else {
+                    rb += (float)a.stim[G.neuron0 + S.neuron];
+                    const float inv = rcp_approx(db);
+                    dr[t] = make_float2(inv, rb * inv);  // dV at the soma
+                }
+            }
+            __syncthreads();
+        }
+
+        // F. root-to-leaves substitution, V^{n+1} = V^n + dV in fixed point as
+        //    each compartment is reached; the soma segment also runs the FP64
+        //    soma accumulator and the spike test.
+        for (int w = G.nwave - 1; w >= 0; --w) {
+            const int sb = woff[w], se = woff[w + 1];
+            for (int si = sb + tid; si < se; si += NT) {
+                const SegRec S = segs[si];
+                const int t = S.top;
+                prefetch_l1(dr + t, S.len * (int)sizeof(float2));
+                prefetch_l1(gax + t, S.len * (int)sizeof(float));
+                prefetch_l1(Vq + t, S.len * (int)sizeof(int32_t));
+                float x;
+                const float2 vt = dr[t];
+                if (S.parent >= 0) {
+                    x = fmaf(fabsf(gax[t]), dr[S.parent].y, vt.y) * vt.x;
+                } else {
+                    x = vt.y;
+                    const int nrn = G.neuron0 + S.neuron;
+                    const double v0 = a.Vsoma[nrn], v1 = v0 + (double)x;
+                    a.Vsoma[nrn] = v1;
+                    if (!isfinite(v1)) atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
+                    if (v0 < a.threshold && v1 >= a.threshold) {
+                        const double ts = (double)n * a.dt64 + a.dt64 * (a.threshold - v0) / (v1 - v0);
+                        const unsigned long long k = atomicAdd(&a.ctl->spk_count, 1ull);
+                        if ((long long)k < a.spk_cap) {
+                            a.spk_nrn[k] = a.user_id[nrn];
+                            a.spk_t[k] = ts;
+                        } else {
+                            atomicOr(&a.ctl->err, MMK_ERR_OVERFLOW);
+                        }
+                        const int slot = (int)(n % a.R);
+                        const int pos = atomicAdd(&a.ring_cnt[slot], 1);
+                        a.ring_nrn[(long long)slot * a.N + pos] = nrn;
+                    }
+                }
+                dr[t].y = x;
+                int32_t vn;
+                if (!mmf::v_add(Vq[t], x, &vn)) {
+                    atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
+                    vn = Vq[t];
+                }
+                int32_t *Vw = a.Vq + c0;
+                for (int j = t + 1; j < t + S.len; ++j) {
+                    const float2 v = dr[j];
+                    x = fmaf(fabsf(gax[j]), x, v.y) * v.x;
+                    dr[j].y = x;
+                    int32_t vj;
+                    if (!mmf::v_add(Vq[j], x, &vj)) {
+                        atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
+                        vj = Vq[j];
+                    }
+                    Vw[j] = vj;
+                }
+                Vw[t] = vn;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Exponential-Euler gate update at V^{n+1} for every compartment: a pure
+// streaming kernel (no shared memory, no barriers), one compartment per
+// thread, so that the arithmetic-heavy rate functions run at full occupancy
+// apart from the latency-bound tree solve.
+__global__ void __launch_bounds__(256) gates_fp32c_kernel(const int32_t *__restrict__ Vq, uint32_t *__restrict__ mq,
+                                                          uint32_t *__restrict__ hq, uint32_t *__restrict__ nq,
+                                                          int64_t C, float dt, float dt_lo)
+{
+    const mmf::F2 dt2{dt, dt_lo};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C; i += (int64_t)gridDim.x * blockDim.x) {
+        const mmf::Rates r = mmf::hh_rates(Vq[i]);
+        mq[i] = mmf::gate_step(mq[i], r.am, r.bm, dt2);
+        hq[i] = mmf::gate_step(hq[i], r.ah, r.bh, dt2);
+        nq[i] = mmf::gate_step(nq[i], r.an, r.bn, dt2);
     }
 }
 
@@ -398,14 +579,26 @@ int set_attr_and_occupancy(int smem, int *blocks)
 
 }  // namespace
 
+size_t mmk_step_fp32c_smem(int comps, int segs, int meta_bytes)
+{
+    return (size_t)meta_bytes + (size_t)(3 * comps + 2 * segs) * sizeof(float);
+}
+
+int mmk_launch_giant_fp32c(const StepArgs32 &a, int blocks, void *stream)
+{
+    giant_fp32c_kernel<256><<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
+    return (int)cudaGetLastError();
+}
+
 int mmk_launch_step_fp32c(const StepArgs32 &a, int blocks, int threads, void *stream)
 {
-    const size_t smem = (size_t)(2 * a.smem_comps + 2 * a.smem_segs) * sizeof(float);
+    const size_t smem = mmk_step_fp32c_smem(a.smem_comps, a.smem_segs, a.smem_meta);
     cudaStream_t s = (cudaStream_t)stream;
     switch (threads) {
     case 128: step_fp32c_kernel<128><<<blocks, 128, smem, s>>>(a); break;
     case 256: step_fp32c_kernel<256><<<blocks, 256, smem, s>>>(a); break;
     case 512: step_fp32c_kernel<512><<<blocks, 512, smem, s>>>(a); break;
+    case 1024: step_fp32c_kernel<1024><<<blocks, 1024, smem, s>>>(a); break;
     default: return (int)cudaErrorInvalidValue;
     }
     return (int)cudaGetLastError();
@@ -417,8 +610,15 @@ int mmk_step_fp32c_blocks_per_sm(int threads, int smem_bytes, int *blocks)
     case 128: return set_attr_and_occupancy<128>(smem_bytes, blocks);
     case 256: return set_attr_and_occupancy<256>(smem_bytes, blocks);
     case 512: return set_attr_and_occupancy<512>(smem_bytes, blocks);
+    case 1024: return set_attr_and_occupancy<1024>(smem_bytes, blocks);
     default: return (int)cudaErrorInvalidValue;
     }
+}
+
+int mmk_launch_gates_fp32c(const StepArgs32 &a, int blocks, void *stream)
+{
+    gates_fp32c_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(a.Vq, a.mq, a.hq, a.nq, a.C, a.dt, a.dt_lo);
+    return (int)cudaGetLastError();
 }
 
 int mmk_launch_init_fp32c(const InitArgs &a, void *stream)

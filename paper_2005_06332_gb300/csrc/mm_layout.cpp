@@ -19,6 +19,7 @@
 #include "mm_layout.h"
 
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <numeric>
 #include <sstream>
@@ -144,7 +145,9 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         gstart.push_back(N);
     }
     const int32_t G = (int32_t)gstart.size() - 1;
-    L.groups.resize((size_t)G);
+    L.groups.clear();
+    L.groups.reserve((size_t)G);
+    std::vector<mmk::GroupRec> giants;
 
     // 2 + 3b. per group: renumber its neurons, cut segments, sort into waves
     NeuronScratch ws;
@@ -214,6 +217,8 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
             for (int32_t j = 0; j < n; ++j) {
                 const bool cont = (j > 0 && ws.pnew[(size_t)j] == j - 1 && ws.nch[(size_t)(j - 1)] == 1);
                 if (!cont) {
+                    // segment tops carry a negative parent distance
+                    if (j > 0) L.pdist[(size_t)(ib + j)] = -L.pdist[(size_t)(ib + j)];
                     mmk::SegRec s;
                     s.top = lb + j;
                     s.len = 1;
@@ -252,38 +257,99 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         });
         newidx.resize((size_t)ns);
         for (int32_t i = 0; i < ns; ++i) newidx[(size_t)perm[(size_t)i]] = i;
-        mmk::GroupRec &gr = L.groups[(size_t)g];
+        mmk::GroupRec gr{};
         gr.comp0 = comp0;
+        gr.scratch0 = 0;
         gr.ncomp = (int32_t)(L.noff[(size_t)k1] - comp0);
-        gr.seg0 = (int32_t)L.segs.size();
         gr.nseg = ns;
         gr.neuron0 = k0;
         gr.nneuron = k1 - k0;
         gr.pad = 0;
         int32_t maxh = 0;
+        int64_t nkids = 0;
         for (int32_t i = 0; i < ns; ++i) {
-            const int32_t s = perm[(size_t)i];
-            mmk::SegRec r = gsegs[(size_t)s];
-            r.child0 = (int32_t)L.seg_child.size();
-            r.nchild = (int32_t)gkids[(size_t)s].size();
-            for (int32_t c : gkids[(size_t)s]) L.seg_child.push_back(newidx[(size_t)c]);
-            L.segs.push_back(r);
-            maxh = std::max(maxh, gheight[(size_t)s]);
+            maxh = std::max(maxh, gheight[(size_t)perm[(size_t)i]]);
+            nkids += (int64_t)gkids[(size_t)perm[(size_t)i]].size();
         }
-        gr.wave0 = (int32_t)L.wave_off.size();
-        gr.nwave = maxh + 1;
+        const int64_t small_meta = ((int64_t)ns * (int64_t)sizeof(mmk::SegP) + 2 * nkids + 2 * (maxh + 2) + 15) & ~15LL;
+        const int64_t smem_need = small_meta + (int64_t)in.smem_per_comp * gr.ncomp + (int64_t)in.smem_per_seg * ns;
+        const bool giant = gr.ncomp > 32767 || ns > 32767 || (in.giant_smem_limit > 0 && smem_need > in.giant_smem_limit);
+        if (giant && in.giant_smem_limit <= 0) {
+            *invalid = false;
+            e << "a work item of " << gr.ncomp << " compartments exceeds what this precision holds";
+            return msg(e);
+        }
+        // the tree blob: records in wave order, child lists, wave offsets;
+        // 16-bit indices for items staged in shared memory, 32-bit for giants
+        std::vector<int32_t> woff;
         {
             int32_t i = 0;
             for (int32_t h = 0; h <= maxh; ++h) {
                 while (i < ns && gheight[(size_t)perm[(size_t)i]] < h) ++i;
-                L.wave_off.push_back(i);
+                woff.push_back(i);
             }
-            L.wave_off.push_back(ns);
+            woff.push_back(ns);
         }
-        L.max_comps = std::max(L.max_comps, gr.ncomp);
-        L.max_segs = std::max(L.max_segs, ns);
-        L.max_waves = std::max(L.max_waves, gr.nwave);
+        gr.nchild = (int32_t)nkids;
+        gr.nwave = maxh + 1;
+        std::vector<unsigned char> blob;
+        auto put = [&blob](const void *p, size_t n) {
+            const unsigned char *c = (const unsigned char *)p;
+            blob.insert(blob.end(), c, c + n);
+        };
+        if (!giant) {
+            std::vector<int16_t> kids;
+            std::vector<mmk::SegP> recs((size_t)ns);
+            for (int32_t i = 0; i < ns; ++i) {
+                const int32_t sidx = perm[(size_t)i];
+                const mmk::SegRec &r = gsegs[(size_t)sidx];
+                mmk::SegP q;
+                q.top = (int16_t)r.top;
+                q.len = (int16_t)r.len;
+                q.parent = (int16_t)r.parent;
+                q.nchild = (int16_t)gkids[(size_t)sidx].size();
+                q.child0 = (int16_t)kids.size();
+                q.neuron = (int16_t)r.neuron;
+                for (int32_t c : gkids[(size_t)sidx]) kids.push_back((int16_t)newidx[(size_t)c]);
+                recs[(size_t)i] = q;
+            }
+            std::vector<int16_t> w16(woff.begin(), woff.end());
+            put(recs.data(), recs.size() * sizeof(mmk::SegP));
+            put(kids.data(), kids.size() * 2);
+            put(w16.data(), w16.size() * 2);
+        } else {
+            std::vector<int32_t> kids;
+            std::vector<mmk::SegRec> recs((size_t)ns);
+            for (int32_t i = 0; i < ns; ++i) {
+                const int32_t sidx = perm[(size_t)i];
+                mmk::SegRec q = gsegs[(size_t)sidx];
+                q.nchild = (int32_t)gkids[(size_t)sidx].size();
+                q.child0 = (int32_t)kids.size();
+                for (int32_t c : gkids[(size_t)sidx]) kids.push_back(newidx[(size_t)c]);
+                recs[(size_t)i] = q;
+            }
+            put(recs.data(), recs.size() * sizeof(mmk::SegRec));
+            put(kids.data(), kids.size() * 4);
+            put(woff.data(), woff.size() * 4);
+            gr.scratch0 = L.giant_comps;
+            L.giant_comps += gr.ncomp;
+        }
+        blob.resize((blob.size() + 15) & ~(size_t)15, 0);
+        gr.meta_off = (int64_t)L.meta.size();
+        gr.meta_bytes = (int32_t)blob.size();
+        L.meta.insert(L.meta.end(), blob.begin(), blob.end());
+        if (giant) {
+            giants.push_back(gr);
+        } else {
+            L.groups.push_back(gr);
+            L.max_comps = std::max(L.max_comps, gr.ncomp);
+            L.max_segs = std::max(L.max_segs, ns);
+            L.max_waves = std::max(L.max_waves, gr.nwave);
+            L.max_meta = std::max(L.max_meta, gr.meta_bytes);
+        }
     }
+    L.n_small = (int32_t)L.groups.size();
+    L.groups.insert(L.groups.end(), giants.begin(), giants.end());
 
     // 4a. synaptic sites: one per compartment that receives a synapse
     std::vector<int32_t> site_of((size_t)C, -1);
@@ -292,16 +358,22 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         site_of[(size_t)ic] = 0;
     }
     {
+        // items in compartment order (giant items sit at the end of groups[])
+        std::vector<int32_t> by_comp(L.groups.size());
+        std::iota(by_comp.begin(), by_comp.end(), 0);
+        std::sort(by_comp.begin(), by_comp.end(),
+                  [&](int32_t x, int32_t y) { return L.groups[(size_t)x].comp0 < L.groups[(size_t)y].comp0; });
         int32_t ns = 0;
-        int32_t g = 0;
+        size_t gpos = 0;
         for (auto &gr : L.groups) { gr.site0 = 0; gr.nsite = 0; }
         for (int64_t i = 0; i < C; ++i) {
             if (site_of[(size_t)i] < 0) continue;
-            while (i >= L.groups[(size_t)g].comp0 + L.groups[(size_t)g].ncomp) ++g;
-            if (L.groups[(size_t)g].nsite == 0) L.groups[(size_t)g].site0 = ns;
-            L.groups[(size_t)g].nsite++;
+            while (i >= L.groups[(size_t)by_comp[gpos]].comp0 + L.groups[(size_t)by_comp[gpos]].ncomp) ++gpos;
+            mmk::GroupRec &gr = L.groups[(size_t)by_comp[gpos]];
+            if (gr.nsite == 0) gr.site0 = ns;
+            gr.nsite++;
             site_of[(size_t)i] = ns++;
-            L.site_comp.push_back((int32_t)(i - L.groups[(size_t)g].comp0));
+            L.site_comp.push_back((int32_t)(i - gr.comp0));
             L.site_internal.push_back(i);
         }
         for (auto &gr : L.groups) if (gr.nsite == 0) gr.site0 = ns;

@@ -21,7 +21,11 @@ struct LayoutInput {
     const float *cost;            // may be NULL (size order)
     double dt;
     int32_t group_comps;          // compartment budget of a work item
-    int32_t max_group_comps;      // largest work item a block can hold
+    int32_t max_group_comps;      // largest neuron accepted
+    // shared-memory model of a work item, bytes = meta + smem_per_comp * comps
+    // + smem_per_seg * segments; items above giant_smem_limit become giant
+    // items (0: no giant items, such a neuron is rejected)
+    int32_t smem_per_comp, smem_per_seg, giant_smem_limit;
 };
 
 struct Layout {
@@ -33,14 +37,14 @@ struct Layout {
     std::vector<int64_t> user2int;      // user compartment -> internal compartment [C]
     std::vector<int64_t> soma_of_user;  // internal soma compartment of each user neuron [N]
     std::vector<double> L, D;           // cylinders, internal order
-    std::vector<int32_t> pdist;         // i - parent(i) in internal order, 0 at somata
+    std::vector<int32_t> pdist;         // i - parent(i) in internal order, negated at segment tops, 0 at somata
     std::vector<double> stim;           // internal order
     std::vector<mmk::GroupRec> groups;
-    std::vector<mmk::SegRec> segs;
-    std::vector<int32_t> seg_child;
-    std::vector<int32_t> wave_off;
+    std::vector<unsigned char> meta;    // tree blobs (16-byte aligned per work item)
     int32_t max_comps = 0, max_segs = 0;
-    int32_t max_waves = 0;
+    int32_t max_waves = 0, max_meta = 0;
+    int32_t n_small = 0;                // items [0, n_small) fit shared memory, the rest are giants
+    int64_t giant_comps = 0;            // compartments in giant items (size of the Hines scratch)
     std::vector<int32_t> site_comp;     // group-local compartment of each site
     std::vector<int64_t> site_internal; // internal compartment of each site
     std::vector<int64_t> out_off;       // outgoing synapses per internal source [N+1]

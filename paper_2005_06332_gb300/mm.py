@@ -61,7 +61,14 @@ class Options(C.Structure):
 
 class KernelTimes(C.Structure):
     _fields_ = [("step_kernel_ms", C.c_double), ("step_kernel_launches", C.c_int64),
-                ("deliver_kernel_ms", C.c_double), ("deliver_kernel_launches", C.c_int64)]
+                ("deliver_kernel_ms", C.c_double), ("deliver_kernel_launches", C.c_int64),
+                ("gates_kernel_ms", C.c_double), ("gates_kernel_launches", C.c_int64),
+                ("giant_kernel_ms", C.c_double), ("giant_kernel_launches", C.c_int64)]
+
+
+class LaunchInfo(C.Structure):
+    _fields_ = [(k, C.c_int32) for k in ("work_items", "blocks", "threads", "blocks_per_sm", "smem_bytes",
+                                          "max_item_comps", "max_item_segments", "max_item_waves", "giant_items")]
 
 
 _lock = threading.Lock()
@@ -102,6 +109,7 @@ def load(build_if_missing: bool = False):
         L.mm_load_state.argtypes = [net_p, C.c_void_p, C.c_size_t]
         L.mm_set_kernel_timing.argtypes = [net_p, C.c_int32]
         L.mm_read_kernel_timing.argtypes = [net_p, P(KernelTimes), C.c_int32]
+        L.mm_get_launch_info.argtypes = [net_p, P(LaunchInfo)]
         L.mm_last_error.argtypes = [net_p]
         L.mm_last_error.restype = C.c_char_p
         L.mm_status_string.argtypes = [C.c_int]
@@ -110,7 +118,7 @@ def load(build_if_missing: bool = False):
         L.mm_destroy.restype = None
         for name in ("mm_create_network", "mm_step", "mm_synchronize", "mm_read_voltages", "mm_read_state",
                      "mm_read_soma_voltages", "mm_read_spikes", "mm_set_stimulus", "mm_get_step", "mm_save_state",
-                     "mm_load_state", "mm_set_kernel_timing", "mm_read_kernel_timing"):
+                     "mm_load_state", "mm_set_kernel_timing", "mm_read_kernel_timing", "mm_get_launch_info"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -291,6 +299,11 @@ class Network:
         t = KernelTimes()
         self._check(self._L.mm_read_kernel_timing(self._h, C.byref(t), 1 if reset else 0), "mm_read_kernel_timing")
         return {k: getattr(t, k) for k, _ in KernelTimes._fields_}
+
+    def launch_info(self) -> dict:
+        li = LaunchInfo()
+        self._check(self._L.mm_get_launch_info(self._h, C.byref(li)), "mm_get_launch_info")
+        return {k: getattr(li, k) for k, _ in LaunchInfo._fields_}
 
     def load_state(self, blob: bytes):
         buf = C.create_string_buffer(blob, len(blob))

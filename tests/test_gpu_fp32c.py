@@ -99,15 +99,42 @@ def test_fp32c_mono64_40ms():
 
 
 def test_fp32c_mono64_100ms():
-    """Over the full 100 ms the spike trains are identical; the voltage error
-    is reported by the accuracy report (the phase error grows with every
-    firing cycle), here bounded at 5x the bar."""
+    """Over the full 100 ms: identical spike trains.  The voltage error has a
+    floor set by the 32-bit state (V at 2^-23 mV, gates at 2^-32): its
+    rounding shifts spike times by ~1e-3 dt, which is 1e-3..5e-3 mV on an
+    upstroke (400 mV/ms); the exact maxima are in the accuracy report."""
     net = netgen.make_config("mono64")
     ref = oracle.simulate(net, net.n_steps)
     V, _, sn, st, _ = _run(net, net.n_steps)
     shift = _spike_match(net, sn, st, ref)
     assert shift is not None, "spike trains differ"
+    assert shift <= 0.01
     assert np.max(np.abs(V - ref.V)) <= 5 * TOL_V
+
+
+def test_fp32c_giant_items_match_oracle():
+    """Neurons too large for one block's shared memory are solved by the
+    giant kernel from a global scratch; they must agree with the oracle like
+    any other neuron (and the small ones next to them too)."""
+    big = netgen.make_network(2, size_dist=("mono", 15000), p_branch=0.05, syn_per_neuron=0, seed=31,
+                              stim_nA=(1.5, 2.5))
+    small = netgen.make_network(12, size_dist=("loguniform", 20, 400), p_branch=0.1, syn_per_neuron=0, seed=32,
+                                stim_nA=(0.3, 0.8))
+    net = netgen.Network(
+        comp_offset=np.concatenate([big.comp_offset, big.comp_offset[-1] + small.comp_offset[1:]]),
+        parent=np.concatenate([big.parent, small.parent]), length_um=np.concatenate([big.length_um, small.length_um]),
+        diam_um=np.concatenate([big.diam_um, small.diam_um]), stim_nA=np.concatenate([big.stim_nA, small.stim_nA]),
+        syn_src=np.zeros(0, np.int32), syn_dst=np.zeros(0, np.int32), syn_comp=np.zeros(0, np.int32),
+        syn_w=np.zeros(0), syn_delay_ms=np.zeros(0), params=dict(netgen.DEFAULT_PARAMS), dt=0.025)
+    steps = 400
+    ref = oracle.simulate(net, steps)
+    with mm.Network(net, precision="fp32c") as g:
+        assert g.launch_info()["giant_items"] == 2
+        g.step(steps)
+        V = g.read_voltages()
+        sn, st = g.read_spikes()
+    assert np.max(np.abs(V - ref.V)) <= TOL_V
+    assert len(sn) == ref.n_spikes
 
 
 def test_fp32c_checkpoint_resume():
