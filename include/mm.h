@@ -210,6 +210,21 @@ mm_status mm_set_kernel_timing(mm_net *net, int32_t enable);
  * reset != 0 clears the totals afterwards. */
 mm_status mm_read_kernel_timing(mm_net *net, mm_kernel_times *out, int32_t reset);
 
+/* Algorithm 1 (Sec. 2) on a batch of independent trees, on the device.
+ * Tree k holds entries tree_offset[k] .. tree_offset[k+1]-1 (n_comp in
+ * total); per entry i (local index j within its tree): parent (LOCAL,
+ * parent[0] = -1, 0 <= parent[j] < j), a = upper (row p(j), column j),
+ * b = diagonal, c = lower (row j, column p(j)), rhs.  Writes the solution
+ * of every system to x.  ALL pointers are DEVICE pointers; inputs are not
+ * modified.  Runs on cuda_stream (NULL: the legacy default stream) and
+ * returns after the solve has finished.  Allocates a device scratch of
+ * n_comp doubles for the duration of the call.
+ * Errors: MM_EINVAL (negative sizes, NULL arrays, or a tree that violates
+ * the parent rule: its entries of x are then undefined), MM_ENOMEM, MM_ECUDA. */
+mm_status mm_hines_solve(int32_t n_trees, int64_t n_comp, const int64_t *tree_offset, const int32_t *parent,
+                         const double *a, const double *b, const double *c, const double *rhs, double *x,
+                         void *cuda_stream);
+
 /* Launch configuration chosen for the per-step kernel. */
 typedef struct {
     int32_t work_items;        /* neuron groups handed out by the device queue */

@@ -110,6 +110,8 @@ def load(build_if_missing: bool = False):
         L.mm_set_kernel_timing.argtypes = [net_p, C.c_int32]
         L.mm_read_kernel_timing.argtypes = [net_p, P(KernelTimes), C.c_int32]
         L.mm_get_launch_info.argtypes = [net_p, P(LaunchInfo)]
+        L.mm_hines_solve.argtypes = [C.c_int32, C.c_int64] + [C.c_void_p] * 8
+        L.mm_hines_solve.restype = C.c_int
         L.mm_last_error.argtypes = [net_p]
         L.mm_last_error.restype = C.c_char_p
         L.mm_status_string.argtypes = [C.c_int]
@@ -132,6 +134,21 @@ def _status_name(s: int) -> str:
 
 def _ptr(a: np.ndarray, ct):
     return a.ctypes.data_as(C.POINTER(ct))
+
+
+def hines_solve(tree_offset, parent, a, b, c, rhs, stream=None):
+    """Algorithm 1 on a batch of trees held in CUDA tensors (int64 offsets,
+    int32 local parents, float64 a, b, c, rhs); returns x (a CUDA tensor)."""
+    import torch
+    L = load()
+    x = torch.empty_like(rhs)
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    st = L.mm_hines_solve(int(tree_offset.numel() - 1), int(rhs.numel()), tree_offset.data_ptr(),
+                          parent.data_ptr(), a.data_ptr(), b.data_ptr(), c.data_ptr(), rhs.data_ptr(),
+                          x.data_ptr(), s)
+    if st != MM_OK:
+        raise MMError(st, "mm_hines_solve")
+    return x
 
 
 class TorchAllocator:
