@@ -225,6 +225,25 @@ mm_status mm_hines_solve(int32_t n_trees, int64_t n_comp, const int64_t *tree_of
                          const double *a, const double *b, const double *c, const double *rhs, double *x,
                          void *cuda_stream);
 
+/* mm_hines_solve without any allocation (the paper has no counterpart):
+ * for callers that may not allocate device memory at all, such as a
+ * component inside a host application whose memory manager owns every
+ * device byte (a cudaMalloc there fails or breaks its accounting), or a
+ * latency-critical loop where an allocation could block or fail mid-run.
+ * Same arguments, results and errors as mm_hines_solve; the caller still
+ * passes every input and the output x.  The scratch is a fixed 8 MiB
+ * device array inside this library (loaded on every GPU that loads the
+ * library, until the process ends), so n_comp must not exceed 1,048,576
+ * (MM_EINVAL otherwise).  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress, with that device current) and
+ * should come before any stream capture.  Every call on a device shares
+ * the same scratch: calls whose work overlaps on the GPU race, so callers
+ * order them (one stream, or wait for the previous call to return).
+ * Calls no cudaMalloc, cudaFree or allocating library routine. */
+mm_status mm_hines_solve_noalloc(int32_t n_trees, int64_t n_comp, const int64_t *tree_offset,
+                                 const int32_t *parent, const double *a, const double *b, const double *c,
+                                 const double *rhs, double *x, void *cuda_stream);
+
 /* Launch configuration chosen for the per-step kernel. */
 typedef struct {
     int32_t work_items;        /* neuron groups handed out by the device queue */

@@ -8,7 +8,16 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "mm.h"
+
+// Scratch of mm_hines_solve_noalloc: a fixed device array in this library
+// image, so that the call never allocates.  The first 256 bytes hold the
+// status word, the rest the eliminated diagonal (MM_NOALLOC_MAX_COMPS doubles,
+// 8 MiB).  Every GPU that loads the library holds it until the process ends.
+#define MM_NOALLOC_MAX_COMPS (1 << 20)
+static __device__ __align__(256) double g_noalloc_scratch[32 + MM_NOALLOC_MAX_COMPS];
 
 namespace {
 
@@ -98,4 +107,38 @@ extern "C" mm_status mm_hines_solve(int32_t n_trees, int64_t n_comp, const int64
     const mm_status st = run_batch(n_trees, n_comp, tree_offset, parent, a, b, c, rhs, x, work, status, s);
     cudaFree(scratch);
     return st;
+}
+
+// Device address of g_noalloc_scratch on each device.  In host code the
+// array's name is only a host-side stand-in, so the address is asked for
+// once per device, with that device current, on the first call there.
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[128];
+
+extern "C" mm_status mm_hines_solve_noalloc(int32_t n_trees, int64_t n_comp, const int64_t *tree_offset,
+                                            const int32_t *parent, const double *a, const double *b,
+                                            const double *c, const double *rhs, double *x, void *cuda_stream)
+{
+    if (!args_ok(n_trees, n_comp, tree_offset, parent, a, b, c, rhs, x)) return MM_EINVAL;
+    if (n_comp > MM_NOALLOC_MAX_COMPS) return MM_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return MM_ECUDA;
+    if (dev >= 128) return MM_ENOTSUP;
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return MM_ECUDA;
+            }
+            g_noalloc_ptr[dev] = p;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    int *status = (int *)base;                       // cleared by run_batch before the kernel
+    double *work = (double *)((char *)base + 256);   // fully written before it is read
+    return run_batch(n_trees, n_comp, tree_offset, parent, a, b, c, rhs, x, work, status,
+                     (cudaStream_t)cuda_stream);
 }

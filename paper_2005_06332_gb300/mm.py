@@ -112,6 +112,8 @@ def load(build_if_missing: bool = False):
         L.mm_get_launch_info.argtypes = [net_p, P(LaunchInfo)]
         L.mm_hines_solve.argtypes = [C.c_int32, C.c_int64] + [C.c_void_p] * 8
         L.mm_hines_solve.restype = C.c_int
+        L.mm_hines_solve_noalloc.argtypes = [C.c_int32, C.c_int64] + [C.c_void_p] * 8
+        L.mm_hines_solve_noalloc.restype = C.c_int
         L.mm_last_error.argtypes = [net_p]
         L.mm_last_error.restype = C.c_char_p
         L.mm_status_string.argtypes = [C.c_int]
