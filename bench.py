@@ -7,8 +7,9 @@ The metric is compartment-updates per second (compartments x steps / time).
 
 Default workload: the 10,000-neuron multi-morphology network (compartment
 counts log-uniform in [50, 5000], branch probability U[0.02, 0.2], 100
-synapses per neuron, dt = 0.025 ms), FP64, in the launch configuration of
-the library's defaults (CUDA graphs of 40 steps).
+synapses per neuron, dt = 0.025 ms) in compensated FP32 (FP32c), in the
+launch configuration of the library's defaults (CUDA graphs of 40 steps);
+the plain FP64 path is timed on the same network beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--config multi10k] [--precision fp64|fp32c]
@@ -175,6 +176,7 @@ def main():
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32c"])
     ap.add_argument("--graph-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--group-comps", type=int, default=0)
@@ -182,7 +184,7 @@ def main():
     args.warmup = max(3, args.warmup)
 
     net = netgen.make_config(args.config)
-    precision = args.precision or net.params.get("precision", "fp64")
+    precision = args.precision or "fp32c"
     if args.impl == "reference":
         run_reference(args, net)
         return
@@ -288,9 +290,27 @@ def main():
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
            "launch": launch}
+    g.close()
+    if precision != "fp64" and not args.no_fp64:
+        # the plain FP64 path on the same network, same launch configuration
+        g64 = mm.Network(net, precision="fp64", graph_steps=args.graph_steps, device=local,
+                         stream=stream.cuda_stream)
+        g64.step(3)
+        g64.synchronize()
+        k64 = max(10, min(K, 40))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g64.step(k64)
+        e1.record(stream)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1) / k64
+        g64.close()
+        v64 = net.n_comp * ws / (ms64 * 1e-3)
+        out["plain_fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": k64}
+        out["speedup_vs_plain_fp64"] = value / v64
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(net)
-    g.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
