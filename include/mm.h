@@ -132,6 +132,8 @@ typedef struct {
     int32_t block_threads;      /* threads per work item's block; 0 = automatic */
     int32_t group_comps;        /* compartment budget of one work item; 0 = automatic */
     int32_t device;             /* CUDA device ordinal */
+    int32_t time_items;         /* MM_FP32C: record each work item's solve time (mm_read_neuron_times) */
+    int32_t reserved0;
     double dt_ms;               /* time step of the network, > 0 */
     int64_t spike_capacity;     /* spikes held between two mm_read_spikes; 0 = automatic */
     void *cuda_stream;          /* cudaStream_t to run on; NULL = a library-owned stream */
@@ -243,6 +245,74 @@ mm_status mm_hines_solve(int32_t n_trees, int64_t n_comp, const int64_t *tree_of
 mm_status mm_hines_solve_noalloc(int32_t n_trees, int64_t n_comp, const int64_t *tree_offset,
                                  const int32_t *parent, const double *a, const double *b, const double *c,
                                  const double *rhs, double *x, void *cuda_stream);
+
+/* Per-neuron solve time, in microseconds per step, for a network created
+ * with MM_FP32C, time_items = 1 and group_comps = 1 (every neuron its own
+ * work item): the wall time from the moment a block takes the neuron's work
+ * item to the end of its V update (%globaltimer), averaged over the steps
+ * run since creation.  These are the labels of the learned cost model.
+ * out [cap >= n_neurons], user neuron order.  Synchronises. */
+mm_status mm_read_neuron_times(mm_net *net, double *out_us, int64_t cap);
+
+/* Morphology features of every neuron (host computation, no GPU needed):
+ * out [16 * n_neurons], row-major, one row of MM_N_FEATURES per neuron:
+ *  0 log n            1 log(1 + depth)        2 log(1 + branch points)
+ *  3 log(1 + leaves)  4 log(1 + segments)     5 log(1 + segment height)
+ *  6 log(1 + critical path: sum over height waves of the longest segment)
+ *  7 log(1 + longest segment)  8 mean segment length / 100
+ *  9 log(1 + mean depth)       10 log(membrane area / um^2)
+ * 11 mean diameter / um       12 branch points / n
+ * 13 log(1 + widest wave)     14 critical path / n
+ * 15 log(1 + children of the soma)
+ * Errors: MM_EINVAL as for mm_create_network's morphology checks. */
+#define MM_N_FEATURES 16
+mm_status mm_neuron_features(const mm_morphologies *morph, float *out, int64_t cap);
+
+/* ---------------------------------------------------------------------
+ * Learned cost model: an MLP 16 -> 64 -> 64 -> 1 (ReLU) with BF16 weights
+ * and FP32 accumulation, trained with Adam on FP32 master weights by the
+ * library's own kernels.  It maps a neuron's MM_N_FEATURES morphology
+ * features to its per-step solve time, the key by which MM_SCHED_COST
+ * orders the work queue (the paper's priority(size) and sorting by size,
+ * Sec. 4, with a learned key).  Parameters, flat (MM_MLP_PARAMS values):
+ * W1 [64 x 16] row-major, b1 [64], W2 [64 x 64], b2 [64], W3 [1 x 64], b3 [1].
+ * Inputs are standardised per feature and targets by mean / std (taken from
+ * the training set by mm_mlp_train, or set by mm_mlp_set_normalisation).
+ * All arrays are HOST arrays; the device holds the model.  Calls run on the
+ * current device's default stream and return when done. */
+#define MM_MLP_PARAMS 5313
+typedef struct mm_mlp mm_mlp;
+
+/* New model, He-uniform weights drawn from seed, zero biases, identity
+ * standardisation. */
+mm_status mm_mlp_create(uint64_t seed, mm_mlp **out);
+
+/* Replace / read the FP32 master parameters (n = MM_MLP_PARAMS); setting
+ * them resets the Adam moments and rounds the compute copy to BF16. */
+mm_status mm_mlp_set_params(mm_mlp *mlp, const float *params, int64_t n);
+mm_status mm_mlp_get_params(mm_mlp *mlp, float *params, int64_t n);
+
+/* Standardisation: x' = (x - mu) / sd per feature (mu, sd [16], sd > 0),
+ * y' = (y - y_mu) / y_sd. */
+mm_status mm_mlp_set_normalisation(mm_mlp *mlp, const float *mu, const float *sd, float y_mu, float y_sd);
+
+/* Mean squared error of the standardised prediction against the
+ * standardised targets y [n] for inputs X [n x 16], and its gradient with
+ * respect to the (BF16) parameters into grad [MM_MLP_PARAMS] (may be NULL). */
+mm_status mm_mlp_loss_grad(mm_mlp *mlp, const float *X, const float *y, int64_t n, float *loss, float *grad,
+                           int64_t grad_cap);
+
+/* Full-batch Adam (beta 0.9 / 0.999, eps 1e-8) for `epochs` steps at
+ * learning rate lr on X [n x 16], y [n]; sets the standardisation from the
+ * data first.  loss_per_epoch [epochs] (may be NULL) receives the loss
+ * before each step. */
+mm_status mm_mlp_train(mm_mlp *mlp, const float *X, const float *y, int64_t n, int32_t epochs, float lr,
+                       float *loss_per_epoch);
+
+/* Predictions in target units for X [n x 16] into out [n]. */
+mm_status mm_mlp_predict(mm_mlp *mlp, const float *X, int64_t n, float *out);
+
+void mm_mlp_destroy(mm_mlp *mlp);
 
 /* Launch configuration chosen for the per-step kernel. */
 typedef struct {

@@ -77,6 +77,10 @@ struct mm_net {
 
     mm_launch_info info{};
 
+    unsigned long long *item_ns = nullptr;
+    std::vector<int32_t> item_neuron0, item_nneuron;   // per work item (host copy)
+    int64_t steps_at_create = 0;
+
     std::vector<int32_t> order;          // internal -> user
     std::vector<int32_t> internal_of;    // user -> internal
     double f_syn = 0.0;
@@ -350,6 +354,10 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
 
     net->N = L.N;
     net->C = L.C;
+    for (const auto &gr : L.groups) {
+        net->item_neuron0.push_back(gr.neuron0);
+        net->item_nneuron.push_back(gr.nneuron);
+    }
     net->nsite = (int64_t)L.site_comp.size();
     net->S = li.S;
     net->R = L.R;
@@ -511,6 +519,10 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.area = net->area32;
         a.gax = net->gax32;
         a.dr = net->dr;
+        if (opt->time_items) {
+            if ((st = zeros(net, &net->item_ns, L.groups.size())) != MM_OK) return st;
+            a.item_ns = net->item_ns;
+        }
         a.stim = net->stim;
         a.user_id = net->user_id;
         a.groups = dgroups;
@@ -884,6 +896,51 @@ mm_status mm_read_kernel_timing(mm_net *net, mm_kernel_times *out, int32_t reset
     if ((st = collect_timing(net)) != MM_OK) return st;
     *out = net->times;
     if (reset) net->times = mm_kernel_times{};
+    return MM_OK;
+}
+
+mm_status mm_neuron_features(const mm_morphologies *morph, float *out, int64_t cap)
+{
+    if (!morph || !out || morph->n_neurons < 1 || !morph->comp_offset || !morph->parent || !morph->length_um ||
+        !morph->diam_um)
+        return MM_EINVAL;
+    const int32_t N = morph->n_neurons;
+    if (cap < (int64_t)N * MM_N_FEATURES) return MM_EINVAL;
+    if (morph->comp_offset[0] != 0) return MM_EINVAL;
+    for (int32_t k = 0; k < N; ++k) {
+        const int64_t b = morph->comp_offset[k], n = morph->comp_offset[k + 1] - b;
+        if (n < 1 || n > INT32_MAX / 2 || morph->parent[b] != -1) return MM_EINVAL;
+        for (int64_t i = 1; i < n; ++i)
+            if (morph->parent[b + i] < 0 || morph->parent[b + i] >= i) return MM_EINVAL;
+        for (int64_t i = 0; i < n; ++i)
+            if (!(morph->length_um[b + i] > 0.0) || !(morph->diam_um[b + i] > 0.0)) return MM_EINVAL;
+    }
+    try {
+        for (int32_t k = 0; k < N; ++k) {
+            const int64_t b = morph->comp_offset[k];
+            mmh::neuron_features((int32_t)(morph->comp_offset[k + 1] - b), morph->parent + b, morph->length_um + b,
+                                 morph->diam_um + b, out + (int64_t)k * MM_N_FEATURES);
+        }
+    } catch (const std::bad_alloc &) {
+        return MM_ENOMEM;
+    }
+    return MM_OK;
+}
+
+mm_status mm_read_neuron_times(mm_net *net, double *out_us, int64_t cap)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    if (!out_us || cap < net->N) return fail(net, MM_EINVAL, "output buffer too small");
+    if (!net->item_ns) return fail(net, MM_EINVAL, "the network was created without time_items");
+    for (int32_t k : net->item_nneuron)
+        if (k != 1) return fail(net, MM_EINVAL, "neuron times need one neuron per work item (group_comps = 1)");
+    if ((st = check_device(net)) != MM_OK) return st;
+    std::vector<unsigned long long> ns(net->item_neuron0.size());
+    MM_CK(net, cudaMemcpy(ns.data(), net->item_ns, ns.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    const double steps = (double)std::max<int64_t>(1, net->steps_done);
+    for (size_t i = 0; i < ns.size(); ++i)
+        out_us[net->order[(size_t)net->item_neuron0[i]]] = (double)ns[i] * 1e-3 / steps;
     return MM_OK;
 }
 

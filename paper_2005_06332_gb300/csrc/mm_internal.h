@@ -128,6 +128,7 @@ struct StepArgs32 {
     const float *area;                // cm^2 [C]
     const float *gax;                 // uS [C], sign bit set at segment tops and somata
     float2 *dr;                       // scratch for giant items: Hines diagonal and rhs
+    unsigned long long *item_ns;      // per work item solve time (ns, summed over steps) or nullptr
     const double *stim;               // nA [N]
     const int32_t *user_id;
     const GroupRec *groups;

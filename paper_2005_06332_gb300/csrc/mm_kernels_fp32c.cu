@@ -132,6 +132,13 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Pull the cache lines of [p, p + bytes) into L1 ahead of a serial walk.
 __device__ __forceinline__ void prefetch_l1(const void *p, int bytes)
 {
@@ -183,6 +190,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         __syncthreads();
         const int gi = s_item;
         if (gi >= a.n_small) break;
+        const unsigned long long t_item = (a.item_ns && tid == 0) ? global_ns() : 0ull;
         const GroupRec G = a.groups[gi];
         const int64_t c0 = G.comp0;
         const int32_t *Vq = a.Vq + c0;
@@ -339,6 +347,10 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             }
             a.Vq[c0 + i] = vq;
         }
+        if (a.item_ns) {  // uniform across the block
+            __syncthreads();
+            if (tid == 0) a.item_ns[gi] += global_ns() - t_item;
+        }
     }
 }
 
@@ -364,6 +376,7 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
         __syncthreads();
         const int gi = s_item;
         if (gi >= a.n_groups) break;
+        const unsigned long long t_item = (a.item_ns && tid == 0) ? global_ns() : 0ull;
         const GroupRec G = a.groups[gi];
         const int64_t c0 = G.comp0;
         const int32_t *Vq = a.Vq + c0;
@@ -523,6 +536,7 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
             }
             __syncthreads();
         }
+        if (a.item_ns && tid == 0) a.item_ns[gi] += global_ns() - t_item;
     }
 }
 

@@ -37,6 +37,95 @@ struct NeuronScratch {
 
 }  // namespace
 
+void neuron_features(int32_t n, const int32_t *parent, const double *L_um, const double *d_um, float *out)
+{
+    // children and depth in the given numbering (parent < child)
+    std::vector<int32_t> nch((size_t)n, 0), depth((size_t)n, 0);
+    for (int32_t i = 1; i < n; ++i) {
+        nch[(size_t)parent[i]]++;
+        depth[(size_t)i] = depth[(size_t)parent[i]] + 1;
+    }
+    int64_t leaves = 0, branch = 0, depth_sum = 0;
+    int32_t depth_max = 0;
+    double area = 0.0, dsum = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        if (nch[(size_t)i] == 0) ++leaves;
+        if (nch[(size_t)i] >= 2) ++branch;
+        depth_sum += depth[(size_t)i];
+        depth_max = std::max(depth_max, depth[(size_t)i]);
+        area += 3.14159265358979323846 * d_um[i] * L_um[i];
+        dsum += d_um[i];
+    }
+    // segments of the depth-first preorder renumbering, their heights and the
+    // critical path of the wave-ordered sweep (as in build_layout)
+    std::vector<int32_t> cstart((size_t)n + 1, 0), clist((size_t)std::max(n - 1, 1)), fill((size_t)n, 0);
+    for (int32_t i = 0; i < n; ++i) cstart[(size_t)i + 1] = cstart[(size_t)i] + nch[(size_t)i];
+    for (int32_t i = 1; i < n; ++i) clist[(size_t)(cstart[(size_t)parent[i]] + fill[(size_t)parent[i]]++)] = i;
+    std::vector<int32_t> newl((size_t)n), oldof((size_t)n), st;
+    st.push_back(0);
+    int32_t next = 0;
+    while (!st.empty()) {
+        const int32_t x = st.back();
+        st.pop_back();
+        newl[(size_t)x] = next;
+        oldof[(size_t)next++] = x;
+        for (int32_t c = cstart[(size_t)x + 1] - 1; c >= cstart[(size_t)x]; --c) st.push_back(clist[(size_t)c]);
+    }
+    std::vector<int32_t> seg_top, seg_len, seg_par, seg_h;
+    std::vector<int32_t> seg_of_bottom((size_t)n, -1);
+    for (int32_t j = 0; j < n; ++j) {
+        const int32_t x = oldof[(size_t)j];
+        const int32_t pj = j == 0 ? -1 : newl[(size_t)parent[x]];
+        const bool cont = j > 0 && pj == j - 1 && nch[(size_t)oldof[(size_t)(j - 1)]] == 1;
+        if (!cont) {
+            seg_top.push_back(j);
+            seg_len.push_back(1);
+            seg_par.push_back(pj);
+            seg_h.push_back(0);
+        } else {
+            seg_len.back()++;
+        }
+    }
+    const int32_t ns = (int32_t)seg_top.size();
+    for (int32_t s = 0; s < ns; ++s) seg_of_bottom[(size_t)(seg_top[(size_t)s] + seg_len[(size_t)s] - 1)] = s;
+    for (int32_t s = ns - 1; s >= 1; --s) {
+        const int32_t ps = seg_of_bottom[(size_t)seg_par[(size_t)s]];
+        if (ps >= 0) seg_h[(size_t)ps] = std::max(seg_h[(size_t)ps], seg_h[(size_t)s] + 1);
+    }
+    int32_t H = 0, maxlen = 0;
+    for (int32_t s = 0; s < ns; ++s) {
+        H = std::max(H, seg_h[(size_t)s]);
+        maxlen = std::max(maxlen, seg_len[(size_t)s]);
+    }
+    std::vector<int32_t> wmax((size_t)H + 1, 0), wcount((size_t)H + 1, 0);
+    for (int32_t s = 0; s < ns; ++s) {
+        wmax[(size_t)seg_h[(size_t)s]] = std::max(wmax[(size_t)seg_h[(size_t)s]], seg_len[(size_t)s]);
+        wcount[(size_t)seg_h[(size_t)s]]++;
+    }
+    int64_t crit = 0;
+    int32_t wwide = 0;
+    for (int32_t w = 0; w <= H; ++w) {
+        crit += wmax[(size_t)w];
+        wwide = std::max(wwide, wcount[(size_t)w]);
+    }
+    out[0] = (float)std::log((double)n);
+    out[1] = (float)std::log1p((double)depth_max);
+    out[2] = (float)std::log1p((double)branch);
+    out[3] = (float)std::log1p((double)leaves);
+    out[4] = (float)std::log1p((double)ns);
+    out[5] = (float)std::log1p((double)(H + 1));
+    out[6] = (float)std::log1p((double)crit);
+    out[7] = (float)std::log1p((double)maxlen);
+    out[8] = (float)((double)n / (double)ns / 100.0);
+    out[9] = (float)std::log1p((double)depth_sum / (double)n);
+    out[10] = (float)std::log(area);
+    out[11] = (float)(dsum / (double)n);
+    out[12] = (float)((double)branch / (double)n);
+    out[13] = (float)std::log1p((double)wwide);
+    out[14] = (float)((double)crit / (double)n);
+    out[15] = (float)std::log1p((double)nch[0]);
+}
+
 std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
 {
     *invalid = true;

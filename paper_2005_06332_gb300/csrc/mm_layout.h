@@ -55,6 +55,10 @@ struct Layout {
     double f_syn = 0.0;                 // fraction of compartments with a synapse
 };
 
+// The MM_N_FEATURES morphology features of one neuron (see mm.h), from its
+// local parent array and cylinders.
+void neuron_features(int32_t n, const int32_t *parent, const double *L_um, const double *d_um, float *out);
+
 // Validates the inputs and builds the layout.  Returns "" on success, else
 // a message; *invalid tells whether the inputs were invalid (vs. unsupported).
 std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid);

@@ -55,7 +55,7 @@ class Allocator(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("schedule", C.c_int32), ("graph_steps", C.c_int32),
                 ("block_threads", C.c_int32), ("group_comps", C.c_int32), ("device", C.c_int32),
-                ("dt_ms", C.c_double), ("spike_capacity", C.c_int64), ("cuda_stream", C.c_void_p),
+                ("time_items", C.c_int32), ("reserved0", C.c_int32), ("dt_ms", C.c_double), ("spike_capacity", C.c_int64), ("cuda_stream", C.c_void_p),
                 ("cost", C.POINTER(C.c_float)), ("allocator", Allocator)]
 
 
@@ -110,6 +110,24 @@ def load(build_if_missing: bool = False):
         L.mm_set_kernel_timing.argtypes = [net_p, C.c_int32]
         L.mm_read_kernel_timing.argtypes = [net_p, P(KernelTimes), C.c_int32]
         L.mm_get_launch_info.argtypes = [net_p, P(LaunchInfo)]
+        L.mm_read_neuron_times.argtypes = [net_p, P(C.c_double), C.c_int64]
+        L.mm_read_neuron_times.restype = C.c_int
+        L.mm_neuron_features.argtypes = [P(Morphologies), P(C.c_float), C.c_int64]
+        L.mm_neuron_features.restype = C.c_int
+        L.mm_mlp_create.argtypes = [C.c_uint64, P(C.c_void_p)]
+        L.mm_mlp_set_params.argtypes = [C.c_void_p, P(C.c_float), C.c_int64]
+        L.mm_mlp_get_params.argtypes = [C.c_void_p, P(C.c_float), C.c_int64]
+        L.mm_mlp_set_normalisation.argtypes = [C.c_void_p, P(C.c_float), P(C.c_float), C.c_float, C.c_float]
+        L.mm_mlp_loss_grad.argtypes = [C.c_void_p, P(C.c_float), P(C.c_float), C.c_int64, P(C.c_float),
+                                       P(C.c_float), C.c_int64]
+        L.mm_mlp_train.argtypes = [C.c_void_p, P(C.c_float), P(C.c_float), C.c_int64, C.c_int32, C.c_float,
+                                   P(C.c_float)]
+        L.mm_mlp_predict.argtypes = [C.c_void_p, P(C.c_float), C.c_int64, P(C.c_float)]
+        L.mm_mlp_destroy.argtypes = [C.c_void_p]
+        L.mm_mlp_destroy.restype = None
+        for name in ("mm_mlp_create", "mm_mlp_set_params", "mm_mlp_get_params", "mm_mlp_set_normalisation",
+                     "mm_mlp_loss_grad", "mm_mlp_train", "mm_mlp_predict"):
+            getattr(L, name).restype = C.c_int
         L.mm_hines_solve.argtypes = [C.c_int32, C.c_int64] + [C.c_void_p] * 8
         L.mm_hines_solve.restype = C.c_int
         L.mm_hines_solve_noalloc.argtypes = [C.c_int32, C.c_int64] + [C.c_void_p] * 8
@@ -136,6 +154,94 @@ def _status_name(s: int) -> str:
 
 def _ptr(a: np.ndarray, ct):
     return a.ctypes.data_as(C.POINTER(ct))
+
+
+N_FEATURES = 16
+
+
+def neuron_features(net) -> np.ndarray:
+    """[n_neurons, 16] morphology features (host computation in the library)."""
+    L = load()
+    off = np.ascontiguousarray(net.comp_offset, np.int64)
+    par = np.ascontiguousarray(net.parent, np.int32)
+    Lu = np.ascontiguousarray(net.length_um, np.float64)
+    Du = np.ascontiguousarray(net.diam_um, np.float64)
+    morph = Morphologies(net.n_neurons, _ptr(off, C.c_int64), _ptr(par, C.c_int32), _ptr(Lu, C.c_double),
+                         _ptr(Du, C.c_double))
+    out = np.empty((net.n_neurons, N_FEATURES), np.float32)
+    st = L.mm_neuron_features(C.byref(morph), _ptr(out, C.c_float), out.size)
+    if st != MM_OK:
+        raise MMError(st, "mm_neuron_features")
+    return out
+
+
+MLP_PARAMS = 5313
+
+
+class MLP:
+    """The learned cost model (16 -> 64 -> 64 -> 1, BF16 weights, FP32
+    accumulation), trained and run by the library's kernels."""
+
+    def __init__(self, seed: int = 0):
+        self._L = load()
+        self._h = C.c_void_p()
+        st = self._L.mm_mlp_create(int(seed), C.byref(self._h))
+        if st != MM_OK:
+            raise MMError(st, "mm_mlp_create")
+
+    def _ok(self, st, what):
+        if st != MM_OK:
+            raise MMError(st, what)
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, np.float32)
+        self._ok(self._L.mm_mlp_set_params(self._h, _ptr(t, C.c_float), t.size), "mm_mlp_set_params")
+
+    def get_params(self) -> np.ndarray:
+        t = np.empty(MLP_PARAMS, np.float32)
+        self._ok(self._L.mm_mlp_get_params(self._h, _ptr(t, C.c_float), t.size), "mm_mlp_get_params")
+        return t
+
+    def set_normalisation(self, mu, sd, y_mu: float, y_sd: float):
+        mu = np.ascontiguousarray(mu, np.float32)
+        sd = np.ascontiguousarray(sd, np.float32)
+        self._ok(self._L.mm_mlp_set_normalisation(self._h, _ptr(mu, C.c_float), _ptr(sd, C.c_float), y_mu, y_sd),
+                 "mm_mlp_set_normalisation")
+
+    def loss_grad(self, X, y):
+        X = np.ascontiguousarray(X, np.float32)
+        y = np.ascontiguousarray(y, np.float32)
+        loss = C.c_float()
+        g = np.empty(MLP_PARAMS, np.float32)
+        self._ok(self._L.mm_mlp_loss_grad(self._h, _ptr(X, C.c_float), _ptr(y, C.c_float), y.size, C.byref(loss),
+                                          _ptr(g, C.c_float), g.size), "mm_mlp_loss_grad")
+        return loss.value, g
+
+    def train(self, X, y, epochs: int, lr: float = 3e-3) -> np.ndarray:
+        X = np.ascontiguousarray(X, np.float32)
+        y = np.ascontiguousarray(y, np.float32)
+        losses = np.empty(max(1, epochs), np.float32)
+        self._ok(self._L.mm_mlp_train(self._h, _ptr(X, C.c_float), _ptr(y, C.c_float), y.size, int(epochs),
+                                      float(lr), _ptr(losses, C.c_float)), "mm_mlp_train")
+        return losses[:epochs]
+
+    def predict(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, np.float32)
+        out = np.empty(X.shape[0], np.float32)
+        self._ok(self._L.mm_mlp_predict(self._h, _ptr(X, C.c_float), X.shape[0], _ptr(out, C.c_float)),
+                 "mm_mlp_predict")
+        return out
+
+    def close(self):
+        if self._h:
+            self._L.mm_mlp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hines_solve(tree_offset, parent, a, b, c, rhs, stream=None):
@@ -188,7 +294,7 @@ class Network:
 
     def __init__(self, net, precision: str = "fp64", cost: Optional[np.ndarray] = None, graph_steps: int = 40,
                  block_threads: int = 0, group_comps: int = 0, spike_capacity: int = 0, device: int = 0,
-                 stream=None, torch_alloc: bool = True):
+                 stream=None, torch_alloc: bool = True, time_items: bool = False):
         L = load()
         self._L = L
         self._h = C.c_void_p()
@@ -220,6 +326,7 @@ class Network:
         opt.device = device
         opt.dt_ms = self.dt
         opt.spike_capacity = spike_capacity
+        opt.time_items = 1 if time_items else 0
         self._cost = None
         if cost is not None:
             self._cost = np.ascontiguousarray(cost, np.float32)
@@ -318,6 +425,11 @@ class Network:
         t = KernelTimes()
         self._check(self._L.mm_read_kernel_timing(self._h, C.byref(t), 1 if reset else 0), "mm_read_kernel_timing")
         return {k: getattr(t, k) for k, _ in KernelTimes._fields_}
+
+    def read_neuron_times(self) -> np.ndarray:
+        out = np.empty(self.n_neurons, np.float64)
+        self._check(self._L.mm_read_neuron_times(self._h, _ptr(out, C.c_double), out.size), "mm_read_neuron_times")
+        return out
 
     def launch_info(self) -> dict:
         li = LaunchInfo()

@@ -1,0 +1,88 @@
+"""The learned cost model's BF16 kernels against the FP64 MLP oracle, its
+training, and the learned work-queue order."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_2005_06332_gb300 import mm, netgen, schedule
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    mm.load(build_if_missing=True)
+
+
+def _theta(rng):
+    t = rng.normal(scale=0.3, size=omlp.N_PARAMS).astype(np.float32)
+    return t
+
+
+def test_loss_and_gradient_match_fp64_oracle():
+    rng = np.random.default_rng(0)
+    theta = _theta(rng)
+    X = rng.normal(size=(257, 16)).astype(np.float32)
+    y = rng.normal(size=257).astype(np.float32)
+    m = mm.MLP(1)
+    try:
+        m.set_params(theta)
+        loss, g = m.loss_grad(X, y)
+    finally:
+        m.close()
+    tb = omlp.bf16(theta)                     # the kernels compute with BF16 weights
+    ref_loss, ref_g = omlp.loss_grad(tb, X.astype(np.float64), y.astype(np.float64))
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    scale = np.max(np.abs(ref_g))
+    assert np.max(np.abs(g - ref_g)) <= 1e-5 * scale
+
+
+def test_prediction_matches_oracle_with_standardisation():
+    rng = np.random.default_rng(3)
+    theta = _theta(rng)
+    X = rng.normal(loc=2.0, scale=3.0, size=(100, 16)).astype(np.float32)
+    mu, sd = X.mean(0), X.std(0)
+    m = mm.MLP(2)
+    try:
+        m.set_params(theta)
+        m.set_normalisation(mu, sd, 1.5, 0.25)
+        p = m.predict(X)
+    finally:
+        m.close()
+    Xs = (X.astype(np.float64) - mu) / sd
+    ref, _ = omlp.forward(omlp.bf16(theta), Xs)
+    np.testing.assert_allclose(p, ref * 0.25 + 1.5, rtol=1e-4, atol=1e-4)
+
+
+def test_training_fits_a_smooth_target():
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(2000, 16)).astype(np.float32)
+    y = (np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2] + 0.3 * X[:, 3]).astype(np.float32)
+    m = mm.MLP(5)
+    try:
+        losses = m.train(X, y, epochs=400, lr=3e-3)
+    finally:
+        m.close()
+    assert losses[-1] < 0.15 * losses[0]
+
+
+def test_cost_order_changes_no_result():
+    """Any work-queue order gives the same voltages (no synapses: neurons are independent)."""
+    net = netgen.make_network(60, size_dist=("loguniform", 20, 600), p_branch=("uniform", 0.02, 0.2),
+                              syn_per_neuron=0, seed=8, stim_nA=(0.3, 0.8))
+    with mm.Network(net, precision="fp32c") as a:
+        a.step(200)
+        va = a.read_voltages()
+    rng = np.random.default_rng(9)
+    with mm.Network(net, precision="fp32c", cost=rng.random(net.n_neurons).astype(np.float32)) as b:
+        b.step(200)
+        vb = b.read_voltages()
+    np.testing.assert_array_equal(va, vb)
+
+
+def test_learned_costs_predict_measured_solve_times():
+    net = netgen.make_config("lognormal100k", n_neurons=1500, syn_per_neuron=10)
+    r = schedule.learn_costs(net, n_timed=1200, steps=30, epochs=500)
+    assert r["cost"].shape == (net.n_neurons,)
+    assert np.all(r["time_us"] > 0)
+    assert r["r2_holdout"] is not None and r["r2_holdout"] > 0.5, r
