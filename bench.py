@@ -177,6 +177,9 @@ def main():
     ap.add_argument("--graph-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--learned", action="store_true",
+                    help="also learn the work-queue order (MLP cost model) and time it against size-sorted")
+    ap.add_argument("--n-timed", type=int, default=5000)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--group-comps", type=int, default=0)
@@ -291,10 +294,38 @@ def main():
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
            "launch": launch}
     g.close()
+    if args.learned:
+        from paper_2005_06332_gb300 import schedule
+        t0 = time.perf_counter()
+        lc = schedule.learn_costs(net, n_timed=args.n_timed, steps=40, epochs=600, device=local)
+        learn_s = time.perf_counter() - t0
+        gl = mm.Network(net, precision=precision, graph_steps=args.graph_steps, device=local,
+                        stream=stream.cuda_stream, cost=lc["cost"], block_threads=args.block_threads,
+                        group_comps=args.group_comps)
+        gl.step(args.warmup)
+        gl.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gl.step(K)
+        e1.record(stream)
+        e1.synchronize()
+        ms_l = e0.elapsed_time(e1) / K
+        gl.close()
+        out["learned_schedule"] = {"ms_per_step": ms_l, "size_sorted_ms_per_step": ms / K,
+                                   "gain": (ms / K) / ms_l - 1.0, "n_timed": int(len(lc["timed"])),
+                                   "r2_holdout": lc["r2_holdout"], "r2_holdout_size_only": lc["r2_holdout_size_only"],
+                                   "final_loss": float(lc["losses"][-1]), "learn_seconds": learn_s,
+                                   "value": net.n_comp * ws / (ms_l * 1e-3)}
     if precision != "fp64" and not args.no_fp64:
         # the plain FP64 path on the same network, same launch configuration
-        g64 = mm.Network(net, precision="fp64", graph_steps=args.graph_steps, device=local,
-                         stream=stream.cuda_stream)
+        try:
+            g64 = mm.Network(net, precision="fp64", graph_steps=args.graph_steps, device=local,
+                             stream=stream.cuda_stream)
+        except mm.MMError as exc:
+            g64 = None
+            out["plain_fp64"] = {"unavailable": str(exc)}
+    if precision != "fp64" and not args.no_fp64 and g64 is not None:
         g64.step(3)
         g64.synchronize()
         k64 = max(10, min(K, 40))
