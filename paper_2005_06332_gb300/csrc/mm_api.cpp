@@ -339,7 +339,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     li.group_comps = opt->group_comps > 0 ? opt->group_comps : kDefaultGroupComps;
     li.max_group_comps = opt->precision == MM_FP64 ? kMaxGroupComps : kMaxGroupComps32;
     li.smem_per_comp = opt->precision == MM_FP64 ? 16 : 12;
-    li.smem_per_seg = opt->precision == MM_FP64 ? 0 : 8;
+    li.smem_per_seg = opt->precision == MM_FP64 ? 0 : 12;
     li.giant_smem_limit = opt->precision == MM_FP64 ? 0 : kGiantSmemLimit;
     mmh::Layout L;
     bool invalid = false;

@@ -11,10 +11,17 @@
 //     compartments are contiguous; one thread block solves one group at a
 //     time, with the group's Hines diagonal and right-hand side in shared
 //     memory;
+//   * the depth-first order visits the deepest child first (deepest: the
+//     longest path to a leaf, in compartments), so that every "path" -- a
+//     segment followed by its deepest child segment, that one's, and so on
+//     down to a leaf -- is one contiguous index range as well;
 //   * the segments of a group are sorted by height (0 = no child segment),
 //     so that all segments of one height ("wave") can be eliminated in
 //     parallel once the lower waves are done (the leaves-to-root sweep of
-//     Algorithm 1), and substituted in the reverse order (root-to-leaves).
+//     Algorithm 1), and substituted in the reverse order (root-to-leaves);
+//   * the paths of a group are sorted by level (0: the path from a soma;
+//     level l + 1: paths that hang off a path of level l), so that the
+//     root-to-leaves substitution can run path by path, one level at a time.
 #pragma once
 #include <stdint.h>
 #include <vector_types.h>
@@ -32,7 +39,7 @@ struct SegRec {
     int32_t neuron;   // soma segment: group-local neuron index; else -1
 };
 
-// Packed form of a segment inside a work item's tree blob (12 bytes;
+// Packed form of a segment inside a work item's tree blob (16 bytes;
 // group-local indices fit 15 bits because a work item holds at most 32767
 // compartments and segments).
 struct SegP {
@@ -42,12 +49,26 @@ struct SegP {
     int16_t nchild;   // number of child segments
     int16_t child0;   // first entry of this segment's children in the blob's child list
     int16_t neuron;   // soma segment: group-local neuron index; else -1
+    int16_t pseg;     // index of the parent segment in the blob; -1 for a soma segment
+    int16_t pad;
+};
+
+// A path of a work item (8 bytes): compartments head .. end-1, contiguous;
+// every compartment after the head has the one before it as its parent.
+struct PathP {
+    int16_t head;     // group-local index of the first compartment
+    int16_t end;      // one past the last compartment (a leaf)
+    int16_t parent;   // group-local parent of head; -1 when head is a soma
+    int16_t neuron;   // path from a soma: group-local neuron index; else -1
 };
 
 // One work item: a run of whole neurons.  Its tree is one contiguous,
 // 16-byte aligned blob in global memory, staged into shared memory with a
 // single bulk copy: SegP[nseg] | int16 child[nchild] | int16 wave_off[nwave+1]
-// (wave w holds segments wave_off[w] .. wave_off[w+1]-1), padded to 16 bytes.
+// (wave w holds segments wave_off[w] .. wave_off[w+1]-1; wave 0 holds the
+// leaf segments) | padding to 8 bytes (at byte path_off:) | PathP[npath] |
+// int16 level_off[nlevel+1] (level l holds paths level_off[l] ..
+// level_off[l+1]-1), padded to 16 bytes.  Giant items carry no paths.
 struct GroupRec {
     int64_t comp0;    // internal index of the first compartment
     int64_t scratch0; // giant items: first entry in the global Hines scratch
@@ -61,6 +82,9 @@ struct GroupRec {
     int32_t nsite;
     int32_t neuron0;  // internal id of the first neuron
     int32_t nneuron;
+    int32_t npath;
+    int32_t nlevel;
+    int32_t path_off; // byte offset of PathP[0] inside the blob
     int32_t pad;
 };
 

@@ -1,9 +1,8 @@
 // mm_kernels_fp32c.cu -- FP32 compensated ("FP32c") kernels (sm_103a).
 //
 // Same step as the FP64 kernel (HH currents, Hines assembly of Eq. 2,
-// Algorithm 1 as segment waves in shared memory, exponential-Euler gates,
-// synaptic decay, soma threshold test), computed in FP32 with the state kept
-// exact between steps:
+// Algorithm 1 in shared memory, exponential-Euler gates, synaptic decay, soma
+// threshold test), computed in FP32 with the state kept exact between steps:
 //   * V is an int32 fixed-point number (2^-23 mV) and each gate a uint32
 //     fixed-point number (2^-32); every step adds an FP32 increment rounded
 //     once, so rounding never accumulates in the state itself;
@@ -154,7 +153,8 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
     // copy), then per compartment the diagonal (after elimination: its
     // reciprocal), the rhs (after substitution: dV) and |g_axial| (staged
     // by phase A, so that the serial sweeps touch only shared memory), then
-    // per segment its contribution to its parent.
+    // per segment its contribution to its parent (diagonal, rhs) and the
+    // number of its child segments still pending in the elimination.
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *smeta = smem_raw;
     float *sd = (float *)(smem_raw + a.smem_meta);
@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
     float *sg = sr + a.smem_comps;
     float *scd = sg + a.smem_comps;
     float *scr = scd + a.smem_segs;
+    int *scnt = (int *)(scr + a.smem_segs);
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_item, s_abort;
 
@@ -198,14 +199,18 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         // A. membrane conductance and current at (V^n, gates^n), plus the
         //    axial terms of every link inside a segment (both ends; a link
         //    (i-1, i) is inside a segment when g_axial[i] has no sign bit).
-        //    Stage |g_axial| for the sweeps.
+        //    Stage |g_axial| for the sweeps.  All reads go through the
+        //    read-only path (nothing here is written by this launch before
+        //    it is read), so that the loads of two iterations overlap.
+#pragma unroll 2
         for (int i = tid; i < G.ncomp; i += NT) {
-            const int32_t vq = Vq[i];
-            const float gs = a.gax[c0 + i];
+            const int32_t vq = __ldg(Vq + i);
+            const float gs = __ldg(a.gax + c0 + i);
             const float g = fabsf(gs);
             sg[i] = g;
-            const float m = mmf::gate_f(a.mq[c0 + i]), h = mmf::gate_f(a.hq[c0 + i]), nn = mmf::gate_f(a.nq[c0 + i]);
-            const float ar = a.area[c0 + i];
+            const float m = mmf::gate_f(__ldg(a.mq + c0 + i)), h = mmf::gate_f(__ldg(a.hq + c0 + i)),
+                        nn = mmf::gate_f(__ldg(a.nq + c0 + i));
+            const float ar = __ldg(a.area + c0 + i);
             const float s = ar * 1e3f;
             const float gna = a.gNa * s * (m * m * m * h);
             const float n2 = nn * nn;
@@ -215,13 +220,13 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             float r = -fmaf(gna, vminus(vq, a.ENa), fmaf(gk, vminus(vq, a.EK), gl * vminus(vq, a.EL)));
             if (!signbit(gs)) {  // link to the parent i-1
                 d += g;
-                r = fmaf(g, mmf::vdiff(Vq[i - 1], vq), r);
+                r = fmaf(g, mmf::vdiff(__ldg(Vq + i - 1), vq), r);
             }
             if (i + 1 < G.ncomp) {
-                const float gc = a.gax[c0 + i + 1];
+                const float gc = __ldg(a.gax + c0 + i + 1);
                 if (!signbit(gc)) {  // link to the child i+1
                     d += gc;
-                    r = fmaf(gc, mmf::vdiff(Vq[i + 1], vq), r);
+                    r = fmaf(gc, mmf::vdiff(__ldg(Vq + i + 1), vq), r);
                 }
             }
             sd[i] = d;
@@ -237,9 +242,12 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         }
         const SegP *segs = (const SegP *)smeta;
         const int16_t *kids = (const int16_t *)(segs + G.nseg);
-        const int16_t *woff = kids + G.nchild;
+        const int16_t *woff = kids + G.nchild;  // wave 0: the leaf segments
 
-        // S. synaptic sites, then decay (sites are distinct compartments)
+        // S. synaptic sites, then decay (sites are distinct compartments).
+        //    Per segment: its pending-child count, and the exact potential
+        //    difference across its top link, V_parent - V_top (for a soma
+        //    segment: the stimulus current), which the elimination needs.
         for (int t = tid; t < G.nsite; t += NT) {
             const int st = G.site0 + t;
             const int c = a.site_comp[st];
@@ -248,69 +256,126 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             sr[c] = fmaf(-g, vminus(Vq[c], a.Esyn), sr[c]);
             a.gsyn[st] = g * a.decay;
         }
+        for (int si = tid; si < G.nseg; si += NT) {
+            const SegP S = segs[si];
+            scnt[si] = S.nchild;
+            scr[si] = S.parent >= 0 ? mmf::vdiff(Vq[S.parent], Vq[S.top]) : (float)a.stim[G.neuron0 + S.neuron];
+        }
         __syncthreads();
 
-        // B. leaves-to-root elimination (Algorithm 1), one segment per thread,
-        //    wave by wave; a segment top adds its link to its parent and
-        //    leaves the parent its contribution.
-        for (int w = 0; w < G.nwave; ++w) {
-            const int sb = woff[w], se = woff[w + 1];
-            for (int si = sb + tid; si < se; si += NT) {
-                const SegP S = segs[si];
-                const int bot = S.top + S.len - 1;
-                float db = sd[bot], rb = sr[bot];
+        // B. leaves-to-root elimination (Algorithm 1) as a dataflow over the
+        //    segments, with no barrier: a thread starts at a leaf segment,
+        //    eliminates it up to its top, leaves the parent segment its
+        //    contribution, and carries on with the parent segment only if
+        //    it was the last of the parent's children to finish.  A thread
+        //    with several leaves finishes all of them before it walks on
+        //    from any but the last; the deferred parent is parked in the
+        //    leaf's own (otherwise unused) pending count.
+        auto eliminate_up = [&](int si, bool may_defer) -> int {
+            SegP S = segs[si];
+            int bot = S.top + S.len - 1;
+            float db = sd[bot], rb = sr[bot];
+            for (int c = 0; c < S.nchild; ++c) {
+                const int cs = kids[S.child0 + c];
+                db += scd[cs];
+                rb += scr[cs];
+            }
+            for (;;) {
+                // links inside the segment are assembled: elimination of j
+                // into its parent j-1 with a = c = -g, eight links at a time
+                // (their operands loaded before any of their stores)
+                for (int j = bot; j > S.top; j -= 8) {
+                    const int cnt = min(8, j - S.top);
+                    float g[8], g2[8], dp[8], rp[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        g[k] = 0.f;
+                        dp[k] = 0.f;
+                        rp[k] = 0.f;
+                        if (k < cnt) {
+                            g[k] = sg[j - k];
+                            dp[k] = sd[j - k - 1];
+                            rp[k] = sr[j - k - 1];
+                        }
+                        g2[k] = g[k] * g[k];
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (k < cnt) {
+                            const float inv = rcp_approx(db);
+                            const float f = g[k] * inv;
+                            sd[j - k] = f;         // x_j = f x_{j-1} + rb / d_j
+                            sr[j - k] = rb * inv;
+                            db = fmaf(-g2[k], inv, dp[k]);
+                            rb = fmaf(f, rb, rp[k]);
+                        }
+                    }
+                }
+                const int t = S.top;
+                const float vt = scr[si];
+                if (S.parent < 0) {  // soma: the stimulus, then its dV
+                    rb += vt;
+                    sr[t] = rb * rcp_approx(db);
+                    return -1;
+                }
+                // the top link to the parent compartment: assembled here, the
+                // top eliminated into the parent segment's bottom
+                const float g = sg[t];
+                db += g;
+                rb = fmaf(g, vt, rb);
+                const float inv = rcp_approx(db);
+                const float f = g * inv;
+                sd[t] = f;
+                sr[t] = rb * inv;
+                scd[si] = fmaf(-f, g, g);
+                scr[si] = fmaf(f, rb, -g * vt);
+                __threadfence_block();
+                const int ps = S.pseg;
+                if (atomicSub(&scnt[ps], 1) != 1) return -1;
+                __threadfence_block();
+                if (may_defer) return ps;
+                // last child in: the parent segment's bottom collects all
+                // contributions (in child-list order) and the walk goes on
+                si = ps;
+                S = segs[si];
+                bot = S.top + S.len - 1;
+                db = sd[bot];
+                rb = sr[bot];
                 for (int c = 0; c < S.nchild; ++c) {
                     const int cs = kids[S.child0 + c];
                     db += scd[cs];
                     rb += scr[cs];
                 }
-                // inside the segment the links are assembled: elimination of
-                // j into its parent j-1 with a = c = -g
-                for (int j = bot; j > S.top; --j) {
-                    const float g = sg[j];
-                    const float inv = rcp_approx(db);
-                    sd[j] = inv;
-                    sr[j] = rb;
-                    const float f = g * inv;
-                    db = fmaf(-f, g, sd[j - 1]);
-                    rb = fmaf(f, rb, sr[j - 1]);
-                }
-                const int t = S.top;
-                if (S.parent >= 0) {
-                    const float g = sg[t];
-                    const float vpt = mmf::vdiff(Vq[S.parent], Vq[t]);
-                    db += g;
-                    rb = fmaf(g, vpt, rb);
-                    const float inv = rcp_approx(db);
-                    sd[t] = inv;
-                    sr[t] = rb;
-                    const float f = g * inv;
-                    scd[si] = fmaf(-f, g, g);
-                    scr[si] = fmaf(f, rb, -g * vpt);
-                } else {
-                    rb += (float)a.stim[G.neuron0 + S.neuron];
-                    const float inv = rcp_approx(db);
-                    sd[t] = inv;
-                    sr[t] = rb * inv;
-                }
             }
-            __syncthreads();
+        };
+        const int nleaf = woff[1];
+        for (int li = tid; li < nleaf; li += NT) {
+            const int ps = eliminate_up(li, li + NT < nleaf);
+            if (ps >= 0) scnt[li] = ps + 1;
         }
+        for (int li = tid; li + NT < nleaf; li += NT) {
+            const int ps = scnt[li] - 1;
+            if (ps >= 0) eliminate_up(ps, false);
+        }
+        __syncthreads();
 
-        // F. root-to-leaves substitution; the soma segment runs the FP64
-        //    soma accumulator and the spike test
-        for (int w = G.nwave - 1; w >= 0; --w) {
-            const int sb = woff[w], se = woff[w + 1];
-            for (int si = sb + tid; si < se; si += NT) {
-                const SegP S = segs[si];
-                const int t = S.top;
+        // F. root-to-leaves substitution path by path, one level at a time
+        //    (a path's head needs its parent, on a path of the level
+        //    before); the path from a soma runs the FP64 soma accumulator and
+        //    the spike test
+        const PathP *paths = (const PathP *)(smeta + G.path_off);
+        const int16_t *loff = (const int16_t *)(paths + G.npath);
+        for (int l = 0; l < G.nlevel; ++l) {
+            for (int pi = loff[l] + tid; pi < loff[l + 1]; pi += NT) {
+                const PathP P = paths[pi];
+                const int h = P.head;
                 float x;
-                if (S.parent >= 0) {
-                    x = fmaf(sg[t], sr[S.parent], sr[t]) * sd[t];
-                    sr[t] = x;
+                if (P.parent >= 0) {
+                    x = fmaf(sd[h], sr[P.parent], sr[h]);
+                    sr[h] = x;
                 } else {
-                    x = sr[t];
-                    const int nrn = G.neuron0 + S.neuron;
+                    x = sr[h];
+                    const int nrn = G.neuron0 + P.neuron;
                     const double v0 = a.Vsoma[nrn], v1 = v0 + (double)x;
                     a.Vsoma[nrn] = v1;
                     if (!isfinite(v1)) atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
@@ -328,9 +393,29 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                         a.ring_nrn[(long long)slot * a.N + pos] = nrn;
                     }
                 }
-                for (int j = t + 1; j < t + S.len; ++j) {
-                    x = fmaf(sg[j], x, sr[j]) * sd[j];
-                    sr[j] = x;
+                // down the path, each compartment's parent is the one before
+                // it: x_j = f_j x_{j-1} + c_j with the coefficients the
+                // elimination left in (sd, sr); eight at a time, operands
+                // loaded before the stores
+                for (int j = h + 1; j < P.end; j += 8) {
+                    const int cnt = min(8, P.end - j);
+                    float r[8], d[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        r[k] = 0.f;
+                        d[k] = 0.f;
+                        if (k < cnt) {
+                            r[k] = sr[j + k];
+                            d[k] = sd[j + k];
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (k < cnt) {
+                            x = fmaf(d[k], x, r[k]);
+                            sr[j + k] = x;
+                        }
+                    }
                 }
             }
             __syncthreads();
@@ -595,7 +680,7 @@ int set_attr_and_occupancy(int smem, int *blocks)
 
 size_t mmk_step_fp32c_smem(int comps, int segs, int meta_bytes)
 {
-    return (size_t)meta_bytes + (size_t)(3 * comps + 2 * segs) * sizeof(float);
+    return (size_t)meta_bytes + (size_t)(3 * comps + 3 * segs) * sizeof(float);
 }
 
 int mmk_launch_giant_fp32c(const StepArgs32 &a, int blocks, void *stream)

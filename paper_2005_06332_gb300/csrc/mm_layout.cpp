@@ -9,10 +9,13 @@
 //      items out first;
 //   2. each tree is renumbered in depth-first preorder, which keeps
 //      parent < child (the numbering Algorithm 1 needs) and makes every
-//      unbranched segment a contiguous index range;
+//      unbranched segment a contiguous index range; the deepest child is
+//      visited first, so that each path (a segment, its deepest child
+//      segment, and so on down to a leaf) is a contiguous range too;
 //   3. consecutive neurons are packed into work items of about
 //      `group_comps` compartments, each with its segments sorted into
-//      height waves for the parallel leaves-to-root / root-to-leaves sweeps;
+//      height waves and its paths sorted into levels, the two schedules of
+//      the parallel leaves-to-root / root-to-leaves sweeps;
 //   4. synapse targets are merged into synaptic sites (one conductance per
 //      compartment that receives synapses) and outgoing synapses are stored
 //      per source neuron, sorted by delay, for delivery.
@@ -31,8 +34,13 @@ namespace {
 std::string msg(const std::ostringstream &o) { return o.str(); }
 
 struct NeuronScratch {
-    std::vector<int32_t> ccount, cstart, clist, newl, oldof, pnew, nch, stack;
-    std::vector<int32_t> seg_top, seg_len, seg_par, seg_height, seg_of_bottom;
+    std::vector<int32_t> ccount, cstart, clist, newl, oldof, pnew, nch, stack, depth;
+    std::vector<int32_t> seg_top, seg_len, seg_par, seg_height, seg_of_bottom, seg_of_top;
+};
+
+// One path of a work item before packing.
+struct PathTmp {
+    int32_t head, end, parent, neuron, level;
 };
 
 }  // namespace
@@ -242,7 +250,8 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
     NeuronScratch ws;
     std::vector<mmk::SegRec> gsegs;
     std::vector<std::vector<int32_t>> gkids;
-    std::vector<int32_t> gheight, perm, newidx;
+    std::vector<int32_t> gheight, gpseg, glevel, perm, newidx;
+    std::vector<PathTmp> gpaths;
     L.max_comps = 0;
     L.max_segs = 0;
     L.max_waves = 0;
@@ -252,6 +261,9 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         gsegs.clear();
         gkids.clear();
         gheight.clear();
+        gpseg.clear();
+        glevel.clear();
+        gpaths.clear();
         for (int32_t k = k0; k < k1; ++k) {
             const int32_t u = L.order[(size_t)k];
             const int64_t ub = in.comp_offset[u];
@@ -273,7 +285,18 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
                     ws.clist[(size_t)(ws.cstart[(size_t)p] + fill[(size_t)p]++)] = i;
                 }
             }
-            // depth-first preorder; the smallest-index child is visited first
+            // depth-first preorder; the deepest child (longest path to a leaf,
+            // in compartments) is visited first, ties by smallest index
+            ws.depth.assign((size_t)n, 1);
+            for (int32_t i = n - 1; i >= 1; --i)
+                ws.depth[(size_t)par[i]] = std::max(ws.depth[(size_t)par[i]], ws.depth[(size_t)i] + 1);
+            for (int32_t x = 0; x < n; ++x) {
+                std::sort(ws.clist.begin() + ws.cstart[(size_t)x], ws.clist.begin() + ws.cstart[(size_t)x + 1],
+                          [&](int32_t a, int32_t b) {
+                              if (ws.depth[(size_t)a] != ws.depth[(size_t)b]) return ws.depth[(size_t)a] > ws.depth[(size_t)b];
+                              return a < b;
+                          });
+            }
             ws.newl.resize((size_t)n);
             ws.oldof.resize((size_t)n);
             ws.stack.clear();
@@ -322,17 +345,42 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
                     gsegs.back().len++;
                 }
             }
+            ws.seg_of_top.assign((size_t)n, -1);
             for (size_t s = s_first; s < gsegs.size(); ++s) {
                 const int32_t bottom = gsegs[s].top + gsegs[s].len - 1 - lb;
                 ws.seg_of_bottom[(size_t)bottom] = (int32_t)s;
+                ws.seg_of_top[(size_t)(gsegs[s].top - lb)] = (int32_t)s;
+                gpseg.push_back(-1);
+                glevel.push_back(0);
             }
             // children and heights (child segments have larger tops than their parents)
             for (size_t s = gsegs.size(); s-- > s_first + 1;) {
                 const int32_t pb = gsegs[s].parent - lb;
                 const int32_t ps = ws.seg_of_bottom[(size_t)pb];
                 if (ps < 0) { e << "internal: segment parent is not a segment bottom"; return msg(e); }
-                gkids[(size_t)ps].push_back((int32_t)s);
+                gkids[(size_t)ps].insert(gkids[(size_t)ps].begin(), (int32_t)s);
                 gheight[(size_t)ps] = std::max(gheight[(size_t)ps], gheight[s] + 1);
+                gpseg[s] = ps;
+            }
+            // paths: a segment heads one unless it is its parent's first
+            // (deepest) child, whose top directly follows the parent's bottom;
+            // a path runs down the first children to a leaf
+            for (size_t s = s_first; s < gsegs.size(); ++s) {
+                const bool head = gsegs[s].parent < 0 || gsegs[s].top != gsegs[s].parent + 1;
+                if (!head) {
+                    glevel[s] = glevel[(size_t)gpseg[s]];
+                    continue;
+                }
+                glevel[s] = gsegs[s].parent < 0 ? 0 : glevel[(size_t)gpseg[s]] + 1;
+                size_t c = s;
+                for (;;) {
+                    const int32_t nb = gsegs[c].top + gsegs[c].len - lb;  // one past the bottom
+                    const int32_t nx = nb < n ? ws.seg_of_top[(size_t)nb] : -1;
+                    if (nx < 0 || gsegs[(size_t)nx].parent != gsegs[c].top + gsegs[c].len - 1) break;
+                    c = (size_t)nx;
+                }
+                gpaths.push_back(PathTmp{gsegs[s].top, gsegs[c].top + gsegs[c].len, gsegs[s].parent, gsegs[s].neuron,
+                                         glevel[s]});
             }
         }
         // sort by (height, longest first, top)
@@ -354,13 +402,22 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         gr.neuron0 = k0;
         gr.nneuron = k1 - k0;
         gr.pad = 0;
+        // paths by (level, longest first, head)
+        std::sort(gpaths.begin(), gpaths.end(), [](const PathTmp &a, const PathTmp &b) {
+            if (a.level != b.level) return a.level < b.level;
+            if (a.end - a.head != b.end - b.head) return a.end - a.head > b.end - b.head;
+            return a.head < b.head;
+        });
+        const int32_t nlevel = gpaths.empty() ? 0 : gpaths.back().level + 1;
         int32_t maxh = 0;
         int64_t nkids = 0;
         for (int32_t i = 0; i < ns; ++i) {
             maxh = std::max(maxh, gheight[(size_t)perm[(size_t)i]]);
             nkids += (int64_t)gkids[(size_t)perm[(size_t)i]].size();
         }
-        const int64_t small_meta = ((int64_t)ns * (int64_t)sizeof(mmk::SegP) + 2 * nkids + 2 * (maxh + 2) + 15) & ~15LL;
+        const int64_t small_path_off = ((int64_t)ns * (int64_t)sizeof(mmk::SegP) + 2 * nkids + 2 * (maxh + 2) + 7) & ~7LL;
+        const int64_t small_meta = (small_path_off + (int64_t)sizeof(mmk::PathP) * (int64_t)gpaths.size() +
+                                    2 * (int64_t)(nlevel + 1) + 15) & ~15LL;
         const int64_t smem_need = small_meta + (int64_t)in.smem_per_comp * gr.ncomp + (int64_t)in.smem_per_seg * ns;
         const bool giant = gr.ncomp > 32767 || ns > 32767 || (in.giant_smem_limit > 0 && smem_need > in.giant_smem_limit);
         if (giant && in.giant_smem_limit <= 0) {
@@ -399,6 +456,8 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
                 q.nchild = (int16_t)gkids[(size_t)sidx].size();
                 q.child0 = (int16_t)kids.size();
                 q.neuron = (int16_t)r.neuron;
+                q.pseg = (int16_t)(gpseg[(size_t)sidx] < 0 ? -1 : newidx[(size_t)gpseg[(size_t)sidx]]);
+                q.pad = 0;
                 for (int32_t c : gkids[(size_t)sidx]) kids.push_back((int16_t)newidx[(size_t)c]);
                 recs[(size_t)i] = q;
             }
@@ -406,6 +465,20 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
             put(recs.data(), recs.size() * sizeof(mmk::SegP));
             put(kids.data(), kids.size() * 2);
             put(w16.data(), w16.size() * 2);
+            blob.resize((blob.size() + 7) & ~(size_t)7, 0);
+            std::vector<mmk::PathP> prec(gpaths.size());
+            std::vector<int16_t> loff((size_t)nlevel + 1, 0);
+            for (size_t i = 0; i < gpaths.size(); ++i) {
+                const PathTmp &q = gpaths[i];
+                prec[i] = mmk::PathP{(int16_t)q.head, (int16_t)q.end, (int16_t)q.parent, (int16_t)q.neuron};
+                loff[(size_t)q.level + 1] = (int16_t)(i + 1);
+            }
+            for (int32_t l = 1; l <= nlevel; ++l) loff[(size_t)l] = std::max(loff[(size_t)l], loff[(size_t)l - 1]);
+            gr.path_off = (int32_t)blob.size();
+            gr.npath = (int32_t)gpaths.size();
+            gr.nlevel = nlevel;
+            put(prec.data(), prec.size() * sizeof(mmk::PathP));
+            put(loff.data(), loff.size() * 2);
         } else {
             std::vector<int32_t> kids;
             std::vector<mmk::SegRec> recs((size_t)ns);
