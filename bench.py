@@ -46,10 +46,12 @@ BYTES_PER_UPDATE = {"fp64": (80.0, 20.0),
                     # FP32c: int32 V and three uint32 gates read + written (32 B),
                     # FP32 area and g_axial read (8 B); per site FP32 g_syn r/w + index
                     "fp32c": (40.0, 12.0)}
-# FP32c splits the step over two kernels; their own algorithmic bytes:
+# FP32c splits the step over several kernels (the solve of each work-item
+# class: regular and large shared-memory items, giant items; then the gate
+# update of all compartments); their own algorithmic bytes:
 #   step (currents, tree solve, V): V r/w 8 + gates read 12 + area, g_axial 8 = 28 B (+12 B per site)
 #   gates (rates and gate update):  V read 4 + gates r/w 24 = 28 B
-KERNEL_BYTES_FP32C = {"step": (28.0, 12.0), "gates": (28.0, 0.0)}
+KERNEL_BYTES_FP32C = {"step": (28.0, 12.0), "big": (28.0, 12.0), "giant": (28.0, 12.0), "gates": (28.0, 0.0)}
 
 
 def _peaks():
@@ -231,7 +233,10 @@ def main():
         dist.barrier()
     G = args.graph_steps
     K = args.steps
-    kps = 2 if precision == "fp64" else 3  # kernels per step (delivery, step[, gates])
+    # kernels per step: delivery, then the solve of each non-empty work-item
+    # class, then (FP32c) the gate update
+    n_reg = launch["work_items"] - launch["big_items"] - launch["giant_items"]
+    kps = 2 if precision == "fp64" else 2 + (n_reg > 0) + (launch["big_items"] > 0) + (launch["giant_items"] > 0)
     launches = (K // G) * (kps * G + 1) + ((K % G > 0) * (kps * (K % G) + 1)) if G > 0 else kps * K + 1
     updates = net.n_comp * K * ws
     value = updates / (ms * 1e-3)
@@ -267,10 +272,17 @@ def main():
     peak, peak_kind = _peaks()
     b0, bsite = BYTES_PER_UPDATE.get(precision, (80.0, 20.0))
     nsite = int(np.unique(net.syn_comp.astype(np.int64) + net.comp_offset[net.syn_dst]).size)
-    kernels = {"step": (step_ms, (b0 * net.n_comp + bsite * nsite) if precision == "fp64" else
-                        KERNEL_BYTES_FP32C["step"][0] * net.n_comp + KERNEL_BYTES_FP32C["step"][1] * nsite),
-               "deliver": (deliver_ms, None)}
-    if precision != "fp64":
+    kernels = {"deliver": (deliver_ms, None)}
+    if precision == "fp64":
+        kernels["step"] = (step_ms, b0 * net.n_comp + bsite * nsite)
+    else:
+        # each solve kernel moves the bytes of the compartments and sites of
+        # its own class (launch info); the gate kernel touches every compartment
+        for cls, (name, key) in enumerate((("step", "step"), ("big", "big"), ("giant", "giant"))):
+            if launch["comps"][cls] > 0:
+                k_ms = kt[f"{key}_kernel_ms"] / max(1, kt[f"{key}_kernel_launches"])
+                kb = KERNEL_BYTES_FP32C[name]
+                kernels[name] = (k_ms, kb[0] * launch["comps"][cls] + kb[1] * launch["sites"][cls])
         gates_ms = kt["gates_kernel_ms"] / max(1, kt["gates_kernel_launches"])
         kernels["gates"] = (gates_ms, KERNEL_BYTES_FP32C["gates"][0] * net.n_comp)
     dom = max((k for k in kernels if kernels[k][1] is not None), key=lambda k: kernels[k][0])

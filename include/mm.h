@@ -202,6 +202,8 @@ typedef struct {
     int64_t gates_kernel_launches;
     double giant_kernel_ms;         /* FP32c giant-neuron solve kernel, summed */
     int64_t giant_kernel_launches;
+    double big_kernel_ms;           /* FP32c per-step kernel on the large shared-memory class, summed */
+    int64_t big_kernel_launches;
 } mm_kernel_times;
 
 /* While enabled (enable != 0), mm_step launches every kernel directly (no
@@ -325,6 +327,17 @@ typedef struct {
     int32_t max_item_segments; /* unbranched segments of the largest work item */
     int32_t max_item_waves;    /* height waves of the deepest work item */
     int32_t giant_items;       /* FP32c work items solved from global memory (too big for shared memory) */
+    /* FP32c work items above the regular shared-memory budget that still fit
+     * one block's shared memory: solved by a second launch of the per-step
+     * kernel, one block per SM (0 items: no such launch) */
+    int32_t big_items;
+    int32_t big_blocks;
+    int32_t big_threads;
+    int32_t big_smem_bytes;
+    int32_t max_big_item_comps;
+    /* compartments and synaptic sites in each class: regular, large, giant */
+    int64_t comps[3];
+    int64_t sites[3];
 } mm_launch_info;
 
 mm_status mm_get_launch_info(const mm_net *net, mm_launch_info *out);

@@ -19,7 +19,9 @@ constexpr int kStepThreads = 256;
 constexpr int kDefaultGroupComps = 4096;
 constexpr int kMaxGroupComps = 8192;
 constexpr int kMaxGroupComps32 = 1 << 30;
-constexpr int kGiantSmemLimit = 110 * 1024;  // FP32c items above this use the giant kernel
+constexpr int kGiantSmemLimit = 110 * 1024;  // FP32c regular class: two blocks per SM
+constexpr int kBigSmemLimit = 224 * 1024;    // FP32c large class (one block per SM); above it: giant kernel
+constexpr int kBigThreads = 1024;
 constexpr size_t kMaxSmem = 227 * 1024;
 
 }  // namespace
@@ -45,11 +47,14 @@ struct mm_net {
     mmk::StepArgs sa{};
     mmk::DeliverArgs da{};
     int step_blocks = 1, step_threads = kStepThreads, deliver_blocks = 1, gates_blocks = 1, giant_blocks = 1;
-    int32_t n_giant = 0;
+    int32_t n_giant = 0, n_small = 0, n_big = 0;
+    int big_blocks = 1;
     int graph_steps = 40;
     cudaGraphExec_t gexec = nullptr;
 
-    mmk::StepArgs32 sa32{};
+    mmk::StepArgs32 sa32{};   // regular shared-memory class
+    mmk::StepArgs32 sa32b{};  // large shared-memory class
+    mmk::StepArgs32 sa32g{};  // giant items
 
     // device arrays (FP64 path)
     double *V = nullptr, *m = nullptr, *h = nullptr, *n = nullptr;
@@ -188,6 +193,9 @@ mm_status collect_timing(mm_net *net)
         } else if (p.kind == 3) {
             net->times.giant_kernel_ms += ms;
             net->times.giant_kernel_launches++;
+        } else if (p.kind == 4) {
+            net->times.big_kernel_ms += ms;
+            net->times.big_kernel_launches++;
         } else if (p.kind == 1) {
             net->times.step_kernel_ms += ms;
             net->times.step_kernel_launches++;
@@ -205,9 +213,21 @@ mm_status collect_timing(mm_net *net)
 mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
 {
     const bool timed = net->timing && s == net->stream;
-    const int kinds = net->precision == MM_FP64 ? 2 : (net->n_giant > 0 ? 4 : 3);
+    // per step: delivery, the solve of each work-item class, then (FP32c)
+    // the gate update at the new voltages of every compartment
+    int kinds[5], nk = 0;
+    kinds[nk++] = 0;
+    if (net->precision == MM_FP64) {
+        kinds[nk++] = 1;
+    } else {
+        if (net->n_small > 0) kinds[nk++] = 1;
+        if (net->n_big > 0) kinds[nk++] = 4;
+        if (net->n_giant > 0) kinds[nk++] = 3;
+        kinds[nk++] = 2;
+    }
     for (int j = 0; j < count; ++j) {
-        for (int kind = 0; kind < kinds; ++kind) {
+        for (int ki = 0; ki < nk; ++ki) {
+            const int kind = kinds[ki];
             mm_net::Pending p{nullptr, nullptr, kind};
             if (timed) {
                 MM_CK(net, take_event(net, &p.a));
@@ -226,10 +246,13 @@ mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
             } else if (kind == 1) {
                 mmk::StepArgs32 sa = net->sa32;
                 sa.step_offset = j;
-                if (net->sa32.n_small > 0)
-                    MM_CKI(net, mmk_launch_step_fp32c(sa, net->step_blocks, net->step_threads, s));
+                MM_CKI(net, mmk_launch_step_fp32c(sa, net->step_blocks, net->step_threads, s));
+            } else if (kind == 4) {
+                mmk::StepArgs32 sa = net->sa32b;
+                sa.step_offset = j;
+                MM_CKI(net, mmk_launch_step_fp32c(sa, net->big_blocks, kBigThreads, s));
             } else if (kind == 3) {
-                mmk::StepArgs32 sa = net->sa32;
+                mmk::StepArgs32 sa = net->sa32g;
                 sa.step_offset = j;
                 MM_CKI(net, mmk_launch_giant_fp32c(sa, net->giant_blocks, s));
             } else {
@@ -341,6 +364,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     li.smem_per_comp = opt->precision == MM_FP64 ? 16 : 12;
     li.smem_per_seg = opt->precision == MM_FP64 ? 0 : 12;
     li.giant_smem_limit = opt->precision == MM_FP64 ? 0 : kGiantSmemLimit;
+    li.big_smem_limit = opt->precision == MM_FP64 ? 0 : kBigSmemLimit;
     mmh::Layout L;
     bool invalid = false;
     std::string m;
@@ -527,7 +551,9 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.user_id = net->user_id;
         a.groups = dgroups;
         a.n_groups = (int32_t)L.groups.size();
-        a.n_small = L.n_small;
+        a.item0 = 0;
+        a.item1 = L.n_small;
+        a.queue = &net->ctl->queue_head;
         a.meta = dmeta;
         a.smem_meta = L.max_meta;
         a.site_comp = dsite;
@@ -574,13 +600,15 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     d.gsyn32 = net->gsyn32;
     d.out_w32 = dout_w32;
 
-    const size_t smem = f64 ? mmk_step_fp64_smem(smem_comps, smem_segs, L.max_meta)
-                            : mmk_step_fp32c_smem(smem_comps, smem_segs, L.max_meta);
+    // FP32c carves each item's shared memory from its own sizes (the largest
+    // per-item need of the class); FP64 uses one carve for all items
+    const size_t smem = f64 ? mmk_step_fp64_smem(smem_comps, smem_segs, L.max_meta) : (size_t)std::max<int64_t>(L.max_smem, 16);
     if (smem > kMaxSmem) return fail(net, MM_ENOTSUP, "a work item needs more shared memory than a block has");
     int threads = opt->block_threads > 0 ? opt->block_threads : (f64 ? kStepThreads : 512);
     if (threads != 128 && threads != 256 && threads != 512 && (f64 || threads != 1024))
         return fail(net, MM_EINVAL, "block_threads must be 128, 256 or 512 (or 1024 for MM_FP32C)");
     net->step_threads = threads;
+    net->sa32.smem_bytes = (int32_t)smem;
     int per_sm = 0;
     if (f64) MM_CKI(net, mmk_step_fp64_blocks_per_sm(threads, (int)smem, &per_sm));
     else MM_CKI(net, mmk_step_fp32c_blocks_per_sm(threads, (int)smem, &per_sm));
@@ -588,8 +616,44 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     int sms = 0;
     MM_CK(net, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, net->device));
     net->step_blocks = std::max(1, std::min(std::max(L.n_small, 1), per_sm * sms));
-    net->n_giant = (int32_t)L.groups.size() - L.n_small;
+    net->n_small = L.n_small;
+    net->n_big = L.n_big;
+    net->n_giant = (int32_t)L.groups.size() - L.n_small - L.n_big;
     net->giant_blocks = std::max(1, std::min(net->n_giant, 4 * sms));
+    if (!f64) {
+        // large class: same kernel, its own queue and shared-memory size
+        mmk::StepArgs32 &b = net->sa32b;
+        b = net->sa32;
+        b.item0 = L.n_small;
+        b.item1 = L.n_small + L.n_big;
+        b.queue = &net->ctl->big_head;
+        b.smem_comps = std::max(L.big_max_comps, 1);
+        b.smem_segs = std::max(L.big_max_segs, 1);
+        b.smem_meta = L.big_max_meta;
+        if (L.n_big > 0) {
+            const size_t bsmem = (size_t)L.big_max_smem;
+            b.smem_bytes = (int32_t)bsmem;
+            if (bsmem > kMaxSmem) return fail(net, MM_ENOTSUP, "a large work item needs more shared memory than a block has");
+            int bper = 0;
+            MM_CKI(net, mmk_step_fp32c_blocks_per_sm(kBigThreads, (int)bsmem, &bper));
+            if (bper < 1) return fail(net, MM_ENOTSUP, "the large-class step kernel does not fit on an SM");
+            net->big_blocks = std::max(1, std::min(L.n_big, bper * sms));
+            net->info.big_items = L.n_big;
+            net->info.big_blocks = net->big_blocks;
+            net->info.big_threads = kBigThreads;
+            net->info.big_smem_bytes = (int32_t)bsmem;
+            net->info.max_big_item_comps = L.big_max_comps;
+            if (threads == kBigThreads) {  // one kernel instance: its limit must cover both classes
+                int tmp = 0;
+                MM_CKI(net, mmk_step_fp32c_blocks_per_sm(threads, (int)std::max(smem, bsmem), &tmp));
+            }
+        }
+        mmk::StepArgs32 &g = net->sa32g;
+        g = net->sa32;
+        g.item0 = L.n_small + L.n_big;
+        g.item1 = (int32_t)L.groups.size();
+        g.queue = &net->ctl->giant_head;
+    }
     net->info.work_items = (int32_t)L.groups.size();
     net->info.blocks = net->step_blocks;
     net->info.threads = threads;
@@ -599,6 +663,11 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     net->info.max_item_segments = L.max_segs;
     net->info.max_item_waves = L.max_waves;
     net->info.giant_items = net->n_giant;
+    for (size_t gi = 0; gi < L.groups.size(); ++gi) {
+        const int cls = (int32_t)gi < L.n_small ? 0 : ((int32_t)gi < L.n_small + L.n_big ? 1 : 2);
+        net->info.comps[cls] += L.groups[gi].ncomp;
+        net->info.sites[cls] += L.groups[gi].nsite;
+    }
     net->deliver_blocks = std::max(1, 2 * sms);
     net->gates_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((L.C + 255) / 256, (int64_t)sms * 8));
     MM_CK(net, cudaStreamSynchronize(net->stream));

@@ -95,7 +95,7 @@ struct DevCtl {
     unsigned int queue_head;        // next work item of the current step
     int err;                        // MMK_ERR_* bits
     unsigned int giant_head;        // next giant work item of the current step
-    unsigned int pad;
+    unsigned int big_head;          // next work item of the large shared-memory class
 };
 
 enum { MMK_ERR_OVERFLOW = 1, MMK_ERR_NUMERIC = 2, MMK_ERR_TIMEOUT = 4 };
@@ -160,7 +160,9 @@ struct StepArgs32 {
     int32_t step_offset;
     const unsigned char *meta;
     int32_t smem_meta;
-    int32_t n_small;                  // items [0, n_small) fit shared memory; the rest are giants
+    int32_t item0, item1;             // this launch's work items: [item0, item1)
+    int32_t smem_bytes;               // dynamic shared memory of the launch (largest item need)
+    unsigned int *queue;              // its work-queue counter (in ctl, reset by the delivery kernel)
     const int32_t *site_comp;
     float *gsyn;                      // per site, uS
     int32_t *ring_nrn;
@@ -219,7 +221,6 @@ int mmk_launch_step_fp64(const mmk::StepArgs &a, int blocks, int threads, void *
 int mmk_step_fp64_blocks_per_sm(int threads, int smem_bytes, int *blocks);
 int mmk_launch_step_fp32c(const mmk::StepArgs32 &a, int blocks, int threads, void *stream);
 int mmk_step_fp32c_blocks_per_sm(int threads, int smem_bytes, int *blocks);
-size_t mmk_step_fp32c_smem(int comps, int segs, int meta_bytes);
 size_t mmk_step_fp64_smem(int comps, int segs, int meta_bytes);
 int mmk_launch_init_fp32c(const mmk::InitArgs &a, void *stream);
 int mmk_launch_gates_fp32c(const mmk::StepArgs32 &a, int blocks, void *stream);

@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(256) deliver_kernel(DeliverArgs a)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctl->queue_head = 0u;
         a.ctl->giant_head = 0u;
+        a.ctl->big_head = 0u;
         a.ring_cnt[n % a.R] = 0;
     }
     for (int k = threadIdx.x; k < a.n_dclass; k += blockDim.x) {

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(256) deliver_fp32c_kernel(DeliverArgs a)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctl->queue_head = 0u;
         a.ctl->giant_head = 0u;
+        a.ctl->big_head = 0u;
         a.ring_cnt[n % a.R] = 0;
     }
     for (int k = threadIdx.x; k < a.n_dclass; k += blockDim.x) {
@@ -149,20 +150,16 @@ __device__ __forceinline__ void prefetch_l1(const void *p, int bytes)
 template <int NT>
 __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
 {
-    // Shared memory of one work item: its tree blob (staged by one bulk
-    // copy), then per compartment the diagonal (after elimination: its
-    // reciprocal), the rhs (after substitution: dV) and |g_axial| (staged
-    // by phase A, so that the serial sweeps touch only shared memory), then
-    // per segment its contribution to its parent (diagonal, rhs) and the
-    // number of its child segments still pending in the elimination.
+    // Shared memory of one work item, carved from the item's own sizes: its
+    // tree blob (staged by one bulk copy), then per compartment the diagonal
+    // (after elimination: the substitution coefficient f), the rhs (after
+    // elimination: c; after substitution: dV) and |g_axial| (staged by
+    // phase A, so that the serial sweeps touch only shared memory), then per
+    // segment its contribution to its parent (diagonal, rhs) and the number
+    // of its child segments still pending in the elimination.  The launch
+    // provides the largest need over its items.
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *smeta = smem_raw;
-    float *sd = (float *)(smem_raw + a.smem_meta);
-    float *sr = sd + a.smem_comps;
-    float *sg = sr + a.smem_comps;
-    float *scd = sg + a.smem_comps;
-    float *scr = scd + a.smem_segs;
-    int *scnt = (int *)(scr + a.smem_segs);
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_item, s_abort;
 
@@ -177,10 +174,10 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
     for (;;) {
         __syncthreads();
         if (tid == 0) {
-            const int item = (int)atomicAdd(&a.ctl->queue_head, 1u);
+            const int item = a.item0 + (int)atomicAdd(a.queue, 1u);
             s_item = item;
             s_abort = 0;
-            if (item < a.n_small) {
+            if (item < a.item1) {
                 const GroupRec *gp = a.groups + item;
                 const uint32_t bytes = (uint32_t)gp->meta_bytes;
                 fence_proxy_async_smem();
@@ -190,11 +187,17 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         }
         __syncthreads();
         const int gi = s_item;
-        if (gi >= a.n_small) break;
+        if (gi >= a.item1) break;
         const unsigned long long t_item = (a.item_ns && tid == 0) ? global_ns() : 0ull;
         const GroupRec G = a.groups[gi];
         const int64_t c0 = G.comp0;
         const int32_t *Vq = a.Vq + c0;
+        float *sd = (float *)(smem_raw + G.meta_bytes);
+        float *sr = sd + G.ncomp;
+        float *sg = sr + G.ncomp;
+        float *scd = sg + G.ncomp;
+        float *scr = scd + G.nseg;
+        int *scnt = (int *)(scr + G.nseg);
 
         // A. membrane conductance and current at (V^n, gates^n), plus the
         //    axial terms of every link inside a segment (both ends; a link
@@ -457,10 +460,10 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_item = a.n_small + (int)atomicAdd(&a.ctl->giant_head, 1u);
+        if (tid == 0) s_item = a.item0 + (int)atomicAdd(a.queue, 1u);
         __syncthreads();
         const int gi = s_item;
-        if (gi >= a.n_groups) break;
+        if (gi >= a.item1) break;
         const unsigned long long t_item = (a.item_ns && tid == 0) ? global_ns() : 0ull;
         const GroupRec G = a.groups[gi];
         const int64_t c0 = G.comp0;
@@ -678,11 +681,6 @@ int set_attr_and_occupancy(int smem, int *blocks)
 
 }  // namespace
 
-size_t mmk_step_fp32c_smem(int comps, int segs, int meta_bytes)
-{
-    return (size_t)meta_bytes + (size_t)(3 * comps + 3 * segs) * sizeof(float);
-}
-
 int mmk_launch_giant_fp32c(const StepArgs32 &a, int blocks, void *stream)
 {
     giant_fp32c_kernel<256><<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
@@ -691,7 +689,7 @@ int mmk_launch_giant_fp32c(const StepArgs32 &a, int blocks, void *stream)
 
 int mmk_launch_step_fp32c(const StepArgs32 &a, int blocks, int threads, void *stream)
 {
-    const size_t smem = mmk_step_fp32c_smem(a.smem_comps, a.smem_segs, a.smem_meta);
+    const size_t smem = (size_t)a.smem_bytes;
     cudaStream_t s = (cudaStream_t)stream;
     switch (threads) {
     case 128: step_fp32c_kernel<128><<<blocks, 128, smem, s>>>(a); break;

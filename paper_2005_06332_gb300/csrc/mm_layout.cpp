@@ -244,7 +244,7 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
     const int32_t G = (int32_t)gstart.size() - 1;
     L.groups.clear();
     L.groups.reserve((size_t)G);
-    std::vector<mmk::GroupRec> giants;
+    std::vector<mmk::GroupRec> bigs, giants;
 
     // 2 + 3b. per group: renumber its neurons, cut segments, sort into waves
     NeuronScratch ws;
@@ -419,7 +419,9 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         const int64_t small_meta = (small_path_off + (int64_t)sizeof(mmk::PathP) * (int64_t)gpaths.size() +
                                     2 * (int64_t)(nlevel + 1) + 15) & ~15LL;
         const int64_t smem_need = small_meta + (int64_t)in.smem_per_comp * gr.ncomp + (int64_t)in.smem_per_seg * ns;
-        const bool giant = gr.ncomp > 32767 || ns > 32767 || (in.giant_smem_limit > 0 && smem_need > in.giant_smem_limit);
+        const bool over = in.giant_smem_limit > 0 && smem_need > in.giant_smem_limit;
+        const bool big = over && in.big_smem_limit > 0 && smem_need <= in.big_smem_limit;
+        const bool giant = gr.ncomp > 32767 || ns > 32767 || (over && !big);
         if (giant && in.giant_smem_limit <= 0) {
             *invalid = false;
             e << "a work item of " << gr.ncomp << " compartments exceeds what this precision holds";
@@ -502,8 +504,15 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         L.meta.insert(L.meta.end(), blob.begin(), blob.end());
         if (giant) {
             giants.push_back(gr);
+        } else if (big) {
+            bigs.push_back(gr);
+            L.big_max_comps = std::max(L.big_max_comps, gr.ncomp);
+            L.big_max_segs = std::max(L.big_max_segs, ns);
+            L.big_max_meta = std::max(L.big_max_meta, gr.meta_bytes);
+            L.big_max_smem = std::max<int64_t>(L.big_max_smem, smem_need);
         } else {
             L.groups.push_back(gr);
+            L.max_smem = std::max<int64_t>(L.max_smem, smem_need);
             L.max_comps = std::max(L.max_comps, gr.ncomp);
             L.max_segs = std::max(L.max_segs, ns);
             L.max_waves = std::max(L.max_waves, gr.nwave);
@@ -511,6 +520,8 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         }
     }
     L.n_small = (int32_t)L.groups.size();
+    L.n_big = (int32_t)bigs.size();
+    L.groups.insert(L.groups.end(), bigs.begin(), bigs.end());
     L.groups.insert(L.groups.end(), giants.begin(), giants.end());
 
     // 4a. synaptic sites: one per compartment that receives a synapse

@@ -23,9 +23,10 @@ struct LayoutInput {
     int32_t group_comps;          // compartment budget of a work item
     int32_t max_group_comps;      // largest neuron accepted
     // shared-memory model of a work item, bytes = meta + smem_per_comp * comps
-    // + smem_per_seg * segments; items above giant_smem_limit become giant
-    // items (0: no giant items, such a neuron is rejected)
-    int32_t smem_per_comp, smem_per_seg, giant_smem_limit;
+    // + smem_per_seg * segments; items above giant_smem_limit go to the large
+    // shared-memory class if they fit big_smem_limit (0: no such class), else
+    // they become giant items (giant_smem_limit 0: no classes at all)
+    int32_t smem_per_comp, smem_per_seg, giant_smem_limit, big_smem_limit;
 };
 
 struct Layout {
@@ -43,7 +44,12 @@ struct Layout {
     std::vector<unsigned char> meta;    // tree blobs (16-byte aligned per work item)
     int32_t max_comps = 0, max_segs = 0;
     int32_t max_waves = 0, max_meta = 0;
-    int32_t n_small = 0;                // items [0, n_small) fit shared memory, the rest are giants
+    // items [0, n_small) fit the regular shared-memory budget, the next n_big
+    // the large one; the rest are giants
+    int32_t n_small = 0, n_big = 0;
+    int32_t big_max_comps = 0, big_max_segs = 0, big_max_meta = 0;
+    // largest shared-memory need (model above) of one item of each class
+    int64_t max_smem = 0, big_max_smem = 0;
     int64_t giant_comps = 0;            // compartments in giant items (size of the Hines scratch)
     std::vector<int32_t> site_comp;     // group-local compartment of each site
     std::vector<int64_t> site_internal; // internal compartment of each site

@@ -63,12 +63,16 @@ class KernelTimes(C.Structure):
     _fields_ = [("step_kernel_ms", C.c_double), ("step_kernel_launches", C.c_int64),
                 ("deliver_kernel_ms", C.c_double), ("deliver_kernel_launches", C.c_int64),
                 ("gates_kernel_ms", C.c_double), ("gates_kernel_launches", C.c_int64),
-                ("giant_kernel_ms", C.c_double), ("giant_kernel_launches", C.c_int64)]
+                ("giant_kernel_ms", C.c_double), ("giant_kernel_launches", C.c_int64),
+                ("big_kernel_ms", C.c_double), ("big_kernel_launches", C.c_int64)]
 
 
 class LaunchInfo(C.Structure):
     _fields_ = [(k, C.c_int32) for k in ("work_items", "blocks", "threads", "blocks_per_sm", "smem_bytes",
-                                          "max_item_comps", "max_item_segments", "max_item_waves", "giant_items")]
+                                          "max_item_comps", "max_item_segments", "max_item_waves", "giant_items",
+                                          "big_items", "big_blocks", "big_threads", "big_smem_bytes",
+                                          "max_big_item_comps")] + [("comps", C.c_int64 * 3),
+                                                                    ("sites", C.c_int64 * 3)]
 
 
 _lock = threading.Lock()
@@ -434,7 +438,7 @@ class Network:
     def launch_info(self) -> dict:
         li = LaunchInfo()
         self._check(self._L.mm_get_launch_info(self._h, C.byref(li)), "mm_get_launch_info")
-        return {k: getattr(li, k) for k, _ in LaunchInfo._fields_}
+        return {k: (list(getattr(li, k)) if k in ("comps", "sites") else getattr(li, k)) for k, _ in LaunchInfo._fields_}
 
     def load_state(self, blob: bytes):
         buf = C.create_string_buffer(blob, len(blob))

@@ -112,29 +112,49 @@ def test_fp32c_mono64_100ms():
     assert np.max(np.abs(V - ref.V)) <= 5 * TOL_V
 
 
-def test_fp32c_giant_items_match_oracle():
-    """Neurons too large for one block's shared memory are solved by the
-    giant kernel from a global scratch; they must agree with the oracle like
-    any other neuron (and the small ones next to them too)."""
-    big = netgen.make_network(2, size_dist=("mono", 15000), p_branch=0.05, syn_per_neuron=0, seed=31,
-                              stim_nA=(1.5, 2.5))
-    small = netgen.make_network(12, size_dist=("loguniform", 20, 400), p_branch=0.1, syn_per_neuron=0, seed=32,
-                                stim_nA=(0.3, 0.8))
-    net = netgen.Network(
-        comp_offset=np.concatenate([big.comp_offset, big.comp_offset[-1] + small.comp_offset[1:]]),
-        parent=np.concatenate([big.parent, small.parent]), length_um=np.concatenate([big.length_um, small.length_um]),
-        diam_um=np.concatenate([big.diam_um, small.diam_um]), stim_nA=np.concatenate([big.stim_nA, small.stim_nA]),
-        syn_src=np.zeros(0, np.int32), syn_dst=np.zeros(0, np.int32), syn_comp=np.zeros(0, np.int32),
-        syn_w=np.zeros(0), syn_delay_ms=np.zeros(0), params=dict(netgen.DEFAULT_PARAMS), dt=0.025)
-    steps = 400
-    ref = oracle.simulate(net, steps)
+def _three_class_network():
+    """One neuron too large for any block's shared memory (giant item), one
+    above the regular shared-memory budget (large class), and small ones;
+    the large neurons are driven hard enough to fire."""
+    parts = [netgen.make_network(1, size_dist=("mono", 20000), p_branch=0.05, syn_per_neuron=0, seed=31,
+                                 stim_nA=(2.0, 2.0)),
+             netgen.make_network(1, size_dist=("mono", 9000), p_branch=0.05, syn_per_neuron=0, seed=33,
+                                 stim_nA=(2.0, 2.0)),
+             netgen.make_network(12, size_dist=("loguniform", 20, 400), p_branch=0.1, syn_per_neuron=0, seed=32,
+                                 stim_nA=(0.3, 0.8))]
+    off = [np.zeros(1, np.int64)]
+    for p in parts:
+        off.append(off[-1][-1] + p.comp_offset[1:])
+    cat = lambda k: np.concatenate([getattr(p, k) for p in parts])
+    return netgen.Network(comp_offset=np.concatenate(off), parent=cat("parent"), length_um=cat("length_um"),
+                          diam_um=cat("diam_um"), stim_nA=cat("stim_nA"), syn_src=np.zeros(0, np.int32),
+                          syn_dst=np.zeros(0, np.int32), syn_comp=np.zeros(0, np.int32), syn_w=np.zeros(0),
+                          syn_delay_ms=np.zeros(0), params=dict(netgen.DEFAULT_PARAMS), dt=0.025)
+
+
+def test_fp32c_all_item_classes_match_oracle():
+    """Regular, large-class and giant work items agree with the oracle on
+    voltages and spikes, and on the gates too: the state after a step is the
+    method's state after that step, compared here in the middle of the giant
+    neuron's upstroke, where one gate update more or less is visible."""
+    net = _three_class_network()
+    full = oracle.simulate(net, 400, record_soma=True)
+    assert full.n_spikes >= 2
+    k = 40 + int(np.argmax(np.diff(full.soma_trace[0][40:]))) + 1  # giant neuron's steepest rise after 1 ms
+    ref = oracle.simulate(net, k)
     with mm.Network(net, precision="fp32c") as g:
-        assert g.launch_info()["giant_items"] == 2
-        g.step(steps)
+        info = g.launch_info()
+        assert info["giant_items"] == 1 and info["big_items"] == 1
+        assert info["comps"] == [int(net.n_comp) - 29000, 9000, 20000]
+        g.step(k)
         V = g.read_voltages()
-        sn, st = g.read_spikes()
+        gates = {w: g.read_state(w) for w in ("m", "h", "n")}
+        g.step(400 - k)
+        sn, _ = g.read_spikes()
     assert np.max(np.abs(V - ref.V)) <= TOL_V
-    assert len(sn) == ref.n_spikes
+    for w, x in gates.items():
+        assert np.max(np.abs(x - getattr(ref, w))) <= 1e-4, w
+    assert len(sn) == full.n_spikes
 
 
 def test_fp32c_checkpoint_resume():
