@@ -185,6 +185,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--group-comps", type=int, default=0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the launch-configuration autotuner (default: tune on a 2M-compartment sample)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -204,6 +206,13 @@ def main():
     torch.cuda.set_device(local)
     mm.load()
     stream = torch.cuda.Stream(device=local)
+    tune = None
+    if not args.no_autotune and not (args.block_threads or args.group_comps):
+        t0 = time.perf_counter()
+        tune = mm.autotune(net, precision=precision, sample_comps=2_000_000, warmup=3, steps=20, device=local,
+                           stream=stream.cuda_stream, graph_steps=args.graph_steps)
+        tune["seconds"] = time.perf_counter() - t0
+        args.block_threads, args.group_comps = tune["block_threads"], tune["group_comps"]
     g = mm.Network(net, precision=precision, graph_steps=args.graph_steps, device=local, stream=stream.cuda_stream,
                    block_threads=args.block_threads, group_comps=args.group_comps)
 
@@ -304,7 +313,7 @@ def main():
                       "l2": f"inputs larger than L2 (state + constants {(48 * net.n_comp) / 1e6:.0f} MB)",
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
-           "launch": launch}
+           "launch": launch, "autotune": tune}
     g.close()
     if args.learned:
         from paper_2005_06332_gb300 import schedule

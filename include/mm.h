@@ -342,6 +342,38 @@ typedef struct {
 
 mm_status mm_get_launch_info(const mm_net *net, mm_launch_info *out);
 
+/* One candidate launch configuration measured by mm_autotune. */
+typedef struct {
+    int32_t block_threads;  /* threads per block of the regular-class step kernel */
+    int32_t group_comps;    /* compartment budget of one work item */
+    mm_status status;       /* MM_OK, or why this candidate could not run */
+    double ms_per_step;     /* mean over the timed steps; < 0 when status != MM_OK */
+} mm_tune_point;
+
+/* Launch-configuration autotuner of the per-step kernel.  The paper balances
+ * its per-neuron tasks by size only (Sec. 4) and has no counterpart; here the
+ * block shape and the work-item size are chosen by measurement.
+ *
+ * Builds a stratified sample of the network (every k-th neuron in size order,
+ * about sample_comps compartments, with the synapses whose two ends are both
+ * in the sample), then for each candidate -- block_threads 256/512/1024
+ * (MM_FP32C) or 128/256/512 (MM_FP64), times group_comps 1024/2048/4096/8192
+ * -- creates the sample network with *opt otherwise unchanged, runs `warmup`
+ * steps and times `steps` steps with CUDA events on opt->cuda_stream (a
+ * library-owned stream when NULL).  *best receives *opt with the fastest
+ * candidate's block_threads and group_comps.  points (cap entries; NULL
+ * allowed when cap == 0) receives the candidates in order, *n_points how many
+ * were written.
+ *
+ * Inputs are as for mm_create_network (host pointers, caller-owned, read
+ * during the call only).  Each candidate's network is created and destroyed
+ * in turn, through opt->allocator.  Synchronous.
+ * Errors: MM_EINVAL for bad arguments or invalid network inputs; MM_ENOTSUP
+ * (or the first candidate's error) when no candidate runs. */
+mm_status mm_autotune(const mm_morphologies *morph, const mm_channel_params *chan, const mm_synapses *syn,
+                      const double *stim_nA, const mm_options *opt, int64_t sample_comps, int32_t warmup,
+                      int32_t steps, mm_tune_point *points, int32_t cap, int32_t *n_points, mm_options *best);
+
 /* Message of the last error on this network ("" if none); never NULL. */
 const char *mm_last_error(const mm_net *net);
 

@@ -114,6 +114,9 @@ def load(build_if_missing: bool = False):
         L.mm_set_kernel_timing.argtypes = [net_p, C.c_int32]
         L.mm_read_kernel_timing.argtypes = [net_p, P(KernelTimes), C.c_int32]
         L.mm_get_launch_info.argtypes = [net_p, P(LaunchInfo)]
+        L.mm_autotune.argtypes = [P(Morphologies), P(ChannelParams), P(Synapses), P(C.c_double), P(Options),
+                                  C.c_int64, C.c_int32, C.c_int32, P(TunePoint), C.c_int32, P(C.c_int32), P(Options)]
+        L.mm_autotune.restype = C.c_int
         L.mm_read_neuron_times.argtypes = [net_p, P(C.c_double), C.c_int64]
         L.mm_read_neuron_times.restype = C.c_int
         L.mm_neuron_features.argtypes = [P(Morphologies), P(C.c_float), C.c_int64]
@@ -293,6 +296,66 @@ class TorchAllocator:
         return sum(t.numel() for t in self.blocks.values())
 
 
+def _marshal(net):
+    """C structs of a netgen.Network (and the arrays they point into, which
+    must stay alive while the structs are used)."""
+    a = dict(
+        off=np.ascontiguousarray(net.comp_offset, np.int64), parent=np.ascontiguousarray(net.parent, np.int32),
+        L=np.ascontiguousarray(net.length_um, np.float64), D=np.ascontiguousarray(net.diam_um, np.float64),
+        src=np.ascontiguousarray(net.syn_src, np.int32), dst=np.ascontiguousarray(net.syn_dst, np.int32),
+        comp=np.ascontiguousarray(net.syn_comp, np.int32), w=np.ascontiguousarray(net.syn_w, np.float64),
+        dl=np.ascontiguousarray(net.syn_delay_ms, np.float64),
+        stim=np.ascontiguousarray(net.stim_nA, np.float64))
+    morph = Morphologies(net.n_neurons, _ptr(a["off"], C.c_int64), _ptr(a["parent"], C.c_int32),
+                         _ptr(a["L"], C.c_double), _ptr(a["D"], C.c_double))
+    p = net.params
+    chan = ChannelParams(p["gNa"], p["gK"], p["gL"], p["ENa"], p["EK"], p["EL"], p["Cm"], p["Ra"], p["v_init"],
+                         p["threshold"])
+    syn = Synapses(len(a["src"]), _ptr(a["src"], C.c_int32), _ptr(a["dst"], C.c_int32), _ptr(a["comp"], C.c_int32),
+                   _ptr(a["w"], C.c_double), _ptr(a["dl"], C.c_double), p["tau_syn"], p["e_syn"])
+    return a, morph, chan, syn
+
+
+class TunePoint(C.Structure):
+    _fields_ = [("block_threads", C.c_int32), ("group_comps", C.c_int32), ("status", C.c_int32),
+                ("ms_per_step", C.c_double)]
+
+
+def autotune(net, precision: str = "fp32c", sample_comps: int = 2_000_000, warmup: int = 3, steps: int = 20,
+             device: int = 0, stream=None, cost: Optional[np.ndarray] = None, graph_steps: int = 40) -> dict:
+    """mm_autotune on a netgen.Network: the fastest (block_threads,
+    group_comps) measured on a stratified sample, and every candidate."""
+    L = load()
+    a, morph, chan, syn = _marshal(net)
+    opt = Options()
+    L.mm_default_options(C.byref(opt))
+    opt.precision = PRECISION[precision]
+    opt.graph_steps = graph_steps
+    opt.device = device
+    opt.dt_ms = float(net.dt)
+    keep = None
+    if cost is not None:
+        keep = np.ascontiguousarray(cost, np.float32)
+        opt.schedule = MM_SCHED_COST
+        opt.cost = _ptr(keep, C.c_float)
+    if stream is not None:
+        opt.cuda_stream = C.c_void_p(int(stream))
+    alloc = TorchAllocator(device)
+    opt.allocator = alloc.struct()
+    pts = (TunePoint * 16)()
+    npts = C.c_int32(0)
+    best = Options()
+    st = L.mm_autotune(C.byref(morph), C.byref(chan), C.byref(syn), _ptr(a["stim"], C.c_double), C.byref(opt),
+                       int(sample_comps), int(warmup), int(steps), pts, 16, C.byref(npts), C.byref(best))
+    if st != MM_OK:
+        raise MMError(st, "mm_autotune failed")
+    del keep
+    points = [{"block_threads": p.block_threads, "group_comps": p.group_comps, "status": _status_name(p.status),
+               "ms_per_step": p.ms_per_step} for p in pts[:npts.value]]
+    return {"block_threads": best.block_threads, "group_comps": best.group_comps, "points": points,
+            "sample_comps": int(sample_comps)}
+
+
 class Network:
     """A network living on one GPU; see include/mm.h for the semantics."""
 
@@ -306,21 +369,8 @@ class Network:
         self.n_comp = net.n_comp
         self.dt = float(net.dt)
         # keep the NumPy inputs alive for the duration of the create call
-        self._in = dict(
-            off=np.ascontiguousarray(net.comp_offset, np.int64), parent=np.ascontiguousarray(net.parent, np.int32),
-            L=np.ascontiguousarray(net.length_um, np.float64), D=np.ascontiguousarray(net.diam_um, np.float64),
-            src=np.ascontiguousarray(net.syn_src, np.int32), dst=np.ascontiguousarray(net.syn_dst, np.int32),
-            comp=np.ascontiguousarray(net.syn_comp, np.int32), w=np.ascontiguousarray(net.syn_w, np.float64),
-            dl=np.ascontiguousarray(net.syn_delay_ms, np.float64),
-            stim=np.ascontiguousarray(net.stim_nA, np.float64))
+        self._in, morph, chan, syn = _marshal(net)
         a = self._in
-        morph = Morphologies(net.n_neurons, _ptr(a["off"], C.c_int64), _ptr(a["parent"], C.c_int32),
-                             _ptr(a["L"], C.c_double), _ptr(a["D"], C.c_double))
-        p = net.params
-        chan = ChannelParams(p["gNa"], p["gK"], p["gL"], p["ENa"], p["EK"], p["EL"], p["Cm"], p["Ra"], p["v_init"],
-                             p["threshold"])
-        syn = Synapses(len(a["src"]), _ptr(a["src"], C.c_int32), _ptr(a["dst"], C.c_int32), _ptr(a["comp"], C.c_int32),
-                       _ptr(a["w"], C.c_double), _ptr(a["dl"], C.c_double), p["tau_syn"], p["e_syn"])
         opt = Options()
         L.mm_default_options(C.byref(opt))
         opt.precision = PRECISION[precision]
