@@ -46,12 +46,12 @@ BYTES_PER_UPDATE = {"fp64": (80.0, 20.0),
                     # FP32c: int32 V and three uint32 gates read + written (32 B),
                     # FP32 area and g_axial read (8 B); per site FP32 g_syn r/w + index
                     "fp32c": (40.0, 12.0)}
-# FP32c splits the step over several kernels (the solve of each work-item
-# class: regular and large shared-memory items, giant items; then the gate
-# update of all compartments); their own algorithmic bytes:
-#   step (currents, tree solve, V): V r/w 8 + gates read 12 + area, g_axial 8 = 28 B (+12 B per site)
-#   gates (rates and gate update):  V read 4 + gates r/w 24 = 28 B
-KERNEL_BYTES_FP32C = {"step": (28.0, 12.0), "big": (28.0, 12.0), "giant": (28.0, 12.0), "gates": (28.0, 0.0)}
+# FP32c splits the step over one solve kernel per work-item class (regular
+# and large shared-memory items, giant items), each also updating the gates
+# of its compartments; their own algorithmic bytes (V and gates read and
+# written, area and g_axial read; per site the conductance read + written
+# and its index): V r/w 8 + gates r/w 24 + area, g_axial 8 = 40 B (+12 B per site)
+KERNEL_BYTES_FP32C = {"step": (40.0, 12.0), "big": (40.0, 12.0), "giant": (40.0, 12.0)}
 
 
 def _peaks():
@@ -245,7 +245,7 @@ def main():
     # kernels per step: delivery, then the solve of each non-empty work-item
     # class, then (FP32c) the gate update
     n_reg = launch["work_items"] - launch["big_items"] - launch["giant_items"]
-    kps = 2 if precision == "fp64" else 2 + (n_reg > 0) + (launch["big_items"] > 0) + (launch["giant_items"] > 0)
+    kps = 2 if precision == "fp64" else 1 + (n_reg > 0) + (launch["big_items"] > 0) + (launch["giant_items"] > 0)
     launches = (K // G) * (kps * G + 1) + ((K % G > 0) * (kps * (K % G) + 1)) if G > 0 else kps * K + 1
     updates = net.n_comp * K * ws
     value = updates / (ms * 1e-3)
@@ -286,14 +286,12 @@ def main():
         kernels["step"] = (step_ms, b0 * net.n_comp + bsite * nsite)
     else:
         # each solve kernel moves the bytes of the compartments and sites of
-        # its own class (launch info); the gate kernel touches every compartment
-        for cls, (name, key) in enumerate((("step", "step"), ("big", "big"), ("giant", "giant"))):
+        # its own class (launch info)
+        for cls, name in enumerate(("step", "big", "giant")):
             if launch["comps"][cls] > 0:
-                k_ms = kt[f"{key}_kernel_ms"] / max(1, kt[f"{key}_kernel_launches"])
+                k_ms = kt[f"{name}_kernel_ms"] / max(1, kt[f"{name}_kernel_launches"])
                 kb = KERNEL_BYTES_FP32C[name]
                 kernels[name] = (k_ms, kb[0] * launch["comps"][cls] + kb[1] * launch["sites"][cls])
-        gates_ms = kt["gates_kernel_ms"] / max(1, kt["gates_kernel_launches"])
-        kernels["gates"] = (gates_ms, KERNEL_BYTES_FP32C["gates"][0] * net.n_comp)
     dom = max((k for k in kernels if kernels[k][1] is not None), key=lambda k: kernels[k][0])
     dom_ms, dom_bytes = kernels[dom]
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9

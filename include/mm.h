@@ -194,12 +194,10 @@ mm_status mm_load_state(mm_net *net, const void *buf, size_t len);
 /* Per-kernel device time, measured with CUDA events recorded on the
  * network's stream around each launch while timing is enabled. */
 typedef struct {
-    double step_kernel_ms;          /* per-step kernel (FP64: everything; FP32c: currents, tree solve, V), summed */
+    double step_kernel_ms;          /* per-step kernel of the regular item class (currents, tree solve, V, gates), summed */
     int64_t step_kernel_launches;
     double deliver_kernel_ms;       /* spike-delivery kernel, summed */
     int64_t deliver_kernel_launches;
-    double gates_kernel_ms;         /* FP32c gate-update kernel, summed (0 for FP64) */
-    int64_t gates_kernel_launches;
     double giant_kernel_ms;         /* FP32c giant-neuron solve kernel, summed */
     int64_t giant_kernel_launches;
     double big_kernel_ms;           /* FP32c per-step kernel on the large shared-memory class, summed */

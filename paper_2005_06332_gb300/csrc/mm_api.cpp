@@ -46,7 +46,7 @@ struct mm_net {
 
     mmk::StepArgs sa{};
     mmk::DeliverArgs da{};
-    int step_blocks = 1, step_threads = kStepThreads, deliver_blocks = 1, gates_blocks = 1, giant_blocks = 1;
+    int step_blocks = 1, step_threads = kStepThreads, deliver_blocks = 1, giant_blocks = 1;
     int32_t n_giant = 0, n_small = 0, n_big = 0;
     int big_blocks = 1;
     int graph_steps = 40;
@@ -196,12 +196,9 @@ mm_status collect_timing(mm_net *net)
         } else if (p.kind == 4) {
             net->times.big_kernel_ms += ms;
             net->times.big_kernel_launches++;
-        } else if (p.kind == 1) {
+        } else {
             net->times.step_kernel_ms += ms;
             net->times.step_kernel_launches++;
-        } else {
-            net->times.gates_kernel_ms += ms;
-            net->times.gates_kernel_launches++;
         }
         net->event_pool.push_back(p.a);
         net->event_pool.push_back(p.b);
@@ -213,9 +210,9 @@ mm_status collect_timing(mm_net *net)
 mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
 {
     const bool timed = net->timing && s == net->stream;
-    // per step: delivery, the solve of each work-item class, then (FP32c)
-    // the gate update at the new voltages of every compartment
-    int kinds[5], nk = 0;
+    // per step: delivery, then the solve of each work-item class (each also
+    // updates the gates of its own compartments at their new voltages)
+    int kinds[4], nk = 0;
     kinds[nk++] = 0;
     if (net->precision == MM_FP64) {
         kinds[nk++] = 1;
@@ -223,7 +220,6 @@ mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
         if (net->n_small > 0) kinds[nk++] = 1;
         if (net->n_big > 0) kinds[nk++] = 4;
         if (net->n_giant > 0) kinds[nk++] = 3;
-        kinds[nk++] = 2;
     }
     for (int j = 0; j < count; ++j) {
         for (int ki = 0; ki < nk; ++ki) {
@@ -255,8 +251,6 @@ mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
                 mmk::StepArgs32 sa = net->sa32g;
                 sa.step_offset = j;
                 MM_CKI(net, mmk_launch_giant_fp32c(sa, net->giant_blocks, s));
-            } else {
-                MM_CKI(net, mmk_launch_gates_fp32c(net->sa32, net->gates_blocks, s));
             }
             if (timed) {
                 MM_CK(net, cudaEventRecord(p.b, s));
@@ -669,7 +663,6 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         net->info.sites[cls] += L.groups[gi].nsite;
     }
     net->deliver_blocks = std::max(1, 2 * sms);
-    net->gates_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((L.C + 255) / 256, (int64_t)sms * 8));
     MM_CK(net, cudaStreamSynchronize(net->stream));
     return MM_OK;
 }

@@ -223,7 +223,6 @@ int mmk_launch_step_fp32c(const mmk::StepArgs32 &a, int blocks, int threads, voi
 int mmk_step_fp32c_blocks_per_sm(int threads, int smem_bytes, int *blocks);
 size_t mmk_step_fp64_smem(int comps, int segs, int meta_bytes);
 int mmk_launch_init_fp32c(const mmk::InitArgs &a, void *stream);
-int mmk_launch_gates_fp32c(const mmk::StepArgs32 &a, int blocks, void *stream);
 int mmk_launch_giant_fp32c(const mmk::StepArgs32 &a, int blocks, void *stream);
 int mmk_launch_deliver_fp32c(const mmk::DeliverArgs &a, int blocks, void *stream);
 int mmk_launch_vq_to_f64(const int32_t *vq, double *dst, int64_t n, void *stream);

@@ -147,6 +147,23 @@ __device__ __forceinline__ void prefetch_l1(const void *p, int bytes)
     for (; c < e; c += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(c));
 }
 
+// Exponential-Euler gate update at V^{n+1} of one compartment (its V is
+// final for this step).
+__device__ __forceinline__ void gate_update(const StepArgs32 &a, int64_t c)
+{
+    const mmf::F2 dt2{a.dt, a.dt_lo};
+    const mmf::Rates r = mmf::hh_rates(a.Vq[c]);
+    a.mq[c] = mmf::gate_step(a.mq[c], r.am, r.bm, dt2);
+    a.hq[c] = mmf::gate_step(a.hq[c], r.ah, r.bh, dt2);
+    a.nq[c] = mmf::gate_step(a.nq[c], r.an, r.bn, dt2);
+}
+
+// Barrier among the first `nthreads` threads of the block only (whole warps).
+__device__ __forceinline__ void solver_sync(int nthreads)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
 {
@@ -158,25 +175,40 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
     // segment its contribution to its parent (diagonal, rhs) and the number
     // of its child segments still pending in the elimination.  The launch
     // provides the largest need over its items.
+    //
+    // Warp roles: the first NS threads ("solver" warps) take the item through
+    // phases A..C, synchronising among themselves with a named barrier; the
+    // last NG threads ("gate" warps) meanwhile update the gates of the
+    // block's previous item at its V^{n+1} (final since that item's phase C).
+    // The two roles meet at the block barriers between items.
+    constexpr int NG = NT / 4;
+    constexpr int NS = NT - NG;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *smeta = smem_raw;
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_item, s_abort;
+    __shared__ long long s_gc0, s_nc0;  // pending gate work: this item's, the next item's
+    __shared__ int s_gncomp, s_nncomp;
 
     const long long n = (long long)a.ctl->step_base + a.step_offset;
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
+        s_abort = 0;
+        s_nc0 = 0;
+        s_nncomp = 0;
     }
     uint32_t parity = 0;
 
     for (;;) {
         __syncthreads();
+        if (s_abort) break;
         if (tid == 0) {
+            s_gc0 = s_nc0;
+            s_gncomp = s_nncomp;
             const int item = a.item0 + (int)atomicAdd(a.queue, 1u);
             s_item = item;
-            s_abort = 0;
             if (item < a.item1) {
                 const GroupRec *gp = a.groups + item;
                 const uint32_t bytes = (uint32_t)gp->meta_bytes;
@@ -188,6 +220,12 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         __syncthreads();
         const int gi = s_item;
         if (gi >= a.item1) break;
+        if (tid >= NS) {  // gate warps: the previous item
+            const int64_t gc0 = s_gc0;
+            const int gncomp = s_gncomp;
+            for (int i = tid - NS; i < gncomp; i += NG) gate_update(a, gc0 + i);
+            continue;
+        }
         const unsigned long long t_item = (a.item_ns && tid == 0) ? global_ns() : 0ull;
         const GroupRec G = a.groups[gi];
         const int64_t c0 = G.comp0;
@@ -206,7 +244,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         //    read-only path (nothing here is written by this launch before
         //    it is read), so that the loads of two iterations overlap.
 #pragma unroll 2
-        for (int i = tid; i < G.ncomp; i += NT) {
+        for (int i = tid; i < G.ncomp; i += NS) {
             const int32_t vq = __ldg(Vq + i);
             const float gs = __ldg(a.gax + c0 + i);
             const float g = fabsf(gs);
@@ -238,10 +276,13 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         // the tree blob must have landed before the sweeps
         if (!mbar_wait_bounded(&bar, parity)) s_abort = 1;
         parity ^= 1u;
-        __syncthreads();
-        if (s_abort) {
-            if (tid == 0) atomicOr(&a.ctl->err, MMK_ERR_TIMEOUT);
-            break;
+        solver_sync(NS);
+        if (s_abort) {  // the whole block leaves at the next item boundary
+            if (tid == 0) {
+                atomicOr(&a.ctl->err, MMK_ERR_TIMEOUT);
+                s_nncomp = 0;  // the gate warps have done the pending item
+            }
+            continue;
         }
         const SegP *segs = (const SegP *)smeta;
         const int16_t *kids = (const int16_t *)(segs + G.nseg);
@@ -251,7 +292,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         //    Per segment: its pending-child count, and the exact potential
         //    difference across its top link, V_parent - V_top (for a soma
         //    segment: the stimulus current), which the elimination needs.
-        for (int t = tid; t < G.nsite; t += NT) {
+        for (int t = tid; t < G.nsite; t += NS) {
             const int st = G.site0 + t;
             const int c = a.site_comp[st];
             const float g = a.gsyn[st];
@@ -259,12 +300,12 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             sr[c] = fmaf(-g, vminus(Vq[c], a.Esyn), sr[c]);
             a.gsyn[st] = g * a.decay;
         }
-        for (int si = tid; si < G.nseg; si += NT) {
+        for (int si = tid; si < G.nseg; si += NS) {
             const SegP S = segs[si];
             scnt[si] = S.nchild;
             scr[si] = S.parent >= 0 ? mmf::vdiff(Vq[S.parent], Vq[S.top]) : (float)a.stim[G.neuron0 + S.neuron];
         }
-        __syncthreads();
+        solver_sync(NS);
 
         // B. leaves-to-root elimination (Algorithm 1) as a dataflow over the
         //    segments, with no barrier: a thread starts at a leaf segment,
@@ -352,15 +393,15 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             }
         };
         const int nleaf = woff[1];
-        for (int li = tid; li < nleaf; li += NT) {
-            const int ps = eliminate_up(li, li + NT < nleaf);
+        for (int li = tid; li < nleaf; li += NS) {
+            const int ps = eliminate_up(li, li + NS < nleaf);
             if (ps >= 0) scnt[li] = ps + 1;
         }
-        for (int li = tid; li + NT < nleaf; li += NT) {
+        for (int li = tid; li + NS < nleaf; li += NS) {
             const int ps = scnt[li] - 1;
             if (ps >= 0) eliminate_up(ps, false);
         }
-        __syncthreads();
+        solver_sync(NS);
 
         // F. root-to-leaves substitution path by path, one level at a time
         //    (a path's head needs its parent, on a path of the level
@@ -369,7 +410,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         const PathP *paths = (const PathP *)(smeta + G.path_off);
         const int16_t *loff = (const int16_t *)(paths + G.npath);
         for (int l = 0; l < G.nlevel; ++l) {
-            for (int pi = loff[l] + tid; pi < loff[l + 1]; pi += NT) {
+            for (int pi = loff[l] + tid; pi < loff[l + 1]; pi += NS) {
                 const PathP P = paths[pi];
                 const int h = P.head;
                 float x;
@@ -421,12 +462,11 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                     }
                 }
             }
-            __syncthreads();
+            solver_sync(NS);
         }
 
-        // C. V^{n+1} = V^n + dV (exact in fixed point); the gates follow in
-        //    gates_fp32c_kernel
-        for (int i = tid; i < G.ncomp; i += NT) {
+        // C. V^{n+1} = V^n + dV (exact in fixed point)
+        for (int i = tid; i < G.ncomp; i += NS) {
             const int32_t vold = Vq[i];
             int32_t vq;
             if (!mmf::v_add(vold, sr[i], &vq)) {
@@ -435,12 +475,26 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             }
             a.Vq[c0 + i] = vq;
         }
-        if (a.item_ns) {  // uniform across the block
-            __syncthreads();
+        if (a.item_ns) {  // uniform across the solver warps
+            solver_sync(NS);
             if (tid == 0) a.item_ns[gi] += global_ns() - t_item;
         }
+        // this item's gates are the gate warps' work during the next item
+        // (its V^{n+1} is visible to the block after the barrier at the top
+        // of the loop)
+        if (tid == 0) {
+            s_nc0 = c0;
+            s_nncomp = G.ncomp;
+        }
+    }
+    // the last item's gates, by the whole block (s_nc0 / s_nncomp name it)
+    {
+        const int64_t gc0 = s_nc0;
+        const int gncomp = s_nncomp;
+        for (int i = tid; i < gncomp; i += NT) gate_update(a, gc0 + i);
     }
 }
+
 
 template <int NT>
 __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
@@ -624,24 +678,12 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
             }
             __syncthreads();
         }
-        if (a.item_ns && tid == 0) a.item_ns[gi] += global_ns() - t_item;
-    }
-}
-
-// Exponential-Euler gate update at V^{n+1} for every compartment: a pure
-// streaming kernel (no shared memory, no barriers), one compartment per
-// thread, so that the arithmetic-heavy rate functions run at full occupancy
-// apart from the latency-bound tree solve.
-__global__ void __launch_bounds__(256) gates_fp32c_kernel(const int32_t *__restrict__ Vq, uint32_t *__restrict__ mq,
-                                                          uint32_t *__restrict__ hq, uint32_t *__restrict__ nq,
-                                                          int64_t C, float dt, float dt_lo)
-{
-    const mmf::F2 dt2{dt, dt_lo};
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C; i += (int64_t)gridDim.x * blockDim.x) {
-        const mmf::Rates r = mmf::hh_rates(Vq[i]);
-        mq[i] = mmf::gate_step(mq[i], r.am, r.bm, dt2);
-        hq[i] = mmf::gate_step(hq[i], r.ah, r.bh, dt2);
-        nq[i] = mmf::gate_step(nq[i], r.an, r.bn, dt2);
+        // gates at V^{n+1} (final after the last wave's barrier)
+        for (int i = tid; i < G.ncomp; i += NT) gate_update(a, c0 + i);
+        if (a.item_ns) {
+            __syncthreads();
+            if (tid == 0) a.item_ns[gi] += global_ns() - t_item;
+        }
     }
 }
 
@@ -710,12 +752,6 @@ int mmk_step_fp32c_blocks_per_sm(int threads, int smem_bytes, int *blocks)
     case 1024: return set_attr_and_occupancy<1024>(smem_bytes, blocks);
     default: return (int)cudaErrorInvalidValue;
     }
-}
-
-int mmk_launch_gates_fp32c(const StepArgs32 &a, int blocks, void *stream)
-{
-    gates_fp32c_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(a.Vq, a.mq, a.hq, a.nq, a.C, a.dt, a.dt_lo);
-    return (int)cudaGetLastError();
 }
 
 int mmk_launch_init_fp32c(const InitArgs &a, void *stream)

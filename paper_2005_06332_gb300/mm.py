@@ -62,7 +62,6 @@ class Options(C.Structure):
 class KernelTimes(C.Structure):
     _fields_ = [("step_kernel_ms", C.c_double), ("step_kernel_launches", C.c_int64),
                 ("deliver_kernel_ms", C.c_double), ("deliver_kernel_launches", C.c_int64),
-                ("gates_kernel_ms", C.c_double), ("gates_kernel_launches", C.c_int64),
                 ("giant_kernel_ms", C.c_double), ("giant_kernel_launches", C.c_int64),
                 ("big_kernel_ms", C.c_double), ("big_kernel_launches", C.c_int64)]
 
