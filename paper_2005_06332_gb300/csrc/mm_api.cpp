@@ -355,8 +355,13 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     li.dt = opt->dt_ms;
     li.group_comps = opt->group_comps > 0 ? opt->group_comps : kDefaultGroupComps;
     li.max_group_comps = opt->precision == MM_FP64 ? kMaxGroupComps : kMaxGroupComps32;
+    // shared memory per item: FP64 d and rhs per compartment (16 B); FP32c
+    // d, rhs and |g| per compartment (12 B) and per path its contribution
+    // to the parent (d, rhs) and the potential across its head link (12 B)
     li.smem_per_comp = opt->precision == MM_FP64 ? 16 : 12;
-    li.smem_per_seg = opt->precision == MM_FP64 ? 0 : 12;
+    li.smem_per_seg = 0;
+    li.path_items = opt->precision != MM_FP64;
+    li.smem_per_path = opt->precision == MM_FP64 ? 0 : 12;
     li.giant_smem_limit = opt->precision == MM_FP64 ? 0 : kGiantSmemLimit;
     li.big_smem_limit = opt->precision == MM_FP64 ? 0 : kBigSmemLimit;
     mmh::Layout L;

@@ -53,22 +53,41 @@ struct SegP {
     int16_t pad;
 };
 
-// A path of a work item (8 bytes): compartments head .. end-1, contiguous;
-// every compartment after the head has the one before it as its parent.
-struct PathP {
+// FP32c work items are solved path by path, one warp per neuron.  Per
+// neuron of an item (8 bytes): its paths are path0 .. path0 + npath - 1 of the
+// item, sorted by level (0: the path from the soma) and, within a level,
+// longest first; level l holds paths loffs[loff0 + l] .. loffs[loff0 + l + 1] - 1.
+struct NrnQ {
+    int16_t path0;
+    int16_t npath;
+    int16_t nlevel;
+    int16_t loff0;
+};
+
+// A path of an FP32c work item (8 bytes).
+struct PathQ {
     int16_t head;     // group-local index of the first compartment
     int16_t end;      // one past the last compartment (a leaf)
     int16_t parent;   // group-local parent of head; -1 when head is a soma
-    int16_t neuron;   // path from a soma: group-local neuron index; else -1
+    int16_t neuron;   // group-local neuron index
 };
+
+// One fold-list entry (4 bytes): low half a path's index in the item, high
+// half the compartment its head hangs off.  The fold list holds the same
+// paths as the path table, level by level (same level offsets), each level
+// sorted by that compartment (deepest first, then head), so that paths
+// sharing a parent compartment are adjacent.
+typedef uint32_t KidQ;
 
 // One work item: a run of whole neurons.  Its tree is one contiguous,
 // 16-byte aligned blob in global memory, staged into shared memory with a
-// single bulk copy: SegP[nseg] | int16 child[nchild] | int16 wave_off[nwave+1]
-// (wave w holds segments wave_off[w] .. wave_off[w+1]-1; wave 0 holds the
-// leaf segments) | padding to 8 bytes (at byte path_off:) | PathP[npath] |
-// int16 level_off[nlevel+1] (level l holds paths level_off[l] ..
-// level_off[l+1]-1), padded to 16 bytes.  Giant items carry no paths.
+// single bulk copy.  FP64 items: SegP[nseg] | int16 child[nchild] |
+// int16 wave_off[nwave+1] (wave w holds segments wave_off[w] ..
+// wave_off[w+1]-1; wave 0 holds the leaf segments), padded to 16 bytes.
+// FP32c items: NrnQ[nneuron] | PathQ[npath] (at byte path_off) |
+// KidQ[npath] (fold list, at fold_off) | int16 loffs[] (at loffs_off),
+// padded to 16 bytes.  Giant items (FP32c, beyond shared memory): SegRec[nseg] |
+// int32 child[nchild] | int32 wave_off[nwave+1].
 struct GroupRec {
     int64_t comp0;    // internal index of the first compartment
     int64_t scratch0; // giant items: first entry in the global Hines scratch
@@ -83,9 +102,10 @@ struct GroupRec {
     int32_t neuron0;  // internal id of the first neuron
     int32_t nneuron;
     int32_t npath;
-    int32_t nlevel;
-    int32_t path_off; // byte offset of PathP[0] inside the blob
-    int32_t pad;
+    int32_t nlevel;   // FP32c: the largest number of path levels of a neuron of the item
+    int32_t path_off; // FP32c: byte offset of PathQ[0] inside the blob
+    int32_t fold_off; // FP32c: byte offset of the fold list
+    int32_t loffs_off;// FP32c: byte offset of the level offsets
 };
 
 // Small device-side control block.
@@ -150,7 +170,9 @@ struct StepArgs32 {
     uint32_t *mq, *hq, *nq;           // [C]
     double *Vsoma;                    // [N] FP64 soma voltage accumulator
     const float *area;                // cm^2 [C]
-    const float *gax;                 // uS [C], sign bit set at segment tops and somata
+    const float *gax;                 // uS [C], sign bit set where the link to the parent is not
+                                      // assembled by the per-compartment pass: path heads (somata
+                                      // included) of shared-memory items, segment tops of giants
     float2 *dr;                       // scratch for giant items: Hines diagonal and rhs
     unsigned long long *item_ns;      // per work item solve time (ns, summed over steps) or nullptr
     const double *stim;               // nA [N]

@@ -158,6 +158,24 @@ __device__ __forceinline__ void gate_update(const StepArgs32 &a, int64_t c)
     a.nq[c] = mmf::gate_step(a.nq[c], r.an, r.bn, dt2);
 }
 
+// Gate updates of the compartments pc0 .. pc0 + pn - 1, in chunks of
+// kGateChunk claimed by whole warps from the shared counter *next until none
+// is left.
+constexpr int kGateChunk = 64;
+
+__device__ __forceinline__ void gate_chunks(const StepArgs32 &a, int64_t pc0, int pn, int *next, int lane)
+{
+    for (;;) {
+        int ch = 0;
+        if (lane == 0) ch = atomicAdd(next, 1);
+        ch = __shfl_sync(0xFFFFFFFFu, ch, 0);
+        const int i0 = ch * kGateChunk;
+        if (i0 >= pn) break;
+        const int i1 = min(i0 + kGateChunk, pn);
+        for (int i = i0 + lane; i < i1; i += 32) gate_update(a, pc0 + i);
+    }
+}
+
 // Barrier among the first `nthreads` threads of the block only (whole warps).
 __device__ __forceinline__ void solver_sync(int nthreads)
 {
@@ -171,24 +189,26 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
     // tree blob (staged by one bulk copy), then per compartment the diagonal
     // (after elimination: the substitution coefficient f), the rhs (after
     // elimination: c; after substitution: dV) and |g_axial| (staged by
-    // phase A, so that the serial sweeps touch only shared memory), then per
-    // segment its contribution to its parent (diagonal, rhs) and the number
-    // of its child segments still pending in the elimination.  The launch
-    // provides the largest need over its items.
+    // phase A, so that the sweeps touch only shared memory), then per path
+    // its contribution to its parent compartment (diagonal, rhs) and the
+    // exact potential difference across its head link (for the path from a
+    // soma: the stimulus current).  The launch provides the largest need
+    // over its items.
     //
-    // Warp roles: the first NS threads ("solver" warps) take the item through
-    // phases A..C, synchronising among themselves with a named barrier; the
-    // last NG threads ("gate" warps) meanwhile update the gates of the
-    // block's previous item at its V^{n+1} (final since that item's phase C).
-    // The two roles meet at the block barriers between items.
-    constexpr int NG = NT / 4;
-    constexpr int NS = NT - NG;
+    // Warp roles: all warps run the streaming phases (A, S, C) of an item.
+    // In the sweeps each warp takes whole neurons of the item, one lane per
+    // path, and synchronises only with itself; warps without a neuron, and
+    // each sweeping warp once its neurons are done, update the gates of the
+    // block's previous item (its V^{n+1} is final since that item's phase
+    // C) in chunks claimed from a shared counter, so that the arithmetic of
+    // the gates fills the issue slots the latency-bound sweeps leave.
+    constexpr int NS = NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *smeta = smem_raw;
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_item, s_abort;
-    __shared__ long long s_gc0, s_nc0;  // pending gate work: this item's, the next item's
-    __shared__ int s_gncomp, s_nncomp;
+    __shared__ long long s_pc0;  // pending gate work: the previous item's compartments
+    __shared__ int s_pn, s_gchunk;
 
     const long long n = (long long)a.ctl->step_base + a.step_offset;
     const int tid = threadIdx.x;
@@ -196,8 +216,9 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         mbar_init(&bar, 1);
         fence_mbar_init();
         s_abort = 0;
-        s_nc0 = 0;
-        s_nncomp = 0;
+        s_pc0 = 0;
+        s_pn = 0;
+        s_gchunk = 0;
     }
     uint32_t parity = 0;
 
@@ -205,8 +226,6 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         __syncthreads();
         if (s_abort) break;
         if (tid == 0) {
-            s_gc0 = s_nc0;
-            s_gncomp = s_nncomp;
             const int item = a.item0 + (int)atomicAdd(a.queue, 1u);
             s_item = item;
             if (item < a.item1) {
@@ -220,12 +239,6 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         __syncthreads();
         const int gi = s_item;
         if (gi >= a.item1) break;
-        if (tid >= NS) {  // gate warps: the previous item
-            const int64_t gc0 = s_gc0;
-            const int gncomp = s_gncomp;
-            for (int i = tid - NS; i < gncomp; i += NG) gate_update(a, gc0 + i);
-            continue;
-        }
         const unsigned long long t_item = (a.item_ns && tid == 0) ? global_ns() : 0ull;
         const GroupRec G = a.groups[gi];
         const int64_t c0 = G.comp0;
@@ -234,12 +247,12 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         float *sr = sd + G.ncomp;
         float *sg = sr + G.ncomp;
         float *scd = sg + G.ncomp;
-        float *scr = scd + G.nseg;
-        int *scnt = (int *)(scr + G.nseg);
+        float *scr = scd + G.npath;
+        float *svt = scr + G.npath;
 
         // A. membrane conductance and current at (V^n, gates^n), plus the
-        //    axial terms of every link inside a segment (both ends; a link
-        //    (i-1, i) is inside a segment when g_axial[i] has no sign bit).
+        //    axial terms of every link inside a path (both ends; a link
+        //    (i-1, i) is inside a path when g_axial[i] has no sign bit).
         //    Stage |g_axial| for the sweeps.  All reads go through the
         //    read-only path (nothing here is written by this launch before
         //    it is read), so that the loads of two iterations overlap.
@@ -278,20 +291,18 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         parity ^= 1u;
         solver_sync(NS);
         if (s_abort) {  // the whole block leaves at the next item boundary
-            if (tid == 0) {
-                atomicOr(&a.ctl->err, MMK_ERR_TIMEOUT);
-                s_nncomp = 0;  // the gate warps have done the pending item
-            }
+            if (tid == 0) atomicOr(&a.ctl->err, MMK_ERR_TIMEOUT);
             continue;
         }
-        const SegP *segs = (const SegP *)smeta;
-        const int16_t *kids = (const int16_t *)(segs + G.nseg);
-        const int16_t *woff = kids + G.nchild;  // wave 0: the leaf segments
+        const NrnQ *nrns = (const NrnQ *)smeta;
+        const PathQ *paths = (const PathQ *)(smeta + G.path_off);
+        const KidQ *fold = (const KidQ *)(smeta + G.fold_off);
+        const int16_t *loffs = (const int16_t *)(smeta + G.loffs_off);
 
         // S. synaptic sites, then decay (sites are distinct compartments).
-        //    Per segment: its pending-child count, and the exact potential
-        //    difference across its top link, V_parent - V_top (for a soma
-        //    segment: the stimulus current), which the elimination needs.
+        //    Per path: the exact potential difference across its head link,
+        //    V_parent - V_head (for the path from a soma: the stimulus
+        //    current), which the elimination needs.
         for (int t = tid; t < G.nsite; t += NS) {
             const int st = G.site0 + t;
             const int c = a.site_comp[st];
@@ -300,170 +311,177 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             sr[c] = fmaf(-g, vminus(Vq[c], a.Esyn), sr[c]);
             a.gsyn[st] = g * a.decay;
         }
-        for (int si = tid; si < G.nseg; si += NS) {
-            const SegP S = segs[si];
-            scnt[si] = S.nchild;
-            scr[si] = S.parent >= 0 ? mmf::vdiff(Vq[S.parent], Vq[S.top]) : (float)a.stim[G.neuron0 + S.neuron];
+        for (int pi = tid; pi < G.npath; pi += NS) {
+            const PathQ P = paths[pi];
+            svt[pi] = P.parent >= 0 ? mmf::vdiff(Vq[P.parent], Vq[P.head]) : (float)a.stim[G.neuron0 + P.neuron];
         }
         solver_sync(NS);
 
-        // B. leaves-to-root elimination (Algorithm 1) as a dataflow over the
-        //    segments, with no barrier: a thread starts at a leaf segment,
-        //    eliminates it up to its top, leaves the parent segment its
-        //    contribution, and carries on with the parent segment only if
-        //    it was the last of the parent's children to finish.  A thread
-        //    with several leaves finishes all of them before it walks on
-        //    from any but the last; the deferred parent is parked in the
-        //    leaf's own (otherwise unused) pending count.
-        auto eliminate_up = [&](int si, bool may_defer) -> int {
-            SegP S = segs[si];
-            int bot = S.top + S.len - 1;
-            float db = sd[bot], rb = sr[bot];
-            for (int c = 0; c < S.nchild; ++c) {
-                const int cs = kids[S.child0 + c];
-                db += scd[cs];
-                rb += scr[cs];
+        // B. leaves-to-root elimination (Algorithm 1) path by path, from the
+        //    deepest level up: every compartment of a path has the one
+        //    before it as its parent, so a path is one chain from its leaf
+        //    up to its head (links inside a path are assembled: a = c = -g),
+        //    eight compartments at a time with their operands loaded before
+        //    any of their stores.  The head is then eliminated into its
+        //    parent compartment through the path's slot; once a level is
+        //    done, the slots of the paths sharing a parent compartment are
+        //    summed in fold-list order and added to that compartment's
+        //    diagonal and rhs.  The elimination leaves the substitution
+        //    coefficients x_j = f_j x_{j-1} + c_j.
+        auto eliminate_path = [&](int pi) {
+            const PathQ P = paths[pi];
+            const int h = P.head;
+            int j = P.end - 1;
+            float db = sd[j], rb = sr[j];
+            for (; j > h; j -= 8) {
+                const int cnt = min(8, j - h);
+                float g[8], dp[8], rp[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    g[k] = 0.f;
+                    dp[k] = 0.f;
+                    rp[k] = 0.f;
+                    if (k < cnt) {
+                        g[k] = sg[j - k];
+                        dp[k] = sd[j - k - 1];
+                        rp[k] = sr[j - k - 1];
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (k < cnt) {
+                        const float inv = rcp_approx(db);
+                        const float f = g[k] * inv;
+                        sd[j - k] = f;
+                        sr[j - k] = rb * inv;
+                        db = fmaf(-g[k], f, dp[k]);
+                        rb = fmaf(f, rb, rp[k]);
+                    }
+                }
             }
-            for (;;) {
-                // links inside the segment are assembled: elimination of j
-                // into its parent j-1 with a = c = -g, eight links at a time
-                // (their operands loaded before any of their stores)
-                for (int j = bot; j > S.top; j -= 8) {
-                    const int cnt = min(8, j - S.top);
-                    float g[8], g2[8], dp[8], rp[8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        g[k] = 0.f;
-                        dp[k] = 0.f;
-                        rp[k] = 0.f;
-                        if (k < cnt) {
-                            g[k] = sg[j - k];
-                            dp[k] = sd[j - k - 1];
-                            rp[k] = sr[j - k - 1];
-                        }
-                        g2[k] = g[k] * g[k];
-                    }
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        if (k < cnt) {
-                            const float inv = rcp_approx(db);
-                            const float f = g[k] * inv;
-                            sd[j - k] = f;         // x_j = f x_{j-1} + rb / d_j
-                            sr[j - k] = rb * inv;
-                            db = fmaf(-g2[k], inv, dp[k]);
-                            rb = fmaf(f, rb, rp[k]);
-                        }
-                    }
+            if (P.parent < 0) {  // soma: the stimulus, then its dV
+                rb += svt[pi];
+                sr[h] = rb * rcp_approx(db);
+                return;
+            }
+            // the head link to the parent compartment: assembled here, the
+            // head eliminated into the parent through the path's slot
+            const float g = sg[h], vt = svt[pi];
+            db += g;
+            rb = fmaf(g, vt, rb);
+            const float inv = rcp_approx(db);
+            const float f = g * inv;
+            sd[h] = f;
+            sr[h] = rb * inv;
+            scd[pi] = fmaf(-f, g, g);
+            scr[pi] = fmaf(f, rb, -g * vt);
+        };
+        // contributions of the level's paths (fold entries e0 .. e1-1) to
+        // their parent compartments; a lane takes the entries that start a
+        // run of equal parents
+        auto fold_level = [&](int e0, int e1, int lane) {
+            for (int e = e0 + lane; e < e1; e += 32) {
+                const KidQ kv = fold[e];
+                const int att = (int)(kv >> 16);
+                if (e > e0 && (int)(fold[e - 1] >> 16) == att) continue;
+                int c = (int)(kv & 0xFFFFu);
+                float ad = scd[c], ar = scr[c];
+                for (int z = e + 1; z < e1; ++z) {
+                    const KidQ kz = fold[z];
+                    if ((int)(kz >> 16) != att) break;
+                    c = (int)(kz & 0xFFFFu);
+                    ad += scd[c];
+                    ar += scr[c];
                 }
-                const int t = S.top;
-                const float vt = scr[si];
-                if (S.parent < 0) {  // soma: the stimulus, then its dV
-                    rb += vt;
-                    sr[t] = rb * rcp_approx(db);
-                    return -1;
-                }
-                // the top link to the parent compartment: assembled here, the
-                // top eliminated into the parent segment's bottom
-                const float g = sg[t];
-                db += g;
-                rb = fmaf(g, vt, rb);
-                const float inv = rcp_approx(db);
-                const float f = g * inv;
-                sd[t] = f;
-                sr[t] = rb * inv;
-                scd[si] = fmaf(-f, g, g);
-                scr[si] = fmaf(f, rb, -g * vt);
-                __threadfence_block();
-                const int ps = S.pseg;
-                if (atomicSub(&scnt[ps], 1) != 1) return -1;
-                __threadfence_block();
-                if (may_defer) return ps;
-                // last child in: the parent segment's bottom collects all
-                // contributions (in child-list order) and the walk goes on
-                si = ps;
-                S = segs[si];
-                bot = S.top + S.len - 1;
-                db = sd[bot];
-                rb = sr[bot];
-                for (int c = 0; c < S.nchild; ++c) {
-                    const int cs = kids[S.child0 + c];
-                    db += scd[cs];
-                    rb += scr[cs];
-                }
+                sd[att] += ad;
+                sr[att] += ar;
             }
         };
-        const int nleaf = woff[1];
-        for (int li = tid; li < nleaf; li += NS) {
-            const int ps = eliminate_up(li, li + NS < nleaf);
-            if (ps >= 0) scnt[li] = ps + 1;
-        }
-        for (int li = tid; li + NS < nleaf; li += NS) {
-            const int ps = scnt[li] - 1;
-            if (ps >= 0) eliminate_up(ps, false);
-        }
-        solver_sync(NS);
 
         // F. root-to-leaves substitution path by path, one level at a time
         //    (a path's head needs its parent, on a path of the level
         //    before); the path from a soma runs the FP64 soma accumulator and
         //    the spike test
-        const PathP *paths = (const PathP *)(smeta + G.path_off);
-        const int16_t *loff = (const int16_t *)(paths + G.npath);
-        for (int l = 0; l < G.nlevel; ++l) {
-            for (int pi = loff[l] + tid; pi < loff[l + 1]; pi += NS) {
-                const PathP P = paths[pi];
-                const int h = P.head;
-                float x;
-                if (P.parent >= 0) {
-                    x = fmaf(sd[h], sr[P.parent], sr[h]);
-                    sr[h] = x;
-                } else {
-                    x = sr[h];
-                    const int nrn = G.neuron0 + P.neuron;
-                    const double v0 = a.Vsoma[nrn], v1 = v0 + (double)x;
-                    a.Vsoma[nrn] = v1;
-                    if (!isfinite(v1)) atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
-                    if (v0 < a.threshold && v1 >= a.threshold) {
-                        const double ts = (double)n * a.dt64 + a.dt64 * (a.threshold - v0) / (v1 - v0);
-                        const unsigned long long k = atomicAdd(&a.ctl->spk_count, 1ull);
-                        if ((long long)k < a.spk_cap) {
-                            a.spk_nrn[k] = a.user_id[nrn];
-                            a.spk_t[k] = ts;
-                        } else {
-                            atomicOr(&a.ctl->err, MMK_ERR_OVERFLOW);
-                        }
-                        const int slot = (int)(n % a.R);
-                        const int pos = atomicAdd(&a.ring_cnt[slot], 1);
-                        a.ring_nrn[(long long)slot * a.N + pos] = nrn;
+        auto substitute_path = [&](int pi) {
+            const PathQ P = paths[pi];
+            const int h = P.head;
+            float x;
+            if (P.parent >= 0) {
+                x = fmaf(sd[h], sr[P.parent], sr[h]);
+                sr[h] = x;
+            } else {
+                x = sr[h];
+                const int nrn = G.neuron0 + P.neuron;
+                const double v0 = a.Vsoma[nrn], v1 = v0 + (double)x;
+                a.Vsoma[nrn] = v1;
+                if (!isfinite(v1)) atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
+                if (v0 < a.threshold && v1 >= a.threshold) {
+                    const double ts = (double)n * a.dt64 + a.dt64 * (a.threshold - v0) / (v1 - v0);
+                    const unsigned long long k = atomicAdd(&a.ctl->spk_count, 1ull);
+                    if ((long long)k < a.spk_cap) {
+                        a.spk_nrn[k] = a.user_id[nrn];
+                        a.spk_t[k] = ts;
+                    } else {
+                        atomicOr(&a.ctl->err, MMK_ERR_OVERFLOW);
+                    }
+                    const int slot = (int)(n % a.R);
+                    const int pos = atomicAdd(&a.ring_cnt[slot], 1);
+                    a.ring_nrn[(long long)slot * a.N + pos] = nrn;
+                }
+            }
+            // down the path, each compartment's parent is the one before
+            // it: x_j = f_j x_{j-1} + c_j with the coefficients the
+            // elimination left in (sd, sr); eight at a time, operands
+            // loaded before the stores
+            for (int j = h + 1; j < P.end; j += 8) {
+                const int cnt = min(8, P.end - j);
+                float r[8], d[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    r[k] = 0.f;
+                    d[k] = 0.f;
+                    if (k < cnt) {
+                        r[k] = sr[j + k];
+                        d[k] = sd[j + k];
                     }
                 }
-                // down the path, each compartment's parent is the one before
-                // it: x_j = f_j x_{j-1} + c_j with the coefficients the
-                // elimination left in (sd, sr); eight at a time, operands
-                // loaded before the stores
-                for (int j = h + 1; j < P.end; j += 8) {
-                    const int cnt = min(8, P.end - j);
-                    float r[8], d[8];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        r[k] = 0.f;
-                        d[k] = 0.f;
-                        if (k < cnt) {
-                            r[k] = sr[j + k];
-                            d[k] = sd[j + k];
-                        }
-                    }
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        if (k < cnt) {
-                            x = fmaf(d[k], x, r[k]);
-                            sr[j + k] = x;
-                        }
+                for (int k = 0; k < 8; ++k) {
+                    if (k < cnt) {
+                        x = fmaf(d[k], x, r[k]);
+                        sr[j + k] = x;
                     }
                 }
             }
-            solver_sync(NS);
+        };
+
+        // one warp per neuron: B from the deepest level up, then F from the
+        // soma down; a level's paths go to the lanes longest first.  Then
+        // gate chunks of the previous item (when timing items, the gates
+        // wait until after phase C, outside the timed span).
+        {
+            const int lane = tid & 31;
+            for (int k = tid >> 5; k < G.nneuron; k += NS / 32) {
+                const NrnQ Nk = nrns[k];
+                const int16_t *lo = loffs + Nk.loff0;
+                for (int l = Nk.nlevel - 1; l >= 0; --l) {
+                    const int pb = lo[l], pe = lo[l + 1];
+                    for (int pi = pb + lane; pi < pe; pi += 32) eliminate_path(pi);
+                    __syncwarp();
+                    if (l > 0) {
+                        fold_level(pb, pe, lane);
+                        __syncwarp();
+                    }
+                }
+                for (int l = 0; l < Nk.nlevel; ++l) {
+                    const int pe = lo[l + 1];
+                    for (int pi = lo[l] + lane; pi < pe; pi += 32) substitute_path(pi);
+                    __syncwarp();
+                }
+            }
+            if (!a.item_ns) gate_chunks(a, s_pc0, s_pn, &s_gchunk, lane);
         }
+        solver_sync(NS);
 
         // C. V^{n+1} = V^n + dV (exact in fixed point)
         for (int i = tid; i < G.ncomp; i += NS) {
@@ -475,24 +493,23 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             }
             a.Vq[c0 + i] = vq;
         }
-        if (a.item_ns) {  // uniform across the solver warps
+        if (a.item_ns) {  // uniform across the block
             solver_sync(NS);
             if (tid == 0) a.item_ns[gi] += global_ns() - t_item;
+            gate_chunks(a, s_pc0, s_pn, &s_gchunk, tid & 31);
+            solver_sync(NS);
         }
-        // this item's gates are the gate warps' work during the next item
-        // (its V^{n+1} is visible to the block after the barrier at the top
-        // of the loop)
+        // this item's gates are pending until the next item's sweeps (its
+        // V^{n+1} is visible to the block after the barrier at the top of
+        // the loop; every chunk of the previous item is done)
         if (tid == 0) {
-            s_nc0 = c0;
-            s_nncomp = G.ncomp;
+            s_pc0 = c0;
+            s_pn = G.ncomp;
+            s_gchunk = 0;
         }
     }
-    // the last item's gates, by the whole block (s_nc0 / s_nncomp name it)
-    {
-        const int64_t gc0 = s_nc0;
-        const int gncomp = s_nncomp;
-        for (int i = tid; i < gncomp; i += NT) gate_update(a, gc0 + i);
-    }
+    // the last item's gates, by the whole block
+    gate_chunks(a, s_pc0, s_pn, &s_gchunk, tid & 31);
 }
 
 

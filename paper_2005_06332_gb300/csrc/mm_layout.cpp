@@ -43,6 +43,73 @@ struct PathTmp {
     int32_t head, end, parent, neuron, level;
 };
 
+// The blob of an FP32c work item solved path by path (see mmk::NrnQ):
+// per neuron its paths by (level, longest first, head); per level a fold
+// list of the same paths sorted by the compartment they hang off (deepest
+// first, then head), so that the contributions of paths sharing a parent
+// compartment are summed in a fixed order.
+struct PathBlob {
+    std::vector<mmk::NrnQ> nrns;
+    std::vector<mmk::PathQ> paths;
+    std::vector<mmk::KidQ> fold;
+    std::vector<int16_t> loffs;
+    int32_t nlevel = 0;
+    int64_t path_off = 0, fold_off = 0, loffs_off = 0, bytes = 0;
+};
+
+// paths: every path of the item (group-local compartments), neurons in
+// order, each neuron's paths contiguous.
+void build_path_blob(std::vector<PathTmp> &paths, int32_t nneuron, PathBlob &b)
+{
+    std::stable_sort(paths.begin(), paths.end(), [](const PathTmp &a, const PathTmp &c) {
+        if (a.neuron != c.neuron) return a.neuron < c.neuron;
+        if (a.level != c.level) return a.level < c.level;
+        if (a.end - a.head != c.end - c.head) return a.end - a.head > c.end - c.head;
+        return a.head < c.head;
+    });
+    const int32_t np = (int32_t)paths.size();
+    b.nrns.assign((size_t)nneuron, mmk::NrnQ{0, 0, 0, 0});
+    b.paths.resize((size_t)np);
+    b.fold.resize((size_t)np);
+    b.loffs.clear();
+    b.nlevel = 0;
+    for (int32_t q = 0; q < np; ++q) {
+        const PathTmp &P = paths[(size_t)q];
+        b.paths[(size_t)q] = mmk::PathQ{(int16_t)P.head, (int16_t)P.end, (int16_t)P.parent, (int16_t)P.neuron};
+    }
+    int32_t i = 0;
+    std::vector<int32_t> lv;
+    for (int32_t k = 0; k < nneuron; ++k) {
+        const int32_t p0 = i;
+        while (i < np && paths[(size_t)i].neuron == k) ++i;
+        const int32_t nl = i > p0 ? paths[(size_t)i - 1].level + 1 : 0;
+        b.nrns[(size_t)k] = mmk::NrnQ{(int16_t)p0, (int16_t)(i - p0), (int16_t)nl, (int16_t)b.loffs.size()};
+        for (int32_t l = 0, q = p0; l <= nl; ++l) {
+            while (q < i && paths[(size_t)q].level < l) ++q;
+            b.loffs.push_back((int16_t)q);
+        }
+        for (int32_t l = 0; l < nl; ++l) {
+            const int32_t s = b.loffs[b.loffs.size() - (size_t)(nl + 1) + (size_t)l];
+            const int32_t e = b.loffs[b.loffs.size() - (size_t)(nl + 1) + (size_t)l + 1];
+            lv.resize((size_t)(e - s));
+            std::iota(lv.begin(), lv.end(), s);
+            std::sort(lv.begin(), lv.end(), [&](int32_t x, int32_t y) {
+                if (paths[(size_t)x].parent != paths[(size_t)y].parent) return paths[(size_t)x].parent > paths[(size_t)y].parent;
+                return paths[(size_t)x].head < paths[(size_t)y].head;
+            });
+            for (int32_t z = s; z < e; ++z) {
+                const int32_t c = lv[(size_t)(z - s)];
+                b.fold[(size_t)z] = (mmk::KidQ)(uint32_t)c | ((mmk::KidQ)(uint16_t)paths[(size_t)c].parent << 16);
+            }
+        }
+        b.nlevel = std::max(b.nlevel, nl);
+    }
+    b.path_off = ((int64_t)sizeof(mmk::NrnQ) * nneuron + 15) & ~15LL;
+    b.fold_off = b.path_off + (int64_t)sizeof(mmk::PathQ) * np;
+    b.loffs_off = b.fold_off + (int64_t)sizeof(mmk::KidQ) * np;
+    b.bytes = (b.loffs_off + 2 * (int64_t)b.loffs.size() + 15) & ~15LL;
+}
+
 }  // namespace
 
 void neuron_features(int32_t n, const int32_t *parent, const double *L_um, const double *d_um, float *out)
@@ -379,7 +446,7 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
                     if (nx < 0 || gsegs[(size_t)nx].parent != gsegs[c].top + gsegs[c].len - 1) break;
                     c = (size_t)nx;
                 }
-                gpaths.push_back(PathTmp{gsegs[s].top, gsegs[c].top + gsegs[c].len, gsegs[s].parent, gsegs[s].neuron,
+                gpaths.push_back(PathTmp{gsegs[s].top, gsegs[c].top + gsegs[c].len, gsegs[s].parent, k - k0,
                                          glevel[s]});
             }
         }
@@ -401,24 +468,27 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         gr.nseg = ns;
         gr.neuron0 = k0;
         gr.nneuron = k1 - k0;
-        gr.pad = 0;
-        // paths by (level, longest first, head)
-        std::sort(gpaths.begin(), gpaths.end(), [](const PathTmp &a, const PathTmp &b) {
-            if (a.level != b.level) return a.level < b.level;
-            if (a.end - a.head != b.end - b.head) return a.end - a.head > b.end - b.head;
-            return a.head < b.head;
-        });
-        const int32_t nlevel = gpaths.empty() ? 0 : gpaths.back().level + 1;
         int32_t maxh = 0;
         int64_t nkids = 0;
         for (int32_t i = 0; i < ns; ++i) {
             maxh = std::max(maxh, gheight[(size_t)perm[(size_t)i]]);
             nkids += (int64_t)gkids[(size_t)perm[(size_t)i]].size();
         }
-        const int64_t small_path_off = ((int64_t)ns * (int64_t)sizeof(mmk::SegP) + 2 * nkids + 2 * (maxh + 2) + 7) & ~7LL;
-        const int64_t small_meta = (small_path_off + (int64_t)sizeof(mmk::PathP) * (int64_t)gpaths.size() +
-                                    2 * (int64_t)(nlevel + 1) + 15) & ~15LL;
-        const int64_t smem_need = small_meta + (int64_t)in.smem_per_comp * gr.ncomp + (int64_t)in.smem_per_seg * ns;
+        // shared-memory need: FP64 items hold the segment blob, FP32c items
+        // the path blob (plus per-path slots)
+        PathBlob pb;
+        int64_t smem_need;
+        if (in.path_items) {
+            if (gr.ncomp <= 32767 && gpaths.size() <= 32767) {
+                build_path_blob(gpaths, gr.nneuron, pb);
+                smem_need = pb.bytes + (int64_t)in.smem_per_comp * gr.ncomp + (int64_t)in.smem_per_path * (int64_t)pb.paths.size();
+            } else {
+                smem_need = INT64_MAX;
+            }
+        } else {
+            const int64_t small_meta = ((int64_t)ns * (int64_t)sizeof(mmk::SegP) + 2 * nkids + 2 * (maxh + 2) + 15) & ~15LL;
+            smem_need = small_meta + (int64_t)in.smem_per_comp * gr.ncomp + (int64_t)in.smem_per_seg * ns;
+        }
         const bool over = in.giant_smem_limit > 0 && smem_need > in.giant_smem_limit;
         const bool big = over && in.big_smem_limit > 0 && smem_need <= in.big_smem_limit;
         const bool giant = gr.ncomp > 32767 || ns > 32767 || (over && !big);
@@ -426,6 +496,14 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
             *invalid = false;
             e << "a work item of " << gr.ncomp << " compartments exceeds what this precision holds";
             return msg(e);
+        }
+        if (in.path_items && !giant) {
+            // links inside paths are assembled per compartment; path heads
+            // (negative parent distance) link to their parent in the sweep
+            for (int64_t c = comp0; c < comp0 + gr.ncomp; ++c) {
+                const int32_t pd = std::abs(L.pdist[(size_t)c]);
+                L.pdist[(size_t)c] = pd == 1 ? 1 : -pd;
+            }
         }
         // the tree blob: records in wave order, child lists, wave offsets;
         // 16-bit indices for items staged in shared memory, 32-bit for giants
@@ -445,7 +523,18 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
             const unsigned char *c = (const unsigned char *)p;
             blob.insert(blob.end(), c, c + n);
         };
-        if (!giant) {
+        if (!giant && in.path_items) {
+            put(pb.nrns.data(), pb.nrns.size() * sizeof(mmk::NrnQ));
+            blob.resize((size_t)pb.path_off, 0);
+            put(pb.paths.data(), pb.paths.size() * sizeof(mmk::PathQ));
+            put(pb.fold.data(), pb.fold.size() * sizeof(mmk::KidQ));
+            put(pb.loffs.data(), pb.loffs.size() * 2);
+            gr.path_off = (int32_t)pb.path_off;
+            gr.fold_off = (int32_t)pb.fold_off;
+            gr.loffs_off = (int32_t)pb.loffs_off;
+            gr.npath = (int32_t)pb.paths.size();
+            gr.nlevel = pb.nlevel;
+        } else if (!giant) {
             std::vector<int16_t> kids;
             std::vector<mmk::SegP> recs((size_t)ns);
             for (int32_t i = 0; i < ns; ++i) {
@@ -467,20 +556,6 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
             put(recs.data(), recs.size() * sizeof(mmk::SegP));
             put(kids.data(), kids.size() * 2);
             put(w16.data(), w16.size() * 2);
-            blob.resize((blob.size() + 7) & ~(size_t)7, 0);
-            std::vector<mmk::PathP> prec(gpaths.size());
-            std::vector<int16_t> loff((size_t)nlevel + 1, 0);
-            for (size_t i = 0; i < gpaths.size(); ++i) {
-                const PathTmp &q = gpaths[i];
-                prec[i] = mmk::PathP{(int16_t)q.head, (int16_t)q.end, (int16_t)q.parent, (int16_t)q.neuron};
-                loff[(size_t)q.level + 1] = (int16_t)(i + 1);
-            }
-            for (int32_t l = 1; l <= nlevel; ++l) loff[(size_t)l] = std::max(loff[(size_t)l], loff[(size_t)l - 1]);
-            gr.path_off = (int32_t)blob.size();
-            gr.npath = (int32_t)gpaths.size();
-            gr.nlevel = nlevel;
-            put(prec.data(), prec.size() * sizeof(mmk::PathP));
-            put(loff.data(), loff.size() * 2);
         } else {
             std::vector<int32_t> kids;
             std::vector<mmk::SegRec> recs((size_t)ns);
@@ -507,15 +582,15 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         } else if (big) {
             bigs.push_back(gr);
             L.big_max_comps = std::max(L.big_max_comps, gr.ncomp);
-            L.big_max_segs = std::max(L.big_max_segs, ns);
+            L.big_max_segs = std::max(L.big_max_segs, in.path_items ? gr.npath : ns);
             L.big_max_meta = std::max(L.big_max_meta, gr.meta_bytes);
             L.big_max_smem = std::max<int64_t>(L.big_max_smem, smem_need);
         } else {
             L.groups.push_back(gr);
             L.max_smem = std::max<int64_t>(L.max_smem, smem_need);
             L.max_comps = std::max(L.max_comps, gr.ncomp);
-            L.max_segs = std::max(L.max_segs, ns);
-            L.max_waves = std::max(L.max_waves, gr.nwave);
+            L.max_segs = std::max(L.max_segs, in.path_items ? gr.npath : ns);
+            L.max_waves = std::max(L.max_waves, in.path_items ? gr.nlevel : gr.nwave);
             L.max_meta = std::max(L.max_meta, gr.meta_bytes);
         }
     }
