@@ -53,10 +53,12 @@ struct SegP {
     int16_t pad;
 };
 
-// FP32c work items are solved path by path, one warp per neuron.  Per
-// neuron of an item (8 bytes): its paths are path0 .. path0 + npath - 1 of the
-// item, sorted by level (0: the path from the soma) and, within a level,
-// longest first; level l holds paths loffs[loff0 + l] .. loffs[loff0 + l + 1] - 1.
+// FP32c work items are solved path by path, by a team of warps per neuron.
+// Per neuron of an item (8 bytes): its paths are path0 .. path0 + npath - 1
+// of the item, sorted by level (0: the path from the soma) and, within a
+// level, longest first; level l holds paths loffs[loff0 + l] ..
+// loffs[loff0 + l + 1] - 1, and the first mcnt[loff0 + l] entries of that
+// level's fold list belong to parent compartments shared by several paths.
 struct NrnQ {
     int16_t path0;
     int16_t npath;
@@ -69,14 +71,19 @@ struct PathQ {
     int16_t head;     // group-local index of the first compartment
     int16_t end;      // one past the last compartment (a leaf)
     int16_t parent;   // group-local parent of head; -1 when head is a soma
-    int16_t neuron;   // group-local neuron index
+    int16_t nflag;    // group-local neuron index | kPathAlone
 };
+// set in PathQ::nflag when no other path hangs off the same parent
+// compartment: the path adds its contribution to the parent directly
+constexpr int16_t kPathAlone = 0x4000;
+constexpr int16_t kPathNeuron = 0x3FFF;
 
 // One fold-list entry (4 bytes): low half a path's index in the item, high
 // half the compartment its head hangs off.  The fold list holds the same
-// paths as the path table, level by level (same level offsets), each level
-// sorted by that compartment (deepest first, then head), so that paths
-// sharing a parent compartment are adjacent.
+// paths as the path table, level by level (same level offsets); within a
+// level the paths that share a parent compartment come first, sorted by that
+// compartment (deepest first, then head), so that their contributions are
+// summed in a fixed order; the paths alone on their parent follow.
 typedef uint32_t KidQ;
 
 // One work item: a run of whole neurons.  Its tree is one contiguous,
@@ -85,8 +92,8 @@ typedef uint32_t KidQ;
 // int16 wave_off[nwave+1] (wave w holds segments wave_off[w] ..
 // wave_off[w+1]-1; wave 0 holds the leaf segments), padded to 16 bytes.
 // FP32c items: NrnQ[nneuron] | PathQ[npath] (at byte path_off) |
-// KidQ[npath] (fold list, at fold_off) | int16 loffs[] (at loffs_off),
-// padded to 16 bytes.  Giant items (FP32c, beyond shared memory): SegRec[nseg] |
+// KidQ[npath] (fold list, at fold_off) | int16 loffs[] (at loffs_off) |
+// int16 mcnt[] (as many as loffs, at mcnt_off), padded to 16 bytes.  Giant items (FP32c, beyond shared memory): SegRec[nseg] |
 // int32 child[nchild] | int32 wave_off[nwave+1].
 struct GroupRec {
     int64_t comp0;    // internal index of the first compartment
@@ -106,6 +113,8 @@ struct GroupRec {
     int32_t path_off; // FP32c: byte offset of PathQ[0] inside the blob
     int32_t fold_off; // FP32c: byte offset of the fold list
     int32_t loffs_off;// FP32c: byte offset of the level offsets
+    int32_t mcnt_off; // FP32c: byte offset of the per-level shared-parent counts
+    int32_t pad;
 };
 
 // Small device-side control block.

@@ -176,11 +176,6 @@ __device__ __forceinline__ void gate_chunks(const StepArgs32 &a, int64_t pc0, in
     }
 }
 
-// Barrier among the first `nthreads` threads of the block only (whole warps).
-__device__ __forceinline__ void solver_sync(int nthreads)
-{
-    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
-}
 
 template <int NT>
 __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
@@ -289,7 +284,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         // the tree blob must have landed before the sweeps
         if (!mbar_wait_bounded(&bar, parity)) s_abort = 1;
         parity ^= 1u;
-        solver_sync(NS);
+        __syncthreads();
         if (s_abort) {  // the whole block leaves at the next item boundary
             if (tid == 0) atomicOr(&a.ctl->err, MMK_ERR_TIMEOUT);
             continue;
@@ -298,11 +293,14 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         const PathQ *paths = (const PathQ *)(smeta + G.path_off);
         const KidQ *fold = (const KidQ *)(smeta + G.fold_off);
         const int16_t *loffs = (const int16_t *)(smeta + G.loffs_off);
+        const int16_t *mcnt = (const int16_t *)(smeta + G.mcnt_off);
 
         // S. synaptic sites, then decay (sites are distinct compartments).
         //    Per path: the exact potential difference across its head link,
         //    V_parent - V_head (for the path from a soma: the stimulus
-        //    current), which the elimination needs.
+        //    current), which the elimination needs; the path from a soma
+        //    also fetches the FP64 soma voltage into its (otherwise unused)
+        //    contribution slot, as two 32-bit halves.
         for (int t = tid; t < G.nsite; t += NS) {
             const int st = G.site0 + t;
             const int c = a.site_comp[st];
@@ -313,74 +311,108 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         }
         for (int pi = tid; pi < G.npath; pi += NS) {
             const PathQ P = paths[pi];
-            svt[pi] = P.parent >= 0 ? mmf::vdiff(Vq[P.parent], Vq[P.head]) : (float)a.stim[G.neuron0 + P.neuron];
+            if (P.parent >= 0) {
+                svt[pi] = mmf::vdiff(Vq[P.parent], Vq[P.head]);
+            } else {
+                const int nrn = G.neuron0 + (P.nflag & kPathNeuron);
+                svt[pi] = (float)a.stim[nrn];
+                const double v0 = a.Vsoma[nrn];
+                scd[pi] = __int_as_float(__double2hiint(v0));
+                scr[pi] = __int_as_float(__double2loint(v0));
+            }
         }
-        solver_sync(NS);
+        __syncthreads();
+
+        // Team of each warp for the sweeps: T warps per neuron (T = 1, 2 or
+        // 4, as many as the item's neurons leave), the teams taking the
+        // item's neurons in turn; a team synchronises on its own named
+        // barrier (1 + team; 0 is the block's).
+        const int nwarp = NS / 32;
+        int T = nwarp / max(G.nneuron, 1);
+        T = T >= 4 ? 4 : (T >= 2 ? 2 : 1);
+        if (T == 2 && nwarp / 2 > 15) T = 4;
+        const int team = (tid >> 5) / T, nteam = nwarp / T;
+        const int tl = tid - team * T * 32;  // lane within the team
+        const int TL = T * 32;
+        auto team_sync = [&]() {
+            if (T == 1) __syncwarp();
+            else asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "r"(TL) : "memory");
+        };
 
         // B. leaves-to-root elimination (Algorithm 1) path by path, from the
         //    deepest level up: every compartment of a path has the one
         //    before it as its parent, so a path is one chain from its leaf
         //    up to its head (links inside a path are assembled: a = c = -g),
         //    eight compartments at a time with their operands loaded before
-        //    any of their stores.  The head is then eliminated into its
-        //    parent compartment through the path's slot; once a level is
-        //    done, the slots of the paths sharing a parent compartment are
-        //    summed in fold-list order and added to that compartment's
-        //    diagonal and rhs.  The elimination leaves the substitution
-        //    coefficients x_j = f_j x_{j-1} + c_j.
+        //    any of their stores (indices past the head are clamped and their
+        //    results dropped).  The head is then eliminated into its parent
+        //    compartment: a path alone on that compartment adds its
+        //    contribution there itself; paths sharing one leave theirs in
+        //    their slots, summed in fold-list order once the level is done.
+        //    The elimination leaves the substitution coefficients
+        //    x_j = f_j x_{j-1} + c_j.
         auto eliminate_path = [&](int pi) {
             const PathQ P = paths[pi];
             const int h = P.head;
+            const float gh = sg[h], vt = svt[pi];
             int j = P.end - 1;
             float db = sd[j], rb = sr[j];
+            float dh = db, rh = rb;
             for (; j > h; j -= 8) {
-                const int cnt = min(8, j - h);
-                float g[8], dp[8], rp[8];
+                const int cnt = j - h;
+                float g[8], g2[8], dp[8], rp[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    g[k] = 0.f;
-                    dp[k] = 0.f;
-                    rp[k] = 0.f;
-                    if (k < cnt) {
-                        g[k] = sg[j - k];
-                        dp[k] = sd[j - k - 1];
-                        rp[k] = sr[j - k - 1];
-                    }
+                    const int q = max(j - k, h + 1);
+                    g[k] = sg[q];
+                    dp[k] = sd[q - 1];
+                    rp[k] = sr[q - 1];
+                    g2[k] = g[k] * g[k];
                 }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
+                    const float inv = rcp_approx(db);
+                    const float f = g[k] * inv;
+                    const float c = rb * inv;
                     if (k < cnt) {
-                        const float inv = rcp_approx(db);
-                        const float f = g[k] * inv;
                         sd[j - k] = f;
-                        sr[j - k] = rb * inv;
-                        db = fmaf(-g[k], f, dp[k]);
-                        rb = fmaf(f, rb, rp[k]);
+                        sr[j - k] = c;
+                    }
+                    rb = fmaf(f, rb, rp[k]);
+                    db = fmaf(-g2[k], inv, dp[k]);
+                    if (k == cnt - 1) {
+                        dh = db;
+                        rh = rb;
                     }
                 }
             }
             if (P.parent < 0) {  // soma: the stimulus, then its dV
-                rb += svt[pi];
-                sr[h] = rb * rcp_approx(db);
+                rh += vt;
+                sr[h] = rh * rcp_approx(dh);
                 return;
             }
             // the head link to the parent compartment: assembled here, the
-            // head eliminated into the parent through the path's slot
-            const float g = sg[h], vt = svt[pi];
-            db += g;
-            rb = fmaf(g, vt, rb);
-            const float inv = rcp_approx(db);
-            const float f = g * inv;
+            // head eliminated into the parent
+            dh += gh;
+            rh = fmaf(gh, vt, rh);
+            const float inv = rcp_approx(dh);
+            const float f = gh * inv;
             sd[h] = f;
-            sr[h] = rb * inv;
-            scd[pi] = fmaf(-f, g, g);
-            scr[pi] = fmaf(f, rb, -g * vt);
+            sr[h] = rh * inv;
+            const float cd = fmaf(-f, gh, gh), cr = fmaf(f, rh, -gh * vt);
+            if (P.nflag & kPathAlone) {
+                sd[P.parent] += cd;
+                sr[P.parent] += cr;
+            } else {
+                scd[pi] = cd;
+                scr[pi] = cr;
+            }
         };
-        // contributions of the level's paths (fold entries e0 .. e1-1) to
-        // their parent compartments; a lane takes the entries that start a
-        // run of equal parents
-        auto fold_level = [&](int e0, int e1, int lane) {
-            for (int e = e0 + lane; e < e1; e += 32) {
+        // contributions of the level's paths that share a parent compartment
+        // (fold entries e0 .. e1-1); a lane takes the entries that start a run
+        // of equal parents
+        auto fold_shared = [&](int e0, int e1) {
+            for (int e = e0 + tl; e < e1; e += TL) {
                 const KidQ kv = fold[e];
                 const int att = (int)(kv >> 16);
                 if (e > e0 && (int)(fold[e - 1] >> 16) == att) continue;
@@ -408,11 +440,11 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             float x;
             if (P.parent >= 0) {
                 x = fmaf(sd[h], sr[P.parent], sr[h]);
-                sr[h] = x;
             } else {
                 x = sr[h];
-                const int nrn = G.neuron0 + P.neuron;
-                const double v0 = a.Vsoma[nrn], v1 = v0 + (double)x;
+                const int nrn = G.neuron0 + (P.nflag & kPathNeuron);
+                const double v0 = __hiloint2double(__float_as_int(scd[pi]), __float_as_int(scr[pi]));
+                const double v1 = v0 + (double)x;
                 a.Vsoma[nrn] = v1;
                 if (!isfinite(v1)) atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
                 if (v0 < a.threshold && v1 >= a.threshold) {
@@ -429,59 +461,55 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                     a.ring_nrn[(long long)slot * a.N + pos] = nrn;
                 }
             }
+            const float xh = x;
             // down the path, each compartment's parent is the one before
             // it: x_j = f_j x_{j-1} + c_j with the coefficients the
             // elimination left in (sd, sr); eight at a time, operands
-            // loaded before the stores
+            // loaded before the stores (indices past the leaf clamped, their
+            // results dropped)
             for (int j = h + 1; j < P.end; j += 8) {
-                const int cnt = min(8, P.end - j);
+                const int cnt = P.end - j;
                 float r[8], d[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    r[k] = 0.f;
-                    d[k] = 0.f;
-                    if (k < cnt) {
-                        r[k] = sr[j + k];
-                        d[k] = sd[j + k];
-                    }
+                    const int q = min(j + k, P.end - 1);
+                    r[k] = sr[q];
+                    d[k] = sd[q];
                 }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    if (k < cnt) {
-                        x = fmaf(d[k], x, r[k]);
-                        sr[j + k] = x;
-                    }
+                    x = fmaf(d[k], x, r[k]);
+                    if (k < cnt) sr[j + k] = x;
                 }
             }
+            if (P.parent >= 0) sr[h] = xh;  // read by the next level only
         };
 
-        // one warp per neuron: B from the deepest level up, then F from the
-        // soma down; a level's paths go to the lanes longest first.  Then
-        // gate chunks of the previous item (when timing items, the gates
-        // wait until after phase C, outside the timed span).
-        {
-            const int lane = tid & 31;
-            for (int k = tid >> 5; k < G.nneuron; k += NS / 32) {
-                const NrnQ Nk = nrns[k];
-                const int16_t *lo = loffs + Nk.loff0;
-                for (int l = Nk.nlevel - 1; l >= 0; --l) {
-                    const int pb = lo[l], pe = lo[l + 1];
-                    for (int pi = pb + lane; pi < pe; pi += 32) eliminate_path(pi);
-                    __syncwarp();
-                    if (l > 0) {
-                        fold_level(pb, pe, lane);
-                        __syncwarp();
-                    }
-                }
-                for (int l = 0; l < Nk.nlevel; ++l) {
-                    const int pe = lo[l + 1];
-                    for (int pi = lo[l] + lane; pi < pe; pi += 32) substitute_path(pi);
-                    __syncwarp();
+        // B from the deepest level up, then F from the soma down; a level's
+        // paths go to the team's lanes longest first.  Then gate chunks of
+        // the previous item (when timing items, the gates wait until after
+        // phase C, outside the timed span).
+        for (int k = team; k < G.nneuron; k += nteam) {
+            const NrnQ Nk = nrns[k];
+            const int16_t *lo = loffs + Nk.loff0;
+            const int16_t *mc = mcnt + Nk.loff0;
+            for (int l = Nk.nlevel - 1; l >= 0; --l) {
+                const int pb = lo[l], pe = lo[l + 1];
+                for (int pi = pb + tl; pi < pe; pi += TL) eliminate_path(pi);
+                team_sync();
+                if (mc[l] > 0) {
+                    fold_shared(pb, pb + mc[l]);
+                    team_sync();
                 }
             }
-            if (!a.item_ns) gate_chunks(a, s_pc0, s_pn, &s_gchunk, lane);
+            for (int l = 0; l < Nk.nlevel; ++l) {
+                const int pe = lo[l + 1];
+                for (int pi = lo[l] + tl; pi < pe; pi += TL) substitute_path(pi);
+                team_sync();
+            }
         }
-        solver_sync(NS);
+        if (!a.item_ns) gate_chunks(a, s_pc0, s_pn, &s_gchunk, tid & 31);
+        __syncthreads();
 
         // C. V^{n+1} = V^n + dV (exact in fixed point)
         for (int i = tid; i < G.ncomp; i += NS) {
@@ -494,10 +522,10 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             a.Vq[c0 + i] = vq;
         }
         if (a.item_ns) {  // uniform across the block
-            solver_sync(NS);
+            __syncthreads();
             if (tid == 0) a.item_ns[gi] += global_ns() - t_item;
             gate_chunks(a, s_pc0, s_pn, &s_gchunk, tid & 31);
-            solver_sync(NS);
+            __syncthreads();
         }
         // this item's gates are pending until the next item's sweeps (its
         // V^{n+1} is visible to the block after the barrier at the top of

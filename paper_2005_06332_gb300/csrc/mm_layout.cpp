@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cstring>
 #include <cmath>
+#include <map>
 #include <numeric>
 #include <sstream>
 
@@ -45,16 +46,16 @@ struct PathTmp {
 
 // The blob of an FP32c work item solved path by path (see mmk::NrnQ):
 // per neuron its paths by (level, longest first, head); per level a fold
-// list of the same paths sorted by the compartment they hang off (deepest
-// first, then head), so that the contributions of paths sharing a parent
-// compartment are summed in a fixed order.
+// list of the same paths, those sharing a parent compartment first (sorted
+// by that compartment, deepest first, then head), then the paths alone on
+// their parent compartment.
 struct PathBlob {
     std::vector<mmk::NrnQ> nrns;
     std::vector<mmk::PathQ> paths;
     std::vector<mmk::KidQ> fold;
-    std::vector<int16_t> loffs;
+    std::vector<int16_t> loffs, mcnt;
     int32_t nlevel = 0;
-    int64_t path_off = 0, fold_off = 0, loffs_off = 0, bytes = 0;
+    int64_t path_off = 0, fold_off = 0, loffs_off = 0, mcnt_off = 0, bytes = 0;
 };
 
 // paths: every path of the item (group-local compartments), neurons in
@@ -68,14 +69,20 @@ void build_path_blob(std::vector<PathTmp> &paths, int32_t nneuron, PathBlob &b)
         return a.head < c.head;
     });
     const int32_t np = (int32_t)paths.size();
+    std::map<int32_t, int32_t> share;  // parent compartment -> paths hanging off it
+    for (int32_t q = 0; q < np; ++q)
+        if (paths[(size_t)q].parent >= 0) share[paths[(size_t)q].parent]++;
     b.nrns.assign((size_t)nneuron, mmk::NrnQ{0, 0, 0, 0});
     b.paths.resize((size_t)np);
     b.fold.resize((size_t)np);
     b.loffs.clear();
+    b.mcnt.clear();
     b.nlevel = 0;
     for (int32_t q = 0; q < np; ++q) {
         const PathTmp &P = paths[(size_t)q];
-        b.paths[(size_t)q] = mmk::PathQ{(int16_t)P.head, (int16_t)P.end, (int16_t)P.parent, (int16_t)P.neuron};
+        const bool alone = P.parent >= 0 && share[P.parent] == 1;
+        b.paths[(size_t)q] = mmk::PathQ{(int16_t)P.head, (int16_t)P.end, (int16_t)P.parent,
+                                        (int16_t)(P.neuron | (alone ? mmk::kPathAlone : 0))};
     }
     int32_t i = 0;
     std::vector<int32_t> lv;
@@ -83,31 +90,38 @@ void build_path_blob(std::vector<PathTmp> &paths, int32_t nneuron, PathBlob &b)
         const int32_t p0 = i;
         while (i < np && paths[(size_t)i].neuron == k) ++i;
         const int32_t nl = i > p0 ? paths[(size_t)i - 1].level + 1 : 0;
-        b.nrns[(size_t)k] = mmk::NrnQ{(int16_t)p0, (int16_t)(i - p0), (int16_t)nl, (int16_t)b.loffs.size()};
+        const size_t lbase = b.loffs.size();
+        b.nrns[(size_t)k] = mmk::NrnQ{(int16_t)p0, (int16_t)(i - p0), (int16_t)nl, (int16_t)lbase};
         for (int32_t l = 0, q = p0; l <= nl; ++l) {
             while (q < i && paths[(size_t)q].level < l) ++q;
             b.loffs.push_back((int16_t)q);
+            b.mcnt.push_back(0);
         }
         for (int32_t l = 0; l < nl; ++l) {
-            const int32_t s = b.loffs[b.loffs.size() - (size_t)(nl + 1) + (size_t)l];
-            const int32_t e = b.loffs[b.loffs.size() - (size_t)(nl + 1) + (size_t)l + 1];
+            const int32_t s = b.loffs[lbase + (size_t)l], e = b.loffs[lbase + (size_t)l + 1];
             lv.resize((size_t)(e - s));
             std::iota(lv.begin(), lv.end(), s);
+            auto shared = [&](int32_t x) { return paths[(size_t)x].parent >= 0 && share[paths[(size_t)x].parent] > 1; };
             std::sort(lv.begin(), lv.end(), [&](int32_t x, int32_t y) {
+                if (shared(x) != shared(y)) return shared(x);
                 if (paths[(size_t)x].parent != paths[(size_t)y].parent) return paths[(size_t)x].parent > paths[(size_t)y].parent;
                 return paths[(size_t)x].head < paths[(size_t)y].head;
             });
+            int32_t m = 0;
             for (int32_t z = s; z < e; ++z) {
                 const int32_t c = lv[(size_t)(z - s)];
+                m += shared(c) ? 1 : 0;
                 b.fold[(size_t)z] = (mmk::KidQ)(uint32_t)c | ((mmk::KidQ)(uint16_t)paths[(size_t)c].parent << 16);
             }
+            b.mcnt[lbase + (size_t)l] = (int16_t)m;
         }
         b.nlevel = std::max(b.nlevel, nl);
     }
     b.path_off = ((int64_t)sizeof(mmk::NrnQ) * nneuron + 15) & ~15LL;
     b.fold_off = b.path_off + (int64_t)sizeof(mmk::PathQ) * np;
     b.loffs_off = b.fold_off + (int64_t)sizeof(mmk::KidQ) * np;
-    b.bytes = (b.loffs_off + 2 * (int64_t)b.loffs.size() + 15) & ~15LL;
+    b.mcnt_off = b.loffs_off + 2 * (int64_t)b.loffs.size();
+    b.bytes = (b.mcnt_off + 2 * (int64_t)b.mcnt.size() + 15) & ~15LL;
 }
 
 }  // namespace
@@ -294,17 +308,21 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         if (in.stim) L.stim[(size_t)k] = in.stim[u];
     }
 
-    // 3a. group boundaries
+    // 3a. group boundaries (at most kPathNeuron + 1 neurons per item, the
+    // range of a path's neuron index)
     std::vector<int32_t> gstart;
     {
         int64_t cur = 0;
+        int32_t cnt = 0;
         for (int32_t k = 0; k < N; ++k) {
             const int64_t n = L.noff[(size_t)k + 1] - L.noff[(size_t)k];
-            if (k == 0 || cur + n > in.group_comps) {
+            if (k == 0 || cur + n > in.group_comps || cnt > mmk::kPathNeuron) {
                 gstart.push_back(k);
                 cur = 0;
+                cnt = 0;
             }
             cur += n;
+            ++cnt;
         }
         gstart.push_back(N);
     }
@@ -529,7 +547,9 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
             put(pb.paths.data(), pb.paths.size() * sizeof(mmk::PathQ));
             put(pb.fold.data(), pb.fold.size() * sizeof(mmk::KidQ));
             put(pb.loffs.data(), pb.loffs.size() * 2);
+            put(pb.mcnt.data(), pb.mcnt.size() * 2);
             gr.path_off = (int32_t)pb.path_off;
+            gr.mcnt_off = (int32_t)pb.mcnt_off;
             gr.fold_off = (int32_t)pb.fold_off;
             gr.loffs_off = (int32_t)pb.loffs_off;
             gr.npath = (int32_t)pb.paths.size();
