@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *smeta = smem_raw;
     __shared__ __align__(8) uint64_t bar;
-    __shared__ int s_item, s_abort;
+    __shared__ int s_item, s_next, s_abort;  // this item, the item claimed after it
     __shared__ long long s_pc0;  // pending gate work: the previous item's compartments
     __shared__ int s_pn, s_gchunk;
 
@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         s_pc0 = 0;
         s_pn = 0;
         s_gchunk = 0;
+        s_next = a.item0 + (int)atomicAdd(a.queue, 1u);
     }
     uint32_t parity = 0;
 
@@ -221,9 +222,12 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         __syncthreads();
         if (s_abort) break;
         if (tid == 0) {
-            const int item = a.item0 + (int)atomicAdd(a.queue, 1u);
+            // items are claimed one ahead, so that the next item's
+            // compartments can be pulled into L2 during this item's sweeps
+            const int item = s_next;
             s_item = item;
             if (item < a.item1) {
+                s_next = a.item0 + (int)atomicAdd(a.queue, 1u);
                 const GroupRec *gp = a.groups + item;
                 const uint32_t bytes = (uint32_t)gp->meta_bytes;
                 fence_proxy_async_smem();
@@ -322,6 +326,26 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             }
         }
         __syncthreads();
+
+        // The next item's per-compartment streams (V, gates, area, g_axial)
+        // into L2, one 128-byte line per prefetch, while the sweeps run.
+        {
+            const int ni = s_next;
+            if (ni < a.item1) {
+                const int64_t b0 = a.groups[ni].comp0 * 4, b1 = b0 + a.groups[ni].ncomp * (int64_t)4;
+                const int64_t l0 = b0 >> 7, nl = ((b1 + 127) >> 7) - l0;  // bytes of any 4-byte stream
+                auto pull = [&](const void *p) {
+                    for (int64_t x = tid; x < nl; x += NS)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"((const char *)p + max((l0 + x) << 7, b0)));
+                };
+                pull(a.Vq);
+                pull(a.mq);
+                pull(a.hq);
+                pull(a.nq);
+                pull(a.area);
+                pull(a.gax);
+            }
+        }
 
         // Team of each warp for the sweeps: T warps per neuron (T = 1, 2 or
         // 4, as many as the item's neurons leave), the teams taking the
