@@ -31,6 +31,11 @@ struct mm_net {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t cap_stream = nullptr;
+    // FP32c giant items run on a side stream, concurrently with the other
+    // work-item classes of the same step (fork after delivery, join at the
+    // end of the step)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     mm_allocator alloc{};
     std::vector<void *> blocks;
     std::string err;
@@ -65,6 +70,7 @@ struct mm_net {
     double *Vsoma = nullptr;
     float *area32 = nullptr, *gax32 = nullptr, *gsyn32 = nullptr;
     float2 *dr = nullptr;
+    float4 *pq = nullptr;
     int64_t *soma_internal = nullptr, *internal_of64 = nullptr;
     // both
     double *stim = nullptr;
@@ -217,18 +223,25 @@ mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
     if (net->precision == MM_FP64) {
         kinds[nk++] = 1;
     } else {
+        if (net->n_giant > 0) kinds[nk++] = 3;  // forked first, so that its blocks start first
         if (net->n_small > 0) kinds[nk++] = 1;
         if (net->n_big > 0) kinds[nk++] = 4;
-        if (net->n_giant > 0) kinds[nk++] = 3;
     }
     for (int j = 0; j < count; ++j) {
         for (int ki = 0; ki < nk; ++ki) {
             const int kind = kinds[ki];
+            // giants: forked onto the side stream right after delivery
+            const bool forked = kind == 3;
+            cudaStream_t ks = forked ? net->side : s;
+            if (forked) {
+                MM_CK(net, cudaEventRecord(net->ev_fork, s));
+                MM_CK(net, cudaStreamWaitEvent(net->side, net->ev_fork, 0));
+            }
             mm_net::Pending p{nullptr, nullptr, kind};
             if (timed) {
                 MM_CK(net, take_event(net, &p.a));
                 MM_CK(net, take_event(net, &p.b));
-                MM_CK(net, cudaEventRecord(p.a, s));
+                MM_CK(net, cudaEventRecord(p.a, ks));
             }
             if (kind == 0) {
                 mmk::DeliverArgs da = net->da;
@@ -250,13 +263,15 @@ mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
             } else if (kind == 3) {
                 mmk::StepArgs32 sa = net->sa32g;
                 sa.step_offset = j;
-                MM_CKI(net, mmk_launch_giant_fp32c(sa, net->giant_blocks, s));
+                MM_CKI(net, mmk_launch_giant_fp32c(sa, net->giant_blocks, ks));
             }
             if (timed) {
-                MM_CK(net, cudaEventRecord(p.b, s));
+                MM_CK(net, cudaEventRecord(p.b, ks));
                 net->pending.push_back(p);
             }
+            if (forked) MM_CK(net, cudaEventRecord(net->ev_join, net->side));
         }
+        if (net->precision != MM_FP64 && net->n_giant > 0) MM_CK(net, cudaStreamWaitEvent(s, net->ev_join, 0));
         if (timed && net->pending.size() > 4096) {
             mm_status st = collect_timing(net);
             if (st != MM_OK) return st;
@@ -292,6 +307,7 @@ void release_all(mm_net *net)
     if (net->gexec) cudaGraphExecDestroy(net->gexec);
     net->gexec = nullptr;
     if (net->stream) cudaStreamSynchronize(net->stream);
+    if (net->side) cudaStreamSynchronize(net->side);
     for (auto &p : net->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -308,6 +324,12 @@ void release_all(mm_net *net)
     }
     net->blocks.clear();
     if (net->cap_stream) cudaStreamDestroy(net->cap_stream);
+    if (net->side) cudaStreamDestroy(net->side);
+    if (net->ev_fork) cudaEventDestroy(net->ev_fork);
+    if (net->ev_join) cudaEventDestroy(net->ev_join);
+    net->side = nullptr;
+    net->ev_fork = nullptr;
+    net->ev_join = nullptr;
     if (net->own_stream && net->stream) cudaStreamDestroy(net->stream);
     net->cap_stream = nullptr;
     net->stream = nullptr;
@@ -336,6 +358,9 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         net->own_stream = true;
     }
     MM_CK(net, cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
+    MM_CK(net, cudaStreamCreateWithFlags(&net->side, cudaStreamNonBlocking));
+    MM_CK(net, cudaEventCreateWithFlags(&net->ev_fork, cudaEventDisableTiming));
+    MM_CK(net, cudaEventCreateWithFlags(&net->ev_join, cudaEventDisableTiming));
 
     // layout
     mmh::LayoutInput li{};
@@ -417,6 +442,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         ZR(net->Vsoma, N);
         ZR(net->gsyn32, (size_t)std::max<int64_t>(net->nsite, 1));
         ZR(net->dr, (size_t)std::max<int64_t>(L.giant_comps, 1));
+        ZR(net->pq, (size_t)std::max<int64_t>(L.giant_paths, 1));
         std::vector<int64_t> soma_int(N), int_of(N);
         for (size_t k = 0; k < N; ++k) soma_int[k] = L.noff[k];
         for (size_t u = 0; u < N; ++u) int_of[u] = L.internal_of[u];
@@ -542,6 +568,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.area = net->area32;
         a.gax = net->gax32;
         a.dr = net->dr;
+        a.pq = net->pq;
         if (opt->time_items) {
             if ((st = zeros(net, &net->item_ns, L.groups.size())) != MM_OK) return st;
             a.item_ns = net->item_ns;

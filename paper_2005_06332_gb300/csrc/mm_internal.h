@@ -86,6 +86,19 @@ constexpr int16_t kPathNeuron = 0x3FFF;
 // summed in a fixed order; the paths alone on their parent follow.
 typedef uint32_t KidQ;
 
+// The same three tables with 32-bit indices, for FP32c giant items (beyond
+// shared memory, solved from a global scratch): NrnG per neuron, PathG per
+// path, KidG per fold entry {path, parent compartment}.
+struct NrnG {
+    int32_t path0, npath, nlevel, loff0;
+};
+struct PathG {
+    int32_t head, end, parent, nflag;  // nflag: neuron index | kPathAloneG
+};
+constexpr int32_t kPathAloneG = 0x40000000;
+constexpr int32_t kPathNeuronG = 0x3FFFFFFF;
+typedef int2 KidG;
+
 // One work item: a run of whole neurons.  Its tree is one contiguous,
 // 16-byte aligned blob in global memory, staged into shared memory with a
 // single bulk copy.  FP64 items: SegP[nseg] | int16 child[nchild] |
@@ -93,8 +106,9 @@ typedef uint32_t KidQ;
 // wave_off[w+1]-1; wave 0 holds the leaf segments), padded to 16 bytes.
 // FP32c items: NrnQ[nneuron] | PathQ[npath] (at byte path_off) |
 // KidQ[npath] (fold list, at fold_off) | int16 loffs[] (at loffs_off) |
-// int16 mcnt[] (as many as loffs, at mcnt_off), padded to 16 bytes.  Giant items (FP32c, beyond shared memory): SegRec[nseg] |
-// int32 child[nchild] | int32 wave_off[nwave+1].
+// int16 mcnt[] (as many as loffs, at mcnt_off), padded to 16 bytes.
+// Giant FP32c items (beyond shared memory) use the same layout with the
+// 32-bit records NrnG, PathG, KidG and int32 loffs / mcnt.
 struct GroupRec {
     int64_t comp0;    // internal index of the first compartment
     int64_t scratch0; // giant items: first entry in the global Hines scratch
@@ -114,7 +128,7 @@ struct GroupRec {
     int32_t fold_off; // FP32c: byte offset of the fold list
     int32_t loffs_off;// FP32c: byte offset of the level offsets
     int32_t mcnt_off; // FP32c: byte offset of the per-level shared-parent counts
-    int32_t pad;
+    int32_t pscratch0;// FP32c giant items: first entry in the global per-path scratch
 };
 
 // Small device-side control block.
@@ -179,10 +193,11 @@ struct StepArgs32 {
     uint32_t *mq, *hq, *nq;           // [C]
     double *Vsoma;                    // [N] FP64 soma voltage accumulator
     const float *area;                // cm^2 [C]
-    const float *gax;                 // uS [C], sign bit set where the link to the parent is not
-                                      // assembled by the per-compartment pass: path heads (somata
-                                      // included) of shared-memory items, segment tops of giants
-    float2 *dr;                       // scratch for giant items: Hines diagonal and rhs
+    const float *gax;                 // uS [C], sign bit set at path heads (somata included): their
+                                      // link to the parent is assembled in the sweep
+    float2 *dr;                       // scratch for giant items: Hines diagonal and rhs per compartment
+    float4 *pq;                       // scratch for giant items: per path its contribution (d, rhs) and
+                                      // the potential across its head link
     unsigned long long *item_ns;      // per work item solve time (ns, summed over steps) or nullptr
     const double *stim;               // nA [N]
     const int32_t *user_id;

@@ -139,13 +139,6 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Pull the cache lines of [p, p + bytes) into L1 ahead of a serial walk.
-__device__ __forceinline__ void prefetch_l1(const void *p, int bytes)
-{
-    const char *c = (const char *)((uintptr_t)p & ~(uintptr_t)127);
-    const char *e = (const char *)p + bytes;
-    for (; c < e; c += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(c));
-}
 
 // Exponential-Euler gate update at V^{n+1} of one compartment (its V is
 // final for this step).
@@ -569,13 +562,15 @@ template <int NT>
 __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
 {
     // Work items too large for shared memory (giant neurons, up to the
-    // int32 index range).  The Hines diagonal and rhs of each compartment
-    // live in a global scratch (float2 per compartment: d, rhs; after
-    // elimination 1/d and rhs; after substitution dV), written and read
-    // again within the item, so it stays in L2; every lane prefetches its
-    // segment into L1 before walking it.  The item's tree is read from its
-    // wide blob in global memory: SegRec[nseg] | int32 child[nchild] |
-    // int32 wave_off[nwave + 1].
+    // int32 index range): the same path-by-path solve as step_fp32c_kernel
+    // with the whole block as one team.  The Hines diagonal and rhs of each
+    // compartment (after elimination f and c, after substitution dV) live in
+    // a global float2 scratch and the per-path slots in a global float4
+    // scratch (contribution d, rhs; potential across the head link), both
+    // written and read again within the item, so they stay in L2.  The
+    // tables are read from the item's blob in global memory (32-bit
+    // records); each lane loads the next eight compartments of its path
+    // while it eliminates (or substitutes) the current eight.
     __shared__ int s_item;
 
     const long long n = (long long)a.ctl->step_base + a.step_offset;
@@ -593,10 +588,17 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
         const int32_t *Vq = a.Vq + c0;
         const float *gax = a.gax + c0;
         float2 *dr = a.dr + G.scratch0;
+        float4 *pq = a.pq + G.pscratch0;
+        const unsigned char *blob = a.meta + G.meta_off;
+        const NrnG *nrns = (const NrnG *)blob;
+        const PathG *paths = (const PathG *)(blob + G.path_off);
+        const KidG *fold = (const KidG *)(blob + G.fold_off);
+        const int32_t *loffs = (const int32_t *)(blob + G.loffs_off);
+        const int32_t *mcnt = (const int32_t *)(blob + G.mcnt_off);
 
         // A. membrane conductance and current at (V^n, gates^n), plus the
-        //    axial terms of every link inside a segment (both ends; a link
-        //    (i-1, i) is inside a segment when g_axial[i] has no sign bit).
+        //    axial terms of every link inside a path (both ends; a link
+        //    (i-1, i) is inside a path when g_axial[i] has no sign bit).
 #pragma unroll 4
         for (int i = tid; i < G.ncomp; i += NT) {
             const int32_t vq = Vq[i];
@@ -625,11 +627,10 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
             dr[i] = make_float2(d, r);
         }
         __syncthreads();
-        const SegRec *segs = (const SegRec *)(a.meta + G.meta_off);
-        const int32_t *kids = (const int32_t *)(segs + G.nseg);
-        const int32_t *woff = kids + G.nchild;
 
-        // S. synaptic sites, then decay (sites are distinct compartments)
+        // S. synaptic sites, then decay (sites are distinct compartments);
+        //    per path the exact potential difference across its head link
+        //    (for the path from a soma: the stimulus current)
         for (int t = tid; t < G.nsite; t += NT) {
             const int st = G.site0 + t;
             const int c = a.site_comp[st];
@@ -640,114 +641,201 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
             dr[c] = v;
             a.gsyn[st] = g * a.decay;
         }
+        for (int pi = tid; pi < G.npath; pi += NT) {
+            const PathG P = paths[pi];
+            pq[pi].z = P.parent >= 0 ? mmf::vdiff(Vq[P.parent], Vq[P.head])
+                                     : (float)a.stim[G.neuron0 + (P.nflag & kPathNeuronG)];
+        }
         __syncthreads();
 
-        // B. leaves-to-root elimination (Algorithm 1), one segment per thread,
-        //    wave by wave.  Each child segment's contribution to the bottom
-        //    compartment is formed from the child top's stored 1/d and rhs:
-        //    link terms (+g, +g (V_t - V_P)) and elimination (-g^2/d_t, +g rhs_t/d_t).
-        for (int w = 0; w < G.nwave; ++w) {
-            const int sb = woff[w], se = woff[w + 1];
-            for (int si = sb + tid; si < se; si += NT) {
-                const SegRec S = segs[si];
-                const int bot = S.top + S.len - 1;
-                prefetch_l1(dr + S.top, S.len * (int)sizeof(float2));
-                prefetch_l1(gax + S.top, S.len * (int)sizeof(float));
-                float2 v = dr[bot];
-                float db = v.x, rb = v.y;
-                if (S.nchild) {
-                    const int32_t vb = Vq[bot];
-                    for (int c = 0; c < S.nchild; ++c) {
-                        const int t = segs[kids[S.child0 + c]].top;
-                        const float2 ct = dr[t];  // (1/d_t, rhs_t)
-                        const float g = fabsf(gax[t]);
-                        const float f = g * ct.x;
-                        db += fmaf(-f, g, g);
-                        rb += fmaf(f, ct.y, g * mmf::vdiff(Vq[t], vb));
+        // B. leaves-to-root elimination path by path, from the deepest level
+        //    up (as in step_fp32c_kernel)
+        auto eliminate_path = [&](int pi) {
+            const PathG P = paths[pi];
+            const int h = P.head;
+            const float gh = fabsf(gax[h]), vt = pq[pi].z;
+            int j = P.end - 1;
+            const float2 v0 = dr[j];
+            float db = v0.x, rb = v0.y, dh = db, rh = rb;
+            float g0[8], d0[8], r0[8], g1[8], d1[8], r1[8];
+            auto load = [&](int jj, float *g, float *d, float *r) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int q = max(jj - k, h + 1);
+                    g[k] = fabsf(gax[q]);
+                    const float2 w = dr[q - 1];
+                    d[k] = w.x;
+                    r[k] = w.y;
+                }
+            };
+            auto chain = [&](int jj, const float *g, const float *d, const float *r) {
+                const int cnt = jj - h;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float inv = rcp_approx(db);
+                    const float f = g[k] * inv;
+                    if (k < cnt) dr[jj - k] = make_float2(f, rb * inv);
+                    rb = fmaf(f, rb, r[k]);
+                    db = fmaf(-g[k] * g[k], inv, d[k]);
+                    if (k == cnt - 1) {
+                        dh = db;
+                        rh = rb;
                     }
                 }
-                for (int j = bot; j > S.top; --j) {
-                    const float g = fabsf(gax[j]);
-                    const float inv = rcp_approx(db);
-                    dr[j] = make_float2(inv, rb);
-                    const float f = g * inv;
-                    const float2 p = dr[j - 1];
-                    db = fmaf(-f, g, p.x);
-                    rb = fmaf(f, rb, p.y);
-                }
-                const int t = S.top;
-                if (S.parent >= 0) {
-                    const float g = fabsf(gax[t]);
-                    db += g;
-                    rb = fmaf(g, mmf::vdiff(Vq[S.parent], Vq[t]), rb);
-                    dr[t] = make_float2(rcp_approx(db), rb);
-                } else {
-                    rb += (float)a.stim[G.neuron0 + S.neuron];
-                    const float inv = rcp_approx(db);
-                    dr[t] = make_float2(inv, rb * inv);  // dV at the soma
+            };
+            if (j > h) {
+                load(j, g0, d0, r0);
+                for (;;) {
+                    int jn = j - 8;
+                    bool more = jn > h;
+                    if (more) load(jn, g1, d1, r1);
+                    chain(j, g0, d0, r0);
+                    j = jn;
+                    if (!more) break;
+                    jn = j - 8;
+                    more = jn > h;
+                    if (more) load(jn, g0, d0, r0);
+                    chain(j, g1, d1, r1);
+                    j = jn;
+                    if (!more) break;
                 }
             }
-            __syncthreads();
+            if (P.parent < 0) {  // soma: the stimulus, then its dV
+                dr[h].y = (rh + vt) * rcp_approx(dh);
+                return;
+            }
+            dh += gh;
+            rh = fmaf(gh, vt, rh);
+            const float inv = rcp_approx(dh);
+            const float f = gh * inv;
+            dr[h] = make_float2(f, rh * inv);
+            const float cd = fmaf(-f, gh, gh), cr = fmaf(f, rh, -gh * vt);
+            if (P.nflag & kPathAloneG) {
+                float2 v = dr[P.parent];
+                v.x += cd;
+                v.y += cr;
+                dr[P.parent] = v;
+            } else {
+                pq[pi].x = cd;
+                pq[pi].y = cr;
+            }
+        };
+        auto fold_shared = [&](int e0, int e1) {
+            for (int e = e0 + tid; e < e1; e += NT) {
+                const KidG kv = fold[e];
+                if (e > e0 && fold[e - 1].y == kv.y) continue;
+                float ad = pq[kv.x].x, ar = pq[kv.x].y;
+                for (int z = e + 1; z < e1; ++z) {
+                    const KidG kz = fold[z];
+                    if (kz.y != kv.y) break;
+                    ad += pq[kz.x].x;
+                    ar += pq[kz.x].y;
+                }
+                float2 v = dr[kv.y];
+                v.x += ad;
+                v.y += ar;
+                dr[kv.y] = v;
+            }
+        };
+        // F. root-to-leaves substitution path by path; the path from a soma
+        //    runs the FP64 soma accumulator and the spike test
+        auto substitute_path = [&](int pi) {
+            const PathG P = paths[pi];
+            const int h = P.head;
+            float x;
+            if (P.parent >= 0) {
+                const float2 fh = dr[h];
+                x = fmaf(fh.x, dr[P.parent].y, fh.y);
+            } else {
+                x = dr[h].y;
+                const int nrn = G.neuron0 + (P.nflag & kPathNeuronG);
+                const double v0 = a.Vsoma[nrn], v1 = v0 + (double)x;
+                a.Vsoma[nrn] = v1;
+                if (!isfinite(v1)) atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
+                if (v0 < a.threshold && v1 >= a.threshold) {
+                    const double ts = (double)n * a.dt64 + a.dt64 * (a.threshold - v0) / (v1 - v0);
+                    const unsigned long long k = atomicAdd(&a.ctl->spk_count, 1ull);
+                    if ((long long)k < a.spk_cap) {
+                        a.spk_nrn[k] = a.user_id[nrn];
+                        a.spk_t[k] = ts;
+                    } else {
+                        atomicOr(&a.ctl->err, MMK_ERR_OVERFLOW);
+                    }
+                    const int slot = (int)(n % a.R);
+                    const int pos = atomicAdd(&a.ring_cnt[slot], 1);
+                    a.ring_nrn[(long long)slot * a.N + pos] = nrn;
+                }
+            }
+            const float xh = x;
+            float f0[8], c0v[8], f1[8], c1v[8];
+            auto load = [&](int jj, float *f, float *c) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float2 w = dr[min(jj + k, P.end - 1)];
+                    f[k] = w.x;
+                    c[k] = w.y;
+                }
+            };
+            auto chain = [&](int jj, const float *f, const float *c) {
+                const int cnt = P.end - jj;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    x = fmaf(f[k], x, c[k]);
+                    if (k < cnt) dr[jj + k].y = x;
+                }
+            };
+            int j = h + 1;
+            if (j < P.end) {
+                load(j, f0, c0v);
+                for (;;) {
+                    int jn = j + 8;
+                    bool more = jn < P.end;
+                    if (more) load(jn, f1, c1v);
+                    chain(j, f0, c0v);
+                    j = jn;
+                    if (!more) break;
+                    jn = j + 8;
+                    more = jn < P.end;
+                    if (more) load(jn, f0, c0v);
+                    chain(j, f1, c1v);
+                    j = jn;
+                    if (!more) break;
+                }
+            }
+            if (P.parent >= 0) dr[h].y = xh;  // read by the next level only
+        };
+
+        for (int k = 0; k < G.nneuron; ++k) {
+            const NrnG Nk = nrns[k];
+            const int32_t *lo = loffs + Nk.loff0;
+            const int32_t *mc = mcnt + Nk.loff0;
+            for (int l = Nk.nlevel - 1; l >= 0; --l) {
+                const int pb = lo[l], pe = lo[l + 1];
+                for (int pi = pb + tid; pi < pe; pi += NT) eliminate_path(pi);
+                __syncthreads();
+                if (mc[l] > 0) {
+                    fold_shared(pb, pb + mc[l]);
+                    __syncthreads();
+                }
+            }
+            for (int l = 0; l < Nk.nlevel; ++l) {
+                const int pe = lo[l + 1];
+                for (int pi = lo[l] + tid; pi < pe; pi += NT) substitute_path(pi);
+                __syncthreads();
+            }
         }
 
-        // F. root-to-leaves substitution, V^{n+1} = V^n + dV in fixed point as
-        //    each compartment is reached; the soma segment also runs the FP64
-        //    soma accumulator and the spike test.
-        for (int w = G.nwave - 1; w >= 0; --w) {
-            const int sb = woff[w], se = woff[w + 1];
-            for (int si = sb + tid; si < se; si += NT) {
-                const SegRec S = segs[si];
-                const int t = S.top;
-                prefetch_l1(dr + t, S.len * (int)sizeof(float2));
-                prefetch_l1(gax + t, S.len * (int)sizeof(float));
-                prefetch_l1(Vq + t, S.len * (int)sizeof(int32_t));
-                float x;
-                const float2 vt = dr[t];
-                if (S.parent >= 0) {
-                    x = fmaf(fabsf(gax[t]), dr[S.parent].y, vt.y) * vt.x;
-                } else {
-                    x = vt.y;
-                    const int nrn = G.neuron0 + S.neuron;
-                    const double v0 = a.Vsoma[nrn], v1 = v0 + (double)x;
-                    a.Vsoma[nrn] = v1;
-                    if (!isfinite(v1)) atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
-                    if (v0 < a.threshold && v1 >= a.threshold) {
-                        const double ts = (double)n * a.dt64 + a.dt64 * (a.threshold - v0) / (v1 - v0);
-                        const unsigned long long k = atomicAdd(&a.ctl->spk_count, 1ull);
-                        if ((long long)k < a.spk_cap) {
-                            a.spk_nrn[k] = a.user_id[nrn];
-                            a.spk_t[k] = ts;
-                        } else {
-                            atomicOr(&a.ctl->err, MMK_ERR_OVERFLOW);
-                        }
-                        const int slot = (int)(n % a.R);
-                        const int pos = atomicAdd(&a.ring_cnt[slot], 1);
-                        a.ring_nrn[(long long)slot * a.N + pos] = nrn;
-                    }
-                }
-                dr[t].y = x;
-                int32_t vn;
-                if (!mmf::v_add(Vq[t], x, &vn)) {
-                    atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
-                    vn = Vq[t];
-                }
-                int32_t *Vw = a.Vq + c0;
-                for (int j = t + 1; j < t + S.len; ++j) {
-                    const float2 v = dr[j];
-                    x = fmaf(fabsf(gax[j]), x, v.y) * v.x;
-                    dr[j].y = x;
-                    int32_t vj;
-                    if (!mmf::v_add(Vq[j], x, &vj)) {
-                        atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
-                        vj = Vq[j];
-                    }
-                    Vw[j] = vj;
-                }
-                Vw[t] = vn;
+        // C. V^{n+1} = V^n + dV (exact in fixed point), then the gates at V^{n+1}
+        for (int i = tid; i < G.ncomp; i += NT) {
+            const int32_t vold = Vq[i];
+            int32_t vq;
+            if (!mmf::v_add(vold, dr[i].y, &vq)) {
+                atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
+                vq = vold;
             }
-            __syncthreads();
+            a.Vq[c0 + i] = vq;
         }
-        // gates at V^{n+1} (final after the last wave's barrier)
+        __syncthreads();
         for (int i = tid; i < G.ncomp; i += NT) gate_update(a, c0 + i);
         if (a.item_ns) {
             __syncthreads();

@@ -22,6 +22,7 @@
 #include "mm_layout.h"
 
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <cmath>
 #include <map>
@@ -44,18 +45,18 @@ struct PathTmp {
     int32_t head, end, parent, neuron, level;
 };
 
-// The blob of an FP32c work item solved path by path (see mmk::NrnQ):
+// The tables of an FP32c work item solved path by path (see mmk::NrnQ):
 // per neuron its paths by (level, longest first, head); per level a fold
 // list of the same paths, those sharing a parent compartment first (sorted
 // by that compartment, deepest first, then head), then the paths alone on
-// their parent compartment.
+// their parent compartment.  Emitted with 16-bit (shared-memory items) or
+// 32-bit (giant items) records.
 struct PathBlob {
-    std::vector<mmk::NrnQ> nrns;
-    std::vector<mmk::PathQ> paths;
-    std::vector<mmk::KidQ> fold;
-    std::vector<int16_t> loffs, mcnt;
-    int32_t nlevel = 0;
-    int64_t path_off = 0, fold_off = 0, loffs_off = 0, mcnt_off = 0, bytes = 0;
+    std::vector<int32_t> nrn;    // 4 per neuron: path0, npath, nlevel, loff0
+    std::vector<int32_t> path;   // 4 per path: head, end, parent, neuron | alone
+    std::vector<int32_t> fold;   // 2 per entry: path, parent compartment
+    std::vector<int32_t> loffs, mcnt;
+    int32_t nlevel = 0, npath = 0;
 };
 
 // paths: every path of the item (group-local compartments), neurons in
@@ -69,20 +70,24 @@ void build_path_blob(std::vector<PathTmp> &paths, int32_t nneuron, PathBlob &b)
         return a.head < c.head;
     });
     const int32_t np = (int32_t)paths.size();
+    b.npath = np;
     std::map<int32_t, int32_t> share;  // parent compartment -> paths hanging off it
     for (int32_t q = 0; q < np; ++q)
         if (paths[(size_t)q].parent >= 0) share[paths[(size_t)q].parent]++;
-    b.nrns.assign((size_t)nneuron, mmk::NrnQ{0, 0, 0, 0});
-    b.paths.resize((size_t)np);
-    b.fold.resize((size_t)np);
+    auto shared = [&](int32_t x) { return paths[(size_t)x].parent >= 0 && share[paths[(size_t)x].parent] > 1; };
+    b.nrn.assign(4 * (size_t)nneuron, 0);
+    b.path.resize(4 * (size_t)np);
+    b.fold.resize(2 * (size_t)np);
     b.loffs.clear();
     b.mcnt.clear();
     b.nlevel = 0;
     for (int32_t q = 0; q < np; ++q) {
         const PathTmp &P = paths[(size_t)q];
         const bool alone = P.parent >= 0 && share[P.parent] == 1;
-        b.paths[(size_t)q] = mmk::PathQ{(int16_t)P.head, (int16_t)P.end, (int16_t)P.parent,
-                                        (int16_t)(P.neuron | (alone ? mmk::kPathAlone : 0))};
+        b.path[4 * (size_t)q] = P.head;
+        b.path[4 * (size_t)q + 1] = P.end;
+        b.path[4 * (size_t)q + 2] = P.parent;
+        b.path[4 * (size_t)q + 3] = P.neuron | (alone ? (1 << 30) : 0);
     }
     int32_t i = 0;
     std::vector<int32_t> lv;
@@ -91,17 +96,19 @@ void build_path_blob(std::vector<PathTmp> &paths, int32_t nneuron, PathBlob &b)
         while (i < np && paths[(size_t)i].neuron == k) ++i;
         const int32_t nl = i > p0 ? paths[(size_t)i - 1].level + 1 : 0;
         const size_t lbase = b.loffs.size();
-        b.nrns[(size_t)k] = mmk::NrnQ{(int16_t)p0, (int16_t)(i - p0), (int16_t)nl, (int16_t)lbase};
+        b.nrn[4 * (size_t)k] = p0;
+        b.nrn[4 * (size_t)k + 1] = i - p0;
+        b.nrn[4 * (size_t)k + 2] = nl;
+        b.nrn[4 * (size_t)k + 3] = (int32_t)lbase;
         for (int32_t l = 0, q = p0; l <= nl; ++l) {
             while (q < i && paths[(size_t)q].level < l) ++q;
-            b.loffs.push_back((int16_t)q);
+            b.loffs.push_back(q);
             b.mcnt.push_back(0);
         }
         for (int32_t l = 0; l < nl; ++l) {
             const int32_t s = b.loffs[lbase + (size_t)l], e = b.loffs[lbase + (size_t)l + 1];
             lv.resize((size_t)(e - s));
             std::iota(lv.begin(), lv.end(), s);
-            auto shared = [&](int32_t x) { return paths[(size_t)x].parent >= 0 && share[paths[(size_t)x].parent] > 1; };
             std::sort(lv.begin(), lv.end(), [&](int32_t x, int32_t y) {
                 if (shared(x) != shared(y)) return shared(x);
                 if (paths[(size_t)x].parent != paths[(size_t)y].parent) return paths[(size_t)x].parent > paths[(size_t)y].parent;
@@ -111,17 +118,68 @@ void build_path_blob(std::vector<PathTmp> &paths, int32_t nneuron, PathBlob &b)
             for (int32_t z = s; z < e; ++z) {
                 const int32_t c = lv[(size_t)(z - s)];
                 m += shared(c) ? 1 : 0;
-                b.fold[(size_t)z] = (mmk::KidQ)(uint32_t)c | ((mmk::KidQ)(uint16_t)paths[(size_t)c].parent << 16);
+                b.fold[2 * (size_t)z] = c;
+                b.fold[2 * (size_t)z + 1] = paths[(size_t)c].parent;
             }
-            b.mcnt[lbase + (size_t)l] = (int16_t)m;
+            b.mcnt[lbase + (size_t)l] = m;
         }
         b.nlevel = std::max(b.nlevel, nl);
     }
-    b.path_off = ((int64_t)sizeof(mmk::NrnQ) * nneuron + 15) & ~15LL;
-    b.fold_off = b.path_off + (int64_t)sizeof(mmk::PathQ) * np;
-    b.loffs_off = b.fold_off + (int64_t)sizeof(mmk::KidQ) * np;
-    b.mcnt_off = b.loffs_off + 2 * (int64_t)b.loffs.size();
-    b.bytes = (b.mcnt_off + 2 * (int64_t)b.mcnt.size() + 15) & ~15LL;
+}
+
+// Byte offsets of the tables in the blob and its size, for 16-bit (wide =
+// false) or 32-bit records.
+struct BlobOffsets {
+    int64_t path_off, fold_off, loffs_off, mcnt_off, bytes;
+};
+
+BlobOffsets blob_offsets(const PathBlob &b, int32_t nneuron, bool wide)
+{
+    BlobOffsets o;
+    const int64_t w = wide ? 4 : 2;  // bytes per index
+    o.path_off = (4 * w * nneuron + 15) & ~15LL;
+    o.fold_off = o.path_off + 4 * w * b.npath;
+    o.loffs_off = o.fold_off + 2 * w * b.npath;
+    o.mcnt_off = o.loffs_off + w * (int64_t)b.loffs.size();
+    o.bytes = (o.mcnt_off + w * (int64_t)b.mcnt.size() + 15) & ~15LL;
+    return o;
+}
+
+// The blob itself (offsets as blob_offsets; 16-bit records pack the alone
+// flag as mmk::kPathAlone and the fold entries as mmk::KidQ).
+std::vector<unsigned char> emit_path_blob(const PathBlob &b, int32_t nneuron, bool wide)
+{
+    const BlobOffsets o = blob_offsets(b, nneuron, wide);
+    std::vector<unsigned char> blob((size_t)o.bytes, 0);
+    auto put32 = [&](int64_t off, const std::vector<int32_t> &v) { std::memcpy(blob.data() + off, v.data(), 4 * v.size()); };
+    auto put16 = [&](int64_t off, const std::vector<int32_t> &v) {
+        for (size_t i = 0; i < v.size(); ++i) {
+            const int16_t x = (int16_t)v[i];
+            std::memcpy(blob.data() + off + 2 * (int64_t)i, &x, 2);
+        }
+    };
+    if (wide) {
+        std::vector<int32_t> pathg(b.path);
+        for (size_t q = 0; q < (size_t)b.npath; ++q)
+            pathg[4 * q + 3] = (b.path[4 * q + 3] & ((1 << 30) - 1)) | ((b.path[4 * q + 3] >> 30) ? mmk::kPathAloneG : 0);
+        put32(0, b.nrn);
+        put32(o.path_off, pathg);
+        put32(o.fold_off, b.fold);
+        put32(o.loffs_off, b.loffs);
+        put32(o.mcnt_off, b.mcnt);
+    } else {
+        std::vector<int32_t> path16(b.path), fold16((size_t)b.npath);
+        for (size_t q = 0; q < (size_t)b.npath; ++q) {
+            path16[4 * q + 3] = (b.path[4 * q + 3] & ((1 << 30) - 1)) | ((b.path[4 * q + 3] >> 30) ? mmk::kPathAlone : 0);
+            fold16[q] = (int32_t)((uint32_t)b.fold[2 * q] | ((uint32_t)(uint16_t)b.fold[2 * q + 1] << 16));
+        }
+        put16(0, b.nrn);
+        put16(o.path_off, path16);
+        put32(o.fold_off, fold16);
+        put16(o.loffs_off, b.loffs);
+        put16(o.mcnt_off, b.mcnt);
+    }
+    return blob;
 }
 
 }  // namespace
@@ -493,13 +551,14 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
             nkids += (int64_t)gkids[(size_t)perm[(size_t)i]].size();
         }
         // shared-memory need: FP64 items hold the segment blob, FP32c items
-        // the path blob (plus per-path slots)
+        // the path tables (16-bit records) plus per-path slots
         PathBlob pb;
         int64_t smem_need;
         if (in.path_items) {
-            if (gr.ncomp <= 32767 && gpaths.size() <= 32767) {
-                build_path_blob(gpaths, gr.nneuron, pb);
-                smem_need = pb.bytes + (int64_t)in.smem_per_comp * gr.ncomp + (int64_t)in.smem_per_path * (int64_t)pb.paths.size();
+            build_path_blob(gpaths, gr.nneuron, pb);
+            if (gr.ncomp <= 32767 && pb.npath <= 32767) {
+                smem_need = blob_offsets(pb, gr.nneuron, false).bytes + (int64_t)in.smem_per_comp * gr.ncomp +
+                            (int64_t)in.smem_per_path * pb.npath;
             } else {
                 smem_need = INT64_MAX;
             }
@@ -509,52 +568,57 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         }
         const bool over = in.giant_smem_limit > 0 && smem_need > in.giant_smem_limit;
         const bool big = over && in.big_smem_limit > 0 && smem_need <= in.big_smem_limit;
-        const bool giant = gr.ncomp > 32767 || ns > 32767 || (over && !big);
+        const bool giant = (in.path_items ? (gr.ncomp > 32767 || pb.npath > 32767) : (gr.ncomp > 32767 || ns > 32767)) ||
+                           (over && !big);
         if (giant && in.giant_smem_limit <= 0) {
             *invalid = false;
             e << "a work item of " << gr.ncomp << " compartments exceeds what this precision holds";
             return msg(e);
         }
-        if (in.path_items && !giant) {
+        std::vector<unsigned char> blob;
+        if (in.path_items) {
             // links inside paths are assembled per compartment; path heads
             // (negative parent distance) link to their parent in the sweep
             for (int64_t c = comp0; c < comp0 + gr.ncomp; ++c) {
                 const int32_t pd = std::abs(L.pdist[(size_t)c]);
                 L.pdist[(size_t)c] = pd == 1 ? 1 : -pd;
             }
-        }
-        // the tree blob: records in wave order, child lists, wave offsets;
-        // 16-bit indices for items staged in shared memory, 32-bit for giants
-        std::vector<int32_t> woff;
-        {
-            int32_t i = 0;
-            for (int32_t h = 0; h <= maxh; ++h) {
-                while (i < ns && gheight[(size_t)perm[(size_t)i]] < h) ++i;
-                woff.push_back(i);
-            }
-            woff.push_back(ns);
-        }
-        gr.nchild = (int32_t)nkids;
-        gr.nwave = maxh + 1;
-        std::vector<unsigned char> blob;
-        auto put = [&blob](const void *p, size_t n) {
-            const unsigned char *c = (const unsigned char *)p;
-            blob.insert(blob.end(), c, c + n);
-        };
-        if (!giant && in.path_items) {
-            put(pb.nrns.data(), pb.nrns.size() * sizeof(mmk::NrnQ));
-            blob.resize((size_t)pb.path_off, 0);
-            put(pb.paths.data(), pb.paths.size() * sizeof(mmk::PathQ));
-            put(pb.fold.data(), pb.fold.size() * sizeof(mmk::KidQ));
-            put(pb.loffs.data(), pb.loffs.size() * 2);
-            put(pb.mcnt.data(), pb.mcnt.size() * 2);
-            gr.path_off = (int32_t)pb.path_off;
-            gr.mcnt_off = (int32_t)pb.mcnt_off;
-            gr.fold_off = (int32_t)pb.fold_off;
-            gr.loffs_off = (int32_t)pb.loffs_off;
-            gr.npath = (int32_t)pb.paths.size();
+            // 16-bit records for items staged in shared memory, 32-bit for giants
+            const BlobOffsets o = blob_offsets(pb, gr.nneuron, giant);
+            blob = emit_path_blob(pb, gr.nneuron, giant);
+            gr.path_off = (int32_t)o.path_off;
+            gr.fold_off = (int32_t)o.fold_off;
+            gr.loffs_off = (int32_t)o.loffs_off;
+            gr.mcnt_off = (int32_t)o.mcnt_off;
+            gr.npath = pb.npath;
             gr.nlevel = pb.nlevel;
-        } else if (!giant) {
+            if (giant) {
+                gr.scratch0 = L.giant_comps;
+                L.giant_comps += gr.ncomp;
+                if (L.giant_paths + pb.npath > INT32_MAX) {
+                    e << "giant work items hold more than 2^31 paths";
+                    return msg(e);
+                }
+                gr.pscratch0 = (int32_t)L.giant_paths;
+                L.giant_paths += pb.npath;
+            }
+        } else {
+            // the segment blob: records in wave order, child lists, wave offsets
+            std::vector<int32_t> woff;
+            {
+                int32_t i = 0;
+                for (int32_t h = 0; h <= maxh; ++h) {
+                    while (i < ns && gheight[(size_t)perm[(size_t)i]] < h) ++i;
+                    woff.push_back(i);
+                }
+                woff.push_back(ns);
+            }
+            gr.nchild = (int32_t)nkids;
+            gr.nwave = maxh + 1;
+            auto put = [&blob](const void *p, size_t n) {
+                const unsigned char *c = (const unsigned char *)p;
+                blob.insert(blob.end(), c, c + n);
+            };
             std::vector<int16_t> kids;
             std::vector<mmk::SegP> recs((size_t)ns);
             for (int32_t i = 0; i < ns; ++i) {
@@ -576,22 +640,6 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
             put(recs.data(), recs.size() * sizeof(mmk::SegP));
             put(kids.data(), kids.size() * 2);
             put(w16.data(), w16.size() * 2);
-        } else {
-            std::vector<int32_t> kids;
-            std::vector<mmk::SegRec> recs((size_t)ns);
-            for (int32_t i = 0; i < ns; ++i) {
-                const int32_t sidx = perm[(size_t)i];
-                mmk::SegRec q = gsegs[(size_t)sidx];
-                q.nchild = (int32_t)gkids[(size_t)sidx].size();
-                q.child0 = (int32_t)kids.size();
-                for (int32_t c : gkids[(size_t)sidx]) kids.push_back(newidx[(size_t)c]);
-                recs[(size_t)i] = q;
-            }
-            put(recs.data(), recs.size() * sizeof(mmk::SegRec));
-            put(kids.data(), kids.size() * 4);
-            put(woff.data(), woff.size() * 4);
-            gr.scratch0 = L.giant_comps;
-            L.giant_comps += gr.ncomp;
         }
         blob.resize((blob.size() + 15) & ~(size_t)15, 0);
         gr.meta_off = (int64_t)L.meta.size();

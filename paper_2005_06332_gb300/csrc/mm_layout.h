@@ -55,6 +55,7 @@ struct Layout {
     // largest shared-memory need (model above) of one item of each class
     int64_t max_smem = 0, big_max_smem = 0;
     int64_t giant_comps = 0;            // compartments in giant items (size of the Hines scratch)
+    int64_t giant_paths = 0;            // paths in giant items (size of the per-path scratch)
     std::vector<int32_t> site_comp;     // group-local compartment of each site
     std::vector<int64_t> site_internal; // internal compartment of each site
     std::vector<int64_t> out_off;       // outgoing synapses per internal source [N+1]
