@@ -198,8 +198,9 @@ typedef struct {
     int64_t step_kernel_launches;
     double deliver_kernel_ms;       /* spike-delivery kernel, summed */
     int64_t deliver_kernel_launches;
-    double giant_kernel_ms;         /* FP32c giant-neuron solve kernel, summed */
-    int64_t giant_kernel_launches;
+    double giant_kernel_ms;         /* FP32c giant items: phase A, solve and phase C + gate kernels, summed
+                                       (the solve runs on a side stream beside the other classes) */
+    int64_t giant_kernel_launches;  /* steps (solve-kernel launches) */
     double big_kernel_ms;           /* FP32c per-step kernel on the large shared-memory class, summed */
     int64_t big_kernel_launches;
 } mm_kernel_times;

@@ -51,7 +51,7 @@ struct mm_net {
 
     mmk::StepArgs sa{};
     mmk::DeliverArgs da{};
-    int step_blocks = 1, step_threads = kStepThreads, deliver_blocks = 1, giant_blocks = 1;
+    int step_blocks = 1, step_threads = kStepThreads, deliver_blocks = 1, giant_blocks = 1, giant_chunk_blocks = 1;
     int32_t n_giant = 0, n_small = 0, n_big = 0;
     int big_blocks = 1;
     int graph_steps = 40;
@@ -196,9 +196,10 @@ mm_status collect_timing(mm_net *net)
         if (p.kind == 0) {
             net->times.deliver_kernel_ms += ms;
             net->times.deliver_kernel_launches++;
-        } else if (p.kind == 3) {
+        } else if (p.kind == 3 || p.kind == 5 || p.kind == 6) {
+            // the three kernels of the giant items; one launch per step
             net->times.giant_kernel_ms += ms;
-            net->times.giant_kernel_launches++;
+            if (p.kind == 3) net->times.giant_kernel_launches++;
         } else if (p.kind == 4) {
             net->times.big_kernel_ms += ms;
             net->times.big_kernel_launches++;
@@ -216,27 +217,36 @@ mm_status collect_timing(mm_net *net)
 mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
 {
     const bool timed = net->timing && s == net->stream;
-    // per step: delivery, then the solve of each work-item class (each also
-    // updates the gates of its own compartments at their new voltages)
-    int kinds[4], nk = 0;
+    // Per step: delivery, then the solve of each work-item class.  FP32c
+    // giant items: phase A of all their compartments (every SM), their
+    // solve forked onto the side stream to run beside the shared-memory
+    // classes, and after the join phase C and the gates (every SM).
+    //   kinds: 0 delivery, 1 regular class, 4 large class, 5 giant phase A,
+    //          3 giant solve (side stream), 6 giant phase C + gates
+    const bool giants = net->precision != MM_FP64 && net->n_giant > 0;
+    int kinds[8], nk = 0;
     kinds[nk++] = 0;
     if (net->precision == MM_FP64) {
         kinds[nk++] = 1;
     } else {
-        if (net->n_giant > 0) kinds[nk++] = 3;  // forked first, so that its blocks start first
+        if (giants) {
+            kinds[nk++] = 5;
+            kinds[nk++] = 3;
+        }
         if (net->n_small > 0) kinds[nk++] = 1;
         if (net->n_big > 0) kinds[nk++] = 4;
+        if (giants) kinds[nk++] = 6;
     }
     for (int j = 0; j < count; ++j) {
         for (int ki = 0; ki < nk; ++ki) {
             const int kind = kinds[ki];
-            // giants: forked onto the side stream right after delivery
             const bool forked = kind == 3;
             cudaStream_t ks = forked ? net->side : s;
             if (forked) {
                 MM_CK(net, cudaEventRecord(net->ev_fork, s));
                 MM_CK(net, cudaStreamWaitEvent(net->side, net->ev_fork, 0));
             }
+            if (kind == 6) MM_CK(net, cudaStreamWaitEvent(s, net->ev_join, 0));
             mm_net::Pending p{nullptr, nullptr, kind};
             if (timed) {
                 MM_CK(net, take_event(net, &p.a));
@@ -260,10 +270,12 @@ mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
                 mmk::StepArgs32 sa = net->sa32b;
                 sa.step_offset = j;
                 MM_CKI(net, mmk_launch_step_fp32c(sa, net->big_blocks, kBigThreads, s));
-            } else if (kind == 3) {
+            } else {
                 mmk::StepArgs32 sa = net->sa32g;
                 sa.step_offset = j;
-                MM_CKI(net, mmk_launch_giant_fp32c(sa, net->giant_blocks, ks));
+                if (kind == 5) MM_CKI(net, mmk_launch_giant_assemble(sa, net->giant_chunk_blocks, s));
+                else if (kind == 3) MM_CKI(net, mmk_launch_giant_fp32c(sa, net->giant_blocks, ks));
+                else MM_CKI(net, mmk_launch_giant_update(sa, net->giant_chunk_blocks, s));
             }
             if (timed) {
                 MM_CK(net, cudaEventRecord(p.b, ks));
@@ -271,7 +283,6 @@ mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
             }
             if (forked) MM_CK(net, cudaEventRecord(net->ev_join, net->side));
         }
-        if (net->precision != MM_FP64 && net->n_giant > 0) MM_CK(net, cudaStreamWaitEvent(s, net->ev_join, 0));
         if (timed && net->pending.size() > 4096) {
             mm_status st = collect_timing(net);
             if (st != MM_OK) return st;
@@ -679,6 +690,17 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         g.item0 = L.n_small + L.n_big;
         g.item1 = (int32_t)L.groups.size();
         g.queue = &net->ctl->giant_head;
+        // the giant items' compartments in chunks for the assembly and
+        // update kernels: first chunk of each giant item, then the total
+        std::vector<int64_t> gch(1, 0);
+        for (int32_t gi = g.item0; gi < g.item1; ++gi) {
+            const int64_t nc = L.groups[(size_t)gi].ncomp;
+            gch.push_back(gch.back() + (nc + mmk_giant_chunk() - 1) / mmk_giant_chunk());
+        }
+        int64_t *dgch = nullptr;
+        if ((st = upload(net, &dgch, gch.data(), gch.size())) != MM_OK) return st;
+        g.gchunk0 = dgch;
+        net->giant_chunk_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(gch.back(), 4 * (int64_t)sms));
     }
     net->info.work_items = (int32_t)L.groups.size();
     net->info.blocks = net->step_blocks;

@@ -198,6 +198,7 @@ struct StepArgs32 {
     float2 *dr;                       // scratch for giant items: Hines diagonal and rhs per compartment
     float4 *pq;                       // scratch for giant items: per path its contribution (d, rhs) and
                                       // the potential across its head link
+    const int64_t *gchunk0;           // giant items: first compartment chunk of each [item1 - item0 + 1]
     unsigned long long *item_ns;      // per work item solve time (ns, summed over steps) or nullptr
     const double *stim;               // nA [N]
     const int32_t *user_id;
@@ -270,6 +271,9 @@ int mmk_step_fp32c_blocks_per_sm(int threads, int smem_bytes, int *blocks);
 size_t mmk_step_fp64_smem(int comps, int segs, int meta_bytes);
 int mmk_launch_init_fp32c(const mmk::InitArgs &a, void *stream);
 int mmk_launch_giant_fp32c(const mmk::StepArgs32 &a, int blocks, void *stream);
+int mmk_launch_giant_assemble(const mmk::StepArgs32 &a, int chunk_blocks, void *stream);
+int mmk_launch_giant_update(const mmk::StepArgs32 &a, int chunk_blocks, void *stream);
+int mmk_giant_chunk();
 int mmk_launch_deliver_fp32c(const mmk::DeliverArgs &a, int blocks, void *stream);
 int mmk_launch_vq_to_f64(const int32_t *vq, double *dst, int64_t n, void *stream);
 int mmk_launch_gq_to_f64(const uint32_t *q, double *dst, int64_t n, void *stream);

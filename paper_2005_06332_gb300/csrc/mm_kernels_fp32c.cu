@@ -563,14 +563,16 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
 {
     // Work items too large for shared memory (giant neurons, up to the
     // int32 index range): the same path-by-path solve as step_fp32c_kernel
-    // with the whole block as one team.  The Hines diagonal and rhs of each
-    // compartment (after elimination f and c, after substitution dV) live in
-    // a global float2 scratch and the per-path slots in a global float4
-    // scratch (contribution d, rhs; potential across the head link), both
-    // written and read again within the item, so they stay in L2.  The
-    // tables are read from the item's blob in global memory (32-bit
-    // records); each lane loads the next eight compartments of its path
-    // while it eliminates (or substitutes) the current eight.
+    // with the whole block as one team, between giant_assemble_kernel
+    // (phase A of every giant compartment, spread over many blocks) and
+    // giant_update_kernel (phase C and the gates, likewise).  The Hines
+    // diagonal and rhs of each compartment (after elimination f and c,
+    // after substitution dV) live in a global float2 scratch and the
+    // per-path slots in a global float4 scratch (contribution d, rhs;
+    // potential across the head link), so they stay in L2.  The tables are
+    // read from the item's blob in global memory (32-bit records); each lane
+    // loads the next eight compartments of its path while it eliminates (or
+    // substitutes) the current eight.
     __shared__ int s_item;
 
     const long long n = (long long)a.ctl->step_base + a.step_offset;
@@ -595,38 +597,6 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
         const KidG *fold = (const KidG *)(blob + G.fold_off);
         const int32_t *loffs = (const int32_t *)(blob + G.loffs_off);
         const int32_t *mcnt = (const int32_t *)(blob + G.mcnt_off);
-
-        // A. membrane conductance and current at (V^n, gates^n), plus the
-        //    axial terms of every link inside a path (both ends; a link
-        //    (i-1, i) is inside a path when g_axial[i] has no sign bit).
-#pragma unroll 4
-        for (int i = tid; i < G.ncomp; i += NT) {
-            const int32_t vq = Vq[i];
-            const float gs = gax[i];
-            const float m = mmf::gate_f(a.mq[c0 + i]), h = mmf::gate_f(a.hq[c0 + i]), nn = mmf::gate_f(a.nq[c0 + i]);
-            const float ar = a.area[c0 + i];
-            const float s = ar * 1e3f;
-            const float gna = a.gNa * s * (m * m * m * h);
-            const float n2 = nn * nn;
-            const float gk = a.gK * s * (n2 * n2);
-            const float gl = a.gL * s;
-            float d = fmaf(ar, a.cm_dt, gna + gk + gl);
-            float r = -fmaf(gna, vminus(vq, a.ENa), fmaf(gk, vminus(vq, a.EK), gl * vminus(vq, a.EL)));
-            if (!signbit(gs)) {  // link to the parent i-1
-                const float g = fabsf(gs);
-                d += g;
-                r = fmaf(g, mmf::vdiff(Vq[i - 1], vq), r);
-            }
-            if (i + 1 < G.ncomp) {
-                const float gc = gax[i + 1];
-                if (!signbit(gc)) {  // link to the child i+1
-                    d += gc;
-                    r = fmaf(gc, mmf::vdiff(Vq[i + 1], vq), r);
-                }
-            }
-            dr[i] = make_float2(d, r);
-        }
-        __syncthreads();
 
         // S. synaptic sites, then decay (sites are distinct compartments);
         //    per path the exact potential difference across its head link
@@ -825,21 +795,89 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
             }
         }
 
-        // C. V^{n+1} = V^n + dV (exact in fixed point), then the gates at V^{n+1}
-        for (int i = tid; i < G.ncomp; i += NT) {
-            const int32_t vold = Vq[i];
+        if (a.item_ns) {
+            __syncthreads();
+            if (tid == 0) a.item_ns[gi] += global_ns() - t_item;
+        }
+    }
+}
+
+// The giant items' compartments in chunks of kGiantChunk: chunk ch belongs
+// to the giant item k with gchunk0[k] <= ch < gchunk0[k + 1].
+constexpr int kGiantChunk = 2048;
+
+__device__ __forceinline__ int giant_of_chunk(const StepArgs32 &a, int64_t ch)
+{
+    int lo = 0, hi = a.item1 - a.item0;  // gchunk0 has item1 - item0 + 1 entries
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a.gchunk0[mid] <= ch) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Phase A of every giant compartment (as in step_fp32c_kernel), into the
+// global scratch.
+__global__ void __launch_bounds__(256) giant_assemble_kernel(StepArgs32 a)
+{
+    const int64_t nch = a.gchunk0[a.item1 - a.item0];
+    for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+        const int k = giant_of_chunk(a, ch);
+        const GroupRec &G = a.groups[a.item0 + k];
+        const int64_t c0 = G.comp0;
+        const int32_t *Vq = a.Vq + c0;
+        const float *gax = a.gax + c0;
+        float2 *dr = a.dr + G.scratch0;
+        const int i0 = (int)(ch - a.gchunk0[k]) * kGiantChunk, i1 = min(i0 + kGiantChunk, G.ncomp);
+        for (int i = i0 + (int)threadIdx.x; i < i1; i += 256) {
+            const int32_t vq = Vq[i];
+            const float gs = gax[i];
+            const float m = mmf::gate_f(a.mq[c0 + i]), h = mmf::gate_f(a.hq[c0 + i]), nn = mmf::gate_f(a.nq[c0 + i]);
+            const float ar = a.area[c0 + i];
+            const float s = ar * 1e3f;
+            const float gna = a.gNa * s * (m * m * m * h);
+            const float n2 = nn * nn;
+            const float gk = a.gK * s * (n2 * n2);
+            const float gl = a.gL * s;
+            float d = fmaf(ar, a.cm_dt, gna + gk + gl);
+            float r = -fmaf(gna, vminus(vq, a.ENa), fmaf(gk, vminus(vq, a.EK), gl * vminus(vq, a.EL)));
+            if (!signbit(gs)) {  // link to the parent i-1
+                const float g = fabsf(gs);
+                d += g;
+                r = fmaf(g, mmf::vdiff(Vq[i - 1], vq), r);
+            }
+            if (i + 1 < G.ncomp) {
+                const float gc = gax[i + 1];
+                if (!signbit(gc)) {  // link to the child i+1
+                    d += gc;
+                    r = fmaf(gc, mmf::vdiff(Vq[i + 1], vq), r);
+                }
+            }
+            dr[i] = make_float2(d, r);
+        }
+    }
+}
+
+// Phase C (V^{n+1} = V^n + dV, exact in fixed point) and the gates at
+// V^{n+1} of every giant compartment.
+__global__ void __launch_bounds__(256) giant_update_kernel(StepArgs32 a)
+{
+    const int64_t nch = a.gchunk0[a.item1 - a.item0];
+    for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+        const int k = giant_of_chunk(a, ch);
+        const GroupRec &G = a.groups[a.item0 + k];
+        const int64_t c0 = G.comp0;
+        const float2 *dr = a.dr + G.scratch0;
+        const int i0 = (int)(ch - a.gchunk0[k]) * kGiantChunk, i1 = min(i0 + kGiantChunk, G.ncomp);
+        for (int i = i0 + (int)threadIdx.x; i < i1; i += 256) {
+            const int32_t vold = a.Vq[c0 + i];
             int32_t vq;
             if (!mmf::v_add(vold, dr[i].y, &vq)) {
                 atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
                 vq = vold;
             }
             a.Vq[c0 + i] = vq;
-        }
-        __syncthreads();
-        for (int i = tid; i < G.ncomp; i += NT) gate_update(a, c0 + i);
-        if (a.item_ns) {
-            __syncthreads();
-            if (tid == 0) a.item_ns[gi] += global_ns() - t_item;
+            gate_update(a, c0 + i);
         }
     }
 }
@@ -884,6 +922,23 @@ int mmk_launch_giant_fp32c(const StepArgs32 &a, int blocks, void *stream)
 {
     giant_fp32c_kernel<256><<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
     return (int)cudaGetLastError();
+}
+
+int mmk_launch_giant_assemble(const StepArgs32 &a, int chunk_blocks, void *stream)
+{
+    giant_assemble_kernel<<<chunk_blocks, 256, 0, (cudaStream_t)stream>>>(a);
+    return (int)cudaGetLastError();
+}
+
+int mmk_launch_giant_update(const StepArgs32 &a, int chunk_blocks, void *stream)
+{
+    giant_update_kernel<<<chunk_blocks, 256, 0, (cudaStream_t)stream>>>(a);
+    return (int)cudaGetLastError();
+}
+
+int mmk_giant_chunk()
+{
+    return kGiantChunk;
 }
 
 int mmk_launch_step_fp32c(const StepArgs32 &a, int blocks, int threads, void *stream)
