@@ -44,6 +44,19 @@ MMF_HD float rcp_rn(float x)
 #endif
 }
 
+// An approximation of 1/x (relative error below 2^-22) for the first
+// quotient of a double-float division, whose remainder step corrects it.
+MMF_HD float rcp_fast(float x)
+{
+#ifdef __CUDA_ARCH__
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+#else
+    return 1.0f / x;
+#endif
+}
+
 MMF_HD int32_t f2i_rn(float x)
 {
 #ifdef __CUDA_ARCH__
@@ -128,11 +141,13 @@ MMF_HD F2 mul_f(F2 a, float b)
 // multiplication by a power of two (exact)
 MMF_HD F2 scale(F2 a, float p2) { return {a.hi * p2, a.lo * p2}; }
 
-// a / b: a first quotient from the reciprocal, then one correction of the
-// double-float remainder a - q b.
+// a / b: a first quotient from an approximate reciprocal, then one
+// correction of the double-float remainder a - q b (the remainder is formed
+// to double-float accuracy, so the quotient's error is the square of the
+// first quotient's, below 2^-44 relative).
 MMF_HD F2 div(F2 a, F2 b)
 {
-    const float r = rcp_rn(b.hi);
+    const float r = rcp_fast(b.hi);
     const float q1 = a.hi * r;
     const F2 rem = add(a, neg(mul_f(b, q1)));
     return quick_two_sum(q1, rem.hi * r);
@@ -282,19 +297,19 @@ struct Rates {
 };
 
 // Hodgkin-Huxley rates (1/ms) at V = vq * 2^-23 mV.  With u = -(V + 65),
-// every exponent is u/k plus a constant: three exponentials
-// E10 = e^{u/10}, E18 = e^{u/18}, E80 = e^{u/80} give all six rates
-// (e^{u/20} = E80^4; e^{-(V+40)/10} = e^{2.5} E10, e^{-(V+55)/10} = e E10,
+// every exponent is u/k plus a constant: two exponentials E18 = e^{u/18}
+// and E80 = e^{u/80} give all six rates (e^{u/20} = E80^4, e^{u/10} =
+// E80^8; e^{-(V+40)/10} = e^{2.5} E10, e^{-(V+55)/10} = e E10,
 // e^{-(V+35)/10} = e^3 E10).  Each u/k is the exact integer difference
 // (Q_{-65} - vq) times 2^-23/k before its single rounding.
 MMF_HD Rates hh_rates(int32_t vq)
 {
     Rates r;
-    const F2 E10 = exp_df(scaled_diff(kQm65, vq, kC10_h, kC10_l));
     const F2 E18 = exp_df(scaled_diff(kQm65, vq, kC18_h, kC18_l));
     const F2 E80 = exp_df(scaled_diff(kQm65, vq, kC80_h, kC80_l));
     F2 E20 = mul(E80, E80);
     E20 = mul(E20, E20);
+    const F2 E10 = mul(E20, E20);
     r.am = xexpm1_given(scaled_diff(kQm40, vq, kC10_h, kC10_l), mul(E10, F2{kE25_h, kE25_l}));
     r.bm = scale(E18, 4.0f);
     r.ah = mul(E20, F2{k007_h, k007_l});

@@ -9,7 +9,7 @@
 //   * differences of potentials (V - E, V_parent - V_child, V + c in the rate
 //     arguments) are taken exactly in integers before the single rounding;
 //   * the rate functions, steady states and relaxation factors are computed
-//     as float pairs (mm_fp32c_math.h: an FMA-only exponential, three per
+//     as float pairs (mm_fp32c_math.h: an FMA-only exponential, two per
 //     compartment, shared by the six rates);
 //   * the soma voltage is also accumulated in FP64 and the spike crossing
 //     time is computed in FP64.
