@@ -174,13 +174,13 @@ template <int NT>
 __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
 {
     // Shared memory of one work item, carved from the item's own sizes: its
-    // tree blob (staged by one bulk copy), then per compartment the diagonal
-    // (after elimination: the substitution coefficient f), the rhs (after
-    // elimination: c; after substitution: dV) and |g_axial| (staged by
-    // phase A, so that the sweeps touch only shared memory), then per path
-    // its contribution to its parent compartment (diagonal, rhs) and the
-    // exact potential difference across its head link (for the path from a
-    // soma: the stimulus current).  The launch provides the largest need
+    // tree blob (staged by one bulk copy), then per compartment the pair
+    // (diagonal, rhs) -- after elimination the substitution coefficients
+    // (f, c), after substitution (f, dV) -- and |g_axial| (staged by phase A,
+    // so that the sweeps touch only shared memory), then per path its
+    // contribution to its parent compartment (diagonal, rhs) and the exact
+    // potential difference across its head link (for the path from a soma:
+    // the stimulus current).  The launch provides the largest need
     // over its items.
     //
     // Warp roles: all warps run the streaming phases (A, S, C) of an item.
@@ -235,9 +235,9 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         const GroupRec G = a.groups[gi];
         const int64_t c0 = G.comp0;
         const int32_t *Vq = a.Vq + c0;
-        float *sd = (float *)(smem_raw + G.meta_bytes);
-        float *sr = sd + G.ncomp;
-        float *sg = sr + G.ncomp;
+        float2 *sdr = (float2 *)(smem_raw + G.meta_bytes);  // (d, rhs), then (f, c), then (f, dV)
+        float *sy = (float *)sdr;                            // sy[2 i + 1]: the second member of sdr[i]
+        float *sg = (float *)(sdr + G.ncomp);
         float *scd = sg + G.ncomp;
         float *scr = scd + G.npath;
         float *svt = scr + G.npath;
@@ -275,8 +275,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                     r = fmaf(gc, mmf::vdiff(__ldg(Vq + i + 1), vq), r);
                 }
             }
-            sd[i] = d;
-            sr[i] = r;
+            sdr[i] = make_float2(d, r);
         }
         // the tree blob must have landed before the sweeps
         if (!mbar_wait_bounded(&bar, parity)) s_abort = 1;
@@ -302,8 +301,10 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             const int st = G.site0 + t;
             const int c = a.site_comp[st];
             const float g = a.gsyn[st];
-            sd[c] += g;
-            sr[c] = fmaf(-g, vminus(Vq[c], a.Esyn), sr[c]);
+            float2 v = sdr[c];
+            v.x += g;
+            v.y = fmaf(-g, vminus(Vq[c], a.Esyn), v.y);
+            sdr[c] = v;
             a.gsyn[st] = g * a.decay;
         }
         for (int pi = tid; pi < G.npath; pi += NS) {
@@ -373,7 +374,8 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             const int h = P.head;
             const float gh = sg[h], vt = svt[pi];
             int j = P.end - 1;
-            float db = sd[j], rb = sr[j];
+            const float2 v0 = sdr[j];
+            float db = v0.x, rb = v0.y;
             float dh = db, rh = rb;
             for (; j > h; j -= 8) {
                 const int cnt = j - h;
@@ -382,8 +384,9 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                 for (int k = 0; k < 8; ++k) {
                     const int q = max(j - k, h + 1);
                     g[k] = sg[q];
-                    dp[k] = sd[q - 1];
-                    rp[k] = sr[q - 1];
+                    const float2 w = sdr[q - 1];
+                    dp[k] = w.x;
+                    rp[k] = w.y;
                     g2[k] = g[k] * g[k];
                 }
 #pragma unroll
@@ -391,10 +394,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                     const float inv = rcp_approx(db);
                     const float f = g[k] * inv;
                     const float c = rb * inv;
-                    if (k < cnt) {
-                        sd[j - k] = f;
-                        sr[j - k] = c;
-                    }
+                    if (k < cnt) sdr[j - k] = make_float2(f, c);
                     rb = fmaf(f, rb, rp[k]);
                     db = fmaf(-g2[k], inv, dp[k]);
                     if (k == cnt - 1) {
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             }
             if (P.parent < 0) {  // soma: the stimulus, then its dV
                 rh += vt;
-                sr[h] = rh * rcp_approx(dh);
+                sy[2 * h + 1] = rh * rcp_approx(dh);
                 return;
             }
             // the head link to the parent compartment: assembled here, the
@@ -414,12 +414,13 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             rh = fmaf(gh, vt, rh);
             const float inv = rcp_approx(dh);
             const float f = gh * inv;
-            sd[h] = f;
-            sr[h] = rh * inv;
+            sdr[h] = make_float2(f, rh * inv);
             const float cd = fmaf(-f, gh, gh), cr = fmaf(f, rh, -gh * vt);
             if (P.nflag & kPathAlone) {
-                sd[P.parent] += cd;
-                sr[P.parent] += cr;
+                float2 v = sdr[P.parent];
+                v.x += cd;
+                v.y += cr;
+                sdr[P.parent] = v;
             } else {
                 scd[pi] = cd;
                 scr[pi] = cr;
@@ -442,8 +443,10 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                     ad += scd[c];
                     ar += scr[c];
                 }
-                sd[att] += ad;
-                sr[att] += ar;
+                float2 v = sdr[att];
+                v.x += ad;
+                v.y += ar;
+                sdr[att] = v;
             }
         };
 
@@ -455,10 +458,11 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             const PathQ P = paths[pi];
             const int h = P.head;
             float x;
+            const float2 vh = sdr[h];
             if (P.parent >= 0) {
-                x = fmaf(sd[h], sr[P.parent], sr[h]);
+                x = fmaf(vh.x, sy[2 * P.parent + 1], vh.y);
             } else {
-                x = sr[h];
+                x = vh.y;
                 const int nrn = G.neuron0 + (P.nflag & kPathNeuron);
                 const double v0 = __hiloint2double(__float_as_int(scd[pi]), __float_as_int(scr[pi]));
                 const double v1 = v0 + (double)x;
@@ -489,17 +493,17 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                 float r[8], d[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    const int q = min(j + k, P.end - 1);
-                    r[k] = sr[q];
-                    d[k] = sd[q];
+                    const float2 w = sdr[min(j + k, P.end - 1)];
+                    d[k] = w.x;
+                    r[k] = w.y;
                 }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     x = fmaf(d[k], x, r[k]);
-                    if (k < cnt) sr[j + k] = x;
+                    if (k < cnt) sy[2 * (j + k) + 1] = x;
                 }
             }
-            if (P.parent >= 0) sr[h] = xh;  // read by the next level only
+            if (P.parent >= 0) sy[2 * h + 1] = xh;  // read by the next level only
         };
 
         // B from the deepest level up, then F from the soma down; a level's
@@ -532,7 +536,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         for (int i = tid; i < G.ncomp; i += NS) {
             const int32_t vold = Vq[i];
             int32_t vq;
-            if (!mmf::v_add(vold, sr[i], &vq)) {
+            if (!mmf::v_add(vold, sy[2 * i + 1], &vq)) {
                 atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
                 vq = vold;
             }
