@@ -156,6 +156,10 @@ __device__ __forceinline__ void gate_update(const StepArgs32 &a, int64_t c)
 // is left.
 constexpr int kGateChunk = 64;
 
+// Compartments per step of a path sweep (their operands are loaded
+// together before the step's dependent chain).
+constexpr int kSweepChunk = 8;
+
 __device__ __forceinline__ void gate_chunks(const StepArgs32 &a, int64_t pc0, int pn, int *next, int lane)
 {
     for (;;) {
@@ -361,7 +365,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         //    deepest level up: every compartment of a path has the one
         //    before it as its parent, so a path is one chain from its leaf
         //    up to its head (links inside a path are assembled: a = c = -g),
-        //    eight compartments at a time with their operands loaded before
+        //    kSweepChunk compartments at a time with their operands loaded before
         //    any of their stores (indices past the head are clamped and their
         //    results dropped).  The head is then eliminated into its parent
         //    compartment: a path alone on that compartment adds its
@@ -377,11 +381,11 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             const float2 v0 = sdr[j];
             float db = v0.x, rb = v0.y;
             float dh = db, rh = rb;
-            for (; j > h; j -= 8) {
+            for (; j > h; j -= kSweepChunk) {
                 const int cnt = j - h;
-                float g[8], g2[8], dp[8], rp[8];
+                float g[kSweepChunk], g2[kSweepChunk], dp[kSweepChunk], rp[kSweepChunk];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
+                for (int k = 0; k < kSweepChunk; ++k) {
                     const int q = max(j - k, h + 1);
                     g[k] = sg[q];
                     const float2 w = sdr[q - 1];
@@ -390,7 +394,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                     g2[k] = g[k] * g[k];
                 }
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
+                for (int k = 0; k < kSweepChunk; ++k) {
                     const float inv = rcp_approx(db);
                     const float f = g[k] * inv;
                     const float c = rb * inv;
@@ -485,20 +489,20 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             const float xh = x;
             // down the path, each compartment's parent is the one before
             // it: x_j = f_j x_{j-1} + c_j with the coefficients the
-            // elimination left in (sd, sr); eight at a time, operands
+            // elimination left in sdr; kSweepChunk at a time, operands
             // loaded before the stores (indices past the leaf clamped, their
             // results dropped)
-            for (int j = h + 1; j < P.end; j += 8) {
+            for (int j = h + 1; j < P.end; j += kSweepChunk) {
                 const int cnt = P.end - j;
-                float r[8], d[8];
+                float r[kSweepChunk], d[kSweepChunk];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
+                for (int k = 0; k < kSweepChunk; ++k) {
                     const float2 w = sdr[min(j + k, P.end - 1)];
                     d[k] = w.x;
                     r[k] = w.y;
                 }
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
+                for (int k = 0; k < kSweepChunk; ++k) {
                     x = fmaf(d[k], x, r[k]);
                     if (k < cnt) sy[2 * (j + k) + 1] = x;
                 }
