@@ -1,0 +1,286 @@
+// Host-side check of the FP32c work-item layout (paper_2005_06332_gb300/csrc/
+// mm_layout.cpp), built and run by tests/test_layout_paths.py.
+//
+// For every work item it checks the invariants the kernels rely on for
+// their shared-memory (16-bit) and giant (32-bit) path tables -- every index
+// inside the item, the paths partitioning its compartments, each
+// compartment after a path head having the previous one as its parent, path
+// levels, the fold lists and the "alone" flags -- and then replays the
+// kernels' path-by-path elimination and substitution in float on random
+// diagonally dominant coefficients, comparing with the elimination of
+// Algorithm 1 in double over the same parent array.
+//
+// Usage: layout_check <network file> <group_comps> <regular smem limit> <large smem limit>
+// Network file: int32 N | int64 C | int64 comp_offset[N+1] | int32 parent[C].
+// Prints "bad=<violations> maxrel=<largest relative error>"; exit 0 iff bad == 0.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "mm_layout.h"
+
+using namespace mmk;
+
+namespace {
+
+struct Tables {  // an item's tables widened to int
+    std::vector<int> nrn;    // 4 per neuron: path0, npath, nlevel, loff0
+    std::vector<int> path;   // 4 per path: head, end, parent, neuron
+    std::vector<int> alone;  // per path
+    std::vector<int> fold;   // 2 per entry: path, parent compartment
+    std::vector<int> loffs, mcnt;
+};
+
+Tables read_tables(const GroupRec &G, const unsigned char *b, bool wide, long long *bad)
+{
+    Tables T;
+    int nlo = 0;
+    if (wide) {
+        const NrnG *nr = (const NrnG *)b;
+        const PathG *P = (const PathG *)(b + G.path_off);
+        const KidG *F = (const KidG *)(b + G.fold_off);
+        for (int k = 0; k < G.nneuron; ++k) {
+            T.nrn.insert(T.nrn.end(), {nr[k].path0, nr[k].npath, nr[k].nlevel, nr[k].loff0});
+            nlo += nr[k].nlevel + 1;
+        }
+        for (int p = 0; p < G.npath; ++p) {
+            T.path.insert(T.path.end(), {P[p].head, P[p].end, P[p].parent, P[p].nflag & kPathNeuronG});
+            T.alone.push_back((P[p].nflag & kPathAloneG) != 0);
+            T.fold.insert(T.fold.end(), {F[p].x, F[p].y});
+        }
+        const int32_t *lo = (const int32_t *)(b + G.loffs_off), *mc = (const int32_t *)(b + G.mcnt_off);
+        T.loffs.assign(lo, lo + nlo);
+        T.mcnt.assign(mc, mc + nlo);
+        if (G.mcnt_off + 4LL * nlo > G.meta_bytes) ++*bad;
+    } else {
+        const NrnQ *nr = (const NrnQ *)b;
+        const PathQ *P = (const PathQ *)(b + G.path_off);
+        const KidQ *F = (const KidQ *)(b + G.fold_off);
+        for (int k = 0; k < G.nneuron; ++k) {
+            T.nrn.insert(T.nrn.end(), {nr[k].path0, nr[k].npath, nr[k].nlevel, nr[k].loff0});
+            nlo += nr[k].nlevel + 1;
+        }
+        for (int p = 0; p < G.npath; ++p) {
+            T.path.insert(T.path.end(), {P[p].head, P[p].end, P[p].parent, P[p].nflag & kPathNeuron});
+            T.alone.push_back((P[p].nflag & kPathAlone) != 0);
+            T.fold.insert(T.fold.end(), {(int)(F[p] & 0xFFFFu), (int)(F[p] >> 16)});
+        }
+        const int16_t *lo = (const int16_t *)(b + G.loffs_off), *mc = (const int16_t *)(b + G.mcnt_off);
+        T.loffs.assign(lo, lo + nlo);
+        T.mcnt.assign(mc, mc + nlo);
+        if (G.mcnt_off + 2LL * nlo > G.meta_bytes) ++*bad;
+    }
+    if (G.path_off % 16 || G.fold_off % 4 || G.meta_bytes % 16) ++*bad;
+    return T;
+}
+
+}  // namespace
+
+int main(int argc, char **argv)
+{
+    if (argc < 5) return 2;
+    FILE *f = std::fopen(argv[1], "rb");
+    if (!f) return 2;
+    int32_t N;
+    int64_t C;
+    if (std::fread(&N, 4, 1, f) != 1 || std::fread(&C, 8, 1, f) != 1) return 2;
+    std::vector<int64_t> off((size_t)N + 1);
+    std::vector<int32_t> par((size_t)C);
+    if (std::fread(off.data(), 8, off.size(), f) != off.size() || std::fread(par.data(), 4, par.size(), f) != par.size())
+        return 2;
+    std::fclose(f);
+    std::vector<double> L((size_t)C, 10.0), D((size_t)C, 1.0);
+    mmh::LayoutInput in{};
+    in.N = N;
+    in.comp_offset = off.data();
+    in.parent = par.data();
+    in.length_um = L.data();
+    in.diam_um = D.data();
+    in.dt = 0.025;
+    in.group_comps = std::atoi(argv[2]);
+    in.max_group_comps = 1 << 30;
+    in.smem_per_comp = 12;
+    in.smem_per_seg = 0;
+    in.giant_smem_limit = std::atoi(argv[3]);
+    in.big_smem_limit = std::atoi(argv[4]);
+    in.path_items = true;
+    in.smem_per_path = 12;
+    mmh::Layout lay;
+    bool invalid = false;
+    const std::string err = mmh::build_layout(in, lay, &invalid);
+    if (!err.empty()) {
+        std::printf("layout error: %s\n", err.c_str());
+        return 1;
+    }
+    long long bad = 0;
+    double maxrel = 0.0;
+    std::mt19937 rng(1);
+    std::uniform_real_distribution<double> U(0.0, 1.0);
+    int64_t gcomps = 0, gpaths = 0, covered = 0;
+    const int nitems = (int)lay.groups.size();
+    for (int gi = 0; gi < nitems; ++gi) {
+        const GroupRec &G = lay.groups[(size_t)gi];
+        const bool wide = gi >= lay.n_small + lay.n_big;
+        const Tables T = read_tables(G, lay.meta.data() + G.meta_off, wide, &bad);
+        if (wide) {
+            if (G.scratch0 != gcomps || G.pscratch0 != gpaths) ++bad;
+            gcomps += G.ncomp;
+            gpaths += G.npath;
+        } else {
+            const int64_t need = G.meta_bytes + 12LL * G.ncomp + 12LL * G.npath;
+            if (need > (gi < lay.n_small ? lay.max_smem : lay.big_max_smem) || G.ncomp > 32767 || G.npath > 32767) ++bad;
+        }
+        covered += G.ncomp;
+        const int64_t c0 = G.comp0;
+        auto H = [&](int p) { return T.path[4 * p]; };
+        auto E = [&](int p) { return T.path[4 * p + 1]; };
+        auto Pa = [&](int p) { return T.path[4 * p + 2]; };
+        std::vector<int> cover(G.ncomp, 0), pathof(G.ncomp, -1), levelof(G.npath, -1), nrnof(G.npath, -1);
+        int pcount = 0;
+        for (int k = 0; k < G.nneuron; ++k) {
+            const int p0 = T.nrn[4 * k], np = T.nrn[4 * k + 1], nl = T.nrn[4 * k + 2], l0 = T.nrn[4 * k + 3];
+            if (p0 != pcount || l0 < 0 || l0 + nl >= (int)T.loffs.size() + 1) { ++bad; continue; }
+            const int *lo = T.loffs.data() + l0;
+            if (lo[0] != p0 || lo[nl] != p0 + np) ++bad;
+            for (int l = 0; l < nl; ++l) {
+                if (lo[l + 1] <= lo[l]) ++bad;
+                int prev = 1 << 30;
+                for (int p = lo[l]; p < lo[l + 1]; ++p) {
+                    levelof[p] = l;
+                    nrnof[p] = k;
+                    if (E(p) - H(p) > prev) ++bad;  // longest first
+                    prev = E(p) - H(p);
+                }
+            }
+            pcount += np;
+        }
+        if (pcount != G.npath) ++bad;
+        for (int p = 0; p < G.npath; ++p) {
+            if (H(p) < 0 || E(p) > G.ncomp || E(p) <= H(p)) { ++bad; continue; }
+            if (T.path[4 * p + 3] != nrnof[p]) ++bad;
+            for (int j = H(p); j < E(p); ++j) { cover[j]++; pathof[j] = p; }
+            for (int j = H(p) + 1; j < E(p); ++j)
+                if (lay.pdist[(size_t)(c0 + j)] != 1) ++bad;  // parent is the compartment before
+            if (Pa(p) < 0) {
+                if (lay.pdist[(size_t)(c0 + H(p))] != 0 || levelof[p] != 0) ++bad;
+            } else if (lay.pdist[(size_t)(c0 + H(p))] >= 0 || H(p) + lay.pdist[(size_t)(c0 + H(p))] != Pa(p)) {
+                ++bad;  // heads carry the negated parent distance
+            }
+            if (E(p) < G.ncomp && lay.pdist[(size_t)(c0 + E(p))] == 1) ++bad;  // ends at a leaf
+        }
+        for (int j = 0; j < G.ncomp; ++j)
+            if (cover[j] != 1) { ++bad; break; }
+        std::vector<int> share(G.ncomp, 0);
+        for (int p = 0; p < G.npath; ++p) if (Pa(p) >= 0) share[Pa(p)]++;
+        for (int p = 0; p < G.npath; ++p) if ((Pa(p) >= 0 && share[Pa(p)] == 1) != (T.alone[p] != 0)) ++bad;
+        for (int k = 0; k < G.nneuron; ++k) {
+            const int nl = T.nrn[4 * k + 2], l0 = T.nrn[4 * k + 3];
+            const int *lo = T.loffs.data() + l0, *mc = T.mcnt.data() + l0;
+            for (int l = 0; l < nl; ++l) {
+                std::vector<int> seen(G.npath, 0);
+                int prev = 1 << 30;
+                if (mc[l] < 0 || mc[l] > lo[l + 1] - lo[l] || (l == 0 && mc[l] != 0)) ++bad;
+                for (int z = lo[l]; z < lo[l + 1]; ++z) {
+                    const int c = T.fold[2 * z], att = T.fold[2 * z + 1];
+                    if (c < lo[l] || c >= lo[l + 1]) { ++bad; continue; }
+                    seen[c]++;
+                    const bool shared = z < lo[l] + mc[l];
+                    if (Pa(c) >= 0 && shared == (T.alone[c] != 0)) ++bad;
+                    if (l > 0) {
+                        if (Pa(c) != att || att < 0 || att >= G.ncomp || levelof[pathof[att]] != l - 1 ||
+                            nrnof[pathof[att]] != k || att >= E(pathof[att]) - 1)
+                            ++bad;
+                        if (shared) {
+                            if (att > prev) ++bad;
+                            prev = att;
+                        }
+                    }
+                }
+                for (int c = lo[l]; c < lo[l + 1]; ++c)
+                    if (seen[c] != 1) { ++bad; break; }
+            }
+        }
+        // the kernels' sweeps in float against Algorithm 1 in double
+        std::vector<int> pp(G.ncomp);
+        for (int j = 0; j < G.ncomp; ++j) {
+            const int pd = lay.pdist[(size_t)(c0 + j)];
+            pp[j] = pd == 0 ? -1 : j - std::abs(pd);
+        }
+        std::vector<double> d(G.ncomp), r(G.ncomp), g(G.ncomp), x(G.ncomp);
+        for (int j = 0; j < G.ncomp; ++j) {
+            g[j] = pp[j] >= 0 ? 0.05 + U(rng) : 0.0;
+            d[j] = 1.0 + 0.1 * U(rng);
+            r[j] = U(rng) - 0.5;
+        }
+        std::vector<double> dd(d);
+        for (int j = 0; j < G.ncomp; ++j) if (pp[j] >= 0) { dd[j] += g[j]; dd[pp[j]] += g[j]; }
+        {
+            std::vector<double> b(dd), rr(r);
+            for (int j = G.ncomp - 1; j >= 1; --j) {
+                if (pp[j] < 0) continue;
+                const double fct = g[j] / b[j];
+                b[pp[j]] -= fct * g[j];
+                rr[pp[j]] += fct * rr[j];
+            }
+            for (int j = 0; j < G.ncomp; ++j) x[j] = (rr[j] + (pp[j] >= 0 ? g[j] * x[pp[j]] : 0.0)) / b[j];
+        }
+        std::vector<float> sd(G.ncomp), sr(G.ncomp), sg(G.ncomp), scd(G.npath), scr(G.npath);
+        for (int j = 0; j < G.ncomp; ++j) {  // phase A: links inside paths at both ends
+            float dj = (float)d[j];
+            if (lay.pdist[(size_t)(c0 + j)] == 1) dj += (float)g[j];
+            if (j + 1 < G.ncomp && lay.pdist[(size_t)(c0 + j + 1)] == 1) dj += (float)g[j + 1];
+            sd[j] = dj;
+            sr[j] = (float)r[j];
+            sg[j] = (float)g[j];
+        }
+        for (int k = 0; k < G.nneuron; ++k) {
+            const int nl = T.nrn[4 * k + 2], l0 = T.nrn[4 * k + 3];
+            const int *lo = T.loffs.data() + l0, *mc = T.mcnt.data() + l0;
+            for (int l = nl - 1; l >= 0; --l) {
+                for (int p = lo[l]; p < lo[l + 1]; ++p) {
+                    const int h = H(p);
+                    int j = E(p) - 1;
+                    float db = sd[j], rb = sr[j];
+                    for (; j > h; --j) {
+                        const float inv = 1.f / db, fj = sg[j] * inv;
+                        sd[j] = fj;
+                        sr[j] = rb * inv;
+                        rb = std::fma(fj, rb, sr[j - 1]);
+                        db = std::fma(-sg[j] * sg[j], inv, sd[j - 1]);
+                    }
+                    if (Pa(p) < 0) { sr[h] = rb / db; continue; }
+                    db += sg[h];
+                    const float inv = 1.f / db, fh = sg[h] * inv;
+                    sd[h] = fh;
+                    sr[h] = rb * inv;
+                    const float cd = std::fma(-fh, sg[h], sg[h]), cr = fh * rb;
+                    if (T.alone[p]) { sd[Pa(p)] += cd; sr[Pa(p)] += cr; } else { scd[p] = cd; scr[p] = cr; }
+                }
+                const int zend = lo[l] + mc[l];
+                for (int z = lo[l]; z < zend; ++z) {
+                    const int att = T.fold[2 * z + 1];
+                    if (z > lo[l] && T.fold[2 * z - 1] == att) continue;
+                    float ad = 0.f, ar = 0.f;
+                    for (int y = z; y < zend && T.fold[2 * y + 1] == att; ++y) { ad += scd[T.fold[2 * y]]; ar += scr[T.fold[2 * y]]; }
+                    sd[att] += ad;
+                    sr[att] += ar;
+                }
+            }
+            for (int l = 0; l < nl; ++l)
+                for (int p = lo[l]; p < lo[l + 1]; ++p) {
+                    const int h = H(p);
+                    float xx = Pa(p) >= 0 ? std::fma(sd[h], sr[Pa(p)], sr[h]) : sr[h];
+                    sr[h] = xx;
+                    for (int j = h + 1; j < E(p); ++j) { xx = std::fma(sd[j], xx, sr[j]); sr[j] = xx; }
+                }
+        }
+        for (int j = 0; j < G.ncomp; ++j) maxrel = std::max(maxrel, std::fabs(sr[j] - x[j]) / (std::fabs(x[j]) + 1e-3));
+    }
+    if (gcomps != lay.giant_comps || gpaths != lay.giant_paths || covered != C) ++bad;
+    std::printf("items=%d small=%d large=%d giant=%d bad=%lld maxrel=%.3e\n", nitems, lay.n_small, lay.n_big,
+                nitems - lay.n_small - lay.n_big, bad, maxrel);
+    return bad ? 1 : 0;
+}
