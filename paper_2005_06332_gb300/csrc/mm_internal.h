@@ -3,25 +3,26 @@
 //
 // Device layout (all per-compartment arrays in INTERNAL order):
 //   * neurons are re-ordered by the schedule (largest cost first);
-//   * inside a neuron, compartments are renumbered in depth-first preorder so
-//     that every unbranched run of the tree (a "segment": a path whose inner
-//     nodes have exactly one child) occupies consecutive indices and its
-//     child segments hang off its last (bottom) compartment;
+//   * inside a neuron, compartments are renumbered in depth-first preorder
+//     (parent < child), visiting the deepest child first (deepest: the
+//     longest path to a leaf, in compartments), so that every "path" -- a
+//     compartment that does not continue its parent's path, its deepest
+//     child, that one's deepest child, and so on down to a leaf -- is one
+//     contiguous index range in which each compartment's parent is the one
+//     before it; an unbranched run of the tree (a "segment") is contiguous
+//     as well;
 //   * consecutive neurons are packed into work items ("groups") whose
 //     compartments are contiguous; one thread block solves one group at a
 //     time, with the group's Hines diagonal and right-hand side in shared
-//     memory;
-//   * the depth-first order visits the deepest child first (deepest: the
-//     longest path to a leaf, in compartments), so that every "path" -- a
-//     segment followed by its deepest child segment, that one's, and so on
-//     down to a leaf -- is one contiguous index range as well;
-//   * the segments of a group are sorted by height (0 = no child segment),
-//     so that all segments of one height ("wave") can be eliminated in
-//     parallel once the lower waves are done (the leaves-to-root sweep of
-//     Algorithm 1), and substituted in the reverse order (root-to-leaves);
-//   * the paths of a group are sorted by level (0: the path from a soma;
-//     level l + 1: paths that hang off a path of level l), so that the
-//     root-to-leaves substitution can run path by path, one level at a time.
+//     memory (giant FP32c items: in a global scratch);
+//   * FP32c: the paths of a neuron are sorted by level (0: the path from its
+//     soma; level l + 1: paths that hang off a path of level l), so that the
+//     leaves-to-root sweep of Algorithm 1 can run path by path from the
+//     deepest level up and the root-to-leaves sweep from level 0 down;
+//   * FP64: the segments of a group are sorted by height (0 = no child
+//     segment), so that all segments of one height ("wave") can be
+//     eliminated in parallel once the lower waves are done, and substituted
+//     in the reverse order.
 #pragma once
 #include <stdint.h>
 #include <vector_types.h>
@@ -164,7 +165,7 @@ struct StepArgs {
     double *spk_t;
     long long spk_cap;
     DevCtl *ctl;
-    int32_t smem_comps, smem_segs;    // shared-memory capacity of one block
+    int32_t smem_comps, smem_segs;    // shared-memory capacity of one block (FP64)
     double gNa, gK, gL, ENa, EK, EL;
     double cm_dt;                     // Cm * 1e3 / dt: C_i/dt = area_i * cm_dt (nF/ms = uS)
     double e_syn, threshold, dt, decay;
@@ -247,7 +248,7 @@ struct DeliverArgs {
 
 struct InitArgs {
     const double *L, *diam;           // internal order
-    const int32_t *parent_dist;       // i - parent(i), negated at segment tops, 0 at a soma
+    const int32_t *parent_dist;       // i - parent(i), negated at segment tops (FP64) or path heads (FP32c), 0 at a soma
     int64_t C;
     double *area, *gax;
     double *V, *m, *h, *n;

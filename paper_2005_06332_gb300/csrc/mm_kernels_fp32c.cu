@@ -50,8 +50,8 @@ __global__ void init_fp32c_kernel(InitArgs a)
             const int64_t q = i - pa;
             g = 1.0 / (half_cyl_resistance_d(a.Ra, L, d) + half_cyl_resistance_d(a.Ra, a.L[q], a.diam[q]));
         }
-        // segment tops (and somata) carry the sign bit: phase A assembles
-        // only the links inside segments, the sweep the links of the tops
+        // path heads (and somata) carry the sign bit: phase A assembles only
+        // the links inside paths, the sweep the links of the heads
         a.gax32[i] = pd > 0 ? (float)g : -(float)g;
         const double v = a.v_init;
         a.Vq[i] = (int32_t)llrint(v * kVScaleD);

@@ -8,14 +8,17 @@
 //      prediction), largest first, so that the work queue hands the longest
 //      items out first;
 //   2. each tree is renumbered in depth-first preorder, which keeps
-//      parent < child (the numbering Algorithm 1 needs) and makes every
-//      unbranched segment a contiguous index range; the deepest child is
-//      visited first, so that each path (a segment, its deepest child
-//      segment, and so on down to a leaf) is a contiguous range too;
+//      parent < child (the numbering Algorithm 1 needs); the deepest child
+//      is visited first, so that each path (a compartment that does not
+//      continue its parent's path, then its deepest child, and so on down to
+//      a leaf) is a contiguous range whose compartments each have the
+//      previous one as their parent, and every unbranched segment is
+//      contiguous too;
 //   3. consecutive neurons are packed into work items of about
-//      `group_comps` compartments, each with its segments sorted into
-//      height waves and its paths sorted into levels, the two schedules of
-//      the parallel leaves-to-root / root-to-leaves sweeps;
+//      `group_comps` compartments; FP32c items get path tables (paths by
+//      level, per-level fold lists of paths sharing a parent compartment),
+//      the schedule of the path-by-path leaves-to-root / root-to-leaves
+//      sweeps; FP64 items get their segments sorted into height waves;
 //   4. synapse targets are merged into synaptic sites (one conductance per
 //      compartment that receives synapses) and outgoing synapses are stored
 //      per source neuron, sorted by delay, for delivery.
@@ -472,7 +475,8 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
             for (int32_t j = 0; j < n; ++j) {
                 const bool cont = (j > 0 && ws.pnew[(size_t)j] == j - 1 && ws.nch[(size_t)(j - 1)] == 1);
                 if (!cont) {
-                    // segment tops carry a negative parent distance
+                    // segment tops carry a negative parent distance (FP32c items
+                    // re-mark path heads instead, below)
                     if (j > 0) L.pdist[(size_t)(ib + j)] = -L.pdist[(size_t)(ib + j)];
                     mmk::SegRec s;
                     s.top = lb + j;

@@ -42,7 +42,8 @@ struct Layout {
     std::vector<int64_t> user2int;      // user compartment -> internal compartment [C]
     std::vector<int64_t> soma_of_user;  // internal soma compartment of each user neuron [N]
     std::vector<double> L, D;           // cylinders, internal order
-    std::vector<int32_t> pdist;         // i - parent(i) in internal order, negated at segment tops, 0 at somata
+    std::vector<int32_t> pdist;         // i - parent(i) in internal order, negated at segment tops (FP64)
+                                        // or path heads (FP32c), 0 at somata
     std::vector<double> stim;           // internal order
     std::vector<mmk::GroupRec> groups;
     std::vector<unsigned char> meta;    // tree blobs (16-byte aligned per work item)
