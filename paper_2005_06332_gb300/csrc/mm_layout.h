@@ -23,12 +23,14 @@ struct LayoutInput {
     int32_t group_comps;          // compartment budget of a work item
     int32_t max_group_comps;      // largest neuron accepted
     // shared-memory model of a work item, bytes = meta + smem_per_comp * comps
-    // + smem_per_seg * segments (+ smem_per_path * paths for path items); items above giant_smem_limit go to the large
-    // shared-memory class if they fit big_smem_limit (0: no such class), else
-    // they become giant items (giant_smem_limit 0: no classes at all)
+    // + smem_per_seg * segments (+ smem_per_path * paths for path items);
+    // items above giant_smem_limit go to the large shared-memory class if
+    // they fit big_smem_limit (0: no such class), else they become giant
+    // items (giant_smem_limit 0: no classes at all)
     int32_t smem_per_comp, smem_per_seg, giant_smem_limit, big_smem_limit;
-    // FP32c: shared-memory items are solved path by path (mmk::NrnQ blobs,
-    // smem_per_path bytes per path); giant items keep the segment blob
+    // FP32c: items are solved path by path (mmk::NrnQ tables with 16-bit
+    // records, mmk::NrnG with 32-bit records for giant items), with
+    // smem_per_path bytes per path
     bool path_items;
     int32_t smem_per_path;
 };
