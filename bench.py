@@ -168,6 +168,58 @@ def run_reference(args, net):
     print(json.dumps(out), flush=True)
 
 
+def run_paper_replay(args):
+    """The paper's multi- vs mono-morphology tests (Sec. 4) on one GPU.
+
+    10,000 neurons of mean size 300 in three workloads -- one morphology
+    for all, sizes from a group of 20 (at most 700 apart), F-distributed
+    sizes -- each timed (FP32c, CUDA graphs, CUDA events) with the work
+    queue in size order (the paper's global sorting) and in a random order
+    (no sorting).  Prints one JSON line with the step times and the
+    overheads of the multi-morphology workloads over the mono-morphology
+    one (the paper reports them for its CPU cluster: 12 % unsorted, 2.8 %
+    after sorting)."""
+    import torch
+    from paper_2005_06332_gb300 import mm
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    mm.load()
+    stream = torch.cuda.Stream(device=local)
+    rng = np.random.default_rng(2019)
+    res = {}
+    for cfg in ("paper_mono", "paper_multi20", "paper_fisher"):
+        net = netgen.make_config(cfg)
+        sizes = net.sizes()
+        r = {"n_comp": int(net.n_comp), "mean_size": float(sizes.mean()), "min_size": int(sizes.min()),
+             "max_size": int(sizes.max())}
+        for label, cost in (("size_sorted", None), ("random_order", rng.random(net.n_neurons).astype(np.float32))):
+            g = mm.Network(net, precision="fp32c", graph_steps=args.graph_steps, device=local,
+                           stream=stream.cuda_stream, cost=cost, block_threads=args.block_threads,
+                           group_comps=args.group_comps)
+            g.step(args.warmup)
+            g.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.step(args.steps)
+            e1.record(stream)
+            e1.synchronize()
+            r[label + "_ms_per_step"] = e0.elapsed_time(e1) / args.steps
+            g.close()
+        res[cfg] = r
+    mono = res["paper_mono"]
+    over = {}
+    for cfg in ("paper_multi20", "paper_fisher"):
+        for label in ("size_sorted", "random_order"):
+            # per compartment, so that the small differences in total size cancel
+            t = res[cfg][label + "_ms_per_step"] / res[cfg]["n_comp"]
+            t0 = mono["size_sorted_ms_per_step"] / mono["n_comp"]
+            over[f"{cfg}_{label}"] = t / t0 - 1.0
+    print(json.dumps({"paper_replay": res, "overhead_vs_mono_per_compartment": over, "steps": args.steps,
+                      "warmup": args.warmup, "precision": "fp32c", "data": "synthetic"}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -187,8 +239,14 @@ def main():
     ap.add_argument("--group-comps", type=int, default=0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the launch-configuration autotuner (default: tune on a 2M-compartment sample)")
+    ap.add_argument("--paper-replay", action="store_true",
+                    help="the paper's load-balance tests instead: one morphology vs a group of 20 sizes vs "
+                         "F-distributed sizes (same mean size), size-sorted vs random work-queue order")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.paper_replay:
+        run_paper_replay(args)
+        return
 
     net = netgen.make_config(args.config)
     precision = args.precision or "fp32c"
@@ -245,7 +303,8 @@ def main():
     # kernels per step: delivery, then the solve of each non-empty work-item
     # class, then (FP32c) the gate update
     n_reg = launch["work_items"] - launch["big_items"] - launch["giant_items"]
-    kps = 2 if precision == "fp64" else 1 + (n_reg > 0) + (launch["big_items"] > 0) + (launch["giant_items"] > 0)
+    # (giant items: phase A, solve and phase C + gates, three kernels)
+    kps = 2 if precision == "fp64" else 1 + (n_reg > 0) + (launch["big_items"] > 0) + 3 * (launch["giant_items"] > 0)
     launches = (K // G) * (kps * G + 1) + ((K % G > 0) * (kps * (K % G) + 1)) if G > 0 else kps * K + 1
     updates = net.n_comp * K * ws
     value = updates / (ms * 1e-3)

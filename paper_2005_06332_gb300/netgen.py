@@ -156,6 +156,10 @@ def draw_sizes(rng: np.random.Generator, n_neurons: int, dist) -> np.ndarray:
 
     dist: ("mono", n) | ("loguniform", a, b) | ("lognormal", median, sigma, lo, hi)
           | ("choice", [sizes...])  (uniform over a fixed group of sizes)
+          | ("group", k, spread, mean)  (k sizes drawn once, largest minus
+            smallest = spread, group mean = mean; neurons pick among them)
+          | ("fisher", d1, d2, mean, lo, hi)  (F(d1, d2)-distributed, scaled
+            to the given mean, clipped)
     """
     kind = dist[0]
     if kind == "mono":
@@ -171,6 +175,30 @@ def draw_sizes(rng: np.random.Generator, n_neurons: int, dist) -> np.ndarray:
     if kind == "choice":
         group = np.asarray(dist[1], dtype=np.int64)
         return group[rng.integers(0, len(group), size=n_neurons)]
+    if kind == "group":
+        # k sizes lo + spread * v^a with v uniform over [0, 1] (its smallest
+        # draw mapped to 0, its largest to 1) and the exponent a chosen by
+        # bisection so that the group's mean is `mean`
+        k, spread, mean = int(dist[1]), float(dist[2]), float(dist[3])
+        lo = 10.0
+        v = np.sort(rng.random(k))
+        v = (v - v[0]) / (v[-1] - v[0])
+        a_lo, a_hi = 1e-3, 1e3
+        for _ in range(200):
+            a = math.sqrt(a_lo * a_hi)
+            if lo + spread * float(np.mean(v ** a)) > mean:
+                a_lo = a
+            else:
+                a_hi = a
+        group = np.rint(lo + spread * v ** math.sqrt(a_lo * a_hi)).astype(np.int64)
+        return group[rng.integers(0, k, size=n_neurons)]
+    if kind == "fisher":
+        # F = (X1 / d1) / (X2 / d2) with X chi-square (sums of squared normals)
+        d1, d2, mean, lo, hi = int(dist[1]), int(dist[2]), float(dist[3]), int(dist[4]), int(dist[5])
+        x1 = (_normal(rng, n_neurons * d1).reshape(n_neurons, d1) ** 2).sum(axis=1) / d1
+        x2 = (_normal(rng, n_neurons * d2).reshape(n_neurons, d2) ** 2).sum(axis=1) / d2
+        f = x1 / x2
+        return np.clip(np.rint(mean * f * (d2 - 2.0) / d2), lo, hi).astype(np.int64)
     raise ValueError(f"unknown size distribution {dist!r}")
 
 
@@ -286,6 +314,18 @@ CONFIGS = {
     "lognormal100k": dict(  # 100k lognormal(800, 1.0) in [20, 20000], 1000 syn/neuron, 50 ms
         n_neurons=100_000, size_dist=("lognormal", 800, 1.0, 20, 20000), p_branch=0.1,
         syn_per_neuron=1000, delay_ms=("const", 1.0), t_stop=50.0, seed_index=3, precision="fp32c"),
+    # The paper's load-balance tests (Sec. 4): 10,000 neurons of the same
+    # mean size (300) -- one morphology for all, a group of 20 sizes at most
+    # 700 apart, F-distributed sizes -- FP32c, 100 synapses per neuron, 50 ms
+    "paper_mono": dict(
+        n_neurons=10_000, size_dist=("mono", 300), p_branch=0.1, syn_per_neuron=100,
+        delay_ms=("const", 1.0), mono_tree=True, t_stop=50.0, seed_index=5, precision="fp32c"),
+    "paper_multi20": dict(
+        n_neurons=10_000, size_dist=("group", 20, 700, 300), p_branch=0.1, syn_per_neuron=100,
+        delay_ms=("const", 1.0), t_stop=50.0, seed_index=6, precision="fp32c"),
+    "paper_fisher": dict(
+        n_neurons=10_000, size_dist=("fisher", 10, 40, 300, 10, 5000), p_branch=0.1, syn_per_neuron=100,
+        delay_ms=("const", 1.0), t_stop=50.0, seed_index=7, precision="fp32c"),
     "mixed200k": dict(  # 200k lognormal(1000, 1.0) + 64 giants of 1e5 compartments, 20 ms
         n_neurons=200_000, size_dist=("lognormal", 1000, 1.0, 20, 20000), p_branch=0.1,
         syn_per_neuron=1000, delay_ms=("uniform", 1.0, 5.0), giants=64, giant_size=100_000,

@@ -74,6 +74,19 @@ def test_fp32c_short_horizon_parity():
     assert ref.n_spikes > 0
 
 
+@pytest.mark.parametrize("dist", [("group", 20, 700, 300), ("fisher", 10, 40, 300, 10, 5000)])
+def test_fp32c_paper_size_distributions_parity(dist):
+    """The size distributions of the paper's load-balance tests (a group of 20
+    sizes, F-distributed sizes), also in a random work-queue order."""
+    net = netgen.make_network(40, size_dist=dist, p_branch=0.1, syn_per_neuron=10, seed=23, stim_nA=(0.2, 0.8))
+    steps = 320
+    ref = oracle.simulate(net, steps)
+    for cost in (None, np.random.default_rng(5).random(net.n_neurons).astype(np.float32)):
+        V, gates, sn, st, _ = _run(net, steps, cost=cost, group_comps=1024)
+        assert np.max(np.abs(V - ref.V)) <= TOL_V
+        assert _spike_match(net, sn, st, ref) is not None
+
+
 def test_fp32c_single_chain_one_step_is_close():
     n = 50
     off = np.array([0, n], dtype=np.int64)
