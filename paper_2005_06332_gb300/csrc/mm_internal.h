@@ -54,9 +54,10 @@ struct SegP {
     int16_t pad;
 };
 
-// FP32c work items are solved path by path, by a team of warps per neuron.
-// Per neuron of an item (8 bytes): its paths are path0 .. path0 + npath - 1
-// of the item, sorted by level (0: the path from the soma) and, within a
+// FP32c work items are solved path by path, by a team of warps per sweep
+// bundle (one neuron, or several consecutive small neurons swept together).
+// Per bundle of an item (8 bytes): its paths are path0 .. path0 + npath - 1
+// of the item, sorted by level (0: the paths from the somata) and, within a
 // level, longest first; level l holds paths loffs[loff0 + l] ..
 // loffs[loff0 + l + 1] - 1, and the first mcnt[loff0 + l] entries of that
 // level's fold list belong to parent compartments shared by several paths.
@@ -88,7 +89,7 @@ constexpr int16_t kPathNeuron = 0x3FFF;
 typedef uint32_t KidQ;
 
 // The same three tables with 32-bit indices, for FP32c giant items (beyond
-// shared memory, solved from a global scratch): NrnG per neuron, PathG per
+// shared memory, solved from a global scratch): NrnG per bundle, PathG per
 // path, KidG per fold entry {path, parent compartment}.
 struct NrnG {
     int32_t path0, npath, nlevel, loff0;
@@ -105,7 +106,7 @@ typedef int2 KidG;
 // single bulk copy.  FP64 items: SegP[nseg] | int16 child[nchild] |
 // int16 wave_off[nwave+1] (wave w holds segments wave_off[w] ..
 // wave_off[w+1]-1; wave 0 holds the leaf segments), padded to 16 bytes.
-// FP32c items: NrnQ[nneuron] | PathQ[npath] (at byte path_off) |
+// FP32c items: NrnQ[nbundle] | PathQ[npath] (at byte path_off) |
 // KidQ[npath] (fold list, at fold_off) | int16 loffs[] (at loffs_off) |
 // int16 mcnt[] (as many as loffs, at mcnt_off), padded to 16 bytes.
 // Giant FP32c items (beyond shared memory) use the same layout with the
@@ -130,6 +131,8 @@ struct GroupRec {
     int32_t loffs_off;// FP32c: byte offset of the level offsets
     int32_t mcnt_off; // FP32c: byte offset of the per-level shared-parent counts
     int32_t pscratch0;// FP32c giant items: first entry in the global per-path scratch
+    int32_t nbundle;  // FP32c: sweep bundles (NrnQ / NrnG records) of the item
+    int32_t pad;
 };
 
 // Small device-side control block.

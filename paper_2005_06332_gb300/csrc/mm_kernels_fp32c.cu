@@ -188,12 +188,13 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
     // over its items.
     //
     // Warp roles: all warps run the streaming phases (A, S, C) of an item.
-    // In the sweeps each warp takes whole neurons of the item, one lane per
-    // path, and synchronises only with itself; warps without a neuron, and
-    // each sweeping warp once its neurons are done, update the gates of the
-    // block's previous item (its V^{n+1} is final since that item's phase
-    // C) in chunks claimed from a shared counter, so that the arithmetic of
-    // the gates fills the issue slots the latency-bound sweeps leave.
+    // In the sweeps teams of 1, 2 or 4 warps take whole sweep bundles of the
+    // item (a neuron, or several small ones), one lane per path, and
+    // synchronise only among themselves; warps without a bundle, and each
+    // team once its bundles are done, update the gates of the block's
+    // previous item (its V^{n+1} is final since that item's phase C) in
+    // chunks claimed from a shared counter, so that the arithmetic of the
+    // gates fills the issue slots the latency-bound sweeps leave.
     constexpr int NS = NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *smeta = smem_raw;
@@ -345,12 +346,12 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             }
         }
 
-        // Team of each warp for the sweeps: T warps per neuron (T = 1, 2 or
-        // 4, as many as the item's neurons leave), the teams taking the
-        // item's neurons in turn; a team synchronises on its own named
+        // Team of each warp for the sweeps: T warps per sweep bundle (T = 1,
+        // 2 or 4, as many as the item's bundles leave), the teams taking the
+        // item's bundles in turn; a team synchronises on its own named
         // barrier (1 + team; 0 is the block's).
         const int nwarp = NS / 32;
-        int T = nwarp / max(G.nneuron, 1);
+        int T = nwarp / max(G.nbundle, 1);
         T = T >= 4 ? 4 : (T >= 2 ? 2 : 1);
         if (T == 2 && nwarp / 2 > 15) T = 4;
         const int team = (tid >> 5) / T, nteam = nwarp / T;
@@ -514,7 +515,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         // paths go to the team's lanes longest first.  Then gate chunks of
         // the previous item (when timing items, the gates wait until after
         // phase C, outside the timed span).
-        for (int k = team; k < G.nneuron; k += nteam) {
+        for (int k = team; k < G.nbundle; k += nteam) {
             const NrnQ Nk = nrns[k];
             const int16_t *lo = loffs + Nk.loff0;
             const int16_t *mc = mcnt + Nk.loff0;
@@ -783,7 +784,7 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
             if (P.parent >= 0) dr[h].y = xh;  // read by the next level only
         };
 
-        for (int k = 0; k < G.nneuron; ++k) {
+        for (int k = 0; k < G.nbundle; ++k) {
             const NrnG Nk = nrns[k];
             const int32_t *lo = loffs + Nk.loff0;
             const int32_t *mc = mcnt + Nk.loff0;

@@ -55,19 +55,39 @@ struct PathTmp {
 // their parent compartment.  Emitted with 16-bit (shared-memory items) or
 // 32-bit (giant items) records.
 struct PathBlob {
-    std::vector<int32_t> nrn;    // 4 per neuron: path0, npath, nlevel, loff0
+    std::vector<int32_t> nrn;    // 4 per bundle: path0, npath, nlevel, loff0
     std::vector<int32_t> path;   // 4 per path: head, end, parent, neuron | alone
     std::vector<int32_t> fold;   // 2 per entry: path, parent compartment
     std::vector<int32_t> loffs, mcnt;
-    int32_t nlevel = 0, npath = 0;
+    int32_t nlevel = 0, npath = 0, nbundle = 0;
 };
 
+// Neurons of an item are swept in bundles: consecutive neurons are merged
+// until a bundle holds at least this many compartments, so that a warp team
+// sweeps the paths of many small neurons level by level together instead of
+// one small neuron after the other (the paths of different neurons never
+// interact).  A neuron at least this large is a bundle of its own.
+constexpr int32_t kBundleComps = 256;
+
 // paths: every path of the item (group-local compartments), neurons in
-// order, each neuron's paths contiguous.
-void build_path_blob(std::vector<PathTmp> &paths, int32_t nneuron, PathBlob &b)
+// order, each neuron's paths contiguous; nsize: compartments per neuron.
+void build_path_blob(std::vector<PathTmp> &paths, int32_t nneuron, const std::vector<int32_t> &nsize, PathBlob &b)
 {
-    std::stable_sort(paths.begin(), paths.end(), [](const PathTmp &a, const PathTmp &c) {
-        if (a.neuron != c.neuron) return a.neuron < c.neuron;
+    std::vector<int32_t> bundle((size_t)nneuron, 0);
+    {
+        int32_t cur = 0, acc = 0;
+        for (int32_t k = 0; k < nneuron; ++k) {
+            if (acc >= kBundleComps) {
+                ++cur;
+                acc = 0;
+            }
+            bundle[(size_t)k] = cur;
+            acc += nsize[(size_t)k];
+        }
+        b.nbundle = cur + 1;
+    }
+    std::stable_sort(paths.begin(), paths.end(), [&](const PathTmp &a, const PathTmp &c) {
+        if (bundle[(size_t)a.neuron] != bundle[(size_t)c.neuron]) return bundle[(size_t)a.neuron] < bundle[(size_t)c.neuron];
         if (a.level != c.level) return a.level < c.level;
         if (a.end - a.head != c.end - c.head) return a.end - a.head > c.end - c.head;
         return a.head < c.head;
@@ -78,7 +98,7 @@ void build_path_blob(std::vector<PathTmp> &paths, int32_t nneuron, PathBlob &b)
     for (int32_t q = 0; q < np; ++q)
         if (paths[(size_t)q].parent >= 0) share[paths[(size_t)q].parent]++;
     auto shared = [&](int32_t x) { return paths[(size_t)x].parent >= 0 && share[paths[(size_t)x].parent] > 1; };
-    b.nrn.assign(4 * (size_t)nneuron, 0);
+    b.nrn.assign(4 * (size_t)b.nbundle, 0);
     b.path.resize(4 * (size_t)np);
     b.fold.resize(2 * (size_t)np);
     b.loffs.clear();
@@ -94,9 +114,9 @@ void build_path_blob(std::vector<PathTmp> &paths, int32_t nneuron, PathBlob &b)
     }
     int32_t i = 0;
     std::vector<int32_t> lv;
-    for (int32_t k = 0; k < nneuron; ++k) {
+    for (int32_t k = 0; k < b.nbundle; ++k) {
         const int32_t p0 = i;
-        while (i < np && paths[(size_t)i].neuron == k) ++i;
+        while (i < np && bundle[(size_t)paths[(size_t)i].neuron] == k) ++i;
         const int32_t nl = i > p0 ? paths[(size_t)i - 1].level + 1 : 0;
         const size_t lbase = b.loffs.size();
         b.nrn[4 * (size_t)k] = p0;
@@ -136,11 +156,11 @@ struct BlobOffsets {
     int64_t path_off, fold_off, loffs_off, mcnt_off, bytes;
 };
 
-BlobOffsets blob_offsets(const PathBlob &b, int32_t nneuron, bool wide)
+BlobOffsets blob_offsets(const PathBlob &b, bool wide)
 {
     BlobOffsets o;
     const int64_t w = wide ? 4 : 2;  // bytes per index
-    o.path_off = (4 * w * nneuron + 15) & ~15LL;
+    o.path_off = (4 * w * b.nbundle + 15) & ~15LL;
     o.fold_off = o.path_off + 4 * w * b.npath;
     o.loffs_off = o.fold_off + 2 * w * b.npath;
     o.mcnt_off = o.loffs_off + w * (int64_t)b.loffs.size();
@@ -150,9 +170,9 @@ BlobOffsets blob_offsets(const PathBlob &b, int32_t nneuron, bool wide)
 
 // The blob itself (offsets as blob_offsets; 16-bit records pack the alone
 // flag as mmk::kPathAlone and the fold entries as mmk::KidQ).
-std::vector<unsigned char> emit_path_blob(const PathBlob &b, int32_t nneuron, bool wide)
+std::vector<unsigned char> emit_path_blob(const PathBlob &b, bool wide)
 {
-    const BlobOffsets o = blob_offsets(b, nneuron, wide);
+    const BlobOffsets o = blob_offsets(b, wide);
     std::vector<unsigned char> blob((size_t)o.bytes, 0);
     auto put32 = [&](int64_t off, const std::vector<int32_t> &v) { std::memcpy(blob.data() + off, v.data(), 4 * v.size()); };
     auto put16 = [&](int64_t off, const std::vector<int32_t> &v) {
@@ -398,6 +418,7 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
     std::vector<std::vector<int32_t>> gkids;
     std::vector<int32_t> gheight, gpseg, glevel, perm, newidx;
     std::vector<PathTmp> gpaths;
+    std::vector<int32_t> gsize;  // compartments of each neuron of the item
     L.max_comps = 0;
     L.max_segs = 0;
     L.max_waves = 0;
@@ -410,10 +431,12 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         gpseg.clear();
         glevel.clear();
         gpaths.clear();
+        gsize.clear();
         for (int32_t k = k0; k < k1; ++k) {
             const int32_t u = L.order[(size_t)k];
             const int64_t ub = in.comp_offset[u];
             const int32_t n = (int32_t)size_of(u);
+            gsize.push_back(n);
             const int64_t ib = L.noff[(size_t)k];
             const int32_t lb = (int32_t)(ib - comp0);
             const int32_t *par = in.parent + ub;
@@ -559,9 +582,9 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         PathBlob pb;
         int64_t smem_need;
         if (in.path_items) {
-            build_path_blob(gpaths, gr.nneuron, pb);
+            build_path_blob(gpaths, gr.nneuron, gsize, pb);
             if (gr.ncomp <= 32767 && pb.npath <= 32767) {
-                smem_need = blob_offsets(pb, gr.nneuron, false).bytes + (int64_t)in.smem_per_comp * gr.ncomp +
+                smem_need = blob_offsets(pb, false).bytes + (int64_t)in.smem_per_comp * gr.ncomp +
                             (int64_t)in.smem_per_path * pb.npath;
             } else {
                 smem_need = INT64_MAX;
@@ -588,8 +611,9 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
                 L.pdist[(size_t)c] = pd == 1 ? 1 : -pd;
             }
             // 16-bit records for items staged in shared memory, 32-bit for giants
-            const BlobOffsets o = blob_offsets(pb, gr.nneuron, giant);
-            blob = emit_path_blob(pb, gr.nneuron, giant);
+            const BlobOffsets o = blob_offsets(pb, giant);
+            blob = emit_path_blob(pb, giant);
+            gr.nbundle = pb.nbundle;
             gr.path_off = (int32_t)o.path_off;
             gr.fold_off = (int32_t)o.fold_off;
             gr.loffs_off = (int32_t)o.loffs_off;

@@ -5,10 +5,11 @@
 // their shared-memory (16-bit) and giant (32-bit) path tables -- every index
 // inside the item, the paths partitioning its compartments, each
 // compartment after a path head having the previous one as its parent, path
-// levels, the fold lists and the "alone" flags -- and then replays the
-// kernels' path-by-path elimination and substitution in float on random
-// diagonally dominant coefficients, comparing with the elimination of
-// Algorithm 1 in double over the same parent array.
+// levels, sweep bundles holding whole neurons, the fold lists and the
+// "alone" flags -- and then replays the kernels' path-by-path elimination
+// and substitution in float on random diagonally dominant coefficients,
+// comparing with the elimination of Algorithm 1 in double over the same
+// parent array.
 //
 // Usage: layout_check <network file> <group_comps> <regular smem limit> <large smem limit>
 // Network file: int32 N | int64 C | int64 comp_offset[N+1] | int32 parent[C].
@@ -27,7 +28,7 @@ using namespace mmk;
 namespace {
 
 struct Tables {  // an item's tables widened to int
-    std::vector<int> nrn;    // 4 per neuron: path0, npath, nlevel, loff0
+    std::vector<int> nrn;    // 4 per sweep bundle: path0, npath, nlevel, loff0
     std::vector<int> path;   // 4 per path: head, end, parent, neuron
     std::vector<int> alone;  // per path
     std::vector<int> fold;   // 2 per entry: path, parent compartment
@@ -42,7 +43,7 @@ Tables read_tables(const GroupRec &G, const unsigned char *b, bool wide, long lo
         const NrnG *nr = (const NrnG *)b;
         const PathG *P = (const PathG *)(b + G.path_off);
         const KidG *F = (const KidG *)(b + G.fold_off);
-        for (int k = 0; k < G.nneuron; ++k) {
+        for (int k = 0; k < G.nbundle; ++k) {
             T.nrn.insert(T.nrn.end(), {nr[k].path0, nr[k].npath, nr[k].nlevel, nr[k].loff0});
             nlo += nr[k].nlevel + 1;
         }
@@ -59,7 +60,7 @@ Tables read_tables(const GroupRec &G, const unsigned char *b, bool wide, long lo
         const NrnQ *nr = (const NrnQ *)b;
         const PathQ *P = (const PathQ *)(b + G.path_off);
         const KidQ *F = (const KidQ *)(b + G.fold_off);
-        for (int k = 0; k < G.nneuron; ++k) {
+        for (int k = 0; k < G.nbundle; ++k) {
             T.nrn.insert(T.nrn.end(), {nr[k].path0, nr[k].npath, nr[k].nlevel, nr[k].loff0});
             nlo += nr[k].nlevel + 1;
         }
@@ -138,9 +139,11 @@ int main(int argc, char **argv)
         auto H = [&](int p) { return T.path[4 * p]; };
         auto E = [&](int p) { return T.path[4 * p + 1]; };
         auto Pa = [&](int p) { return T.path[4 * p + 2]; };
+        // nrnof: the sweep bundle of each path
         std::vector<int> cover(G.ncomp, 0), pathof(G.ncomp, -1), levelof(G.npath, -1), nrnof(G.npath, -1);
         int pcount = 0;
-        for (int k = 0; k < G.nneuron; ++k) {
+        if (G.nbundle < 1 || G.nbundle > G.nneuron) ++bad;
+        for (int k = 0; k < G.nbundle; ++k) {
             const int p0 = T.nrn[4 * k], np = T.nrn[4 * k + 1], nl = T.nrn[4 * k + 2], l0 = T.nrn[4 * k + 3];
             if (p0 != pcount || l0 < 0 || l0 + nl >= (int)T.loffs.size() + 1) { ++bad; continue; }
             const int *lo = T.loffs.data() + l0;
@@ -158,14 +161,23 @@ int main(int argc, char **argv)
             pcount += np;
         }
         if (pcount != G.npath) ++bad;
+        // every neuron has one soma path and all its paths in one bundle
+        std::vector<int> somas(G.nneuron, 0), bundle_of(G.nneuron, -1);
+        for (int p = 0; p < G.npath; ++p) {
+            const int nrn = T.path[4 * p + 3];
+            if (nrn < 0 || nrn >= G.nneuron) { ++bad; continue; }
+            if (Pa(p) < 0) somas[nrn]++;
+            if (bundle_of[nrn] < 0) bundle_of[nrn] = nrnof[p];
+            else if (bundle_of[nrn] != nrnof[p]) ++bad;
+        }
+        for (int k = 0; k < G.nneuron; ++k) if (somas[k] != 1) ++bad;
         for (int p = 0; p < G.npath; ++p) {
             if (H(p) < 0 || E(p) > G.ncomp || E(p) <= H(p)) { ++bad; continue; }
-            if (T.path[4 * p + 3] != nrnof[p]) ++bad;
             for (int j = H(p); j < E(p); ++j) { cover[j]++; pathof[j] = p; }
             for (int j = H(p) + 1; j < E(p); ++j)
                 if (lay.pdist[(size_t)(c0 + j)] != 1) ++bad;  // parent is the compartment before
             if (Pa(p) < 0) {
-                if (lay.pdist[(size_t)(c0 + H(p))] != 0 || levelof[p] != 0) ++bad;
+                if (lay.pdist[(size_t)(c0 + H(p))] != 0 || levelof[p] != 0) ++bad;  // somata on level 0
             } else if (lay.pdist[(size_t)(c0 + H(p))] >= 0 || H(p) + lay.pdist[(size_t)(c0 + H(p))] != Pa(p)) {
                 ++bad;  // heads carry the negated parent distance
             }
@@ -176,7 +188,7 @@ int main(int argc, char **argv)
         std::vector<int> share(G.ncomp, 0);
         for (int p = 0; p < G.npath; ++p) if (Pa(p) >= 0) share[Pa(p)]++;
         for (int p = 0; p < G.npath; ++p) if ((Pa(p) >= 0 && share[Pa(p)] == 1) != (T.alone[p] != 0)) ++bad;
-        for (int k = 0; k < G.nneuron; ++k) {
+        for (int k = 0; k < G.nbundle; ++k) {
             const int nl = T.nrn[4 * k + 2], l0 = T.nrn[4 * k + 3];
             const int *lo = T.loffs.data() + l0, *mc = T.mcnt.data() + l0;
             for (int l = 0; l < nl; ++l) {
@@ -236,7 +248,7 @@ int main(int argc, char **argv)
             sr[j] = (float)r[j];
             sg[j] = (float)g[j];
         }
-        for (int k = 0; k < G.nneuron; ++k) {
+        for (int k = 0; k < G.nbundle; ++k) {
             const int nl = T.nrn[4 * k + 2], l0 = T.nrn[4 * k + 3];
             const int *lo = T.loffs.data() + l0, *mc = T.mcnt.data() + l0;
             for (int l = nl - 1; l >= 0; --l) {
