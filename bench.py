@@ -267,8 +267,11 @@ def main():
     tune = None
     if not args.no_autotune and not (args.block_threads or args.group_comps):
         t0 = time.perf_counter()
-        tune = mm.autotune(net, precision=precision, sample_comps=2_000_000, warmup=3, steps=20, device=local,
-                           stream=stream.cuda_stream, graph_steps=args.graph_steps)
+        # candidates are timed on the whole network up to 16 M compartments
+        # (a small sample gives each block too few items to show the load
+        # balance of the full run), else on a stratified 16 M sample
+        tune = mm.autotune(net, precision=precision, sample_comps=min(int(net.n_comp), 16_000_000), warmup=3,
+                           steps=20, device=local, stream=stream.cuda_stream, graph_steps=args.graph_steps)
         tune["seconds"] = time.perf_counter() - t0
         args.block_threads, args.group_comps = tune["block_threads"], tune["group_comps"]
     g = mm.Network(net, precision=precision, graph_steps=args.graph_steps, device=local, stream=stream.cuda_stream,
