@@ -75,11 +75,11 @@ def lib():
             L.orc_geometry.argtypes = [C.c_int32, _I64, _I32, _D, _D, C.POINTER(Params), _D, _D, _D]
             L.orc_assemble.restype = None
             L.orc_assemble.argtypes = [C.c_int32, _I32, _D, _D, _D, _D, _D, _D, _D, _D, C.c_double,
-                                       C.POINTER(Params), C.c_double, _D, _D, _D, _D]
+                                       C.POINTER(Params), C.c_double, C.c_int, _D, _D, _D, _D]
             L.orc_simulate.restype = C.c_int
             L.orc_simulate.argtypes = [C.c_int32, _I64, _I32, _D, _D, _D,
                                        C.c_int64, _I32, _I32, _I32, _D, _D,
-                                       C.POINTER(Params), C.c_double, C.c_int64, _D,
+                                       C.POINTER(Params), C.c_double, C.c_int, C.c_int64, _D,
                                        _D, _D, _D, _D, _D, _D, _I32, _D, C.c_int64, _I64, C.c_int]
             _lib = L
     return _lib
@@ -152,15 +152,22 @@ def geometry(comp_offset, parent, length_um, diam_um, params: dict):
     return area, Cn, gax
 
 
-def assemble(parent, V, m, h, n, gsyn, area, Cn, gax, stim_nA, params: dict, dt: float):
-    """Hines system (a, b, c, rhs) of one neuron for dV."""
+SCHEMES = {"be": 0, "cn": 1}
+
+
+def assemble(parent, V, m, h, n, gsyn, area, Cn, gax, stim_nA, params: dict, dt: float, scheme: str = "be"):
+    """Hines system (a, b, c, rhs) of one neuron for dV.
+
+    scheme "be": backward Euler with the membrane conductance implicit (the
+    default reading of Eq. 2); "cn": Eq. 2 as printed, half of each axial
+    coupling implicit and the current explicit (Crank-Nicolson diffusion)."""
     k = len(V)
     parent = _i32(parent)
     arrs = [_f64(x) for x in (V, m, h, n, gsyn, area, Cn, gax)]
     a, b, c, rhs = np.zeros(k), np.zeros(k), np.zeros(k), np.zeros(k)
     pr = params_from(params)
     lib().orc_assemble(k, _p(parent, C.c_int32), *[_p(x, C.c_double) for x in arrs], float(stim_nA),
-                       C.byref(pr), float(dt), _p(a, C.c_double), _p(b, C.c_double), _p(c, C.c_double),
+                       C.byref(pr), float(dt), SCHEMES[scheme], _p(a, C.c_double), _p(b, C.c_double), _p(c, C.c_double),
                        _p(rhs, C.c_double))
     return a, b, c, rhs
 
@@ -182,8 +189,9 @@ class Result:
 
 
 def simulate(net, n_steps: int, dt: float = None, params: dict = None, V_init=None,
-             record_soma: bool = False, spike_cap: int = None, threads: int = 0) -> Result:
-    """Run the oracle on a ``netgen.Network`` for n_steps steps."""
+             record_soma: bool = False, spike_cap: int = None, threads: int = 0, scheme: str = "be") -> Result:
+    """Run the oracle on a ``netgen.Network`` for n_steps steps (scheme as
+    in ``assemble``)."""
     dt = net.dt if dt is None else dt
     params = net.params if params is None else params
     pr = params_from(params)
@@ -204,7 +212,7 @@ def simulate(net, n_steps: int, dt: float = None, params: dict = None, V_init=No
     rc = lib().orc_simulate(N, _p(off, C.c_int64), _p(parent, C.c_int32), _p(L, C.c_double),
                             _p(d, C.c_double), _p(stim, C.c_double), len(src), _p(src, C.c_int32),
                             _p(dst, C.c_int32), _p(comp, C.c_int32), _p(w, C.c_double), _p(dl, C.c_double),
-                            C.byref(pr), float(dt), int(n_steps), _p(vi, C.c_double),
+                            C.byref(pr), float(dt), SCHEMES[scheme], int(n_steps), _p(vi, C.c_double),
                             _p(V, C.c_double), _p(m, C.c_double), _p(h, C.c_double), _p(n, C.c_double),
                             _p(g, C.c_double), _p(trace, C.c_double), _p(spn, C.c_int32), _p(spt, C.c_double), cap,
                             _p(nsp, C.c_int64), int(threads))

@@ -37,6 +37,14 @@
  *   - Compartment indices are 0-based with parent[0] = -1, parent[i] < i.
  *   - Capacitance is constant (Cm * area).
  *   - The spike test is at the soma, threshold theta, upward crossing only.
+ *
+ * Scheme 1 (scheme argument of orc_assemble / orc_simulate) is Eq. 2 taken
+ * as printed instead: off-diagonals a_i = b_i = -g/2 (half of each link's
+ * coupling implicit), d_i = C_i/dt - (a_i + b_i), and a rhs with the other
+ * half of the coupling and the current I explicit -- Crank-Nicolson in the
+ * diffusion, forward Euler in the membrane current.  In the dV form used
+ * here: b_i = C_i/dt + sum_j g_ij / 2, a_i = c_i = -g_{i,p(i)} / 2,
+ * rhs_i = -I_i + sum_j g_ij (V_j - V_i).
  */
 #include <math.h>
 #include <stdint.h>
@@ -191,21 +199,25 @@ static void membrane(const orc_params *p, double area, double V, double m, doubl
     *I = gna * (V - p->ENa) + gk * (V - p->EK) + gl * (V - p->EL) + gsyn * (V - p->e_syn);
 }
 
-/* Hines system of one neuron for dV (Eq. 2, symmetric reading):
+/* Hines system of one neuron for dV (Eq. 2, symmetric reading), scheme 0:
  *   b_i   = C_i/dt + G_i + sum_{j~i} g_ij
  *   a_i = c_i = -g_{i,p(i)}                       (i >= 1)
  *   rhs_i = -I_i + sum_{j~i} g_ij (V_j - V_i)  (+ stim at the soma)
+ * scheme 1 (Eq. 2 as printed: half of each coupling implicit, I explicit):
+ *   b_i   = C_i/dt + sum_{j~i} g_ij / 2,  a_i = c_i = -g_{i,p(i)} / 2,
+ *   rhs_i as in scheme 0.
  * All arrays are local to the neuron (length n). */
 void orc_assemble(int32_t n, const int32_t *parent, const double *V, const double *m,
                   const double *h, const double *nn, const double *gsyn,
                   const double *area, const double *C, const double *gax,
-                  double stim_nA, const orc_params *p, double dt,
+                  double stim_nA, const orc_params *p, double dt, int scheme,
                   double *a, double *b, double *c, double *rhs)
 {
+    const double w = scheme == 1 ? 0.5 : 1.0;  /* implicit share of each coupling */
     for (int32_t i = 0; i < n; ++i) {
         double G, I;
         membrane(p, area[i], V[i], m[i], h[i], nn[i], gsyn[i], &G, &I);
-        b[i] = C[i] / dt + G;
+        b[i] = scheme == 1 ? C[i] / dt : C[i] / dt + G;
         rhs[i] = -I;
         a[i] = 0.0;
         c[i] = 0.0;
@@ -214,10 +226,10 @@ void orc_assemble(int32_t n, const int32_t *parent, const double *V, const doubl
     for (int32_t i = 1; i < n; ++i) {
         int32_t q = parent[i];
         double g = gax[i];
-        a[i] = -g;
-        c[i] = -g;
-        b[i] += g;
-        b[q] += g;
+        a[i] = -w * g;
+        c[i] = -w * g;
+        b[i] += w * g;
+        b[q] += w * g;
         rhs[i] += g * (V[q] - V[i]);
         rhs[q] += g * (V[i] - V[q]);
     }
@@ -250,7 +262,8 @@ static int cmp_i64(const void *x, const void *y)
 }
 
 /* Simulate n_steps steps of the whole network from rest (or from the given
- * initial V; gates start at their steady state for that V, g_syn at 0).
+ * initial V; gates start at their steady state for that V, g_syn at 0),
+ * with the assembly of the given scheme (0 or 1, see orc_assemble).
  *
  * Outputs (any may be NULL):
  *   V_out, m_out, h_out, n_out, g_out [n_comp] state after the last step
@@ -263,14 +276,14 @@ int orc_simulate(int32_t n_neurons, const int64_t *off, const int32_t *parent,
                  const double *L, const double *diam, const double *stim_nA,
                  int64_t n_syn, const int32_t *syn_src, const int32_t *syn_dst,
                  const int32_t *syn_comp, const double *syn_w, const double *syn_delay_ms,
-                 const orc_params *p, double dt, int64_t n_steps, const double *V_init,
+                 const orc_params *p, double dt, int scheme, int64_t n_steps, const double *V_init,
                  double *V_out, double *m_out, double *h_out, double *n_out,
                  double *g_out, double *soma_trace, int32_t *spk_neuron, double *spk_t, int64_t spk_cap,
                  int64_t *n_spk, int n_threads)
 {
     int64_t C = off[n_neurons];
     int rc = 0;
-    if (dt <= 0.0 || n_neurons < 0) return -1;
+    if (dt <= 0.0 || n_neurons < 0 || scheme < 0 || scheme > 1) return -1;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #else
@@ -360,7 +373,7 @@ int orc_simulate(int32_t n_neurons, const int64_t *off, const int32_t *parent,
             int32_t n = (int32_t)(off[k + 1] - off[k]);
             double v0 = V[b0];
             orc_assemble(n, parent + b0, V + b0, m + b0, h + b0, nn + b0, gs + b0,
-                         area + b0, Cn + b0, gax + b0, stim_nA[k], p, dt,
+                         area + b0, Cn + b0, gax + b0, stim_nA[k], p, dt, scheme,
                          wa + b0, wb + b0, wc + b0, wr + b0);
             orc_hines_solve(wa + b0, wb + b0, wc + b0, wr + b0, parent + b0, n, NULL);
             for (int32_t i = 0; i < n; ++i) {

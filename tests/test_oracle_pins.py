@@ -372,3 +372,105 @@ def test_causality_within_min_delay():
     b2 = oracle.simulate(iso, 8 * d)
     assert a.n_spikes > 0
     assert np.max(np.abs(a2.V - b2.V)) > 1e-3
+
+
+# ------------------------------------- Eq. 2 as printed (scheme "cn"): pins
+
+def test_cn_single_passive_compartment_is_forward_euler_in_the_current():
+    """With one compartment there is no axial coupling: Eq. 2 as printed keeps
+    the membrane current explicit, so the approach to the Ohm's-law steady
+    state is the forward-Euler recurrence (1 - dt/tau)^k, not (1 + dt/tau)^-k."""
+    L_um, d_um, I = 20.0, 5.0, 0.05
+    net = _chain_net(1, L=L_um, d=d_um, stim=I, params=_passive())
+    area_cm2 = math.pi * (d_um * 1e-4) * (L_um * 1e-4)
+    gL_uS = P["gL"] * 1e-3 * area_cm2 * 1e6
+    v_ss = P["EL"] + I * 1e-9 / (gL_uS * 1e-6) * 1e3
+    tau = (P["Cm"] * 1e-6) / (P["gL"] * 1e-3) * 1e3
+    dt = 0.025
+    for k in (1, 7, 200, 4000):
+        V = oracle.simulate(net, k, dt=dt, params=_passive(), scheme="cn").V[0]
+        expect = v_ss + (P["v_init"] - v_ss) * (1.0 - dt / tau) ** k
+        assert abs(V - expect) <= 1e-10 * max(1.0, abs(expect)), k
+
+
+def test_cn_passive_cable_steady_state_is_the_same_closed_form():
+    """The discrete steady state does not depend on the time scheme: the
+    sealed passive chain reaches the cosh profile of the backward-Euler pin."""
+    N, L_um, d_um, I = 40, 10.0, 1.0, 0.1
+    net = _chain_net(N, L=L_um, d=d_um, stim=I, params=_passive())
+    V = oracle.simulate(net, 16000, params=_passive(), scheme="cn").V
+    area_cm2 = math.pi * (d_um * 1e-4) * (L_um * 1e-4)
+    g_m = P["gL"] * 1e-3 * area_cm2 * 1e6
+    r_seg = P["Ra"] * (L_um * 1e-4) / (math.pi * (d_um * 1e-4) ** 2 / 4)
+    g_a = 1.0 / r_seg * 1e6
+    kappa = math.acosh(1.0 + g_m / (2.0 * g_a))
+    k = np.arange(N)
+    shape = np.cosh(kappa * (N - 0.5 - k))
+    A = I / (g_m * shape[0] + g_a * (shape[0] - shape[1]))
+    np.testing.assert_allclose(V - P["EL"], A * shape, rtol=0, atol=1e-10)
+
+
+def test_cn_pure_diffusion_is_second_order_in_dt_backward_euler_first():
+    """No membrane current (gL = 0): C dV/dt = -K V + b with K the chain's
+    axial Laplacian and b the current into compartment 0 -- exactly solvable
+    with a matrix exponential.  Half of each coupling implicit and half
+    explicit (Eq. 2 as printed) is Crank-Nicolson: once dt resolves the
+    stiffest coupling, the error at t = 2 ms falls 4x per halving of dt; the
+    backward-Euler reading falls 2x."""
+    N, L_um, d_um, I, T = 12, 20.0, 1.0, 0.05, 2.0
+    params = dict(_passive())
+    params["gL"] = 0.0
+    net = _chain_net(N, L=L_um, d=d_um, stim=I, params=params)
+    area, Cn, gax = oracle.geometry(net.comp_offset, net.parent, net.length_um, net.diam_um, params)
+    K = np.zeros((N, N))
+    for i in range(1, N):
+        g = gax[i]
+        K[i, i] += g
+        K[i - 1, i - 1] += g
+        K[i, i - 1] -= g
+        K[i - 1, i] -= g
+    Minv = np.diag(1.0 / Cn)
+    b = np.zeros(N)
+    b[0] = I
+    # augmented system d/dt [V; 1] = [[-M^-1 K, M^-1 b], [0, 0]] [V; 1]
+    Aug = np.zeros((N + 1, N + 1))
+    Aug[:N, :N] = -Minv @ K
+    Aug[:N, N] = Minv @ b
+    y0 = np.append(np.full(N, params["v_init"]), 1.0)
+    exact = (scipy.linalg.expm(Aug * T) @ y0)[:N]
+    errs = {}
+    for scheme in ("cn", "be"):
+        errs[scheme] = []
+        for dt in (0.05, 0.025, 0.0125):
+            V = oracle.simulate(net, int(round(T / dt)), dt=dt, params=params, scheme=scheme).V
+            errs[scheme].append(np.max(np.abs(V - exact)))
+    e = errs["cn"]
+    assert 3.6 < e[0] / e[1] < 4.4 and 3.6 < e[1] / e[2] < 4.4, e
+    e = errs["be"]
+    assert 1.8 < e[0] / e[1] < 2.5 and 1.8 < e[1] / e[2] < 2.5, e
+
+
+def test_cn_assembly_conserves_charge_and_halves_the_couplings():
+    """Eq. 2 as printed: off-diagonals are half the axial conductances, the
+    diagonal is C/dt plus half the couplings of the row (rows of the coupling
+    part sum to zero), and the axial terms still only move charge:
+    sum_i (C_i/dt) dV_i = sum_i (-I_i) + I_stim."""
+    net = netgen.make_network(1, size_dist=("mono", 90), p_branch=0.2, syn_per_neuron=0, seed=6)
+    rng = np.random.default_rng(6)
+    n = net.n_comp
+    area, Cn, gax = oracle.geometry(net.comp_offset, net.parent, net.length_um, net.diam_um, P)
+    V = rng.uniform(-80, 30, n)
+    m, h, nn = rng.uniform(0, 1, (3, n))
+    gs = rng.uniform(0, 0.01, n)
+    dt = 0.025
+    a, b, c, rhs = oracle.assemble(net.parent, V, m, h, nn, gs, area, Cn, gax, 0.3, P, dt, scheme="cn")
+    np.testing.assert_array_equal(a, c)
+    np.testing.assert_allclose(a[1:], -0.5 * gax[1:], rtol=1e-15)
+    A = _dense(a, b, c, net.parent)
+    np.testing.assert_allclose(A.sum(axis=1), Cn / dt, rtol=1e-12)
+    _, _, _, rhs_be = oracle.assemble(net.parent, V, m, h, nn, gs, area, Cn, gax, 0.3, P, dt)
+    np.testing.assert_array_equal(rhs, rhs_be)  # same explicit rhs in both readings
+    dV = oracle.hines_solve(a, b, c, rhs, net.parent)
+    lhs = np.sum(Cn / dt * dV)
+    _, _, _, rhs0 = oracle.assemble(net.parent, V, m, h, nn, gs, area, Cn, np.zeros(n), 0.3, P, dt, scheme="cn")
+    assert abs(lhs - np.sum(rhs0)) <= 1e-12 * np.sum(np.abs(rhs0))
