@@ -55,9 +55,22 @@ typedef enum {
 /* Arithmetic of the time step. */
 enum {
     MM_FP64 = 0,   /* everything in FP64 */
-    MM_FP32C = 1   /* FP32 gates, currents and solve with compensated (TwoSum)
-                      elimination and voltage updates; FP64 soma voltage and
-                      spike-crossing time */
+    MM_FP32C = 1   /* FP32 increments on a fixed-point state (V in 2^-23 mV, gates
+                      in 2^-32), rate functions as float pairs; FP64 soma
+                      voltage and spike-crossing time */
+};
+
+/* Time discretisation of the voltage equation (Eq. 1) -- the reading of
+ * Eq. 2 the Hines system follows. */
+enum {
+    MM_SCHEME_BE = 0,  /* backward Euler for dV with the membrane conductance
+                          implicit: d_i = C_i/dt + G_i + sum_j g_ij, off-diagonal
+                          -g_ij, rhs_i = -I_i + sum_j g_ij (V_j - V_i) (default) */
+    MM_SCHEME_CN = 1   /* Eq. 2 as printed: half of each axial coupling implicit,
+                          half and the membrane current explicit (Crank-Nicolson
+                          in the diffusion): d_i = C_i/dt + sum_j g_ij / 2,
+                          off-diagonal -g_ij / 2, same rhs.  Stable only while
+                          dt G_i / C_i < 2 in every compartment */
 };
 
 /* Order in which the per-step kernel takes its work items. */
@@ -133,7 +146,7 @@ typedef struct {
     int32_t group_comps;        /* compartment budget of one work item; 0 = automatic */
     int32_t device;             /* CUDA device ordinal */
     int32_t time_items;         /* MM_FP32C: record each work item's solve time (mm_read_neuron_times) */
-    int32_t reserved0;
+    int32_t scheme;             /* MM_SCHEME_BE | MM_SCHEME_CN */
     double dt_ms;               /* time step of the network, > 0 */
     int64_t spike_capacity;     /* spikes held between two mm_read_spikes; 0 = automatic */
     void *cuda_stream;          /* cudaStream_t to run on; NULL = a library-owned stream */

@@ -357,6 +357,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     if (opt->precision != MM_FP64 && opt->precision != MM_FP32C) return fail(net, MM_EINVAL, "unknown precision");
     if (opt->schedule != MM_SCHED_SIZE_SORTED && opt->schedule != MM_SCHED_COST)
         return fail(net, MM_EINVAL, "unknown schedule");
+    if (opt->scheme != MM_SCHEME_BE && opt->scheme != MM_SCHEME_CN) return fail(net, MM_EINVAL, "unknown scheme");
     if (opt->schedule == MM_SCHED_COST && !opt->cost) return fail(net, MM_EINVAL, "MM_SCHED_COST needs mm_options.cost");
     if (syn && !(syn->tau_ms > 0.0)) return fail(net, MM_EINVAL, "tau_ms must be > 0");
     if (!chan) return fail(net, MM_EINVAL, "channel parameters must not be NULL");
@@ -556,6 +557,8 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.EK = chan->EK;
         a.EL = chan->EL;
         a.cm_dt = chan->Cm * 1e3 / opt->dt_ms;
+        a.gimp = opt->scheme == MM_SCHEME_CN ? 0.5 : 1.0;
+        a.g_implicit = opt->scheme == MM_SCHEME_CN ? 0 : 1;
         a.e_syn = syn ? syn->e_rev_mV : 0.0;
         a.threshold = chan->threshold_mV;
         a.dt = opt->dt_ms;
@@ -613,6 +616,8 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.EL = pot(chan->EL);
         a.Esyn = pot(syn ? syn->e_rev_mV : 0.0);
         a.cm_dt = (float)(chan->Cm * 1e3 / opt->dt_ms);
+        a.gimp = opt->scheme == MM_SCHEME_CN ? 0.5f : 1.0f;
+        a.g_implicit = opt->scheme == MM_SCHEME_CN ? 0 : 1;
         a.dt = (float)opt->dt_ms;
         a.dt_lo = (float)(opt->dt_ms - (double)a.dt);
         a.decay = (float)decay;

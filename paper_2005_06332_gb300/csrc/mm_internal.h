@@ -172,6 +172,12 @@ struct StepArgs {
     double gNa, gK, gL, ENa, EK, EL;
     double cm_dt;                     // Cm * 1e3 / dt: C_i/dt = area_i * cm_dt (nF/ms = uS)
     double e_syn, threshold, dt, decay;
+    // time discretisation (MM_SCHEME_*): the implicit share of each axial
+    // coupling (1, or 1/2 for Eq. 2 as printed) and whether the membrane
+    // conductance enters the diagonal (backward Euler) or stays explicit
+    double gimp;
+    int32_t g_implicit;
+    int32_t pad_scheme;
 };
 
 // Fixed-point state of the FP32c path: V = Vq * 2^-23 mV (int32, +-256 mV),
@@ -230,6 +236,8 @@ struct StepArgs32 {
     float dt, dt_lo, decay;           // dt as a float pair (dt + dt_lo)
     int64_t C;                        // compartments (gate kernel)
     double threshold, dt64;
+    float gimp;                       // implicit share of each axial coupling: 1 or 1/2 (as in StepArgs)
+    int32_t g_implicit;               // membrane conductance in the diagonal (backward Euler)
 };
 
 struct DeliverArgs {

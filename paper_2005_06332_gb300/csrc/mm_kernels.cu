@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
             const double n2 = nn * nn;
             const double gk = a.gK * s * (n2 * n2);
             const double gl = a.gL * s;
-            sd[i] = ar * a.cm_dt + gna + gk + gl;
+            sd[i] = ar * a.cm_dt + (a.g_implicit ? gna + gk + gl : 0.0);
             sr[i] = -(gna * (v - a.ENa) + gk * (v - a.EK) + gl * (v - a.EL));
         }
         if (!mbar_wait_bounded(&bar, parity)) s_abort = 1;
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
             const int st = G.site0 + t;
             const int c = a.site_comp[st];
             const double g = a.gsyn[st];
-            sd[c] += g;
+            if (a.g_implicit) sd[c] += g;
             sr[c] -= g * (V[c] - a.e_syn);
             a.gsyn[st] = g * a.decay;
         }
@@ -221,9 +221,10 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
 
         // B. leaves-to-root elimination, one segment per thread, wave by wave.
         //    The axial terms of each link (i, p(i)) are folded in as the sweep
-        //    reaches i: d_i += g, rhs_i += g (V_p - V_i) and, for the parent,
-        //    d_p += g, rhs_p += g (V_i - V_p), next to the elimination update
-        //    d_p -= (a_i/d_i) c_i, rhs_p -= (a_i/d_i) rhs_i with a_i = c_i = -g.
+        //    reaches i: d_i += w g, rhs_i += g (V_p - V_i) and, for the parent,
+        //    d_p += w g, rhs_p += g (V_i - V_p), next to the elimination update
+        //    d_p -= (a_i/d_i) c_i, rhs_p -= (a_i/d_i) rhs_i with a_i = c_i = -w g
+        //    (w = gimp: 1, or 1/2 for Eq. 2 as printed).
         for (int w = 0; w < G.nwave; ++w) {
             const int sb = woff[w], se = woff[w + 1];
             for (int si = sb + tid; si < se; si += NT) {
@@ -235,27 +236,27 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
                 // its elimination (-g^2/d_t, +g rhs_t/d_t)
                 for (int c = 0; c < S.nchild; ++c) {
                     const int t = segs[kids[S.child0 + c]].top;
-                    const double g = gax[t];
-                    const double f = g * sd[t];
-                    db += g - f * g;
+                    const double g = gax[t], gi = a.gimp * g;
+                    const double f = gi * sd[t];
+                    db += gi - f * gi;
                     rb += g * (V[t] - V[bot]) + f * sr[t];
                 }
                 for (int j = bot; j > S.top; --j) {
-                    const double g = gax[j];
+                    const double g = gax[j], gi = a.gimp * g;
                     const double vj = V[j], vp = V[j - 1];
-                    db += g;
+                    db += gi;
                     rb += g * (vp - vj);
                     const double inv = 1.0 / db;
                     sd[j] = inv;
                     sr[j] = rb;
-                    const double f = g * inv;
-                    db = sd[j - 1] + g - f * g;
+                    const double f = gi * inv;
+                    db = sd[j - 1] + gi - f * gi;
                     rb = sr[j - 1] + g * (vj - vp) + f * rb;
                 }
                 const int t = S.top;
                 if (S.parent >= 0) {
                     const double g = gax[t];
-                    db += g;
+                    db += a.gimp * g;
                     rb += g * (V[S.parent] - V[t]);
                     sd[t] = 1.0 / db;
                     sr[t] = rb;
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
                 const int t = S.top;
                 double x;
                 if (S.parent >= 0) {
-                    x = (sr[t] + gax[t] * sr[S.parent]) * sd[t];
+                    x = (sr[t] + a.gimp * gax[t] * sr[S.parent]) * sd[t];
                     sr[t] = x;
                 } else {
                     x = sr[t];
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
                     }
                 }
                 for (int j = t + 1; j < t + S.len; ++j) {
-                    x = (sr[j] + gax[j] * x) * sd[j];
+                    x = (sr[j] + a.gimp * gax[j] * x) * sd[j];
                     sr[j] = x;
                 }
             }

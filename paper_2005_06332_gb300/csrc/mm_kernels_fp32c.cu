@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             const int32_t vq = __ldg(Vq + i);
             const float gs = __ldg(a.gax + c0 + i);
             const float g = fabsf(gs);
-            sg[i] = g;
+            sg[i] = a.gimp * g;  // the implicit coupling, used by the sweeps
             const float m = mmf::gate_f(__ldg(a.mq + c0 + i)), h = mmf::gate_f(__ldg(a.hq + c0 + i)),
                         nn = mmf::gate_f(__ldg(a.nq + c0 + i));
             const float ar = __ldg(a.area + c0 + i);
@@ -267,16 +267,19 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             const float n2 = nn * nn;
             const float gk = a.gK * s * (n2 * n2);
             const float gl = a.gL * s;
-            float d = fmaf(ar, a.cm_dt, gna + gk + gl);
+            // the membrane conductance is implicit except in Eq. 2 as
+            // printed; of each axial coupling the share gimp enters the
+            // diagonal, all of it the explicit rhs
+            float d = fmaf(ar, a.cm_dt, a.g_implicit ? gna + gk + gl : 0.f);
             float r = -fmaf(gna, vminus(vq, a.ENa), fmaf(gk, vminus(vq, a.EK), gl * vminus(vq, a.EL)));
             if (!signbit(gs)) {  // link to the parent i-1
-                d += g;
+                d = fmaf(a.gimp, g, d);
                 r = fmaf(g, mmf::vdiff(__ldg(Vq + i - 1), vq), r);
             }
             if (i + 1 < G.ncomp) {
                 const float gc = __ldg(a.gax + c0 + i + 1);
                 if (!signbit(gc)) {  // link to the child i+1
-                    d += gc;
+                    d = fmaf(a.gimp, gc, d);
                     r = fmaf(gc, mmf::vdiff(__ldg(Vq + i + 1), vq), r);
                 }
             }
@@ -307,7 +310,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             const int c = a.site_comp[st];
             const float g = a.gsyn[st];
             float2 v = sdr[c];
-            v.x += g;
+            if (a.g_implicit) v.x += g;
             v.y = fmaf(-g, vminus(Vq[c], a.Esyn), v.y);
             sdr[c] = v;
             a.gsyn[st] = g * a.decay;
@@ -413,14 +416,16 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                 sy[2 * h + 1] = rh * rcp_approx(dh);
                 return;
             }
-            // the head link to the parent compartment: assembled here, the
-            // head eliminated into the parent
+            // the head link to the parent compartment: assembled here (gh
+            // the implicit share of its coupling, ge all of it), the head
+            // eliminated into the parent
+            const float ge = a.gimp < 1.f ? 2.f * gh : gh;
             dh += gh;
-            rh = fmaf(gh, vt, rh);
+            rh = fmaf(ge, vt, rh);
             const float inv = rcp_approx(dh);
             const float f = gh * inv;
             sdr[h] = make_float2(f, rh * inv);
-            const float cd = fmaf(-f, gh, gh), cr = fmaf(f, rh, -gh * vt);
+            const float cd = fmaf(-f, gh, gh), cr = fmaf(f, rh, -ge * vt);
             if (P.nflag & kPathAlone) {
                 float2 v = sdr[P.parent];
                 v.x += cd;
@@ -615,7 +620,7 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
             const int c = a.site_comp[st];
             const float g = a.gsyn[st];
             float2 v = dr[c];
-            v.x += g;
+            if (a.g_implicit) v.x += g;
             v.y = fmaf(-g, vminus(Vq[c], a.Esyn), v.y);
             dr[c] = v;
             a.gsyn[st] = g * a.decay;
@@ -632,7 +637,7 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
         auto eliminate_path = [&](int pi) {
             const PathG P = paths[pi];
             const int h = P.head;
-            const float gh = fabsf(gax[h]), vt = pq[pi].z;
+            const float ge = fabsf(gax[h]), gh = a.gimp * ge, vt = pq[pi].z;
             int j = P.end - 1;
             const float2 v0 = dr[j];
             float db = v0.x, rb = v0.y, dh = db, rh = rb;
@@ -641,7 +646,7 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int q = max(jj - k, h + 1);
-                    g[k] = fabsf(gax[q]);
+                    g[k] = a.gimp * fabsf(gax[q]);
                     const float2 w = dr[q - 1];
                     d[k] = w.x;
                     r[k] = w.y;
@@ -684,11 +689,11 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
                 return;
             }
             dh += gh;
-            rh = fmaf(gh, vt, rh);
+            rh = fmaf(ge, vt, rh);
             const float inv = rcp_approx(dh);
             const float f = gh * inv;
             dr[h] = make_float2(f, rh * inv);
-            const float cd = fmaf(-f, gh, gh), cr = fmaf(f, rh, -gh * vt);
+            const float cd = fmaf(-f, gh, gh), cr = fmaf(f, rh, -ge * vt);
             if (P.nflag & kPathAloneG) {
                 float2 v = dr[P.parent];
                 v.x += cd;
@@ -848,17 +853,17 @@ __global__ void __launch_bounds__(256) giant_assemble_kernel(StepArgs32 a)
             const float n2 = nn * nn;
             const float gk = a.gK * s * (n2 * n2);
             const float gl = a.gL * s;
-            float d = fmaf(ar, a.cm_dt, gna + gk + gl);
+            float d = fmaf(ar, a.cm_dt, a.g_implicit ? gna + gk + gl : 0.f);
             float r = -fmaf(gna, vminus(vq, a.ENa), fmaf(gk, vminus(vq, a.EK), gl * vminus(vq, a.EL)));
             if (!signbit(gs)) {  // link to the parent i-1
                 const float g = fabsf(gs);
-                d += g;
+                d = fmaf(a.gimp, g, d);
                 r = fmaf(g, mmf::vdiff(Vq[i - 1], vq), r);
             }
             if (i + 1 < G.ncomp) {
                 const float gc = gax[i + 1];
                 if (!signbit(gc)) {  // link to the child i+1
-                    d += gc;
+                    d = fmaf(a.gimp, gc, d);
                     r = fmaf(gc, mmf::vdiff(Vq[i + 1], vq), r);
                 }
             }

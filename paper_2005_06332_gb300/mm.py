@@ -20,6 +20,7 @@ MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ETIMEOUT, MM_ENUMERIC, MM_EOVERFLOW, M
 MM_FP64, MM_FP32C = 0, 1
 MM_SCHED_SIZE_SORTED, MM_SCHED_COST = 0, 1
 STATE = {"V": 0, "m": 1, "h": 2, "n": 3, "gsyn": 4}
+SCHEMES = {"be": 0, "cn": 1}  # MM_SCHEME_BE, MM_SCHEME_CN
 PRECISION = {"fp64": MM_FP64, "fp32c": MM_FP32C}
 
 
@@ -55,7 +56,7 @@ class Allocator(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("schedule", C.c_int32), ("graph_steps", C.c_int32),
                 ("block_threads", C.c_int32), ("group_comps", C.c_int32), ("device", C.c_int32),
-                ("time_items", C.c_int32), ("reserved0", C.c_int32), ("dt_ms", C.c_double), ("spike_capacity", C.c_int64), ("cuda_stream", C.c_void_p),
+                ("time_items", C.c_int32), ("scheme", C.c_int32), ("dt_ms", C.c_double), ("spike_capacity", C.c_int64), ("cuda_stream", C.c_void_p),
                 ("cost", C.POINTER(C.c_float)), ("allocator", Allocator)]
 
 
@@ -360,7 +361,7 @@ class Network:
 
     def __init__(self, net, precision: str = "fp64", cost: Optional[np.ndarray] = None, graph_steps: int = 40,
                  block_threads: int = 0, group_comps: int = 0, spike_capacity: int = 0, device: int = 0,
-                 stream=None, torch_alloc: bool = True, time_items: bool = False):
+                 stream=None, torch_alloc: bool = True, time_items: bool = False, scheme: str = "be"):
         L = load()
         self._L = L
         self._h = C.c_void_p()
@@ -380,6 +381,7 @@ class Network:
         opt.dt_ms = self.dt
         opt.spike_capacity = spike_capacity
         opt.time_items = 1 if time_items else 0
+        opt.scheme = SCHEMES[scheme]
         self._cost = None
         if cost is not None:
             self._cost = np.ascontiguousarray(cost, np.float32)

@@ -170,6 +170,22 @@ def test_fp32c_all_item_classes_match_oracle():
     assert len(sn) == full.n_spikes
 
 
+def test_fp32c_eq2_as_printed_scheme_all_item_classes():
+    """MM_SCHEME_CN (Eq. 2 as printed) in FP32c on regular, large-class and
+    giant work items against the oracle's scheme "cn"."""
+    net = _three_class_network()
+    steps = 200
+    ref = oracle.simulate(net, steps, scheme="cn")
+    with mm.Network(net, precision="fp32c", scheme="cn") as g:
+        info = g.launch_info()
+        assert info["giant_items"] == 1 and info["big_items"] == 1
+        g.step(steps)
+        V = g.read_voltages()
+        sn, st = g.read_spikes()
+    assert np.max(np.abs(V - ref.V)) <= TOL_V
+    assert _spike_match(net, sn, st, ref) is not None
+
+
 def test_fp32c_checkpoint_resume():
     net = netgen.make_network(25, size_dist=("loguniform", 10, 300), p_branch=0.1, syn_per_neuron=6, seed=12,
                               stim_nA=(0.3, 0.9))
