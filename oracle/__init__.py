@@ -78,9 +78,9 @@ def lib():
                                        C.POINTER(Params), C.c_double, C.c_int, _D, _D, _D, _D]
             L.orc_simulate.restype = C.c_int
             L.orc_simulate.argtypes = [C.c_int32, _I64, _I32, _D, _D, _D,
-                                       C.c_int64, _I32, _I32, _I32, _D, _D,
+                                       C.c_int64, _I32, _I32, _I32, _D, _D, _I32,
                                        C.POINTER(Params), C.c_double, C.c_int, C.c_int64, _D,
-                                       _D, _D, _D, _D, _D, _D, _I32, _D, C.c_int64, _I64, C.c_int]
+                                       _D, _D, _D, _D, _D, _D, _I32, _I32, _D, C.c_int64, _I64, C.c_int]
             _lib = L
     return _lib
 
@@ -175,23 +175,35 @@ def assemble(parent, V, m, h, n, gsyn, area, Cn, gax, stim_nA, params: dict, dt:
 # --------------------------------------------------------------- simulation
 
 class Result:
-    def __init__(self, V, m, h, n, g, soma_trace, spk_neuron, spk_t, n_spikes):
+    def __init__(self, V, m, h, n, g, soma_trace, spk_neuron, spk_t, n_spikes, spk_comp=None):
         self.V, self.m, self.h, self.n, self.g = V, m, h, n, g
         self.soma_trace = soma_trace
         self.spk_neuron = spk_neuron
         self.spk_t = spk_t
         self.n_spikes = n_spikes
+        self.spk_comp = np.zeros_like(spk_neuron) if spk_comp is None else spk_comp
 
     def spikes_sorted(self):
         """(neuron, t) ordered by (t, neuron)."""
         o = np.lexsort((self.spk_neuron, self.spk_t))
         return self.spk_neuron[o], self.spk_t[o]
 
+    def point_spikes_sorted(self):
+        """(neuron, local compartment, t) ordered by (t, neuron, compartment)."""
+        o = np.lexsort((self.spk_comp, self.spk_neuron, self.spk_t))
+        return self.spk_neuron[o], self.spk_comp[o], self.spk_t[o]
+
 
 def simulate(net, n_steps: int, dt: float = None, params: dict = None, V_init=None,
-             record_soma: bool = False, spike_cap: int = None, threads: int = 0, scheme: str = "be") -> Result:
+             record_soma: bool = False, spike_cap: int = None, threads: int = 0, scheme: str = "be",
+             detect: str = "soma") -> Result:
     """Run the oracle on a ``netgen.Network`` for n_steps steps (scheme as
-    in ``assemble``)."""
+    in ``assemble``).  detect "soma": the threshold test runs at every soma;
+    "points": at every distinct (source neuron, ``syn_src_comp``) point that
+    synapses leave from (all somata when the network has no source
+    compartments), Sec. 2's spike computation over the synapse points."""
+    if detect not in ("soma", "points"):
+        raise ValueError(f"unknown detection mode {detect!r}")
     dt = net.dt if dt is None else dt
     params = net.params if params is None else params
     pr = params_from(params)
@@ -200,21 +212,29 @@ def simulate(net, n_steps: int, dt: float = None, params: dict = None, V_init=No
     L, d, stim = _f64(net.length_um), _f64(net.diam_um), _f64(net.stim_nA)
     src, dst, comp = _i32(net.syn_src), _i32(net.syn_dst), _i32(net.syn_comp)
     w, dl = _f64(net.syn_w), _f64(net.syn_delay_ms)
+    scomp = None
+    if detect == "points":
+        sc = getattr(net, "syn_src_comp", None)
+        scomp = _i32(np.zeros(len(src), np.int32) if sc is None else sc)
     N = len(off) - 1
     Cc = int(off[-1])
     V, m, h, n, g = np.zeros(Cc), np.zeros(Cc), np.zeros(Cc), np.zeros(Cc), np.zeros(Cc)
     trace = np.zeros((N, n_steps + 1)) if record_soma else None
-    cap = spike_cap if spike_cap is not None else max(1024, N * (n_steps // 40 + 2))
+    n_pt = N if scomp is None else len(np.unique(src.astype(np.int64) * (1 << 32) + scomp))
+    cap = spike_cap if spike_cap is not None else max(1024, n_pt * (n_steps // 40 + 2))
     spn = np.zeros(cap, np.int32)
+    spc = np.zeros(cap, np.int32)
     spt = np.zeros(cap, np.float64)
     nsp = np.zeros(1, np.int64)
     vi = None if V_init is None else _f64(V_init)
     rc = lib().orc_simulate(N, _p(off, C.c_int64), _p(parent, C.c_int32), _p(L, C.c_double),
                             _p(d, C.c_double), _p(stim, C.c_double), len(src), _p(src, C.c_int32),
                             _p(dst, C.c_int32), _p(comp, C.c_int32), _p(w, C.c_double), _p(dl, C.c_double),
+                            _p(scomp, C.c_int32),
                             C.byref(pr), float(dt), SCHEMES[scheme], int(n_steps), _p(vi, C.c_double),
                             _p(V, C.c_double), _p(m, C.c_double), _p(h, C.c_double), _p(n, C.c_double),
-                            _p(g, C.c_double), _p(trace, C.c_double), _p(spn, C.c_int32), _p(spt, C.c_double), cap,
+                            _p(g, C.c_double), _p(trace, C.c_double), _p(spn, C.c_int32), _p(spc, C.c_int32),
+                            _p(spt, C.c_double), cap,
                             _p(nsp, C.c_int64), int(threads))
     if rc == -1:
         raise ValueError("oracle: invalid network")
@@ -223,4 +243,4 @@ def simulate(net, n_steps: int, dt: float = None, params: dict = None, V_init=No
     if rc == -3:
         raise OverflowError("oracle: spike capacity exceeded")
     k = int(nsp[0])
-    return Result(V, m, h, n, g, trace, spn[:k].copy(), spt[:k].copy(), k)
+    return Result(V, m, h, n, g, trace, spn[:k].copy(), spt[:k].copy(), k, spc[:k].copy())

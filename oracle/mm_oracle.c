@@ -21,9 +21,14 @@
  *      root over parent[], then forward substitution), V += dV;
  *   5. exponential-Euler gate update at V^{n+1};
  *   6. synaptic decay g_syn *= exp(-dt/tau);
- *   7. soma threshold test: an upward crossing of theta between V^n and
- *      V^{n+1} is a spike at the linearly interpolated time; each outgoing
- *      synapse s then arrives at step n + 1 + round(delay_s/dt).
+ *   7. threshold test at every detection point: an upward crossing of
+ *      theta between V^n and V^{n+1} is a spike at the linearly
+ *      interpolated time; each synapse s leaving that point then arrives
+ *      at step n + 1 + round(delay_s/dt).  The detection points are the
+ *      somata (default), or, when synapses carry source compartments, the
+ *      distinct (neuron, compartment) points where synapses leave
+ *      (Sec. 2's spike computation over the points of a morphology that
+ *      hold a synapse).
  *
  * Readings of the paper (Sec. 2) taken here:
  *   - Eq. 2 prints the same g_{i+1/2} for both off-diagonals and a
@@ -36,7 +41,8 @@
  *     rhs[0] /= b[0].
  *   - Compartment indices are 0-based with parent[0] = -1, parent[i] < i.
  *   - Capacitance is constant (Cm * area).
- *   - The spike test is at the soma, threshold theta, upward crossing only.
+ *   - The spike test is at the soma (or at the synapse points, as above),
+ *     threshold theta, upward crossing only.
  *
  * Scheme 1 (scheme argument of orc_assemble / orc_simulate) is Eq. 2 taken
  * as printed instead: off-diagonals a_i = b_i = -g/2 (half of each link's
@@ -269,17 +275,23 @@ static int cmp_i64(const void *x, const void *y)
  *   V_out, m_out, h_out, n_out, g_out [n_comp] state after the last step
  *                                             (g_out: merged synaptic conductance)
  *   soma_trace [n_neurons * (n_steps + 1)]    soma V at t_0 .. t_nsteps
- *   spk_neuron, spk_t [spk_cap]               spikes in detection order
+ *   spk_neuron, spk_comp, spk_t [spk_cap]     spikes in detection order: each step
+ *                                             by (neuron, compartment); spk_comp is
+ *                                             the local compartment (0: soma)
+ * syn_src_comp [n_syn] (may be NULL) is the local compartment of the source
+ * neuron each synapse leaves from; with it the threshold test runs at every
+ * distinct (src, src_comp) point instead of at every soma.
  * Returns 0, -1 on bad input, -2 on allocation failure, -3 if more than
  * spk_cap spikes were detected (n_spk still counts all of them). */
 int orc_simulate(int32_t n_neurons, const int64_t *off, const int32_t *parent,
                  const double *L, const double *diam, const double *stim_nA,
                  int64_t n_syn, const int32_t *syn_src, const int32_t *syn_dst,
                  const int32_t *syn_comp, const double *syn_w, const double *syn_delay_ms,
+                 const int32_t *syn_src_comp,
                  const orc_params *p, double dt, int scheme, int64_t n_steps, const double *V_init,
                  double *V_out, double *m_out, double *h_out, double *n_out,
-                 double *g_out, double *soma_trace, int32_t *spk_neuron, double *spk_t, int64_t spk_cap,
-                 int64_t *n_spk, int n_threads)
+                 double *g_out, double *soma_trace, int32_t *spk_neuron, int32_t *spk_comp, double *spk_t,
+                 int64_t spk_cap, int64_t *n_spk, int n_threads)
 {
     int64_t C = off[n_neurons];
     int rc = 0;
@@ -301,15 +313,23 @@ int orc_simulate(int32_t n_neurons, const int64_t *off, const int32_t *parent,
     double *wb = malloc((size_t)C * sizeof(double));
     double *wc = malloc((size_t)C * sizeof(double));
     double *wr = malloc((size_t)C * sizeof(double));
-    unsigned char *fired = calloc((size_t)(n_neurons > 0 ? n_neurons : 1), 1);
-    double *tfire = malloc((size_t)(n_neurons > 0 ? n_neurons : 1) * sizeof(double));
-    int64_t *out_start = calloc((size_t)n_neurons + 1, sizeof(int64_t));
+    /* detection points: pt_start[k] .. pt_start[k+1]-1 are neuron k's,
+     * ascending compartment pt_comp; out_start / out_syn list the synapses
+     * leaving each point, ascending synapse id */
+    int64_t n_pt_max = syn_src_comp ? (n_syn > 0 ? n_syn : 1) : (n_neurons > 0 ? n_neurons : 1);
+    int64_t *pt_start = calloc((size_t)n_neurons + 1, sizeof(int64_t));
+    int32_t *pt_comp = malloc((size_t)n_pt_max * sizeof(int32_t));
+    int64_t *syn_pt = malloc((size_t)(n_syn > 0 ? n_syn : 1) * sizeof(int64_t));
+    unsigned char *fired = calloc((size_t)n_pt_max, 1);
+    double *tfire = malloc((size_t)n_pt_max * sizeof(double));
+    double *vpre = malloc((size_t)n_pt_max * sizeof(double));
+    int64_t *out_start = calloc((size_t)n_pt_max + 1, sizeof(int64_t));
     int64_t *out_syn = malloc((size_t)(n_syn > 0 ? n_syn : 1) * sizeof(int64_t));
     int64_t *dsteps = malloc((size_t)(n_syn > 0 ? n_syn : 1) * sizeof(int64_t));
     idlist *ring = NULL;
     int64_t R = 2;
     if (!area || !Cn || !gax || !V || !m || !h || !nn || !gs || !wa || !wb || !wc || !wr ||
-        !fired || !tfire || !out_start || !out_syn || !dsteps) {
+        !fired || !tfire || !vpre || !pt_start || !pt_comp || !syn_pt || !out_start || !out_syn || !dsteps) {
         rc = -2;
         goto done;
     }
@@ -324,6 +344,10 @@ int orc_simulate(int32_t n_neurons, const int64_t *off, const int32_t *parent,
     for (int64_t s = 0; s < n_syn; ++s) {
         if (syn_src[s] < 0 || syn_src[s] >= n_neurons || syn_dst[s] < 0 || syn_dst[s] >= n_neurons ||
             syn_comp[s] < 0 || syn_comp[s] >= off[syn_dst[s] + 1] - off[syn_dst[s]]) { rc = -1; goto done; }
+        if (syn_src_comp && (syn_src_comp[s] < 0 || syn_src_comp[s] >= off[syn_src[s] + 1] - off[syn_src[s]])) {
+            rc = -1;
+            goto done;
+        }
         dsteps[s] = (int64_t)llround(syn_delay_ms[s] / dt);
         if (dsteps[s] < 1) { rc = -1; goto done; }
         if (dsteps[s] + 2 > R) R = dsteps[s] + 2;
@@ -331,16 +355,57 @@ int orc_simulate(int32_t n_neurons, const int64_t *off, const int32_t *parent,
 
     orc_geometry(n_neurons, off, parent, L, diam, p, area, Cn, gax);
 
-    /* outgoing synapses of each source, ascending synapse id */
-    for (int64_t s = 0; s < n_syn; ++s) out_start[syn_src[s] + 1]++;
-    for (int32_t k = 0; k < n_neurons; ++k) out_start[k + 1] += out_start[k];
-    {
-        int64_t *fill = calloc((size_t)n_neurons + 1, sizeof(int64_t));
-        if (!fill) { rc = -2; goto done; }
-        for (int64_t s = 0; s < n_syn; ++s) {
-            int32_t src = syn_src[s];
-            out_syn[out_start[src] + fill[src]++] = s;
+    /* detection points and the point each synapse leaves from */
+    int64_t n_pt = 0;
+    if (!syn_src_comp) {
+        for (int32_t k = 0; k < n_neurons; ++k) {
+            pt_start[k] = k;
+            pt_comp[k] = 0;
         }
+        pt_start[n_neurons] = n_neurons;
+        n_pt = n_neurons;
+        for (int64_t s = 0; s < n_syn; ++s) syn_pt[s] = syn_src[s];
+    } else {
+        /* the distinct compartments each neuron's synapses leave from, by a
+         * mark per compartment (one neuron at a time) */
+        int64_t *by_src = malloc((size_t)(n_syn > 0 ? n_syn : 1) * sizeof(int64_t));
+        int64_t *bstart = calloc((size_t)n_neurons + 1, sizeof(int64_t));
+        int64_t *mark = malloc((size_t)(C > 0 ? C : 1) * sizeof(int64_t));
+        if (!by_src || !bstart || !mark) { free(by_src); free(bstart); free(mark); rc = -2; goto done; }
+        for (int64_t i = 0; i < C; ++i) mark[i] = -1;
+        for (int64_t s = 0; s < n_syn; ++s) bstart[syn_src[s] + 1]++;
+        for (int32_t k = 0; k < n_neurons; ++k) bstart[k + 1] += bstart[k];
+        {
+            int64_t *fill = calloc((size_t)n_neurons + 1, sizeof(int64_t));
+            if (!fill) { free(by_src); free(bstart); free(mark); rc = -2; goto done; }
+            for (int64_t s = 0; s < n_syn; ++s) by_src[bstart[syn_src[s]] + fill[syn_src[s]]++] = s;
+            free(fill);
+        }
+        for (int32_t k = 0; k < n_neurons; ++k) {
+            pt_start[k] = n_pt;
+            int32_t nk = (int32_t)(off[k + 1] - off[k]);
+            for (int64_t e = bstart[k]; e < bstart[k + 1]; ++e) mark[off[k] + syn_src_comp[by_src[e]]] = 0;
+            for (int32_t i = 0; i < nk; ++i)
+                if (mark[off[k] + i] == 0) {
+                    mark[off[k] + i] = n_pt;
+                    pt_comp[n_pt++] = i;
+                }
+            for (int64_t e = bstart[k]; e < bstart[k + 1]; ++e) {
+                int64_t s = by_src[e];
+                syn_pt[s] = mark[off[k] + syn_src_comp[s]];
+            }
+        }
+        pt_start[n_neurons] = n_pt;
+        free(by_src); free(bstart); free(mark);
+    }
+
+    /* synapses leaving each point, ascending synapse id */
+    for (int64_t s = 0; s < n_syn; ++s) out_start[syn_pt[s] + 1]++;
+    for (int64_t q = 0; q < n_pt; ++q) out_start[q + 1] += out_start[q];
+    {
+        int64_t *fill = calloc((size_t)n_pt + 1, sizeof(int64_t));
+        if (!fill) { rc = -2; goto done; }
+        for (int64_t s = 0; s < n_syn; ++s) out_syn[out_start[syn_pt[s]] + fill[syn_pt[s]]++] = s;
         free(fill);
     }
     ring = calloc((size_t)R, sizeof(idlist));
@@ -371,7 +436,7 @@ int orc_simulate(int32_t n_neurons, const int64_t *off, const int32_t *parent,
         for (int32_t k = 0; k < n_neurons; ++k) {
             int64_t b0 = off[k];
             int32_t n = (int32_t)(off[k + 1] - off[k]);
-            double v0 = V[b0];
+            for (int64_t q = pt_start[k]; q < pt_start[k + 1]; ++q) vpre[q] = V[b0 + pt_comp[q]];
             orc_assemble(n, parent + b0, V + b0, m + b0, h + b0, nn + b0, gs + b0,
                          area + b0, Cn + b0, gax + b0, stim_nA[k], p, dt, scheme,
                          wa + b0, wb + b0, wc + b0, wr + b0);
@@ -381,27 +446,32 @@ int orc_simulate(int32_t n_neurons, const int64_t *off, const int32_t *parent,
                 orc_gate_step(V[b0 + i], dt, &m[b0 + i], &h[b0 + i], &nn[b0 + i]);
                 gs[b0 + i] *= decay;
             }
-            double v1 = V[b0];
-            fired[k] = 0;
-            if (v0 < p->threshold && v1 >= p->threshold) {
-                fired[k] = 1;
-                tfire[k] = (double)step * dt + dt * (p->threshold - v0) / (v1 - v0);
+            for (int64_t q = pt_start[k]; q < pt_start[k + 1]; ++q) {
+                double v0 = vpre[q], v1 = V[b0 + pt_comp[q]];
+                fired[q] = 0;
+                if (v0 < p->threshold && v1 >= p->threshold) {
+                    fired[q] = 1;
+                    tfire[q] = (double)step * dt + dt * (p->threshold - v0) / (v1 - v0);
+                }
             }
         }
-        /* spikes in neuron order; schedule their events */
+        /* spikes in point order (neuron, compartment); schedule their events */
         for (int32_t k = 0; k < n_neurons; ++k) {
-            if (!fired[k]) continue;
-            if (nsp < spk_cap) {
-                if (spk_neuron) spk_neuron[nsp] = k;
-                if (spk_t) spk_t[nsp] = tfire[k];
-            } else {
-                rc = -3;
-            }
-            nsp++;
-            for (int64_t o = out_start[k]; o < out_start[k + 1]; ++o) {
-                int64_t s = out_syn[o];
-                int64_t arrival = step + 1 + dsteps[s];
-                if (idlist_push(&ring[arrival % R], s)) { rc = -2; goto done; }
+            for (int64_t q = pt_start[k]; q < pt_start[k + 1]; ++q) {
+                if (!fired[q]) continue;
+                if (nsp < spk_cap) {
+                    if (spk_neuron) spk_neuron[nsp] = k;
+                    if (spk_comp) spk_comp[nsp] = pt_comp[q];
+                    if (spk_t) spk_t[nsp] = tfire[q];
+                } else {
+                    rc = -3;
+                }
+                nsp++;
+                for (int64_t o = out_start[q]; o < out_start[q + 1]; ++o) {
+                    int64_t s = out_syn[o];
+                    int64_t arrival = step + 1 + dsteps[s];
+                    if (idlist_push(&ring[arrival % R], s)) { rc = -2; goto done; }
+                }
             }
         }
         if (soma_trace)
@@ -421,7 +491,8 @@ done:
         free(ring);
     }
     free(area); free(Cn); free(gax); free(V); free(m); free(h); free(nn); free(gs);
-    free(wa); free(wb); free(wc); free(wr); free(fired); free(tfire);
+    free(wa); free(wb); free(wc); free(wr); free(fired); free(tfire); free(vpre);
+    free(pt_start); free(pt_comp); free(syn_pt);
     free(out_start); free(out_syn); free(dsteps);
     return rc;
 }

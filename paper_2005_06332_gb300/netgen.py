@@ -61,6 +61,10 @@ class Network:
       syn_comp     int32[S]    LOCAL compartment of the postsynaptic neuron
       syn_w        float64[S]  peak conductance increment (uS)
       syn_delay_ms float64[S]  axonal + synaptic delay
+      syn_src_comp int32[S] or None: LOCAL compartment of the presynaptic
+                   neuron the synapse leaves from (the point whose threshold
+                   crossings it carries when spikes are detected at synapse
+                   points); None: every synapse leaves from the soma
     """
     comp_offset: np.ndarray
     parent: np.ndarray
@@ -76,6 +80,7 @@ class Network:
     dt: float = 0.025
     t_stop: float = 100.0
     name: str = "custom"
+    syn_src_comp: Optional[np.ndarray] = None
 
     @property
     def n_neurons(self) -> int:
@@ -127,6 +132,7 @@ class Network:
             syn_delay_ms=self.syn_delay_ms[keep].copy(),
             params=dict(self.params), dt=self.dt, t_stop=self.t_stop,
             name=self.name + "-subset",
+            syn_src_comp=None if self.syn_src_comp is None else self.syn_src_comp[keep].copy(),
         )
 
 
@@ -221,6 +227,7 @@ def make_network(
     t_stop: float = 100.0,
     params: Optional[dict] = None,
     name: str = "custom",
+    src_points: bool = False,
 ) -> Network:
     """Draw a network.
 
@@ -229,6 +236,9 @@ def make_network(
                (the paper's mono-morphology case, Sec. 3).
     giants:    extra neurons of ``giant_size`` compartments appended last.
     delay_ms:  ("const", d) or ("uniform", lo, hi).
+    src_points: every synapse also leaves from a compartment drawn uniformly
+               over its source neuron (drawn after everything else, so the
+               rest of the network is the one drawn without it).
     """
     rng = np.random.default_rng(seed)
     sizes = draw_sizes(rng, n_neurons, size_dist)
@@ -289,13 +299,17 @@ def make_network(
     else:
         src = comp = np.zeros(0, np.int64)
         w = dl = np.zeros(0, np.float64)
+    src_comp = None
+    if src_points:
+        src_comp = np.minimum(np.floor(rng.random(S) * sizes[src]).astype(np.int64), sizes[src] - 1)
+        src_comp = src_comp.astype(np.int32)
 
     return Network(
         comp_offset=off, parent=parent, length_um=L, diam_um=D, stim_nA=stim,
         syn_src=src.astype(np.int32), syn_dst=dst.astype(np.int32), syn_comp=comp.astype(np.int32),
         syn_w=w, syn_delay_ms=dl,
         params=dict(DEFAULT_PARAMS if params is None else params),
-        dt=dt, t_stop=t_stop, name=name,
+        dt=dt, t_stop=t_stop, name=name, syn_src_comp=src_comp,
     )
 
 

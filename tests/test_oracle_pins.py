@@ -474,3 +474,148 @@ def test_cn_assembly_conserves_charge_and_halves_the_couplings():
     lhs = np.sum(Cn / dt * dV)
     _, _, _, rhs0 = oracle.assemble(net.parent, V, m, h, nn, gs, area, Cn, np.zeros(n), 0.3, P, dt, scheme="cn")
     assert abs(lhs - np.sum(rhs0)) <= 1e-12 * np.sum(np.abs(rhs0))
+
+
+# ------------------------- spike detection at synapse points (Sec. 2): pins
+
+def _points_net(n_src, parent, L, d, stim, points, w=None, delays=None, params=None):
+    """Neuron 0 (the given tree) with one synapse leaving each listed point
+    towards a 3-compartment passive neuron 1 (compartment k % 3)."""
+    n0 = len(parent)
+    off = np.array([0, n0, n0 + 3], dtype=np.int64)
+    S = len(points)
+    return netgen.Network(
+        comp_offset=off, parent=np.concatenate([parent, [-1, 0, 1]]).astype(np.int32),
+        length_um=np.concatenate([L, np.full(3, 10.0)]), diam_um=np.concatenate([d, np.full(3, 1.0)]),
+        stim_nA=np.array([stim, 0.0]),
+        syn_src=np.zeros(S, np.int32), syn_dst=np.ones(S, np.int32),
+        syn_comp=(np.arange(S) % 3).astype(np.int32),
+        syn_w=np.zeros(S) if w is None else np.asarray(w, np.float64),
+        syn_delay_ms=np.full(S, 1.0) if delays is None else np.asarray(delays, np.float64),
+        params=dict(params or P), dt=0.025, syn_src_comp=np.asarray(points, np.int32))
+
+
+def test_point_spike_times_match_a_dense_passive_recurrence():
+    """A passive tree under a soma current rises monotonically towards its
+    steady state, so each point crosses a threshold below its steady state
+    exactly once.  The oracle's point spikes (compartment and interpolated
+    time) must be those of the backward-Euler recurrence written as a dense
+    linear system, (C/dt + G_m + K) dV = -G_m (V - E_L) - K V + b, and points
+    whose steady state stays below the threshold must never fire."""
+    rng = np.random.default_rng(21)
+    n = 24
+    parent = _rand_tree(rng, n, 0.3)
+    L = rng.uniform(5.0, 20.0, n)
+    d = rng.uniform(0.5, 2.0, n)
+    I, dt, steps = 0.05, 0.025, 1200
+    params = _passive()
+    params["threshold"] = 0.0  # replaced below
+    net0 = _points_net(1, parent, L, d, I, [0])
+    area, Cn, gax = oracle.geometry(net0.comp_offset[:2], net0.parent[:n], L, d, params)
+    Gm = params["gL"] * area * 1e3
+    K = np.zeros((n, n))
+    for i in range(1, n):
+        g, q = gax[i], parent[i]
+        K[i, i] += g
+        K[q, q] += g
+        K[i, q] -= g
+        K[q, i] -= g
+    A = np.diag(Cn / dt + Gm) + K
+    b = np.zeros(n)
+    b[0] = I
+    V = np.full(n, params["v_init"])
+    trace = [V.copy()]
+    for _ in range(steps):
+        V = V + np.linalg.solve(A, -Gm * (V - params["EL"]) - K @ V + b)
+        trace.append(V.copy())
+    trace = np.array(trace)
+    assert np.all(np.diff(trace, axis=0) >= -1e-12)  # monotone rise
+    final = trace[-1]
+    theta = 0.5 * (final.max() + final.min())
+    params["threshold"] = theta
+    points = list(range(n))
+    net = _points_net(1, parent, L, d, I, points, params=params)
+    r = oracle.simulate(net, steps, dt=dt, params=params, detect="points")
+    nrn, comp, t = r.point_spikes_sorted()
+    expect = {}
+    for c in points:
+        k = np.nonzero((trace[:-1, c] < theta) & (trace[1:, c] >= theta))[0]
+        if len(k):
+            v0, v1 = trace[k[0], c], trace[k[0] + 1, c]
+            expect[c] = k[0] * dt + dt * (theta - v0) / (v1 - v0)
+    assert 0 < len(expect) < n
+    assert np.all(nrn == 0)
+    got = dict(zip(comp.tolist(), t.tolist()))
+    assert sorted(got) == sorted(expect)
+    for c in expect:
+        assert got[c] == pytest.approx(expect[c], abs=1e-9)
+
+
+def test_point_spikes_route_to_the_synapses_leaving_each_point():
+    """An HH neuron firing repeatedly, with synapses of different weights and
+    delays leaving the soma, a middle and a distal compartment towards a
+    passive neuron: the target conductances after the run are the sum over
+    the recorded spikes of each point, over the synapses leaving it, of
+    w exp(-(n - arrival) dt / tau), arrival = spike step + 1 + round(delay/dt)."""
+    n = 40
+    parent = np.arange(-1, n - 1, dtype=np.int32)
+    L, d = np.full(n, 10.0), np.full(n, 2.0)
+    points = [0, 20, 39, 39, 0, 20]
+    w = [0.011, 0.023, 0.037, 0.041, 0.053, 0.067]
+    delays = [1.0, 2.5, 1.3, 4.0, 3.1, 1.7]
+    params = dict(P)
+    params["gL"] = 0.3
+    net = _points_net(1, parent, L, d, 0.4, points, w=w, delays=delays, params=params)
+    steps = 1600
+    r = oracle.simulate(net, steps, detect="points")
+    nrn, comp, t = r.point_spikes_sorted()
+    assert r.n_spikes >= 6 and set(comp.tolist()) == {0, 20, 39}
+    dt, tau = net.dt, P["tau_syn"]
+    g = np.zeros(3)
+    for c, ts in zip(comp, t):
+        step = int(math.ceil(ts / dt - 1e-9)) - 1
+        for s, pc in enumerate(points):
+            if pc != c:
+                continue
+            arrival = step + 1 + int(round(delays[s] / dt))
+            if arrival < steps:
+                g[s % 3] += w[s] * math.exp(-(steps - arrival) * dt / tau)
+    np.testing.assert_allclose(r.g[n:], g, rtol=1e-12, atol=1e-300)
+
+
+def test_point_spikes_propagate_along_an_unbranched_cable():
+    """The action potential that the onset of a soma current starts on a
+    uniform HH cable reaches every point, later the farther the point is from
+    the soma, at a constant speed away from the ends (equal delays between
+    equally spaced interior points)."""
+    n = 60
+    parent = np.arange(-1, n - 1, dtype=np.int32)
+    points = [0, 10, 20, 30, 40, 50, 59]
+    net = _points_net(1, parent, np.full(n, 10.0), np.full(n, 2.0), 0.6, points)
+    r = oracle.simulate(net, 400, detect="points")
+    nrn, comp, t = r.point_spikes_sorted()
+    first = [np.min(t[comp == c]) for c in points]
+    assert np.all(np.diff(first) > 0), first
+    lag = np.diff(first)[1:4]  # 10 -> 20 -> 30 -> 40
+    assert np.max(lag) < 1.1 * np.min(lag), lag
+
+
+def test_points_at_every_soma_are_soma_detection():
+    """With every synapse leaving its source's soma, detection at synapse
+    points is the soma test of every neuron that has an outgoing synapse:
+    the same spikes (bit for bit) and the same final state."""
+    net = netgen.make_network(16, size_dist=("loguniform", 20, 120), p_branch=0.15, syn_per_neuron=6, seed=23,
+                              stim_nA=(0.3, 0.6), weight_uS=(0.0, 0.02))
+    net.syn_src_comp = np.zeros(net.n_syn, np.int32)
+    a = oracle.simulate(net, 1200)
+    b = oracle.simulate(net, 1200, detect="points")
+    np.testing.assert_array_equal(a.V, b.V)
+    has_out = np.zeros(net.n_neurons, bool)
+    has_out[net.syn_src] = True
+    na, ta = a.spikes_sorted()
+    keep = has_out[na]
+    nb, cb, tb = b.point_spikes_sorted()
+    assert a.n_spikes > 10
+    np.testing.assert_array_equal(nb, na[keep])
+    np.testing.assert_array_equal(tb, ta[keep])
+    assert np.all(cb == 0)
