@@ -73,6 +73,17 @@ enum {
                           dt G_i / C_i < 2 in every compartment */
 };
 
+/* Where the threshold test runs (Sec. 2, spike computation). */
+enum {
+    MM_DETECT_SOMA = 0,            /* at every soma; a spike of neuron k reaches every
+                                      synapse with src_neuron k (default) */
+    MM_DETECT_SYNAPSE_POINTS = 1   /* at every point of a morphology that a synapse leaves
+                                      from: the distinct (src_neuron, src_comp) pairs.  A
+                                      crossing at a point reaches the synapses leaving that
+                                      point only; somata without such a synapse are not
+                                      tested */
+};
+
 /* Order in which the per-step kernel takes its work items. */
 enum {
     MM_SCHED_SIZE_SORTED = 0,  /* neurons sorted by compartment count, largest first */
@@ -118,7 +129,10 @@ typedef struct {
  * raise the conductance of compartment dst_comp[s] (LOCAL index) of neuron
  * dst_neuron[s] by weight_uS[s], round(delay_ms[s]/dt) + 1 steps after the
  * step in which the spike was detected; conductances decay with tau_ms and
- * drive the current g (V - e_rev_mV).  Arrays have n entries (n may be 0). */
+ * drive the current g (V - e_rev_mV).  Arrays have n entries (n may be 0).
+ * src_comp (may be NULL = every synapse leaves from the soma) is the LOCAL
+ * compartment of src_neuron[s] the synapse leaves from; it is used under
+ * MM_DETECT_SYNAPSE_POINTS only. */
 typedef struct {
     int64_t n;
     const int32_t *src_neuron;
@@ -128,6 +142,7 @@ typedef struct {
     const double *delay_ms;    /* round(delay/dt) >= 1 */
     double tau_ms;             /* > 0 */
     double e_rev_mV;
+    const int32_t *src_comp;   /* may be NULL */
 } mm_synapses;
 
 /* Device-memory allocator: alloc returns a device pointer (256-byte aligned)
@@ -147,6 +162,8 @@ typedef struct {
     int32_t device;             /* CUDA device ordinal */
     int32_t time_items;         /* MM_FP32C: record each work item's solve time (mm_read_neuron_times) */
     int32_t scheme;             /* MM_SCHEME_BE | MM_SCHEME_CN */
+    int32_t detect;             /* MM_DETECT_SOMA | MM_DETECT_SYNAPSE_POINTS */
+    int32_t reserved0;          /* must be 0 */
     double dt_ms;               /* time step of the network, > 0 */
     int64_t spike_capacity;     /* spikes held between two mm_read_spikes; 0 = automatic */
     void *cuda_stream;          /* cudaStream_t to run on; NULL = a library-owned stream */
@@ -162,7 +179,8 @@ void mm_default_options(mm_options *opt);
  * current injected into each soma from t = 0 (may be NULL: no stimulus).
  * On success *out owns the network; on failure *out is NULL.
  * Errors: MM_EINVAL (bad sizes, parent[i] >= i, non-positive geometry,
- * dst_comp out of range, delay < dt, dt <= 0), MM_ENOMEM, MM_ECUDA, MM_ENOTSUP. */
+ * dst_comp or src_comp out of range, delay < dt, dt <= 0, unknown scheme or
+ * detection mode, reserved0 != 0), MM_ENOMEM, MM_ECUDA, MM_ENOTSUP. */
 mm_status mm_create_network(const mm_morphologies *morph, const mm_channel_params *chan,
                             const mm_synapses *syn, const double *stim_nA,
                             const mm_options *opt, mm_net **out);
@@ -189,6 +207,13 @@ mm_status mm_read_soma_voltages(mm_net *net, double *out, int64_t cap);
  * records and the count to *n_out.  MM_EOVERFLOW if the device buffer
  * overflowed (the records it held are still returned).  Synchronises. */
 mm_status mm_read_spikes(mm_net *net, int32_t *neuron, double *t_ms, int64_t cap, int64_t *n_out);
+
+/* mm_read_spikes with the point of each spike: comp [cap] receives the
+ * LOCAL compartment where the crossing was detected (0 under
+ * MM_DETECT_SOMA); records ordered by (t, neuron, comp).  Drains the same
+ * buffer as mm_read_spikes. */
+mm_status mm_read_spike_points(mm_net *net, int32_t *neuron, int32_t *comp, double *t_ms, int64_t cap,
+                               int64_t *n_out);
 
 /* Replace the soma stimulus of every neuron (host array [n], n = n_neurons). */
 mm_status mm_set_stimulus(mm_net *net, const double *stim_nA, int64_t n);

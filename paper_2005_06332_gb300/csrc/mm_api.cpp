@@ -46,6 +46,8 @@ struct mm_net {
     int32_t N = 0;
     int64_t C = 0, nsite = 0, S = 0;
     int32_t R = 2;
+    int32_t n_src = 0;        // spike sources: neurons, or detection points
+    int detect = MM_DETECT_SOMA;
     int64_t spk_cap = 0;
     int64_t steps_done = 0;
 
@@ -76,6 +78,11 @@ struct mm_net {
     double *stim = nullptr;
     double *spk_t = nullptr, *scratch = nullptr;
     int32_t *spk_nrn = nullptr, *ring_nrn = nullptr, *ring_cnt = nullptr, *user_id = nullptr;
+    int32_t *spk_comp = nullptr;
+    // detection points (MM_DETECT_SYNAPSE_POINTS)
+    uint32_t *pmask = nullptr;
+    int64_t *pt_comp = nullptr;
+    int32_t *pt_user_nrn = nullptr, *pt_user_comp = nullptr, *soma_src = nullptr;
     int64_t *user2int = nullptr, *soma_of_user = nullptr, *site_internal = nullptr;
     mmk::DevCtl *ctl = nullptr;
 
@@ -358,6 +365,9 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     if (opt->schedule != MM_SCHED_SIZE_SORTED && opt->schedule != MM_SCHED_COST)
         return fail(net, MM_EINVAL, "unknown schedule");
     if (opt->scheme != MM_SCHEME_BE && opt->scheme != MM_SCHEME_CN) return fail(net, MM_EINVAL, "unknown scheme");
+    if (opt->detect != MM_DETECT_SOMA && opt->detect != MM_DETECT_SYNAPSE_POINTS)
+        return fail(net, MM_EINVAL, "unknown detection mode");
+    if (opt->reserved0 != 0) return fail(net, MM_EINVAL, "mm_options.reserved0 must be 0");
     if (opt->schedule == MM_SCHED_COST && !opt->cost) return fail(net, MM_EINVAL, "MM_SCHED_COST needs mm_options.cost");
     if (syn && !(syn->tau_ms > 0.0)) return fail(net, MM_EINVAL, "tau_ms must be > 0");
     if (!chan) return fail(net, MM_EINVAL, "channel parameters must not be NULL");
@@ -387,6 +397,8 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     li.dcomp = syn ? syn->dst_comp : nullptr;
     li.w = syn ? syn->weight_uS : nullptr;
     li.delay_ms = syn ? syn->delay_ms : nullptr;
+    li.points = opt->detect == MM_DETECT_SYNAPSE_POINTS;
+    li.scomp = syn ? syn->src_comp : nullptr;
     li.stim = stim_nA;
     li.cost = opt->schedule == MM_SCHED_COST ? opt->cost : nullptr;
     li.dt = opt->dt_ms;
@@ -421,10 +433,13 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     net->nsite = (int64_t)L.site_comp.size();
     net->S = li.S;
     net->R = L.R;
+    net->n_src = L.n_src;
+    net->detect = opt->detect;
     net->order = L.order;
     net->internal_of = L.internal_of;
     net->f_syn = L.f_syn;
-    net->spk_cap = opt->spike_capacity > 0 ? opt->spike_capacity : std::max<int64_t>(1 << 16, (int64_t)L.N * 64);
+    net->spk_cap = opt->spike_capacity > 0 ? opt->spike_capacity
+                 : std::max<int64_t>(1 << 16, (int64_t)L.n_src * (li.points ? 16 : 64));
 
     const size_t C = (size_t)L.C, N = (size_t)L.N;
     mm_status st;
@@ -467,9 +482,19 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     UP(net->user2int, L.user2int.data(), C);
     UP(net->soma_of_user, L.soma_of_user.data(), N);
     UP(net->site_internal, L.site_internal.data(), (size_t)net->nsite);
-    ZR(net->ring_nrn, (size_t)net->R * N);
+    ZR(net->ring_nrn, (size_t)net->R * (size_t)std::max(net->n_src, 1));
     ZR(net->ring_cnt, (size_t)net->R);
     ZR(net->spk_nrn, (size_t)net->spk_cap);
+    ZR(net->spk_comp, (size_t)net->spk_cap);
+    if (li.points) {
+        UP(net->pmask, L.pmask.data(), L.pmask.size());
+        UP(net->soma_src, L.soma_src.data(), N);
+        if (L.n_src > 0) {
+            UP(net->pt_comp, L.pt_comp.data(), L.pt_comp.size());
+            UP(net->pt_user_nrn, L.pt_user_nrn.data(), L.pt_user_nrn.size());
+            UP(net->pt_user_comp, L.pt_user_comp.data(), L.pt_user_comp.size());
+        }
+    }
     ZR(net->spk_t, (size_t)net->spk_cap);
     ZR(net->ctl, 1);
     mmk::GroupRec *dgroups = nullptr;
@@ -543,10 +568,17 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.ring_nrn = net->ring_nrn;
         a.ring_cnt = net->ring_cnt;
         a.R = net->R;
-        a.N = net->N;
+        a.N = std::max(net->n_src, 1);
         a.spk_nrn = net->spk_nrn;
+        a.spk_comp = net->spk_comp;
         a.spk_t = net->spk_t;
         a.spk_cap = net->spk_cap;
+        a.pmask = net->pmask;
+        a.pt_comp = net->pt_comp;
+        a.pt_user_nrn = net->pt_user_nrn;
+        a.pt_user_comp = net->pt_user_comp;
+        a.soma_src = net->soma_src;
+        a.n_pt = li.points ? net->n_src : 0;
         a.ctl = net->ctl;
         a.smem_comps = smem_comps;
         a.smem_segs = smem_segs;
@@ -601,10 +633,17 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.ring_nrn = net->ring_nrn;
         a.ring_cnt = net->ring_cnt;
         a.R = net->R;
-        a.N = net->N;
+        a.N = std::max(net->n_src, 1);
         a.spk_nrn = net->spk_nrn;
+        a.spk_comp = net->spk_comp;
         a.spk_t = net->spk_t;
         a.spk_cap = net->spk_cap;
+        a.pmask = net->pmask;
+        a.pt_comp = net->pt_comp;
+        a.pt_user_nrn = net->pt_user_nrn;
+        a.pt_user_comp = net->pt_user_comp;
+        a.soma_src = net->soma_src;
+        a.n_pt = li.points ? net->n_src : 0;
         a.ctl = net->ctl;
         a.smem_comps = smem_comps;
         a.smem_segs = smem_segs;
@@ -630,7 +669,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     d.ring_nrn = net->ring_nrn;
     d.ring_cnt = net->ring_cnt;
     d.R = net->R;
-    d.N = net->N;
+    d.N = std::max(net->n_src, 1);
     d.out_off = dout_off;
     d.out_site = dout_site;
     d.out_w = dout_w;
@@ -846,7 +885,8 @@ mm_status mm_read_soma_voltages(mm_net *net, double *out, int64_t cap)
     return check_device(net);
 }
 
-mm_status mm_read_spikes(mm_net *net, int32_t *neuron, double *t_ms, int64_t cap, int64_t *n_out)
+mm_status mm_read_spike_points(mm_net *net, int32_t *neuron, int32_t *comp, double *t_ms, int64_t cap,
+                               int64_t *n_out)
 {
     mm_status st = guard(net);
     if (st != MM_OK) return st;
@@ -855,21 +895,24 @@ mm_status mm_read_spikes(mm_net *net, int32_t *neuron, double *t_ms, int64_t cap
     mmk::DevCtl c;
     MM_CK(net, cudaMemcpy(&c, net->ctl, sizeof(c), cudaMemcpyDeviceToHost));
     const int64_t held = std::min<int64_t>((int64_t)c.spk_count, net->spk_cap);
-    std::vector<int32_t> nr((size_t)held);
+    std::vector<int32_t> nr((size_t)held), cp((size_t)held);
     std::vector<double> tt((size_t)held);
     if (held) {
         MM_CK(net, cudaMemcpy(nr.data(), net->spk_nrn, (size_t)held * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        MM_CK(net, cudaMemcpy(cp.data(), net->spk_comp, (size_t)held * sizeof(int32_t), cudaMemcpyDeviceToHost));
         MM_CK(net, cudaMemcpy(tt.data(), net->spk_t, (size_t)held * sizeof(double), cudaMemcpyDeviceToHost));
     }
     std::vector<int64_t> idx((size_t)held);
     for (int64_t i = 0; i < held; ++i) idx[(size_t)i] = i;
     std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
         if (tt[(size_t)a] != tt[(size_t)b]) return tt[(size_t)a] < tt[(size_t)b];
-        return nr[(size_t)a] < nr[(size_t)b];
+        if (nr[(size_t)a] != nr[(size_t)b]) return nr[(size_t)a] < nr[(size_t)b];
+        return cp[(size_t)a] < cp[(size_t)b];
     });
     const int64_t w = std::min<int64_t>(held, cap);
     for (int64_t i = 0; i < w; ++i) {
         neuron[i] = nr[(size_t)idx[(size_t)i]];
+        if (comp) comp[i] = cp[(size_t)idx[(size_t)i]];
         t_ms[i] = tt[(size_t)idx[(size_t)i]];
     }
     *n_out = held;
@@ -882,6 +925,11 @@ mm_status mm_read_spikes(mm_net *net, int32_t *neuron, double *t_ms, int64_t cap
     if (overflow) return fail(net, MM_EOVERFLOW, "spike buffer overflowed; raise mm_options.spike_capacity or read more often");
     if (w < held) return fail(net, MM_EOVERFLOW, "caller's spike arrays are smaller than the spike count");
     return MM_OK;
+}
+
+mm_status mm_read_spikes(mm_net *net, int32_t *neuron, double *t_ms, int64_t cap, int64_t *n_out)
+{
+    return mm_read_spike_points(net, neuron, nullptr, t_ms, cap, n_out);
 }
 
 mm_status mm_set_stimulus(mm_net *net, const double *stim_nA, int64_t n)
@@ -913,7 +961,7 @@ namespace {
 struct CkptHeader {
     char magic[8];
     int64_t C, nsite, N, R, spk_cap, steps_done;
-    int32_t precision, pad;
+    int32_t precision, n_src;
 };
 
 std::vector<std::pair<void *, size_t>> ckpt_regions(mm_net *net)
@@ -936,9 +984,10 @@ std::vector<std::pair<void *, size_t>> ckpt_regions(mm_net *net)
     }
     r.push_back({net->stim, N * sizeof(double)});
     r.push_back({net->ring_cnt, (size_t)net->R * sizeof(int32_t)});
-    r.push_back({net->ring_nrn, (size_t)net->R * N * sizeof(int32_t)});
+    r.push_back({net->ring_nrn, (size_t)net->R * (size_t)std::max(net->n_src, 1) * sizeof(int32_t)});
     r.push_back({net->ctl, sizeof(mmk::DevCtl)});
     r.push_back({net->spk_nrn, (size_t)net->spk_cap * sizeof(int32_t)});
+    r.push_back({net->spk_comp, (size_t)net->spk_cap * sizeof(int32_t)});
     r.push_back({net->spk_t, (size_t)net->spk_cap * sizeof(double)});
     return r;
 }
@@ -963,7 +1012,7 @@ mm_status mm_save_state(mm_net *net, void *buf, size_t cap, size_t *len)
     if ((st = check_device(net)) != MM_OK) return st;
     char *p = (char *)buf;
     CkptHeader h{};
-    std::memcpy(h.magic, "MMCKPT02", 8);
+    std::memcpy(h.magic, "MMCKPT03", 8);
     h.C = net->C;
     h.nsite = net->nsite;
     h.N = net->N;
@@ -971,6 +1020,7 @@ mm_status mm_save_state(mm_net *net, void *buf, size_t cap, size_t *len)
     h.spk_cap = net->spk_cap;
     h.steps_done = net->steps_done;
     h.precision = net->precision;
+    h.n_src = net->n_src;
     std::memcpy(p, &h, sizeof(h));
     p += sizeof(h);
     for (auto &r : ckpt_regions(net)) {
@@ -988,8 +1038,8 @@ mm_status mm_load_state(mm_net *net, const void *buf, size_t len)
     const char *p = (const char *)buf;
     CkptHeader h;
     std::memcpy(&h, p, sizeof(h));
-    if (std::memcmp(h.magic, "MMCKPT02", 8) != 0 || h.C != net->C || h.nsite != net->nsite || h.N != net->N ||
-        h.R != net->R || h.spk_cap != net->spk_cap || h.precision != net->precision)
+    if (std::memcmp(h.magic, "MMCKPT03", 8) != 0 || h.C != net->C || h.nsite != net->nsite || h.N != net->N ||
+        h.R != net->R || h.spk_cap != net->spk_cap || h.precision != net->precision || h.n_src != net->n_src)
         return fail(net, MM_EINVAL, "checkpoint was saved from a different network");
     p += sizeof(h);
     MM_CK(net, cudaStreamSynchronize(net->stream));

@@ -161,12 +161,22 @@ struct StepArgs {
     int32_t smem_meta;                // bytes reserved for the largest blob
     const int32_t *site_comp;         // group-local compartment of each synaptic site
     double *gsyn;                     // merged synaptic conductance per site, uS
-    int32_t *ring_nrn;                // [R * N] internal ids of neurons that spiked, per step slot
+    int32_t *ring_nrn;                // [R * N] spike sources that fired, per step slot
     int32_t *ring_cnt;                // [R]
-    int32_t R, N;
+    int32_t R, N;                     // ring depth (steps) and slot capacity (spike sources)
     int32_t *spk_nrn;                 // output spikes (user ids) [spk_cap]
+    int32_t *spk_comp;                // output spikes: LOCAL compartment of the crossing
     double *spk_t;
     long long spk_cap;
+    // detection at synapse points (MM_DETECT_SYNAPSE_POINTS; all null under
+    // soma detection, where a neuron's source id is its internal id)
+    const uint32_t *pmask;            // bit c: compartment c is a detection point other than a soma
+    const int64_t *pt_comp;           // internal compartment of each point, ascending [n_pt]
+    const int32_t *pt_user_nrn;       // user neuron and LOCAL compartment of each point
+    const int32_t *pt_user_comp;
+    const int32_t *soma_src;          // source id of each internal neuron's soma point, -1: none
+    int32_t n_pt;
+    int32_t pad_pt;
     DevCtl *ctl;
     int32_t smem_comps, smem_segs;    // shared-memory capacity of one block (FP64)
     double gNa, gK, gL, ENa, EK, EL;
@@ -186,6 +196,7 @@ struct StepArgs {
 constexpr float kVScale = 8388608.0f;          // 2^23 per mV
 constexpr float kVInv = 1.0f / 8388608.0f;
 constexpr double kVScaleD = 8388608.0;
+constexpr double kVInvD = 1.0 / 8388608.0;
 constexpr float kGScale = 4294967296.0f;       // 2^32
 constexpr float kGInv = 1.0f / 4294967296.0f;
 constexpr double kGScaleD = 4294967296.0;
@@ -226,8 +237,16 @@ struct StepArgs32 {
     int32_t *ring_cnt;
     int32_t R, N;
     int32_t *spk_nrn;
+    int32_t *spk_comp;
     double *spk_t;
     long long spk_cap;
+    const uint32_t *pmask;            // detection points, as in StepArgs
+    const int64_t *pt_comp;
+    const int32_t *pt_user_nrn;
+    const int32_t *pt_user_comp;
+    const int32_t *soma_src;
+    int32_t n_pt;
+    int32_t pad_pt;
     DevCtl *ctl;
     int32_t smem_comps, smem_segs;
     float gNa, gK, gL;
@@ -239,6 +258,60 @@ struct StepArgs32 {
     float gimp;                       // implicit share of each axial coupling: 1 or 1/2 (as in StepArgs)
     int32_t g_implicit;               // membrane conductance in the diagonal (backward Euler)
 };
+
+
+#ifdef __CUDACC__
+// One threshold crossing of spike source src (user neuron, LOCAL compartment)
+// at time ts within step n: the output record, and the source's entry in the
+// ring slot of step n (delivered by the delivery kernel of the next step).
+template <class A>
+__device__ __forceinline__ void record_spike(const A &a, int src, int user_nrn, int user_comp, double ts,
+                                             long long n)
+{
+    const unsigned long long k = atomicAdd(&a.ctl->spk_count, 1ull);
+    if ((long long)k < a.spk_cap) {
+        a.spk_nrn[k] = user_nrn;
+        a.spk_comp[k] = user_comp;
+        a.spk_t[k] = ts;
+    } else {
+        atomicOr(&a.ctl->err, MMK_ERR_OVERFLOW);
+    }
+    const int slot = (int)(n % a.R);
+    const int pos = atomicAdd(&a.ring_cnt[slot], 1);
+    a.ring_nrn[(long long)slot * a.N + pos] = src;
+}
+
+// Whether internal compartment c is a detection point other than a soma.
+template <class A>
+__device__ __forceinline__ bool is_point(const A &a, int64_t c)
+{
+    return a.pmask && ((a.pmask[c >> 5] >> (c & 31)) & 1u);
+}
+
+// Threshold test of the point at internal compartment c between V^n = v0
+// and V^{n+1} = v1 (upward crossing, linearly interpolated time); the
+// point's id is found by bisection of the ascending point table.
+template <class A>
+__device__ __forceinline__ void point_test(const A &a, int64_t c, double v0, double v1, long long n, double dt)
+{
+    if (!(v0 < a.threshold && v1 >= a.threshold)) return;
+    int lo = 0, hi = a.n_pt - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a.pt_comp[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    const double ts = (double)n * dt + dt * (a.threshold - v0) / (v1 - v0);
+    record_spike(a, lo, a.pt_user_nrn[lo], a.pt_user_comp[lo], ts, n);
+}
+
+// Spike source of the soma of internal neuron nrn (-1: not tested).
+template <class A>
+__device__ __forceinline__ int soma_source(const A &a, int nrn)
+{
+    return a.soma_src ? a.soma_src[nrn] : nrn;
+}
+#endif
 
 struct DeliverArgs {
     const int32_t *ring_nrn;

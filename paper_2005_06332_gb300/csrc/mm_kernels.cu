@@ -287,17 +287,10 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
                     const int nrn = G.neuron0 + S.neuron;
                     if (!isfinite(v1)) atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
                     if (v0 < a.threshold && v1 >= a.threshold) {
-                        const double ts = (double)n * a.dt + a.dt * (a.threshold - v0) / (v1 - v0);
-                        const unsigned long long k = atomicAdd(&a.ctl->spk_count, 1ull);
-                        if ((long long)k < a.spk_cap) {
-                            a.spk_nrn[k] = a.user_id[nrn];
-                            a.spk_t[k] = ts;
-                        } else {
-                            atomicOr(&a.ctl->err, MMK_ERR_OVERFLOW);
-                        }
-                        const int slot = (int)(n % a.R);
-                        const int pos = atomicAdd(&a.ring_cnt[slot], 1);
-                        a.ring_nrn[(long long)slot * a.N + pos] = nrn;
+                        const int src = soma_source(a, nrn);
+                        if (src >= 0)
+                            record_spike(a, src, a.user_id[nrn], 0,
+                                         (double)n * a.dt + a.dt * (a.threshold - v0) / (v1 - v0), n);
                     }
                 }
                 for (int j = t + 1; j < t + S.len; ++j) {
@@ -308,10 +301,12 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
             __syncthreads();
         }
 
-        // C. V^{n+1} = V^n + dV, then exponential-Euler gates at V^{n+1}.
+        // C. V^{n+1} = V^n + dV, the threshold test of the detection points
+        //    other than somata, then exponential-Euler gates at V^{n+1}.
         for (int i = tid; i < G.ncomp; i += NT) {
-            const double v = V[i] + sr[i];
+            const double v0 = V[i], v = v0 + sr[i];
             a.V[c0 + i] = v;
+            if (is_point(a, c0 + i)) point_test(a, c0 + i, v0, v, n, a.dt);
             const Rates r = hh_rates(v);
             a.m[c0 + i] = relax(a.m[c0 + i], r.am, r.bm, a.dt);
             a.h[c0 + i] = relax(a.h[c0 + i], r.ah, r.bh, a.dt);

@@ -479,17 +479,10 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                 a.Vsoma[nrn] = v1;
                 if (!isfinite(v1)) atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
                 if (v0 < a.threshold && v1 >= a.threshold) {
-                    const double ts = (double)n * a.dt64 + a.dt64 * (a.threshold - v0) / (v1 - v0);
-                    const unsigned long long k = atomicAdd(&a.ctl->spk_count, 1ull);
-                    if ((long long)k < a.spk_cap) {
-                        a.spk_nrn[k] = a.user_id[nrn];
-                        a.spk_t[k] = ts;
-                    } else {
-                        atomicOr(&a.ctl->err, MMK_ERR_OVERFLOW);
-                    }
-                    const int slot = (int)(n % a.R);
-                    const int pos = atomicAdd(&a.ring_cnt[slot], 1);
-                    a.ring_nrn[(long long)slot * a.N + pos] = nrn;
+                    const int src = soma_source(a, nrn);
+                    if (src >= 0)
+                        record_spike(a, src, a.user_id[nrn], 0,
+                                     (double)n * a.dt64 + a.dt64 * (a.threshold - v0) / (v1 - v0), n);
                 }
             }
             const float xh = x;
@@ -542,7 +535,8 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         if (!a.item_ns) gate_chunks(a, s_pc0, s_pn, &s_gchunk, tid & 31);
         __syncthreads();
 
-        // C. V^{n+1} = V^n + dV (exact in fixed point)
+        // C. V^{n+1} = V^n + dV (exact in fixed point), and the threshold
+        //    test of the detection points other than somata
         for (int i = tid; i < G.ncomp; i += NS) {
             const int32_t vold = Vq[i];
             int32_t vq;
@@ -551,6 +545,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                 vq = vold;
             }
             a.Vq[c0 + i] = vq;
+            if (is_point(a, c0 + i)) point_test(a, c0 + i, (double)vold * kVInvD, (double)vq * kVInvD, n, a.dt64);
         }
         if (a.item_ns) {  // uniform across the block
             __syncthreads();
@@ -737,17 +732,10 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
                 a.Vsoma[nrn] = v1;
                 if (!isfinite(v1)) atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
                 if (v0 < a.threshold && v1 >= a.threshold) {
-                    const double ts = (double)n * a.dt64 + a.dt64 * (a.threshold - v0) / (v1 - v0);
-                    const unsigned long long k = atomicAdd(&a.ctl->spk_count, 1ull);
-                    if ((long long)k < a.spk_cap) {
-                        a.spk_nrn[k] = a.user_id[nrn];
-                        a.spk_t[k] = ts;
-                    } else {
-                        atomicOr(&a.ctl->err, MMK_ERR_OVERFLOW);
-                    }
-                    const int slot = (int)(n % a.R);
-                    const int pos = atomicAdd(&a.ring_cnt[slot], 1);
-                    a.ring_nrn[(long long)slot * a.N + pos] = nrn;
+                    const int src = soma_source(a, nrn);
+                    if (src >= 0)
+                        record_spike(a, src, a.user_id[nrn], 0,
+                                     (double)n * a.dt64 + a.dt64 * (a.threshold - v0) / (v1 - v0), n);
                 }
             }
             const float xh = x;
@@ -876,6 +864,7 @@ __global__ void __launch_bounds__(256) giant_assemble_kernel(StepArgs32 a)
 // V^{n+1} of every giant compartment.
 __global__ void __launch_bounds__(256) giant_update_kernel(StepArgs32 a)
 {
+    const long long n = (long long)a.ctl->step_base + a.step_offset;
     const int64_t nch = a.gchunk0[a.item1 - a.item0];
     for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
         const int k = giant_of_chunk(a, ch);
@@ -891,6 +880,7 @@ __global__ void __launch_bounds__(256) giant_update_kernel(StepArgs32 a)
                 vq = vold;
             }
             a.Vq[c0 + i] = vq;
+            if (is_point(a, c0 + i)) point_test(a, c0 + i, (double)vold * kVInvD, (double)vq * kVInvD, n, a.dt64);
             gate_update(a, c0 + i);
         }
     }

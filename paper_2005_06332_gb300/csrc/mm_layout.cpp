@@ -332,6 +332,11 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         if (a < 0 || a >= N || b < 0 || b >= N) { e << "synapse " << s << ": neuron id out of range"; return msg(e); }
         const int64_t nb = in.comp_offset[b + 1] - in.comp_offset[b];
         if (in.dcomp[s] < 0 || in.dcomp[s] >= nb) { e << "synapse " << s << ": dst_comp out of range"; return msg(e); }
+        if (in.points && in.scomp &&
+            (in.scomp[s] < 0 || in.scomp[s] >= in.comp_offset[a + 1] - in.comp_offset[a])) {
+            e << "synapse " << s << ": src_comp out of range";
+            return msg(e);
+        }
         if (!(in.w[s] >= 0.0) || !std::isfinite(in.w[s])) { e << "synapse " << s << ": weight must be finite and >= 0"; return msg(e); }
         const double q = in.delay_ms[s] / in.dt;
         if (!std::isfinite(q)) { e << "synapse " << s << ": delay must be finite"; return msg(e); }
@@ -732,16 +737,48 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         for (int64_t d = 1; d <= max_ds; ++d) if (seen[(size_t)d]) L.dclass.push_back((int32_t)d);
         L.R = (int32_t)(max_ds + 2);
     }
-    L.out_off.assign((size_t)N + 1, 0);
-    for (int64_t s = 0; s < in.S; ++s) L.out_off[(size_t)L.internal_of[(size_t)in.src[s]] + 1]++;
-    for (int32_t k = 0; k < N; ++k) L.out_off[(size_t)k + 1] += L.out_off[(size_t)k];
+    // 4c. spike sources: the internal neurons, or the detection points in
+    //     internal compartment order
+    std::vector<int32_t> src_id((size_t)in.S);
+    if (!in.points) {
+        L.n_src = N;
+        for (int64_t s = 0; s < in.S; ++s) src_id[(size_t)s] = L.internal_of[(size_t)in.src[s]];
+    } else {
+        std::vector<int64_t> ic((size_t)in.S);
+        for (int64_t s = 0; s < in.S; ++s)
+            ic[(size_t)s] = L.user2int[(size_t)(in.comp_offset[in.src[s]] + (in.scomp ? in.scomp[s] : 0))];
+        L.pt_comp = ic;
+        std::sort(L.pt_comp.begin(), L.pt_comp.end());
+        L.pt_comp.erase(std::unique(L.pt_comp.begin(), L.pt_comp.end()), L.pt_comp.end());
+        if (L.pt_comp.size() > (size_t)INT32_MAX / 2) { *invalid = false; e << "too many detection points"; return msg(e); }
+        L.n_src = (int32_t)L.pt_comp.size();
+        L.pt_user_nrn.assign(L.pt_comp.size(), 0);
+        L.pt_user_comp.assign(L.pt_comp.size(), 0);
+        L.soma_src.assign((size_t)N, -1);
+        L.pmask.assign((size_t)((C + 31) / 32), 0u);
+        for (int64_t s = 0; s < in.S; ++s) {
+            const int64_t c = ic[(size_t)s];
+            const int32_t id = (int32_t)(std::lower_bound(L.pt_comp.begin(), L.pt_comp.end(), c) - L.pt_comp.begin());
+            src_id[(size_t)s] = id;
+            const int32_t uc = in.scomp ? in.scomp[s] : 0;
+            L.pt_user_nrn[(size_t)id] = in.src[s];
+            L.pt_user_comp[(size_t)id] = uc;
+            if (uc == 0)
+                L.soma_src[(size_t)L.internal_of[(size_t)in.src[s]]] = id;
+            else
+                L.pmask[(size_t)(c >> 5)] |= 1u << (c & 31);
+        }
+    }
+    L.out_off.assign((size_t)L.n_src + 1, 0);
+    for (int64_t s = 0; s < in.S; ++s) L.out_off[(size_t)src_id[(size_t)s] + 1]++;
+    for (int32_t k = 0; k < L.n_src; ++k) L.out_off[(size_t)k + 1] += L.out_off[(size_t)k];
     std::vector<int64_t> order_s((size_t)in.S);
     {
         std::vector<int64_t> fill(L.out_off.begin(), L.out_off.end() - 1);
-        for (int64_t s = 0; s < in.S; ++s) order_s[(size_t)fill[(size_t)L.internal_of[(size_t)in.src[s]]]++] = s;
+        for (int64_t s = 0; s < in.S; ++s) order_s[(size_t)fill[(size_t)src_id[(size_t)s]]++] = s;
     }
     if (L.dclass.size() > 1) {
-        for (int32_t k = 0; k < N; ++k)
+        for (int32_t k = 0; k < L.n_src; ++k)
             std::stable_sort(order_s.begin() + L.out_off[(size_t)k], order_s.begin() + L.out_off[(size_t)k + 1],
                              [&](int64_t a, int64_t b) { return dsteps[(size_t)a] < dsteps[(size_t)b]; });
     }

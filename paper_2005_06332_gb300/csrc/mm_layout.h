@@ -17,6 +17,10 @@ struct LayoutInput {
     int64_t S;
     const int32_t *src, *dst, *dcomp;
     const double *w, *delay_ms;
+    // threshold tests at the synapse points (distinct (src, scomp) pairs;
+    // scomp NULL: every synapse leaves from the soma) instead of the somata
+    bool points;
+    const int32_t *scomp;
     const double *stim;           // may be NULL
     const float *cost;            // may be NULL (size order)
     double dt;
@@ -61,7 +65,14 @@ struct Layout {
     int64_t giant_paths = 0;            // paths in giant items (size of the per-path scratch)
     std::vector<int32_t> site_comp;     // group-local compartment of each site
     std::vector<int64_t> site_internal; // internal compartment of each site
-    std::vector<int64_t> out_off;       // outgoing synapses per internal source [N+1]
+    // spike sources: internal neurons (soma detection) or detection points
+    int32_t n_src = 0;
+    std::vector<int64_t> pt_comp;       // points: internal compartment of each, ascending
+    std::vector<int32_t> pt_user_nrn;   // points: user neuron and LOCAL user compartment
+    std::vector<int32_t> pt_user_comp;
+    std::vector<int32_t> soma_src;      // points: source id of each internal neuron's soma point, -1 if none
+    std::vector<uint32_t> pmask;        // points: bit c set where compartment c is a point other than a soma
+    std::vector<int64_t> out_off;       // outgoing synapses per source [n_src+1]
     std::vector<int32_t> out_site, out_dsteps;
     std::vector<double> out_w;
     std::vector<int32_t> dclass;        // distinct delays in steps, ascending

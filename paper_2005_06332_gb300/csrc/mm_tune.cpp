@@ -24,7 +24,7 @@ struct Sample {
     std::vector<int32_t> parent;
     std::vector<double> L, d, stim;
     std::vector<float> cost;
-    std::vector<int32_t> src, dst, dcomp;
+    std::vector<int32_t> src, dst, dcomp, scomp;
     std::vector<double> w, delay;
 };
 
@@ -65,6 +65,7 @@ void make_sample(const mm_morphologies *m, const mm_synapses *syn, const double 
             s.src.push_back(newid[(size_t)a]);
             s.dst.push_back(newid[(size_t)b]);
             s.dcomp.push_back(syn->dst_comp[q]);
+            if (syn->src_comp) s.scomp.push_back(syn->src_comp[q]);
             s.w.push_back(syn->weight_uS[q]);
             s.delay.push_back(syn->delay_ms[q]);
         }
@@ -105,6 +106,7 @@ extern "C" mm_status mm_autotune(const mm_morphologies *morph, const mm_channel_
         ss.src_neuron = s.src.data();
         ss.dst_neuron = s.dst.data();
         ss.dst_comp = s.dcomp.data();
+        ss.src_comp = syn->src_comp ? s.scomp.data() : nullptr;
         ss.weight_uS = s.w.data();
         ss.delay_ms = s.delay.data();
     }

@@ -20,7 +20,8 @@ MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ETIMEOUT, MM_ENUMERIC, MM_EOVERFLOW, M
 MM_FP64, MM_FP32C = 0, 1
 MM_SCHED_SIZE_SORTED, MM_SCHED_COST = 0, 1
 STATE = {"V": 0, "m": 1, "h": 2, "n": 3, "gsyn": 4}
-SCHEMES = {"be": 0, "cn": 1}  # MM_SCHEME_BE, MM_SCHEME_CN
+SCHEMES = {"be": 0, "cn": 1}
+DETECT = {"soma": 0, "points": 1}  # MM_SCHEME_BE, MM_SCHEME_CN
 PRECISION = {"fp64": MM_FP64, "fp32c": MM_FP32C}
 
 
@@ -42,7 +43,8 @@ class ChannelParams(C.Structure):
 class Synapses(C.Structure):
     _fields_ = [("n", C.c_int64), ("src_neuron", C.POINTER(C.c_int32)), ("dst_neuron", C.POINTER(C.c_int32)),
                 ("dst_comp", C.POINTER(C.c_int32)), ("weight_uS", C.POINTER(C.c_double)),
-                ("delay_ms", C.POINTER(C.c_double)), ("tau_ms", C.c_double), ("e_rev_mV", C.c_double)]
+                ("delay_ms", C.POINTER(C.c_double)), ("tau_ms", C.c_double), ("e_rev_mV", C.c_double),
+                ("src_comp", C.POINTER(C.c_int32))]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -56,7 +58,8 @@ class Allocator(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("schedule", C.c_int32), ("graph_steps", C.c_int32),
                 ("block_threads", C.c_int32), ("group_comps", C.c_int32), ("device", C.c_int32),
-                ("time_items", C.c_int32), ("scheme", C.c_int32), ("dt_ms", C.c_double), ("spike_capacity", C.c_int64), ("cuda_stream", C.c_void_p),
+                ("time_items", C.c_int32), ("scheme", C.c_int32), ("detect", C.c_int32), ("reserved0", C.c_int32),
+                ("dt_ms", C.c_double), ("spike_capacity", C.c_int64), ("cuda_stream", C.c_void_p),
                 ("cost", C.POINTER(C.c_float)), ("allocator", Allocator)]
 
 
@@ -107,6 +110,8 @@ def load(build_if_missing: bool = False):
         L.mm_read_state.argtypes = [net_p, C.c_int32, P(C.c_double), C.c_int64]
         L.mm_read_soma_voltages.argtypes = [net_p, P(C.c_double), C.c_int64]
         L.mm_read_spikes.argtypes = [net_p, P(C.c_int32), P(C.c_double), C.c_int64, P(C.c_int64)]
+        L.mm_read_spike_points.argtypes = [net_p, P(C.c_int32), P(C.c_int32), P(C.c_double), C.c_int64,
+                                           P(C.c_int64)]
         L.mm_set_stimulus.argtypes = [net_p, P(C.c_double), C.c_int64]
         L.mm_get_step.argtypes = [net_p, P(C.c_int64)]
         L.mm_save_state.argtypes = [net_p, C.c_void_p, C.c_size_t, P(C.c_size_t)]
@@ -146,8 +151,9 @@ def load(build_if_missing: bool = False):
         L.mm_destroy.argtypes = [net_p]
         L.mm_destroy.restype = None
         for name in ("mm_create_network", "mm_step", "mm_synchronize", "mm_read_voltages", "mm_read_state",
-                     "mm_read_soma_voltages", "mm_read_spikes", "mm_set_stimulus", "mm_get_step", "mm_save_state",
-                     "mm_load_state", "mm_set_kernel_timing", "mm_read_kernel_timing", "mm_get_launch_info"):
+                     "mm_read_soma_voltages", "mm_read_spikes", "mm_read_spike_points", "mm_set_stimulus", "mm_get_step",
+                     "mm_save_state", "mm_load_state", "mm_set_kernel_timing", "mm_read_kernel_timing",
+                     "mm_get_launch_info"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -306,13 +312,16 @@ def _marshal(net):
         comp=np.ascontiguousarray(net.syn_comp, np.int32), w=np.ascontiguousarray(net.syn_w, np.float64),
         dl=np.ascontiguousarray(net.syn_delay_ms, np.float64),
         stim=np.ascontiguousarray(net.stim_nA, np.float64))
+    sc = getattr(net, "syn_src_comp", None)
+    a["scomp"] = None if sc is None else np.ascontiguousarray(sc, np.int32)
     morph = Morphologies(net.n_neurons, _ptr(a["off"], C.c_int64), _ptr(a["parent"], C.c_int32),
                          _ptr(a["L"], C.c_double), _ptr(a["D"], C.c_double))
     p = net.params
     chan = ChannelParams(p["gNa"], p["gK"], p["gL"], p["ENa"], p["EK"], p["EL"], p["Cm"], p["Ra"], p["v_init"],
                          p["threshold"])
     syn = Synapses(len(a["src"]), _ptr(a["src"], C.c_int32), _ptr(a["dst"], C.c_int32), _ptr(a["comp"], C.c_int32),
-                   _ptr(a["w"], C.c_double), _ptr(a["dl"], C.c_double), p["tau_syn"], p["e_syn"])
+                   _ptr(a["w"], C.c_double), _ptr(a["dl"], C.c_double), p["tau_syn"], p["e_syn"],
+                   _ptr(a["scomp"], C.c_int32) if a["scomp"] is not None else None)
     return a, morph, chan, syn
 
 
@@ -361,7 +370,8 @@ class Network:
 
     def __init__(self, net, precision: str = "fp64", cost: Optional[np.ndarray] = None, graph_steps: int = 40,
                  block_threads: int = 0, group_comps: int = 0, spike_capacity: int = 0, device: int = 0,
-                 stream=None, torch_alloc: bool = True, time_items: bool = False, scheme: str = "be"):
+                 stream=None, torch_alloc: bool = True, time_items: bool = False, scheme: str = "be",
+                 detect: str = "soma"):
         L = load()
         self._L = L
         self._h = C.c_void_p()
@@ -382,6 +392,16 @@ class Network:
         opt.spike_capacity = spike_capacity
         opt.time_items = 1 if time_items else 0
         opt.scheme = SCHEMES[scheme]
+        opt.detect = DETECT[detect]
+        # the library's automatic spike-buffer size (mm_options.spike_capacity)
+        if spike_capacity > 0:
+            self._spk_cap = int(spike_capacity)
+        elif detect == "points":
+            sc = a["scomp"] if a["scomp"] is not None else np.zeros(len(a["src"]), np.int32)
+            n_pt = len(np.unique(a["src"].astype(np.int64) * (1 << 32) + sc))
+            self._spk_cap = max(1 << 16, n_pt * 16)
+        else:
+            self._spk_cap = max(1 << 16, self.n_neurons * 64)
         self._cost = None
         if cost is not None:
             self._cost = np.ascontiguousarray(cost, np.float32)
@@ -448,10 +468,24 @@ class Network:
         self._check(self._L.mm_read_soma_voltages(self._h, _ptr(out, C.c_double), out.size), "mm_read_soma_voltages")
         return out
 
+    def read_spike_points(self, cap: Optional[int] = None):
+        """(neuron, LOCAL compartment, t_ms) drained since the last call,
+        ordered by (t, neuron, compartment)."""
+        if cap is None:
+            cap = self._spk_cap
+        nr = np.empty(cap, np.int32)
+        cp = np.empty(cap, np.int32)
+        tt = np.empty(cap, np.float64)
+        n = C.c_int64()
+        st = self._L.mm_read_spike_points(self._h, _ptr(nr, C.c_int32), _ptr(cp, C.c_int32), _ptr(tt, C.c_double),
+                                          cap, C.byref(n))
+        self._check(st, "mm_read_spike_points")
+        return nr[:n.value].copy(), cp[:n.value].copy(), tt[:n.value].copy()
+
     def read_spikes(self, cap: Optional[int] = None, allow_overflow: bool = False):
         """(neuron, t_ms) drained since the last call, ordered by (t, neuron)."""
         if cap is None:
-            cap = max(1 << 16, self.n_neurons * 64)
+            cap = self._spk_cap
         nr = np.empty(cap, np.int32)
         tt = np.empty(cap, np.float64)
         n = C.c_int64()
