@@ -122,7 +122,7 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_baseline(net, seconds_hint: float = 15.0):
+def cpu_baseline(net, seconds_hint: float = 15.0, detect: str = "soma"):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload."""
     import oracle
     rng = np.random.default_rng(0)
@@ -131,11 +131,11 @@ def cpu_baseline(net, seconds_hint: float = 15.0):
     sub = net.subset(pick, keep_synapses=True)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.simulate(sub, 4, threads=cores)
+    oracle.simulate(sub, 4, threads=cores, detect=detect)
     probe = max(1e-3, time.perf_counter() - t0)
     steps = int(max(8, min(400, 4 * seconds_hint / probe)))
     t0 = time.perf_counter()
-    oracle.simulate(sub, steps, threads=cores)
+    oracle.simulate(sub, steps, threads=cores, detect=detect)
     el = time.perf_counter() - t0
     return {"value": sub.n_comp * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{k} of {net.n_neurons} neurons ({sub.n_comp} compartments, synapses among them), "
@@ -152,9 +152,9 @@ def run_reference(args, net):
     pick = np.sort(rng.choice(net.n_neurons, k, replace=False))
     sub = net.subset(pick, keep_synapses=True)
     cores = os.cpu_count() or 1
-    oracle.simulate(sub, max(1, args.warmup), threads=cores)
+    oracle.simulate(sub, max(1, args.warmup), threads=cores, detect=args.detect)
     t0 = time.perf_counter()
-    oracle.simulate(sub, args.steps, threads=cores)
+    oracle.simulate(sub, args.steps, threads=cores, detect=args.detect)
     el = time.perf_counter() - t0
     v = sub.n_comp * args.steps / el
     sample = (f"{k} of {net.n_neurons} neurons ({sub.n_comp} compartments, synapses among them), "
@@ -239,6 +239,9 @@ def main():
     ap.add_argument("--group-comps", type=int, default=0)
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the launch-configuration autotuner (default: tune on a 2M-compartment sample)")
+    ap.add_argument("--detect", default="soma", choices=["soma", "points"],
+                    help="threshold test at every soma, or at the points synapses leave from (each synapse "
+                         "leaving a compartment drawn uniformly over its source neuron)")
     ap.add_argument("--paper-replay", action="store_true",
                     help="the paper's load-balance tests instead: one morphology vs a group of 20 sizes vs "
                          "F-distributed sizes (same mean size), size-sorted vs random work-queue order")
@@ -248,7 +251,7 @@ def main():
         run_paper_replay(args)
         return
 
-    net = netgen.make_config(args.config)
+    net = netgen.make_config(args.config, src_points=args.detect == "points")
     precision = args.precision or "fp32c"
     if args.impl == "reference":
         run_reference(args, net)
@@ -271,11 +274,12 @@ def main():
         # (a small sample gives each block too few items to show the load
         # balance of the full run), else on a stratified 16 M sample
         tune = mm.autotune(net, precision=precision, sample_comps=min(int(net.n_comp), 16_000_000), warmup=3,
-                           steps=20, device=local, stream=stream.cuda_stream, graph_steps=args.graph_steps)
+                           steps=20, device=local, stream=stream.cuda_stream, graph_steps=args.graph_steps,
+                           detect=args.detect)
         tune["seconds"] = time.perf_counter() - t0
         args.block_threads, args.group_comps = tune["block_threads"], tune["group_comps"]
     g = mm.Network(net, precision=precision, graph_steps=args.graph_steps, device=local, stream=stream.cuda_stream,
-                   block_threads=args.block_threads, group_comps=args.group_comps)
+                   block_threads=args.block_threads, group_comps=args.group_comps, detect=args.detect)
 
     launch = g.launch_info()
     # warm-up (also captures the CUDA graph)
@@ -372,6 +376,7 @@ def main():
            "config": {"workload": net.name, "precision": precision, "n_neurons": net.n_neurons,
                       "block_threads": args.block_threads, "group_comps": args.group_comps,
                       "n_comp": net.n_comp, "n_syn": net.n_syn, "dt_ms": net.dt, "graph_steps": G,
+                      "spike_detection": args.detect,
                       "l2": f"inputs larger than L2 (state + constants {((48 if precision == 'fp64' else 24) * net.n_comp) / 1e6:.0f} MB)",
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
@@ -424,7 +429,7 @@ def main():
         out["plain_fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": k64}
         out["speedup_vs_plain_fp64"] = value / v64
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(net)
+        out["cpu_baseline"] = cpu_baseline(net, detect=args.detect)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:

@@ -80,8 +80,7 @@ struct mm_net {
     int32_t *spk_nrn = nullptr, *ring_nrn = nullptr, *ring_cnt = nullptr, *user_id = nullptr;
     int32_t *spk_comp = nullptr;
     // detection points (MM_DETECT_SYNAPSE_POINTS)
-    uint32_t *pmask = nullptr;
-    int64_t *pt_comp = nullptr;
+    int32_t *pt_of = nullptr;
     int32_t *pt_user_nrn = nullptr, *pt_user_comp = nullptr, *soma_src = nullptr;
     int64_t *user2int = nullptr, *soma_of_user = nullptr, *site_internal = nullptr;
     mmk::DevCtl *ctl = nullptr;
@@ -487,10 +486,9 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     ZR(net->spk_nrn, (size_t)net->spk_cap);
     ZR(net->spk_comp, (size_t)net->spk_cap);
     if (li.points) {
-        UP(net->pmask, L.pmask.data(), L.pmask.size());
+        UP(net->pt_of, L.pt_of.data(), L.pt_of.size());
         UP(net->soma_src, L.soma_src.data(), N);
         if (L.n_src > 0) {
-            UP(net->pt_comp, L.pt_comp.data(), L.pt_comp.size());
             UP(net->pt_user_nrn, L.pt_user_nrn.data(), L.pt_user_nrn.size());
             UP(net->pt_user_comp, L.pt_user_comp.data(), L.pt_user_comp.size());
         }
@@ -573,8 +571,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.spk_comp = net->spk_comp;
         a.spk_t = net->spk_t;
         a.spk_cap = net->spk_cap;
-        a.pmask = net->pmask;
-        a.pt_comp = net->pt_comp;
+        a.pt_of = net->pt_of;
         a.pt_user_nrn = net->pt_user_nrn;
         a.pt_user_comp = net->pt_user_comp;
         a.soma_src = net->soma_src;
@@ -638,8 +635,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.spk_comp = net->spk_comp;
         a.spk_t = net->spk_t;
         a.spk_cap = net->spk_cap;
-        a.pmask = net->pmask;
-        a.pt_comp = net->pt_comp;
+        a.pt_of = net->pt_of;
         a.pt_user_nrn = net->pt_user_nrn;
         a.pt_user_comp = net->pt_user_comp;
         a.soma_src = net->soma_src;
@@ -661,6 +657,10 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.dt_lo = (float)(opt->dt_ms - (double)a.dt);
         a.decay = (float)decay;
         a.threshold = chan->threshold_mV;
+        {
+            const double q = std::ceil(chan->threshold_mV * mmk::kVScaleD);
+            a.thr_q = (int32_t)std::max(-2147483647.0, std::min(2147483647.0, q));
+        }
         a.dt64 = opt->dt_ms;
         a.C = L.C;
     }
@@ -676,6 +676,18 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     d.out_dsteps = dout_ds;
     d.dclass = ddclass;
     d.n_dclass = (int32_t)L.dclass.size();
+    {
+        // lanes per spike in the delivery kernel: the mean number of synapses
+        // of a (source, delay) pair, rounded up to a power of two, <= 32
+        int64_t pairs = 0;
+        for (int32_t k = 0; k < L.n_src; ++k)
+            for (int64_t q = L.out_off[(size_t)k]; q < L.out_off[(size_t)k + 1]; ++q)
+                if (q == L.out_off[(size_t)k] || L.out_dsteps[(size_t)q] != L.out_dsteps[(size_t)q - 1]) ++pairs;
+        const double fan = pairs > 0 ? (double)li.S / (double)pairs : 32.0;
+        int gl = 1;
+        while (gl < 32 && gl < fan) gl *= 2;
+        d.lanes_per_src = gl;
+    }
     d.gsyn = net->gsyn;
     d.ctl = net->ctl;
     d.gsyn32 = net->gsyn32;
@@ -902,18 +914,26 @@ mm_status mm_read_spike_points(mm_net *net, int32_t *neuron, int32_t *comp, doub
         MM_CK(net, cudaMemcpy(cp.data(), net->spk_comp, (size_t)held * sizeof(int32_t), cudaMemcpyDeviceToHost));
         MM_CK(net, cudaMemcpy(tt.data(), net->spk_t, (size_t)held * sizeof(double), cudaMemcpyDeviceToHost));
     }
-    std::vector<int64_t> idx((size_t)held);
-    for (int64_t i = 0; i < held; ++i) idx[(size_t)i] = i;
-    std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
-        if (tt[(size_t)a] != tt[(size_t)b]) return tt[(size_t)a] < tt[(size_t)b];
-        if (nr[(size_t)a] != nr[(size_t)b]) return nr[(size_t)a] < nr[(size_t)b];
-        return cp[(size_t)a] < cp[(size_t)b];
-    });
+    // order by (t, neuron, comp) as two unsigned keys: the bits of t mapped
+    // to an order-preserving integer, then neuron and compartment
+    struct Rec {
+        uint64_t tk, nc;
+        double t;
+    };
+    std::vector<Rec> rec((size_t)held);
+    for (int64_t i = 0; i < held; ++i) {
+        uint64_t b;
+        std::memcpy(&b, &tt[(size_t)i], sizeof(b));
+        b = (b >> 63) ? ~b : (b | (1ull << 63));
+        rec[(size_t)i] = {b, ((uint64_t)(uint32_t)nr[(size_t)i] << 32) | (uint32_t)cp[(size_t)i], tt[(size_t)i]};
+    }
+    std::sort(rec.begin(), rec.end(), [](const Rec &a, const Rec &b) { return a.tk != b.tk ? a.tk < b.tk : a.nc < b.nc; });
     const int64_t w = std::min<int64_t>(held, cap);
     for (int64_t i = 0; i < w; ++i) {
-        neuron[i] = nr[(size_t)idx[(size_t)i]];
-        if (comp) comp[i] = cp[(size_t)idx[(size_t)i]];
-        t_ms[i] = tt[(size_t)idx[(size_t)i]];
+        const Rec &r = rec[(size_t)i];
+        neuron[i] = (int32_t)(r.nc >> 32);
+        if (comp) comp[i] = (int32_t)(uint32_t)r.nc;
+        t_ms[i] = r.t;
     }
     *n_out = held;
     const bool overflow = (c.err & mmk::MMK_ERR_OVERFLOW) != 0 || (int64_t)c.spk_count > net->spk_cap;

@@ -170,8 +170,8 @@ struct StepArgs {
     long long spk_cap;
     // detection at synapse points (MM_DETECT_SYNAPSE_POINTS; all null under
     // soma detection, where a neuron's source id is its internal id)
-    const uint32_t *pmask;            // bit c: compartment c is a detection point other than a soma
-    const int64_t *pt_comp;           // internal compartment of each point, ascending [n_pt]
+    const int32_t *pt_of;             // point id of each compartment [C]; -1 where none and at somata
+                                      // (a soma point is tested by the soma path)
     const int32_t *pt_user_nrn;       // user neuron and LOCAL compartment of each point
     const int32_t *pt_user_comp;
     const int32_t *soma_src;          // source id of each internal neuron's soma point, -1: none
@@ -240,8 +240,7 @@ struct StepArgs32 {
     int32_t *spk_comp;
     double *spk_t;
     long long spk_cap;
-    const uint32_t *pmask;            // detection points, as in StepArgs
-    const int64_t *pt_comp;
+    const int32_t *pt_of;             // detection points, as in StepArgs
     const int32_t *pt_user_nrn;
     const int32_t *pt_user_comp;
     const int32_t *soma_src;
@@ -257,6 +256,8 @@ struct StepArgs32 {
     double threshold, dt64;
     float gimp;                       // implicit share of each axial coupling: 1 or 1/2 (as in StepArgs)
     int32_t g_implicit;               // membrane conductance in the diagonal (backward Euler)
+    int32_t thr_q;                    // ceil(threshold * 2^23): V^n < threshold <= V^{n+1} is exactly
+                                      // Vq^n < thr_q <= Vq^{n+1}
 };
 
 
@@ -264,11 +265,28 @@ struct StepArgs32 {
 // One threshold crossing of spike source src (user neuron, LOCAL compartment)
 // at time ts within step n: the output record, and the source's entry in the
 // ring slot of step n (delivered by the delivery kernel of the next step).
+// The lanes of a warp that record together reserve their entries with one
+// atomic per counter (a volley of point spikes would otherwise serialise on
+// the two counters).
 template <class A>
 __device__ __forceinline__ void record_spike(const A &a, int src, int user_nrn, int user_comp, double ts,
                                              long long n)
 {
-    const unsigned long long k = atomicAdd(&a.ctl->spk_count, 1ull);
+    const unsigned mask = __activemask();
+    const int lane = (int)(threadIdx.x & 31u);
+    const int leader = __ffs(mask) - 1;
+    const int cnt = __popc(mask);
+    const int rank = __popc(mask & ((1u << lane) - 1u));
+    const int slot = (int)(n % a.R);
+    unsigned long long k0 = 0;
+    int p0 = 0;
+    if (lane == leader) {
+        k0 = atomicAdd(&a.ctl->spk_count, (unsigned long long)cnt);
+        p0 = atomicAdd(&a.ring_cnt[slot], cnt);
+    }
+    k0 = __shfl_sync(mask, k0, leader);
+    p0 = __shfl_sync(mask, p0, leader);
+    const unsigned long long k = k0 + (unsigned long long)rank;
     if ((long long)k < a.spk_cap) {
         a.spk_nrn[k] = user_nrn;
         a.spk_comp[k] = user_comp;
@@ -276,33 +294,17 @@ __device__ __forceinline__ void record_spike(const A &a, int src, int user_nrn, 
     } else {
         atomicOr(&a.ctl->err, MMK_ERR_OVERFLOW);
     }
-    const int slot = (int)(n % a.R);
-    const int pos = atomicAdd(&a.ring_cnt[slot], 1);
-    a.ring_nrn[(long long)slot * a.N + pos] = src;
+    a.ring_nrn[(long long)slot * a.N + p0 + rank] = src;
 }
 
-// Whether internal compartment c is a detection point other than a soma.
+// An upward crossing of the threshold between V^n = v0 and V^{n+1} = v1 at
+// detection point p (linearly interpolated time).  The kernels test the
+// crossing first and read the compartment's point id only where it crossed.
 template <class A>
-__device__ __forceinline__ bool is_point(const A &a, int64_t c)
+__device__ __forceinline__ void point_spike(const A &a, int p, double v0, double v1, long long n, double dt)
 {
-    return a.pmask && ((a.pmask[c >> 5] >> (c & 31)) & 1u);
-}
-
-// Threshold test of the point at internal compartment c between V^n = v0
-// and V^{n+1} = v1 (upward crossing, linearly interpolated time); the
-// point's id is found by bisection of the ascending point table.
-template <class A>
-__device__ __forceinline__ void point_test(const A &a, int64_t c, double v0, double v1, long long n, double dt)
-{
-    if (!(v0 < a.threshold && v1 >= a.threshold)) return;
-    int lo = 0, hi = a.n_pt - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a.pt_comp[mid] < c) lo = mid + 1;
-        else hi = mid;
-    }
     const double ts = (double)n * dt + dt * (a.threshold - v0) / (v1 - v0);
-    record_spike(a, lo, a.pt_user_nrn[lo], a.pt_user_comp[lo], ts, n);
+    record_spike(a, p, a.pt_user_nrn[p], a.pt_user_comp[p], ts, n);
 }
 
 // Spike source of the soma of internal neuron nrn (-1: not tested).
@@ -323,6 +325,7 @@ struct DeliverArgs {
     const int32_t *out_dsteps;        // round(delay/dt), ascending within a source
     const int32_t *dclass;            // distinct delays (steps), ascending
     int32_t n_dclass;
+    int32_t lanes_per_src;            // lanes that scatter one spike's synapses (1, 2, 4, ..., 32)
     int32_t step_offset;
     double *gsyn;
     DevCtl *ctl;

@@ -117,9 +117,11 @@ __global__ void __launch_bounds__(256) deliver_kernel(DeliverArgs a)
     }
     __syncthreads();
     const int total = s_pref[a.n_dclass];
-    const int lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < total; u += nwarps) {
+    // groups of lanes_per_src lanes take one spike each (see the FP32c kernel)
+    const int GL = a.lanes_per_src;
+    const int lane = threadIdx.x & (GL - 1);
+    const int ngroups = (gridDim.x * blockDim.x) / GL;
+    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) / GL; u < total; u += ngroups) {
         int lo = 0, hi = a.n_dclass;
         while (hi - lo > 1) {
             int mid = (lo + hi) >> 1;
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(256) deliver_kernel(DeliverArgs a)
             while (l2 < r2) { long long m = (l2 + r2) >> 1; if (a.out_dsteps[m] <= D) l2 = m + 1; else r2 = m; }
             b = l; e = l2;
         }
-        for (long long q = b + lane; q < e; q += 32) atomicAdd(&a.gsyn[a.out_site[q]], a.out_w[q]);
+        for (long long q = b + lane; q < e; q += GL) atomicAdd(&a.gsyn[a.out_site[q]], a.out_w[q]);
     }
 }
 
@@ -306,7 +308,10 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
         for (int i = tid; i < G.ncomp; i += NT) {
             const double v0 = V[i], v = v0 + sr[i];
             a.V[c0 + i] = v;
-            if (is_point(a, c0 + i)) point_test(a, c0 + i, v0, v, n, a.dt);
+            if (a.pt_of && v0 < a.threshold && v >= a.threshold) {
+                const int p = a.pt_of[c0 + i];
+                if (p >= 0) point_spike(a, p, v0, v, n, a.dt);
+            }
             const Rates r = hh_rates(v);
             a.m[c0 + i] = relax(a.m[c0 + i], r.am, r.bm, a.dt);
             a.h[c0 + i] = relax(a.h[c0 + i], r.ah, r.bh, a.dt);

@@ -15,6 +15,8 @@
 //     time is computed in FP64.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "mm_fp32c_math.h"
 #include "mm_internal.h"
 #include "mm_tma.h"
@@ -100,9 +102,13 @@ __global__ void __launch_bounds__(256) deliver_fp32c_kernel(DeliverArgs a)
     }
     __syncthreads();
     const int total = s_pref[a.n_dclass];
-    const int lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < total; u += nwarps) {
+    // groups of lanes_per_src lanes take one spike each (a power of two up to
+    // the warp: the sources' mean fan-out, so that sparse sources such as
+    // synapse points do not leave most of a warp idle)
+    const int GL = a.lanes_per_src;
+    const int lane = threadIdx.x & (GL - 1);
+    const int ngroups = (gridDim.x * blockDim.x) / GL;
+    for (int u = (blockIdx.x * blockDim.x + threadIdx.x) / GL; u < total; u += ngroups) {
         int lo = 0, hi = a.n_dclass;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -119,7 +125,7 @@ __global__ void __launch_bounds__(256) deliver_fp32c_kernel(DeliverArgs a)
             b = l;
             e = l2;
         }
-        for (long long q = b + lane; q < e; q += 32) atomicAdd(&a.gsyn32[a.out_site[q]], a.out_w32[q]);
+        for (long long q = b + lane; q < e; q += GL) atomicAdd(&a.gsyn32[a.out_site[q]], a.out_w32[q]);
     }
 }
 
@@ -537,16 +543,27 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
 
         // C. V^{n+1} = V^n + dV (exact in fixed point), and the threshold
         //    test of the detection points other than somata
-        for (int i = tid; i < G.ncomp; i += NS) {
-            const int32_t vold = Vq[i];
-            int32_t vq;
-            if (!mmf::v_add(vold, sy[2 * i + 1], &vq)) {
-                atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
-                vq = vold;
+        //    (two copies of the loop, chosen by the uniform detection mode,
+        //    so that soma detection runs the loop without the test)
+        auto phase_c = [&](auto points) {
+            for (int i = tid; i < G.ncomp; i += NS) {
+                const int32_t vold = Vq[i];
+                int32_t vq;
+                if (!mmf::v_add(vold, sy[2 * i + 1], &vq)) {
+                    atomicOr(&a.ctl->err, MMK_ERR_NUMERIC);
+                    vq = vold;
+                }
+                a.Vq[c0 + i] = vq;
+                if constexpr (decltype(points)::value) {
+                    if (vold < a.thr_q && vq >= a.thr_q) {
+                        const int p = a.pt_of[c0 + i];
+                        if (p >= 0) point_spike(a, p, (double)vold * kVInvD, (double)vq * kVInvD, n, a.dt64);
+                    }
+                }
             }
-            a.Vq[c0 + i] = vq;
-            if (is_point(a, c0 + i)) point_test(a, c0 + i, (double)vold * kVInvD, (double)vq * kVInvD, n, a.dt64);
-        }
+        };
+        if (a.pt_of) phase_c(std::true_type{});
+        else phase_c(std::false_type{});
         if (a.item_ns) {  // uniform across the block
             __syncthreads();
             if (tid == 0) a.item_ns[gi] += global_ns() - t_item;
@@ -880,7 +897,10 @@ __global__ void __launch_bounds__(256) giant_update_kernel(StepArgs32 a)
                 vq = vold;
             }
             a.Vq[c0 + i] = vq;
-            if (is_point(a, c0 + i)) point_test(a, c0 + i, (double)vold * kVInvD, (double)vq * kVInvD, n, a.dt64);
+            if (a.pt_of && vold < a.thr_q && vq >= a.thr_q) {
+                const int p = a.pt_of[c0 + i];
+                if (p >= 0) point_spike(a, p, (double)vold * kVInvD, (double)vq * kVInvD, n, a.dt64);
+            }
             gate_update(a, c0 + i);
         }
     }

@@ -755,7 +755,7 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         L.pt_user_nrn.assign(L.pt_comp.size(), 0);
         L.pt_user_comp.assign(L.pt_comp.size(), 0);
         L.soma_src.assign((size_t)N, -1);
-        L.pmask.assign((size_t)((C + 31) / 32), 0u);
+        L.pt_of.assign((size_t)C, -1);
         for (int64_t s = 0; s < in.S; ++s) {
             const int64_t c = ic[(size_t)s];
             const int32_t id = (int32_t)(std::lower_bound(L.pt_comp.begin(), L.pt_comp.end(), c) - L.pt_comp.begin());
@@ -766,7 +766,7 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
             if (uc == 0)
                 L.soma_src[(size_t)L.internal_of[(size_t)in.src[s]]] = id;
             else
-                L.pmask[(size_t)(c >> 5)] |= 1u << (c & 31);
+                L.pt_of[(size_t)c] = id;
         }
     }
     L.out_off.assign((size_t)L.n_src + 1, 0);

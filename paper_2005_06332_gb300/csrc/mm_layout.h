@@ -71,7 +71,7 @@ struct Layout {
     std::vector<int32_t> pt_user_nrn;   // points: user neuron and LOCAL user compartment
     std::vector<int32_t> pt_user_comp;
     std::vector<int32_t> soma_src;      // points: source id of each internal neuron's soma point, -1 if none
-    std::vector<uint32_t> pmask;        // points: bit c set where compartment c is a point other than a soma
+    std::vector<int32_t> pt_of;         // points: point id of each compartment, -1 where none and at somata
     std::vector<int64_t> out_off;       // outgoing synapses per source [n_src+1]
     std::vector<int32_t> out_site, out_dsteps;
     std::vector<double> out_w;

@@ -331,7 +331,8 @@ class TunePoint(C.Structure):
 
 
 def autotune(net, precision: str = "fp32c", sample_comps: int = 2_000_000, warmup: int = 3, steps: int = 20,
-             device: int = 0, stream=None, cost: Optional[np.ndarray] = None, graph_steps: int = 40) -> dict:
+             device: int = 0, stream=None, cost: Optional[np.ndarray] = None, graph_steps: int = 40,
+             detect: str = "soma") -> dict:
     """mm_autotune on a netgen.Network: the fastest (block_threads,
     group_comps) measured on a stratified sample, and every candidate."""
     L = load()
@@ -342,6 +343,7 @@ def autotune(net, precision: str = "fp32c", sample_comps: int = 2_000_000, warmu
     opt.graph_steps = graph_steps
     opt.device = device
     opt.dt_ms = float(net.dt)
+    opt.detect = DETECT[detect]
     keep = None
     if cost is not None:
         keep = np.ascontiguousarray(cost, np.float32)
@@ -402,6 +404,7 @@ class Network:
             self._spk_cap = max(1 << 16, n_pt * 16)
         else:
             self._spk_cap = max(1 << 16, self.n_neurons * 64)
+        self._spk_buf = None
         self._cost = None
         if cost is not None:
             self._cost = np.ascontiguousarray(cost, np.float32)
@@ -468,14 +471,19 @@ class Network:
         self._check(self._L.mm_read_soma_voltages(self._h, _ptr(out, C.c_double), out.size), "mm_read_soma_voltages")
         return out
 
+    def _spike_arrays(self, cap: Optional[int]):
+        # host arrays as large as the device buffer, kept between calls
+        if cap is not None and cap != self._spk_cap:
+            return np.empty(cap, np.int32), np.empty(cap, np.int32), np.empty(cap, np.float64), cap
+        if self._spk_buf is None:
+            c = self._spk_cap
+            self._spk_buf = (np.empty(c, np.int32), np.empty(c, np.int32), np.empty(c, np.float64))
+        return (*self._spk_buf, self._spk_cap)
+
     def read_spike_points(self, cap: Optional[int] = None):
         """(neuron, LOCAL compartment, t_ms) drained since the last call,
         ordered by (t, neuron, compartment)."""
-        if cap is None:
-            cap = self._spk_cap
-        nr = np.empty(cap, np.int32)
-        cp = np.empty(cap, np.int32)
-        tt = np.empty(cap, np.float64)
+        nr, cp, tt, cap = self._spike_arrays(cap)
         n = C.c_int64()
         st = self._L.mm_read_spike_points(self._h, _ptr(nr, C.c_int32), _ptr(cp, C.c_int32), _ptr(tt, C.c_double),
                                           cap, C.byref(n))
@@ -484,10 +492,7 @@ class Network:
 
     def read_spikes(self, cap: Optional[int] = None, allow_overflow: bool = False):
         """(neuron, t_ms) drained since the last call, ordered by (t, neuron)."""
-        if cap is None:
-            cap = self._spk_cap
-        nr = np.empty(cap, np.int32)
-        tt = np.empty(cap, np.float64)
+        nr, _, tt, cap = self._spike_arrays(cap)
         n = C.c_int64()
         st = self._L.mm_read_spikes(self._h, _ptr(nr, C.c_int32), _ptr(tt, C.c_double), cap, C.byref(n))
         if st == MM_EOVERFLOW and allow_overflow:

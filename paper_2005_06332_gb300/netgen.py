@@ -348,8 +348,10 @@ CONFIGS = {
 
 
 def make_config(name: str, scale: float = 1.0, n_neurons: Optional[int] = None,
-                t_stop: Optional[float] = None, syn_per_neuron: Optional[int] = None) -> Network:
-    """Network of a named workload (optionally scaled down in neuron count)."""
+                t_stop: Optional[float] = None, syn_per_neuron: Optional[int] = None,
+                src_points: bool = False) -> Network:
+    """Network of a named workload (optionally scaled down in neuron count;
+    src_points: synapses also leave from uniformly drawn compartments)."""
     cfg = dict(CONFIGS[name])
     precision = cfg.pop("precision")
     seed = SEED_BASE + cfg.pop("seed_index")
@@ -364,6 +366,6 @@ def make_config(name: str, scale: float = 1.0, n_neurons: Optional[int] = None,
         cfg["giants"] = max(1, int(round(cfg["giants"] * scale)))
         cfg["giant_size"] = max(1000, int(round(cfg["giant_size"] * min(1.0, scale * 10))))
     cfg["syn_per_neuron"] = min(cfg["syn_per_neuron"], max(1, n_neurons - 1))
-    net = make_network(seed=seed, name=name, **cfg)
+    net = make_network(seed=seed, name=name, src_points=src_points, **cfg)
     net.params["precision"] = precision
     return net
