@@ -36,6 +36,15 @@ struct mm_net {
     // end of the step)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // pinned host staging, so that the per-step host calls copy
+    // asynchronously and synchronise once: the control block (read and
+    // written back), the stimulus (with the event of its last upload) and
+    // a buffer for soma voltages and spike records
+    mmk::DevCtl *pin_ctl = nullptr, *pin_ctl_w = nullptr;
+    double *pin_stim = nullptr;
+    cudaEvent_t ev_stim = nullptr;
+    unsigned char *pin = nullptr;
+    size_t pin_cap = 0;
     mm_allocator alloc{};
     std::vector<void *> blocks;
     std::string err;
@@ -57,7 +66,8 @@ struct mm_net {
     int32_t n_giant = 0, n_small = 0, n_big = 0;
     int big_blocks = 1;
     int graph_steps = 40;
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec = nullptr;   // graph_steps steps
+    cudaGraphExec_t gexec1 = nullptr;  // one step (single-step calls)
 
     mmk::StepArgs32 sa32{};   // regular shared-memory class
     mmk::StepArgs32 sa32b{};  // large shared-memory class
@@ -173,13 +183,41 @@ mm_status guard(mm_net *net)
     return MM_OK;
 }
 
+// Snapshot of the control block into pinned memory, enqueued on the stream
+// behind everything issued so far (read it after the next synchronisation).
+mm_status snap_ctl(mm_net *net)
+{
+    MM_CK(net, cudaMemcpyAsync(net->pin_ctl, net->ctl, sizeof(mmk::DevCtl), cudaMemcpyDeviceToHost, net->stream));
+    return MM_OK;
+}
+
+// The device error word of a snapshot -> status.
+mm_status ctl_status(mm_net *net, const mmk::DevCtl &c)
+{
+    if (c.err & mmk::MMK_ERR_NUMERIC) return fail(net, MM_ENUMERIC, "a soma voltage became NaN or infinite");
+    return MM_OK;
+}
+
 // Device error word -> status (synchronising).
 mm_status check_device(mm_net *net)
 {
+    mm_status st = snap_ctl(net);
+    if (st != MM_OK) return st;
     MM_CK(net, cudaStreamSynchronize(net->stream));
-    mmk::DevCtl c;
-    MM_CK(net, cudaMemcpy(&c, net->ctl, sizeof(c), cudaMemcpyDeviceToHost));
-    if (c.err & mmk::MMK_ERR_NUMERIC) return fail(net, MM_ENUMERIC, "a soma voltage became NaN or infinite");
+    return ctl_status(net, *net->pin_ctl);
+}
+
+// Pinned staging of at least `bytes` (contents not kept).
+mm_status pinned(mm_net *net, size_t bytes)
+{
+    if (bytes <= net->pin_cap) return MM_OK;
+    MM_CK(net, cudaStreamSynchronize(net->stream));
+    if (net->pin) cudaFreeHost(net->pin);
+    net->pin = nullptr;
+    net->pin_cap = 0;
+    const size_t cap = std::max<size_t>(bytes, 1 << 20);
+    MM_CK(net, cudaMallocHost((void **)&net->pin, cap));
+    net->pin_cap = cap;
     return MM_OK;
 }
 
@@ -298,22 +336,23 @@ mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
     return MM_OK;
 }
 
-mm_status ensure_graph(mm_net *net)
+// Captures `steps` steps into *exec (once).
+mm_status ensure_graph(mm_net *net, int steps, cudaGraphExec_t *exec)
 {
-    if (net->gexec || net->graph_steps <= 0) return MM_OK;
+    if (*exec || steps <= 0) return MM_OK;
     cudaGraph_t graph = nullptr;
     MM_CK(net, cudaStreamBeginCapture(net->cap_stream, cudaStreamCaptureModeThreadLocal));
-    mm_status st = launch_steps(net, net->cap_stream, net->graph_steps);
+    mm_status st = launch_steps(net, net->cap_stream, steps);
     cudaError_t e = cudaStreamEndCapture(net->cap_stream, &graph);
     if (st != MM_OK) {
         if (graph) cudaGraphDestroy(graph);
         return st;
     }
     if (e != cudaSuccess) return cuda_fail(net, e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&net->gexec, graph, 0);
+    e = cudaGraphInstantiate(exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
-        net->gexec = nullptr;
+        *exec = nullptr;
         return cuda_fail(net, e, "cudaGraphInstantiate");
     }
     return MM_OK;
@@ -322,7 +361,8 @@ mm_status ensure_graph(mm_net *net)
 void release_all(mm_net *net)
 {
     if (net->gexec) cudaGraphExecDestroy(net->gexec);
-    net->gexec = nullptr;
+    if (net->gexec1) cudaGraphExecDestroy(net->gexec1);
+    net->gexec = net->gexec1 = nullptr;
     if (net->stream) cudaStreamSynchronize(net->stream);
     if (net->side) cudaStreamSynchronize(net->side);
     for (auto &p : net->pending) {
@@ -344,6 +384,15 @@ void release_all(mm_net *net)
     if (net->side) cudaStreamDestroy(net->side);
     if (net->ev_fork) cudaEventDestroy(net->ev_fork);
     if (net->ev_join) cudaEventDestroy(net->ev_join);
+    if (net->ev_stim) cudaEventDestroy(net->ev_stim);
+    if (net->pin_ctl) cudaFreeHost(net->pin_ctl);
+    if (net->pin_stim) cudaFreeHost(net->pin_stim);
+    if (net->pin) cudaFreeHost(net->pin);
+    net->ev_stim = nullptr;
+    net->pin_ctl = net->pin_ctl_w = nullptr;
+    net->pin_stim = nullptr;
+    net->pin = nullptr;
+    net->pin_cap = 0;
     net->side = nullptr;
     net->ev_fork = nullptr;
     net->ev_join = nullptr;
@@ -382,6 +431,10 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     MM_CK(net, cudaStreamCreateWithFlags(&net->side, cudaStreamNonBlocking));
     MM_CK(net, cudaEventCreateWithFlags(&net->ev_fork, cudaEventDisableTiming));
     MM_CK(net, cudaEventCreateWithFlags(&net->ev_join, cudaEventDisableTiming));
+    MM_CK(net, cudaEventCreateWithFlags(&net->ev_stim, cudaEventDisableTiming));
+    MM_CK(net, cudaMallocHost((void **)&net->pin_ctl, 2 * sizeof(mmk::DevCtl)));
+    net->pin_ctl_w = net->pin_ctl + 1;
+    MM_CK(net, cudaMallocHost((void **)&net->pin_stim, (size_t)std::max(morph->n_neurons, 1) * sizeof(double)));
 
     // layout
     mmh::LayoutInput li{};
@@ -819,10 +872,16 @@ mm_status mm_step(mm_net *net, int64_t n_steps, double dt_ms)
     if (n_steps < 0) return fail(net, MM_EINVAL, "n_steps must be >= 0");
     if (!(dt_ms == net->dt)) return fail(net, MM_EINVAL, "dt differs from the network's dt");
     while (!net->timing && net->graph_steps > 0 && n_steps >= net->graph_steps) {
-        if ((st = ensure_graph(net)) != MM_OK) return st;
+        if ((st = ensure_graph(net, net->graph_steps, &net->gexec)) != MM_OK) return st;
         MM_CK(net, cudaGraphLaunch(net->gexec, net->stream));
         n_steps -= net->graph_steps;
         net->steps_done += net->graph_steps;
+    }
+    if (!net->timing && net->graph_steps > 0 && n_steps == 1) {
+        if ((st = ensure_graph(net, 1, &net->gexec1)) != MM_OK) return st;
+        MM_CK(net, cudaGraphLaunch(net->gexec1, net->stream));
+        n_steps = 0;
+        net->steps_done += 1;
     }
     while (n_steps > 0) {
         const int k = (int)std::min<int64_t>(n_steps, 1 << 20);
@@ -889,12 +948,16 @@ mm_status mm_read_soma_voltages(mm_net *net, double *out, int64_t cap)
     mm_status st = guard(net);
     if (st != MM_OK) return st;
     if (!out || cap < net->N) return fail(net, MM_EINVAL, "output buffer too small");
+    const size_t bytes = (size_t)net->N * sizeof(double);
+    if ((st = pinned(net, bytes)) != MM_OK) return st;
     if (net->precision == MM_FP64)
         MM_CKI(net, mmk_launch_gather_f64(net->V, net->soma_of_user, net->scratch, net->N, net->stream));
     else
         MM_CKI(net, mmk_launch_gather_f64(net->Vsoma, net->internal_of64, net->scratch, net->N, net->stream));
-    MM_CK(net, cudaMemcpyAsync(out, net->scratch, (size_t)net->N * sizeof(double), cudaMemcpyDeviceToHost, net->stream));
-    return check_device(net);
+    MM_CK(net, cudaMemcpyAsync(net->pin, net->scratch, bytes, cudaMemcpyDeviceToHost, net->stream));
+    if ((st = check_device(net)) != MM_OK) return st;
+    std::memcpy(out, net->pin, bytes);
+    return MM_OK;
 }
 
 mm_status mm_read_spike_points(mm_net *net, int32_t *neuron, int32_t *comp, double *t_ms, int64_t cap,
@@ -904,15 +967,21 @@ mm_status mm_read_spike_points(mm_net *net, int32_t *neuron, int32_t *comp, doub
     if (st != MM_OK) return st;
     if (!n_out || cap < 0 || (cap > 0 && (!neuron || !t_ms))) return fail(net, MM_EINVAL, "bad spike output arguments");
     if ((st = check_device(net)) != MM_OK) return st;
-    mmk::DevCtl c;
-    MM_CK(net, cudaMemcpy(&c, net->ctl, sizeof(c), cudaMemcpyDeviceToHost));
+    mmk::DevCtl c = *net->pin_ctl;
     const int64_t held = std::min<int64_t>((int64_t)c.spk_count, net->spk_cap);
-    std::vector<int32_t> nr((size_t)held), cp((size_t)held);
-    std::vector<double> tt((size_t)held);
+    const int32_t *nr = nullptr, *cp = nullptr;
+    const double *tt = nullptr;
     if (held) {
-        MM_CK(net, cudaMemcpy(nr.data(), net->spk_nrn, (size_t)held * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        MM_CK(net, cudaMemcpy(cp.data(), net->spk_comp, (size_t)held * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        MM_CK(net, cudaMemcpy(tt.data(), net->spk_t, (size_t)held * sizeof(double), cudaMemcpyDeviceToHost));
+        // one staging area: times, neurons, compartments
+        const size_t bt = (size_t)held * sizeof(double), bi = (size_t)held * sizeof(int32_t);
+        if ((st = pinned(net, bt + 2 * bi)) != MM_OK) return st;
+        MM_CK(net, cudaMemcpyAsync(net->pin, net->spk_t, bt, cudaMemcpyDeviceToHost, net->stream));
+        MM_CK(net, cudaMemcpyAsync(net->pin + bt, net->spk_nrn, bi, cudaMemcpyDeviceToHost, net->stream));
+        MM_CK(net, cudaMemcpyAsync(net->pin + bt + bi, net->spk_comp, bi, cudaMemcpyDeviceToHost, net->stream));
+        MM_CK(net, cudaStreamSynchronize(net->stream));
+        tt = (const double *)net->pin;
+        nr = (const int32_t *)(net->pin + bt);
+        cp = (const int32_t *)(net->pin + bt + bi);
     }
     // order by (t, neuron, comp) as two unsigned keys: the bits of t mapped
     // to an order-preserving integer, then neuron and compartment
@@ -923,9 +992,9 @@ mm_status mm_read_spike_points(mm_net *net, int32_t *neuron, int32_t *comp, doub
     std::vector<Rec> rec((size_t)held);
     for (int64_t i = 0; i < held; ++i) {
         uint64_t b;
-        std::memcpy(&b, &tt[(size_t)i], sizeof(b));
+        std::memcpy(&b, &tt[i], sizeof(b));
         b = (b >> 63) ? ~b : (b | (1ull << 63));
-        rec[(size_t)i] = {b, ((uint64_t)(uint32_t)nr[(size_t)i] << 32) | (uint32_t)cp[(size_t)i], tt[(size_t)i]};
+        rec[(size_t)i] = {b, ((uint64_t)(uint32_t)nr[i] << 32) | (uint32_t)cp[i], tt[i]};
     }
     std::sort(rec.begin(), rec.end(), [](const Rec &a, const Rec &b) { return a.tk != b.tk ? a.tk < b.tk : a.nc < b.nc; });
     const int64_t w = std::min<int64_t>(held, cap);
@@ -937,11 +1006,12 @@ mm_status mm_read_spike_points(mm_net *net, int32_t *neuron, int32_t *comp, doub
     }
     *n_out = held;
     const bool overflow = (c.err & mmk::MMK_ERR_OVERFLOW) != 0 || (int64_t)c.spk_count > net->spk_cap;
-    // drain: reset the count and the overflow bit
+    // drain: reset the count and the overflow bit (the device is idle since
+    // the synchronisation above; the write is ordered before later steps)
     c.spk_count = 0;
     c.err &= ~mmk::MMK_ERR_OVERFLOW;
-    MM_CK(net, cudaMemcpy(&net->ctl->spk_count, &c.spk_count, sizeof(c.spk_count), cudaMemcpyHostToDevice));
-    MM_CK(net, cudaMemcpy(&net->ctl->err, &c.err, sizeof(c.err), cudaMemcpyHostToDevice));
+    *net->pin_ctl_w = c;
+    MM_CK(net, cudaMemcpyAsync(net->ctl, net->pin_ctl_w, sizeof(mmk::DevCtl), cudaMemcpyHostToDevice, net->stream));
     if (overflow) return fail(net, MM_EOVERFLOW, "spike buffer overflowed; raise mm_options.spike_capacity or read more often");
     if (w < held) return fail(net, MM_EOVERFLOW, "caller's spike arrays are smaller than the spike count");
     return MM_OK;
@@ -957,13 +1027,15 @@ mm_status mm_set_stimulus(mm_net *net, const double *stim_nA, int64_t n)
     mm_status st = guard(net);
     if (st != MM_OK) return st;
     if (!stim_nA || n != net->N) return fail(net, MM_EINVAL, "stimulus must have n_neurons entries");
-    std::vector<double> s((size_t)net->N);
-    for (int32_t k = 0; k < net->N; ++k) {
-        if (!std::isfinite(stim_nA[net->order[(size_t)k]])) return fail(net, MM_EINVAL, "stimulus must be finite");
-        s[(size_t)k] = stim_nA[net->order[(size_t)k]];
-    }
-    MM_CK(net, cudaMemcpyAsync(net->stim, s.data(), s.size() * sizeof(double), cudaMemcpyHostToDevice, net->stream));
-    MM_CK(net, cudaStreamSynchronize(net->stream));
+    for (int32_t k = 0; k < net->N; ++k)
+        if (!std::isfinite(stim_nA[k])) return fail(net, MM_EINVAL, "stimulus must be finite");
+    // the staging buffer is rewritten once its last upload has run; the
+    // upload is ordered on the stream before every later step
+    MM_CK(net, cudaEventSynchronize(net->ev_stim));
+    for (int32_t k = 0; k < net->N; ++k) net->pin_stim[k] = stim_nA[net->order[(size_t)k]];
+    MM_CK(net, cudaMemcpyAsync(net->stim, net->pin_stim, (size_t)net->N * sizeof(double), cudaMemcpyHostToDevice,
+                               net->stream));
+    MM_CK(net, cudaEventRecord(net->ev_stim, net->stream));
     return MM_OK;
 }
 
