@@ -53,6 +53,28 @@ BYTES_PER_UPDATE = {"fp64": (80.0, 20.0),
 # and its index): V r/w 8 + gates r/w 24 + area, g_axial 8 = 40 B (+12 B per site)
 KERNEL_BYTES_FP32C = {"step": (40.0, 12.0), "big": (40.0, 12.0), "giant": (40.0, 12.0)}
 
+# Counters of one `ncu --set full` capture of the regular-class step kernel
+# (profiles/step_fp32c_multi10k.md): DRAM bytes read + written and warp
+# instructions executed per launch.  They describe the kernel built from the
+# sources whose SHA-256 is recorded; after any change they are not reported.
+KERNEL_SOURCES = ("mm_kernels_fp32c.cu", "mm_fp32c_math.h", "mm_internal.h", "mm_tma.h")
+PROFILED = {
+    ("multi10k", "fp32c", "step", "soma"): {
+        "sha256": "a43721536f41c3fa57b73f217fb86682b6b637d84332a3e672e620f4a9709336",
+        "dram_bytes": 298258432 + 124148480,
+        "warp_instructions": 350060923,
+    },
+}
+
+
+def _kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2005_06332_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
 
 def _peaks():
     try:
@@ -363,13 +385,31 @@ def main():
     dom = max((k for k in kernels if kernels[k][1] is not None), key=lambda k: kernels[k][1])
     dom_ms, dom_bytes = kernels[dom]
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    prof = PROFILED.get((net.name, precision, dom, args.detect))
+    if prof is not None and prof["sha256"] != _kernel_sources_sha256():
+        prof = None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_kind": peak_kind, "kernel": f"{dom}_{precision}",
+                "traffic": prof["dram_bytes"] if prof else None,
+                "traffic_gbs": (prof["dram_bytes"] / 1e9 / (dom_ms * 1e-3)) if prof else None,
+                "peak_kind": peak_kind, "kernel": f"{dom}_{precision}",
                 "kernel_ms": dom_ms, "bytes_per_launch": dom_bytes,
                 "kernels_ms": {k: v[0] for k, v in kernels.items()},
                 "step_bytes_per_update": f"{b0:g} B per compartment + {bsite:g} B per synaptic site",
                 "step_achieved_gbs": (b0 * net.n_comp + bsite * nsite) / (ms / K * 1e-3) / 1e9}
 
+    clocks = clk.summary()
+    # the bound the step kernel meets in practice: instruction issue (four
+    # schedulers per SM, one warp instruction each per cycle, at the SM clock
+    # sampled during the timed region), with the executed warp instructions
+    # of the profiled launch
+    roofline_issue = None
+    if prof is not None and clocks.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        ipeak = 4.0 * sms * clocks["sm_mhz"] * 1e6
+        iach = prof["warp_instructions"] / (dom_ms * 1e-3)
+        roofline_issue = {"bound": "issue", "achieved": iach, "peak": ipeak, "unit": "warp-instructions/s",
+                          "frac": iach / ipeak, "warp_instructions_per_launch": prof["warp_instructions"],
+                          "per_compartment": prof["warp_instructions"] / launch["comps"][0]}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if precision == "fp64" else "f32", "data": "synthetic",
@@ -379,7 +419,8 @@ def main():
                       "spike_detection": args.detect,
                       "l2": f"inputs larger than L2 (state + constants {((48 if precision == 'fp64' else 24) * net.n_comp) / 1e6:.0f} MB)",
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+           "roofline": roofline, "roofline_issue": roofline_issue, "e2e": e2e, "gpu_launches": launches,
+           "clocks": clocks,
            "launch": launch, "autotune": tune}
     g.close()
     if args.learned:
