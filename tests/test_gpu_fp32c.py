@@ -226,3 +226,49 @@ def test_fp32c_accuracy_report():
     print(json.dumps(rows, indent=1))
     for r in rows:
         assert r["identical_spike_counts"], r
+
+
+def _first_window_sampled(name, block_threads=0, group_comps=0, n_pick=40):
+    """Full-size network, first min-delay window: no event can arrive before
+    step round(min delay / dt) + 1, so each sampled neuron (plus the largest
+    and the smallest) must follow the oracle's run of that neuron alone."""
+    net = netgen.make_config(name)
+    steps = int(round(float(np.min(net.syn_delay_ms)) / net.dt)) + 1
+    with mm.Network(net, precision="fp32c", block_threads=block_threads, group_comps=group_comps) as g:
+        info = g.launch_info()
+        g.step(steps)
+        V = g.read_voltages()
+        gates = {k: g.read_state(k) for k in ("m", "h", "n")}
+    rng = np.random.default_rng(0)
+    sizes = net.sizes()
+    pick = np.unique(np.concatenate([rng.choice(net.n_neurons, n_pick, replace=False),
+                                     [int(np.argmax(sizes)), int(np.argmin(sizes))]]))
+    sub = net.subset(pick, keep_synapses=False)
+    ref = oracle.simulate(sub, steps)
+    idx = np.concatenate([np.arange(net.comp_offset[k], net.comp_offset[k + 1]) for k in pick])
+    assert np.max(np.abs(V[idx] - ref.V)) <= TOL_V
+    for k in ("m", "h", "n"):
+        assert np.max(np.abs(gates[k][idx] - getattr(ref, k))) <= 1e-5, k
+    return info
+
+
+def test_fp32c_multi10k_full_size_first_window_sampled():
+    """multi10k (10.9 M compartments) in the launch configuration the
+    benchmark's autotuner picks (512 threads, 4096-compartment items)."""
+    _first_window_sampled("multi10k", block_threads=512, group_comps=4096)
+
+
+def test_fp32c_lognormal100k_full_size_first_window_sampled():
+    """lognormal100k (132 M compartments, 100 M synapses), library defaults:
+    regular and large-class items (neurons up to 20,000 compartments)."""
+    info = _first_window_sampled("lognormal100k")
+    assert info["big_items"] > 0
+
+
+def test_fp32c_mixed200k_full_size_first_window_sampled():
+    """mixed200k (200,000 neurons and 64 giants of 100,000 compartments,
+    200 M synapses with delays U[1, 5] ms), library defaults: all three item
+    classes (the 64 giants and the lognormal neurons beyond the large class);
+    a giant is always among the sampled neurons (the largest)."""
+    info = _first_window_sampled("mixed200k")
+    assert info["giant_items"] >= 64 and info["big_items"] > 0
