@@ -144,6 +144,23 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device: str) -> float:
+    """The largest x over the ranks of the process group (every rank gets it)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, ws: int, seconds_slowest: float) -> float:
+    """Whole-job rate: the units all ranks processed (each rank the same
+    replica workload) over the slowest rank's time."""
+    return units_per_rank * ws / seconds_slowest
+
+
 def cpu_baseline(net, seconds_hint: float = 15.0, detect: str = "soma"):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload."""
     import oracle
@@ -321,11 +338,8 @@ def main():
         ev1.record(stream)
         ev1.synchronize()
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ws, "cuda")
     if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     G = args.graph_steps
     K = args.steps
@@ -335,8 +349,7 @@ def main():
     # (giant items: phase A, solve and phase C + gates, three kernels)
     kps = 2 if precision == "fp64" else 1 + (n_reg > 0) + (launch["big_items"] > 0) + 3 * (launch["giant_items"] > 0)
     launches = (K // G) * (kps * G + 1) + ((K % G > 0) * (kps * (K % G) + 1)) if G > 0 else kps * K + 1
-    updates = net.n_comp * K * ws
-    value = updates / (ms * 1e-3)
+    value = job_throughput(net.n_comp * K, ws, ms * 1e-3)
 
     # per-kernel times (events around each launch, direct launches)
     kt_steps = max(10, K // 4)
@@ -361,8 +374,8 @@ def main():
         g.read_soma(soma)
         sn, _st = g.read_spikes(allow_overflow=True)
         n_spk += len(sn)
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": net.n_comp * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * net.n_neurons,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, "cuda")
+    e2e = {"value": job_throughput(net.n_comp * ke, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 8 * net.n_neurons,
            "d2h_bytes_per_step": int(8 * net.n_neurons + round(12 * n_spk / ke)), "steps": ke,
            "calls_per_step": "mm_set_stimulus, mm_step(1), mm_read_soma_voltages, mm_read_spikes"}
 

@@ -1,0 +1,61 @@
+"""The multi-rank host logic of bench.py on CPU (gloo, world size 2): the
+timed region's max over ranks and the whole-job throughput of replicas, and
+the reference arm's other ranks leaving without work."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as tmp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, ws, port, local_ms, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        ms = bench.max_over_ranks(local_ms[rank], ws, "cpu")
+        dist.barrier()
+        value = bench.job_throughput(1000.0 * 40, ws, ms * 1e-3)
+        with open(os.path.join(out_dir, f"r{rank}.json"), "w") as f:
+            json.dump({"ms": ms, "value": value}, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_job_throughput_gloo(tmp_path):
+    ws = 2
+    local_ms = [10.0, 15.0]
+    tmp.spawn(_rank, args=(ws, _free_port(), local_ms, str(tmp_path)), nprocs=ws, join=True)
+    got = [json.load(open(tmp_path / f"r{r}.json")) for r in range(ws)]
+    for g in got:
+        assert g["ms"] == 15.0                      # the slowest rank's time, on every rank
+        assert g["value"] == pytest.approx(1000.0 * 40 * ws / 15e-3)   # all ranks' units / that time
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
+    assert bench.job_throughput(100.0, 1, 0.5) == 200.0
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--config", "mono64", "--steps", "1",
+                        "--warmup", "3"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
