@@ -281,6 +281,8 @@ def main():
     ap.add_argument("--detect", default="soma", choices=["soma", "points"],
                     help="threshold test at every soma, or at the points synapses leave from (each synapse "
                          "leaving a compartment drawn uniformly over its source neuron)")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="deterministic event delivery (each site adds its events in ascending synapse id)")
     ap.add_argument("--paper-replay", action="store_true",
                     help="the paper's load-balance tests instead: one morphology vs a group of 20 sizes vs "
                          "F-distributed sizes (same mean size), size-sorted vs random work-queue order")
@@ -318,7 +320,8 @@ def main():
         tune["seconds"] = time.perf_counter() - t0
         args.block_threads, args.group_comps = tune["block_threads"], tune["group_comps"]
     g = mm.Network(net, precision=precision, graph_steps=args.graph_steps, device=local, stream=stream.cuda_stream,
-                   block_threads=args.block_threads, group_comps=args.group_comps, detect=args.detect)
+                   block_threads=args.block_threads, group_comps=args.group_comps, detect=args.detect,
+                   deterministic=args.deterministic)
 
     launch = g.launch_info()
     # warm-up (also captures the CUDA graph)
@@ -429,7 +432,7 @@ def main():
            "config": {"workload": net.name, "precision": precision, "n_neurons": net.n_neurons,
                       "block_threads": args.block_threads, "group_comps": args.group_comps,
                       "n_comp": net.n_comp, "n_syn": net.n_syn, "dt_ms": net.dt, "graph_steps": G,
-                      "spike_detection": args.detect,
+                      "spike_detection": args.detect, "deterministic_delivery": args.deterministic,
                       "l2": f"inputs larger than L2 (state + constants {((48 if precision == 'fp64' else 24) * net.n_comp) / 1e6:.0f} MB)",
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
            "roofline": roofline, "roofline_issue": roofline_issue, "e2e": e2e, "gpu_launches": launches,

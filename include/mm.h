@@ -163,7 +163,11 @@ typedef struct {
     int32_t time_items;         /* MM_FP32C: record each work item's solve time (mm_read_neuron_times) */
     int32_t scheme;             /* MM_SCHEME_BE | MM_SCHEME_CN */
     int32_t detect;             /* MM_DETECT_SOMA | MM_DETECT_SYNAPSE_POINTS */
-    int32_t reserved0;          /* must be 0 */
+    int32_t deterministic_delivery; /* 0: spike events added to the synaptic conductances with
+                                       atomics (order unspecified); 1: each site adds its events
+                                       in ascending synapse id, as the oracle does (Sec. 2's
+                                       event delivery made reproducible: runs repeat bit for bit,
+                                       and under MM_FP64 the conductances equal the oracle's) */
     double dt_ms;               /* time step of the network, > 0 */
     int64_t spike_capacity;     /* spikes held between two mm_read_spikes; 0 = automatic */
     void *cuda_stream;          /* cudaStream_t to run on; NULL = a library-owned stream */
@@ -180,7 +184,7 @@ void mm_default_options(mm_options *opt);
  * On success *out owns the network; on failure *out is NULL.
  * Errors: MM_EINVAL (bad sizes, parent[i] >= i, non-positive geometry,
  * dst_comp or src_comp out of range, delay < dt, dt <= 0, unknown scheme or
- * detection mode, reserved0 != 0), MM_ENOMEM, MM_ECUDA, MM_ENOTSUP. */
+ * detection mode, deterministic_delivery not 0 or 1), MM_ENOMEM, MM_ECUDA, MM_ENOTSUP. */
 mm_status mm_create_network(const mm_morphologies *morph, const mm_channel_params *chan,
                             const mm_synapses *syn, const double *stim_nA,
                             const mm_options *opt, mm_net **out);

@@ -57,6 +57,11 @@ struct mm_net {
     int32_t R = 2;
     int32_t n_src = 0;        // spike sources: neurons, or detection points
     int detect = MM_DETECT_SOMA;
+    // deterministic delivery: per step slot a bitmask of the sources that fired
+    bool ordered = false;
+    uint32_t *fired = nullptr;
+    int32_t fired_words = 0;
+    int ordered_blocks = 1;
     int64_t spk_cap = 0;
     int64_t steps_done = 0;
 
@@ -300,8 +305,14 @@ mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
             if (kind == 0) {
                 mmk::DeliverArgs da = net->da;
                 da.step_offset = j;
-                if (net->precision == MM_FP64) MM_CKI(net, mmk_launch_deliver(da, net->deliver_blocks, s));
-                else MM_CKI(net, mmk_launch_deliver_fp32c(da, net->deliver_blocks, s));
+                if (net->ordered && net->precision == MM_FP64)
+                    MM_CKI(net, mmk_launch_deliver_ordered(da, net->ordered_blocks, s));
+                else if (net->ordered)
+                    MM_CKI(net, mmk_launch_deliver_ordered_fp32c(da, net->ordered_blocks, s));
+                else if (net->precision == MM_FP64)
+                    MM_CKI(net, mmk_launch_deliver(da, net->deliver_blocks, s));
+                else
+                    MM_CKI(net, mmk_launch_deliver_fp32c(da, net->deliver_blocks, s));
             } else if (net->precision == MM_FP64) {
                 mmk::StepArgs sa = net->sa;
                 sa.step_offset = j;
@@ -415,7 +426,8 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     if (opt->scheme != MM_SCHEME_BE && opt->scheme != MM_SCHEME_CN) return fail(net, MM_EINVAL, "unknown scheme");
     if (opt->detect != MM_DETECT_SOMA && opt->detect != MM_DETECT_SYNAPSE_POINTS)
         return fail(net, MM_EINVAL, "unknown detection mode");
-    if (opt->reserved0 != 0) return fail(net, MM_EINVAL, "mm_options.reserved0 must be 0");
+    if (opt->deterministic_delivery != 0 && opt->deterministic_delivery != 1)
+        return fail(net, MM_EINVAL, "mm_options.deterministic_delivery must be 0 or 1");
     if (opt->schedule == MM_SCHED_COST && !opt->cost) return fail(net, MM_EINVAL, "MM_SCHED_COST needs mm_options.cost");
     if (syn && !(syn->tau_ms > 0.0)) return fail(net, MM_EINVAL, "tau_ms must be > 0");
     if (!chan) return fail(net, MM_EINVAL, "channel parameters must not be NULL");
@@ -538,6 +550,24 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     ZR(net->ring_cnt, (size_t)net->R);
     ZR(net->spk_nrn, (size_t)net->spk_cap);
     ZR(net->spk_comp, (size_t)net->spk_cap);
+    int64_t *din_off = nullptr;
+    int32_t *din_src = nullptr, *din_ds = nullptr;
+    double *din_w = nullptr;
+    float *din_w32 = nullptr;
+    if (opt->deterministic_delivery) {
+        net->ordered = true;
+        net->fired_words = std::max(1, (net->n_src + 31) / 32);
+        ZR(net->fired, (size_t)net->R * (size_t)net->fired_words);
+        UP(din_off, L.in_off.data(), L.in_off.size());
+        UP(din_src, L.in_src.data(), std::max<size_t>(L.in_src.size(), 1));
+        UP(din_ds, L.in_dsteps.data(), std::max<size_t>(L.in_dsteps.size(), 1));
+        if (f64) {
+            UP(din_w, L.in_w.data(), std::max<size_t>(L.in_w.size(), 1));
+        } else {
+            std::vector<float> w32(L.in_w.begin(), L.in_w.end());
+            UP(din_w32, w32.data(), std::max<size_t>(w32.size(), 1));
+        }
+    }
     if (li.points) {
         UP(net->pt_of, L.pt_of.data(), L.pt_of.size());
         UP(net->soma_src, L.soma_src.data(), N);
@@ -629,6 +659,8 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.pt_user_comp = net->pt_user_comp;
         a.soma_src = net->soma_src;
         a.n_pt = li.points ? net->n_src : 0;
+        a.fired = net->fired;
+        a.fired_words = net->fired_words;
         a.ctl = net->ctl;
         a.smem_comps = smem_comps;
         a.smem_segs = smem_segs;
@@ -693,6 +725,8 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.pt_user_comp = net->pt_user_comp;
         a.soma_src = net->soma_src;
         a.n_pt = li.points ? net->n_src : 0;
+        a.fired = net->fired;
+        a.fired_words = net->fired_words;
         a.ctl = net->ctl;
         a.smem_comps = smem_comps;
         a.smem_segs = smem_segs;
@@ -745,6 +779,14 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     d.ctl = net->ctl;
     d.gsyn32 = net->gsyn32;
     d.out_w32 = dout_w32;
+    d.in_off = din_off;
+    d.in_src = din_src;
+    d.in_dsteps = din_ds;
+    d.in_w = din_w;
+    d.in_w32 = din_w32;
+    d.fired = net->fired;
+    d.fired_words = net->fired_words;
+    d.nsite = net->nsite;
 
     // FP32c carves each item's shared memory from its own sizes (the largest
     // per-item need of the class); FP64 uses one carve for all items
@@ -826,6 +868,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         net->info.sites[cls] += L.groups[gi].nsite;
     }
     net->deliver_blocks = std::max(1, 2 * sms);
+    net->ordered_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((net->nsite + 255) / 256, 16 * (int64_t)sms));
     MM_CK(net, cudaStreamSynchronize(net->stream));
     return MM_OK;
 }
@@ -1080,6 +1123,7 @@ std::vector<std::pair<void *, size_t>> ckpt_regions(mm_net *net)
     r.push_back({net->ctl, sizeof(mmk::DevCtl)});
     r.push_back({net->spk_nrn, (size_t)net->spk_cap * sizeof(int32_t)});
     r.push_back({net->spk_comp, (size_t)net->spk_cap * sizeof(int32_t)});
+    if (net->fired) r.push_back({net->fired, (size_t)net->R * (size_t)net->fired_words * sizeof(uint32_t)});
     r.push_back({net->spk_t, (size_t)net->spk_cap * sizeof(double)});
     return r;
 }

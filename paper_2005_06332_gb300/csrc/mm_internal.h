@@ -176,7 +176,9 @@ struct StepArgs {
     const int32_t *pt_user_comp;
     const int32_t *soma_src;          // source id of each internal neuron's soma point, -1: none
     int32_t n_pt;
-    int32_t pad_pt;
+    int32_t fired_words;              // deterministic delivery: 32-bit words per step slot of `fired`
+    uint32_t *fired;                  // deterministic delivery: [R * fired_words] bit per source that
+                                      // fired in each step slot (nullptr otherwise)
     DevCtl *ctl;
     int32_t smem_comps, smem_segs;    // shared-memory capacity of one block (FP64)
     double gNa, gK, gL, ENa, EK, EL;
@@ -245,7 +247,8 @@ struct StepArgs32 {
     const int32_t *pt_user_comp;
     const int32_t *soma_src;
     int32_t n_pt;
-    int32_t pad_pt;
+    int32_t fired_words;              // deterministic delivery, as in StepArgs
+    uint32_t *fired;
     DevCtl *ctl;
     int32_t smem_comps, smem_segs;
     float gNa, gK, gL;
@@ -295,6 +298,7 @@ __device__ __forceinline__ void record_spike(const A &a, int src, int user_nrn, 
         atomicOr(&a.ctl->err, MMK_ERR_OVERFLOW);
     }
     a.ring_nrn[(long long)slot * a.N + p0 + rank] = src;
+    if (a.fired) atomicOr(&a.fired[(long long)slot * a.fired_words + (src >> 5)], 1u << (src & 31));
 }
 
 // An upward crossing of the threshold between V^n = v0 and V^{n+1} = v1 at
@@ -326,6 +330,17 @@ struct DeliverArgs {
     const int32_t *dclass;            // distinct delays (steps), ascending
     int32_t n_dclass;
     int32_t lanes_per_src;            // lanes that scatter one spike's synapses (1, 2, 4, ..., 32)
+    // deterministic delivery: the incoming synapses of each site in
+    // ascending synapse id (source id, delay in steps, weight) and the ring
+    // of per-step bitmasks of the sources that fired
+    const int64_t *in_off;            // [nsite + 1]
+    const int32_t *in_src;
+    const int32_t *in_dsteps;
+    const double *in_w;               // FP64 weights
+    const float *in_w32;              // FP32c weights
+    uint32_t *fired;                  // [R * fired_words]
+    int32_t fired_words;
+    int64_t nsite;
     int32_t step_offset;
     double *gsyn;
     DevCtl *ctl;
@@ -363,6 +378,8 @@ int mmk_launch_giant_assemble(const mmk::StepArgs32 &a, int chunk_blocks, void *
 int mmk_launch_giant_update(const mmk::StepArgs32 &a, int chunk_blocks, void *stream);
 int mmk_giant_chunk();
 int mmk_launch_deliver_fp32c(const mmk::DeliverArgs &a, int blocks, void *stream);
+int mmk_launch_deliver_ordered(const mmk::DeliverArgs &a, int blocks, void *stream);
+int mmk_launch_deliver_ordered_fp32c(const mmk::DeliverArgs &a, int blocks, void *stream);
 int mmk_launch_vq_to_f64(const int32_t *vq, double *dst, int64_t n, void *stream);
 int mmk_launch_gq_to_f64(const uint32_t *q, double *dst, int64_t n, void *stream);
 int mmk_launch_scatter_f32_to_f64(const float *src, const int64_t *idx, double *dst, int64_t n, void *stream);

@@ -141,6 +141,43 @@ __global__ void __launch_bounds__(256) deliver_kernel(DeliverArgs a)
     }
 }
 
+// Deterministic delivery (mm_options.deterministic_delivery): each site adds
+// the weights of its synapses whose source fired round(delay/dt) + 1 steps
+// ago, in ascending synapse id (the oracle's order), one thread per site;
+// also the per-step resets of the work queues, of this step's spike-ring
+// count and of this step's slot of the fired bitmasks (last written R steps
+// ago, all of whose events are delivered).
+__global__ void __launch_bounds__(256) deliver_ordered_kernel(DeliverArgs a)
+{
+    const long long n = (long long)a.ctl->step_base + a.step_offset;
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long nt = (long long)gridDim.x * blockDim.x;
+    if (gt == 0) {
+        a.ctl->queue_head = 0u;
+        a.ctl->giant_head = 0u;
+        a.ctl->big_head = 0u;
+        a.ring_cnt[n % a.R] = 0;
+    }
+    uint32_t *slot = a.fired + (n % a.R) * a.fired_words;
+    for (long long w = gt; w < a.fired_words; w += nt) slot[w] = 0u;
+    for (long long st = gt; st < a.nsite; st += nt) {
+        const long long e0 = a.in_off[st], e1 = a.in_off[st + 1];
+        if (e0 == e1) continue;
+        double g = a.gsyn[st];
+        bool hit = false;
+        for (long long e = e0; e < e1; ++e) {
+            const long long m = n - 1 - a.in_dsteps[e];
+            if (m < 0) continue;
+            const int src = a.in_src[e];
+            if ((a.fired[(m % a.R) * a.fired_words + (src >> 5)] >> (src & 31)) & 1u) {
+                g += a.in_w[e];
+                hit = true;
+            }
+        }
+        if (hit) a.gsyn[st] = g;
+    }
+}
+
 // ------------------------------------------------------------ FP64 step
 
 template <int NT>
@@ -360,6 +397,12 @@ int mmk_launch_deliver(const DeliverArgs &a, int blocks, void *stream)
 {
     if (a.n_dclass > kMaxDClass) return (int)cudaErrorInvalidValue;
     deliver_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
+    return (int)cudaGetLastError();
+}
+
+int mmk_launch_deliver_ordered(const DeliverArgs &a, int blocks, void *stream)
+{
+    deliver_ordered_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
     return (int)cudaGetLastError();
 }
 

@@ -129,6 +129,40 @@ __global__ void __launch_bounds__(256) deliver_fp32c_kernel(DeliverArgs a)
     }
 }
 
+// Deterministic delivery, FP32c conductances (as deliver_ordered_kernel of
+// the FP64 path: each site adds its arrived weights in ascending synapse
+// id, one thread per site, plus the per-step resets).
+__global__ void __launch_bounds__(256) deliver_ordered_fp32c_kernel(DeliverArgs a)
+{
+    const long long n = (long long)a.ctl->step_base + a.step_offset;
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long nt = (long long)gridDim.x * blockDim.x;
+    if (gt == 0) {
+        a.ctl->queue_head = 0u;
+        a.ctl->giant_head = 0u;
+        a.ctl->big_head = 0u;
+        a.ring_cnt[n % a.R] = 0;
+    }
+    uint32_t *slot = a.fired + (n % a.R) * a.fired_words;
+    for (long long w = gt; w < a.fired_words; w += nt) slot[w] = 0u;
+    for (long long st = gt; st < a.nsite; st += nt) {
+        const long long e0 = a.in_off[st], e1 = a.in_off[st + 1];
+        if (e0 == e1) continue;
+        float g = a.gsyn32[st];
+        bool hit = false;
+        for (long long e = e0; e < e1; ++e) {
+            const long long m = n - 1 - a.in_dsteps[e];
+            if (m < 0) continue;
+            const int src = a.in_src[e];
+            if ((a.fired[(m % a.R) * a.fired_words + (src >> 5)] >> (src & 31)) & 1u) {
+                g += a.in_w32[e];
+                hit = true;
+            }
+        }
+        if (hit) a.gsyn32[st] = g;
+    }
+}
+
 // ------------------------------------------------------------ FP32c step
 
 __device__ __forceinline__ float rcp_approx(float x)
@@ -1000,6 +1034,12 @@ int mmk_launch_deliver_fp32c(const DeliverArgs &a, int blocks, void *stream)
 {
     if (a.n_dclass > kMaxDClass32) return (int)cudaErrorInvalidValue;
     deliver_fp32c_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
+    return (int)cudaGetLastError();
+}
+
+int mmk_launch_deliver_ordered_fp32c(const DeliverArgs &a, int blocks, void *stream)
+{
+    deliver_ordered_fp32c_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
     return (int)cudaGetLastError();
 }
 

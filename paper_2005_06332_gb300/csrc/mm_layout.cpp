@@ -792,6 +792,28 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
         L.out_dsteps[(size_t)q] = dsteps[(size_t)s];
         L.out_w[(size_t)q] = in.w[s];
     }
+    // 4d. incoming synapses of each site, ascending synapse id
+    {
+        const size_t nsite = L.site_comp.size();
+        std::vector<int32_t> tsite((size_t)in.S);
+        L.in_off.assign(nsite + 1, 0);
+        for (int64_t s = 0; s < in.S; ++s) {
+            const int64_t ic = L.user2int[(size_t)(in.comp_offset[in.dst[s]] + in.dcomp[s])];
+            tsite[(size_t)s] = site_of[(size_t)ic];
+            L.in_off[(size_t)tsite[(size_t)s] + 1]++;
+        }
+        for (size_t k = 0; k < nsite; ++k) L.in_off[k + 1] += L.in_off[k];
+        L.in_src.resize((size_t)in.S);
+        L.in_dsteps.resize((size_t)in.S);
+        L.in_w.resize((size_t)in.S);
+        std::vector<int64_t> fill(L.in_off.begin(), L.in_off.end() - 1);
+        for (int64_t s = 0; s < in.S; ++s) {
+            const int64_t q = fill[(size_t)tsite[(size_t)s]]++;
+            L.in_src[(size_t)q] = src_id[(size_t)s];
+            L.in_dsteps[(size_t)q] = dsteps[(size_t)s];
+            L.in_w[(size_t)q] = in.w[s];
+        }
+    }
     return "";
 }
 

@@ -76,6 +76,11 @@ struct Layout {
     std::vector<int32_t> out_site, out_dsteps;
     std::vector<double> out_w;
     std::vector<int32_t> dclass;        // distinct delays in steps, ascending
+    // incoming synapses of each site in ascending synapse id (deterministic
+    // delivery): source id, delay in steps, weight
+    std::vector<int64_t> in_off;        // [nsite+1]
+    std::vector<int32_t> in_src, in_dsteps;
+    std::vector<double> in_w;
     int32_t R = 2;                      // spike ring depth (steps)
     double f_syn = 0.0;                 // fraction of compartments with a synapse
 };

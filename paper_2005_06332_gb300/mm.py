@@ -58,7 +58,8 @@ class Allocator(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("schedule", C.c_int32), ("graph_steps", C.c_int32),
                 ("block_threads", C.c_int32), ("group_comps", C.c_int32), ("device", C.c_int32),
-                ("time_items", C.c_int32), ("scheme", C.c_int32), ("detect", C.c_int32), ("reserved0", C.c_int32),
+                ("time_items", C.c_int32), ("scheme", C.c_int32), ("detect", C.c_int32),
+                ("deterministic_delivery", C.c_int32),
                 ("dt_ms", C.c_double), ("spike_capacity", C.c_int64), ("cuda_stream", C.c_void_p),
                 ("cost", C.POINTER(C.c_float)), ("allocator", Allocator)]
 
@@ -373,7 +374,7 @@ class Network:
     def __init__(self, net, precision: str = "fp64", cost: Optional[np.ndarray] = None, graph_steps: int = 40,
                  block_threads: int = 0, group_comps: int = 0, spike_capacity: int = 0, device: int = 0,
                  stream=None, torch_alloc: bool = True, time_items: bool = False, scheme: str = "be",
-                 detect: str = "soma"):
+                 detect: str = "soma", deterministic: bool = False):
         L = load()
         self._L = L
         self._h = C.c_void_p()
@@ -395,6 +396,7 @@ class Network:
         opt.time_items = 1 if time_items else 0
         opt.scheme = SCHEMES[scheme]
         opt.detect = DETECT[detect]
+        opt.deterministic_delivery = 1 if deterministic else 0
         # the library's automatic spike-buffer size (mm_options.spike_capacity)
         if spike_capacity > 0:
             self._spk_cap = int(spike_capacity)
