@@ -357,6 +357,32 @@ mm_status mm_mlp_predict(mm_mlp *mlp, const float *X, int64_t n, float *out);
 
 void mm_mlp_destroy(mm_mlp *mlp);
 
+/* The learned work-queue order, end to end (Sec. 4's priority(size)
+ * ordering with a learned key): from the network's inputs, time n_timed
+ * neurons drawn from seed (each its own work item, MM_FP32C, `steps` steps,
+ * no synapses, mm_read_neuron_times), train a fresh MLP (mm_mlp_train,
+ * `epochs` Adam steps at lr) on 80 % of them to predict log time from the
+ * morphology features, and write exp(prediction) for every neuron into
+ * cost [cap >= n_neurons] (user neuron order): the key for
+ * mm_options.cost with MM_SCHED_COST.  A network's layout is fixed when it
+ * is created, so the costs serve the next mm_create_network.
+ * opt: device, stream, allocator and dt_ms are used (the rest is ignored);
+ * report (may be NULL) receives the held-out R^2 of log time and the last
+ * training loss.  Synchronises.
+ * Errors: MM_EINVAL (bad arguments or morphology, n_timed < 10, steps < 1,
+ * epochs < 1, lr <= 0), MM_ENOMEM, MM_ECUDA. */
+typedef struct {
+    int32_t n_timed;        /* neurons timed (min(n_timed, n_neurons)) */
+    int32_t n_holdout;      /* of which held out of the training */
+    double r2_holdout;      /* R^2 of the predicted log time on the held-out neurons */
+    double final_loss;      /* standardised MSE before the last Adam step */
+    double mean_time_us;    /* mean measured solve time per step of the timed neurons */
+} mm_schedule_report;
+
+mm_status mm_train_schedule(const mm_morphologies *morph, const mm_channel_params *chan, const double *stim_nA,
+                            const mm_options *opt, int32_t n_timed, int32_t steps, int32_t epochs, float lr,
+                            uint64_t seed, float *cost, int64_t cap, mm_schedule_report *report);
+
 /* Launch configuration chosen for the per-step kernel. */
 typedef struct {
     int32_t work_items;        /* neuron groups handed out by the device queue */

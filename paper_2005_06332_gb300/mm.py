@@ -113,6 +113,10 @@ def load(build_if_missing: bool = False):
         L.mm_read_spikes.argtypes = [net_p, P(C.c_int32), P(C.c_double), C.c_int64, P(C.c_int64)]
         L.mm_read_spike_points.argtypes = [net_p, P(C.c_int32), P(C.c_int32), P(C.c_double), C.c_int64,
                                            P(C.c_int64)]
+        L.mm_train_schedule.argtypes = [P(Morphologies), P(ChannelParams), P(C.c_double), P(Options), C.c_int32,
+                                        C.c_int32, C.c_int32, C.c_float, C.c_uint64, P(C.c_float), C.c_int64,
+                                        C.c_void_p]
+        L.mm_train_schedule.restype = C.c_int
         L.mm_set_stimulus.argtypes = [net_p, P(C.c_double), C.c_int64]
         L.mm_get_step.argtypes = [net_p, P(C.c_int64)]
         L.mm_save_state.argtypes = [net_p, C.c_void_p, C.c_size_t, P(C.c_size_t)]
@@ -324,6 +328,36 @@ def _marshal(net):
                    _ptr(a["w"], C.c_double), _ptr(a["dl"], C.c_double), p["tau_syn"], p["e_syn"],
                    _ptr(a["scomp"], C.c_int32) if a["scomp"] is not None else None)
     return a, morph, chan, syn
+
+
+class ScheduleReport(C.Structure):
+    _fields_ = [("n_timed", C.c_int32), ("n_holdout", C.c_int32), ("r2_holdout", C.c_double),
+                ("final_loss", C.c_double), ("mean_time_us", C.c_double)]
+
+
+def train_schedule(net, n_timed: int = 5000, steps: int = 40, epochs: int = 600, lr: float = 3e-3, seed: int = 0,
+                   device: int = 0, stream=None) -> dict:
+    """mm_train_schedule on a netgen.Network: the learned per-neuron cost
+    (for Network(cost=...)) and the report."""
+    L = load()
+    a, morph, chan, _syn = _marshal(net)
+    opt = Options()
+    L.mm_default_options(C.byref(opt))
+    opt.device = device
+    opt.dt_ms = float(net.dt)
+    if stream is not None:
+        opt.cuda_stream = C.c_void_p(int(stream))
+    alloc = TorchAllocator(device)
+    opt.allocator = alloc.struct()
+    cost = np.empty(net.n_neurons, np.float32)
+    rep = ScheduleReport()
+    st = L.mm_train_schedule(C.byref(morph), C.byref(chan), _ptr(a["stim"], C.c_double), C.byref(opt),
+                             int(n_timed), int(steps), int(epochs), float(lr), C.c_uint64(seed),
+                             _ptr(cost, C.c_float), cost.size, C.byref(rep))
+    if st != MM_OK:
+        raise MMError(st, "mm_train_schedule failed")
+    return {"cost": cost, "n_timed": rep.n_timed, "n_holdout": rep.n_holdout, "r2_holdout": rep.r2_holdout,
+            "final_loss": rep.final_loss, "mean_time_us": rep.mean_time_us}
 
 
 class TunePoint(C.Structure):

@@ -86,3 +86,29 @@ def test_learned_costs_predict_measured_solve_times():
     assert r["cost"].shape == (net.n_neurons,)
     assert np.all(r["time_us"] > 0)
     assert r["r2_holdout"] is not None and r["r2_holdout"] > 0.5, r
+
+
+def test_native_train_schedule_learns_solve_times():
+    """mm_train_schedule, the same pipeline as one native call: costs for
+    every neuron, positive and finite, ordering the neurons like their
+    measured solve times (held-out R^2 of log time) and, for this size
+    distribution, nearly like their sizes; a network built with them runs."""
+    net = netgen.make_config("lognormal100k", n_neurons=1500, syn_per_neuron=10)
+    r = mm.train_schedule(net, n_timed=1200, steps=30, epochs=500, seed=3)
+    c = r["cost"]
+    assert c.shape == (net.n_neurons,) and np.all(np.isfinite(c)) and np.all(c > 0)
+    assert r["n_timed"] == 1200 and r["n_holdout"] == 240
+    assert r["r2_holdout"] > 0.5, r
+    rank = lambda x: np.argsort(np.argsort(x))
+    rho = np.corrcoef(rank(c), rank(net.sizes()))[0, 1]
+    assert rho > 0.8, rho
+    with mm.Network(net, precision="fp32c", cost=c) as g:
+        g.step(20)
+        assert np.all(np.isfinite(g.read_voltages()))
+
+
+def test_native_train_schedule_rejects_bad_arguments():
+    net = netgen.make_network(20, size_dist=("mono", 30), syn_per_neuron=0, seed=4)
+    with pytest.raises(mm.MMError) as e:
+        mm.train_schedule(net, n_timed=5)
+    assert e.value.status == mm.MM_EINVAL
