@@ -60,9 +60,9 @@ KERNEL_BYTES_FP32C = {"step": (40.0, 12.0), "big": (40.0, 12.0), "giant": (40.0,
 KERNEL_SOURCES = ("mm_kernels_fp32c.cu", "mm_fp32c_math.h", "mm_internal.h", "mm_tma.h")
 PROFILED = {
     ("multi10k", "fp32c", "step", "soma"): {
-        "sha256": "a43721536f41c3fa57b73f217fb86682b6b637d84332a3e672e620f4a9709336",
-        "dram_bytes": 298258432 + 124148480,
-        "warp_instructions": 350060923,
+        "sha256": "be1015ab0833dee5de0afa9af58ab0b5f1968fe65f83e3d04d589f294fd3a729",
+        "dram_bytes": 298201600 + 123973888,
+        "warp_instructions": 350648274,
     },
 }
 
