@@ -4,7 +4,7 @@ The FP32c step keeps V and the gates in fixed point and computes every
 increment in FP32.  Its bar: max |dV| <= 1e-3 mV and identical spike trains
 (same neurons, same steps) against the FP64 oracle.  The accuracy report at
 the end measures max |dV| and the spike-time shift (in dt) per workload and
-writes them to gpurun_out/accuracy_fp32c.json when that folder exists.
+writes them to $MM_REPORT_DIR/accuracy_fp32c.json when that variable names a folder.
 """
 import json
 import os
@@ -219,7 +219,7 @@ def test_fp32c_accuracy_report():
     rows = [_report("mono64 (64 x 255 compartments), 100 ms", netgen.make_config("mono64"), 4000, 1),
             _report("multi10k distribution, 1000-neuron sample, 100 ms",
                     netgen.make_config("multi10k_fp32c", n_neurons=1000), 4000, 10)]
-    out = os.path.join(ROOT, "gpurun_out")
+    out = os.environ.get("MM_REPORT_DIR", "")
     if os.path.isdir(out):
         with open(os.path.join(out, "accuracy_fp32c.json"), "w") as f:
             json.dump(rows, f, indent=1)
