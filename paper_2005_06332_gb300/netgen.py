@@ -231,7 +231,8 @@ def make_network(
 ) -> Network:
     """Draw a network.
 
-    p_branch: float, or ("uniform", lo, hi) drawn per neuron.
+    p_branch: float, ("uniform", lo, hi) drawn per neuron, or ("choice", p1,
+               p2, ...): each neuron one of the listed values, uniformly.
     mono_tree: every neuron shares one tree and one set of cylinder sizes
                (the paper's mono-morphology case, Sec. 3).
     giants:    extra neurons of ``giant_size`` compartments appended last.
@@ -250,9 +251,13 @@ def make_network(
     C = int(off[-1])
 
     if isinstance(p_branch, tuple):
-        if p_branch[0] != "uniform":
+        if p_branch[0] == "uniform":
+            pb = p_branch[1] + rng.random(n_neurons) * (p_branch[2] - p_branch[1])
+        elif p_branch[0] == "choice":
+            vals = np.asarray(p_branch[1:], dtype=np.float64)
+            pb = vals[np.minimum((rng.random(n_neurons) * len(vals)).astype(np.int64), len(vals) - 1)]
+        else:
             raise ValueError(f"unknown branch-probability distribution {p_branch!r}")
-        pb = p_branch[1] + rng.random(n_neurons) * (p_branch[2] - p_branch[1])
     else:
         pb = np.full(n_neurons, float(p_branch))
     if giants:
@@ -340,6 +345,12 @@ CONFIGS = {
     "paper_fisher": dict(
         n_neurons=10_000, size_dist=("fisher", 10, 40, 300, 10, 5000), p_branch=0.1, syn_per_neuron=100,
         delay_ms=("const", 1.0), t_stop=50.0, seed_index=7, precision="fp32c"),
+    # Neurons whose cost is not their size: log-uniform sizes, half of them
+    # unbranched chains (one long serial sweep), half bushy trees (branch
+    # probability 0.5, short paths), FP32c, 100 synapses per neuron, 50 ms
+    "shapes10k": dict(
+        n_neurons=10_000, size_dist=("loguniform", 200, 3000), p_branch=("choice", 0.0, 0.5),
+        syn_per_neuron=100, delay_ms=("const", 1.0), t_stop=50.0, seed_index=8, precision="fp32c"),
     "mixed200k": dict(  # 200k lognormal(1000, 1.0) + 64 giants of 1e5 compartments, 20 ms
         n_neurons=200_000, size_dist=("lognormal", 1000, 1.0, 20, 20000), p_branch=0.1,
         syn_per_neuron=1000, delay_ms=("uniform", 1.0, 5.0), giants=64, giant_size=100_000,
