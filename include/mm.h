@@ -5,7 +5,8 @@
  * Each neuron is a tree of cylinder compartments; every time step it
  * updates the membrane voltage of every compartment: Hodgkin-Huxley gating
  * and currents, assembly of the neuron's Hines matrix, the Hines tree solve,
- * synaptic currents, soma spike detection and delayed spike delivery.  The
+ * synaptic currents, spike detection (at the somata, or at the points where
+ * synapses leave) and delayed spike delivery.  The
  * calls follow the paper's statement of the problem (Sec. 2): a network is
  * created from morphologies (compartment trees given by parent arrays),
  * channel parameters and synapses, stepped in time, and its voltages and
