@@ -220,6 +220,15 @@ mm_status mm_read_spikes(mm_net *net, int32_t *neuron, double *t_ms, int64_t cap
 mm_status mm_read_spike_points(mm_net *net, int32_t *neuron, int32_t *comp, double *t_ms, int64_t cap,
                                int64_t *n_out);
 
+/* The per-step outputs of a host loop in one round trip: the soma voltage
+ * of every neuron into soma [soma_cap >= n_neurons] (as
+ * mm_read_soma_voltages) and the spikes detected since the last drain into
+ * neuron, comp (may be NULL), t_ms [cap] with their count in *n_out (as
+ * mm_read_spike_points, same order, same errors).  Synchronises once when
+ * at most 4096 spikes are pending, twice otherwise. */
+mm_status mm_read_outputs(mm_net *net, double *soma, int64_t soma_cap, int32_t *neuron, int32_t *comp,
+                          double *t_ms, int64_t cap, int64_t *n_out);
+
 /* Replace the soma stimulus of every neuron (host array [n], n = n_neurons). */
 mm_status mm_set_stimulus(mm_net *net, const double *stim_nA, int64_t n);
 

@@ -1003,28 +1003,38 @@ mm_status mm_read_soma_voltages(mm_net *net, double *out, int64_t cap)
     return MM_OK;
 }
 
-mm_status mm_read_spike_points(mm_net *net, int32_t *neuron, int32_t *comp, double *t_ms, int64_t cap,
-                               int64_t *n_out)
+namespace {
+constexpr int64_t kSpikePrefetch = 4096;  // spike records copied with the soma voltages
+
+// Drains the spike buffer given the control block snapshot c (taken after
+// the stream synchronised); `pre` records (pre <= c.spk_count) already sit
+// in the pinned buffer at pin_off as times, neurons, compartments.
+mm_status drain_spikes(mm_net *net, mmk::DevCtl c, size_t pin_off, int64_t pre, int32_t *neuron, int32_t *comp,
+                       double *t_ms, int64_t cap, int64_t *n_out)
 {
-    mm_status st = guard(net);
-    if (st != MM_OK) return st;
-    if (!n_out || cap < 0 || (cap > 0 && (!neuron || !t_ms))) return fail(net, MM_EINVAL, "bad spike output arguments");
-    if ((st = check_device(net)) != MM_OK) return st;
-    mmk::DevCtl c = *net->pin_ctl;
+    mm_status st;
     const int64_t held = std::min<int64_t>((int64_t)c.spk_count, net->spk_cap);
     const int32_t *nr = nullptr, *cp = nullptr;
     const double *tt = nullptr;
     if (held) {
-        // one staging area: times, neurons, compartments
+        // times, neurons, compartments; the records not prefetched are copied now
         const size_t bt = (size_t)held * sizeof(double), bi = (size_t)held * sizeof(int32_t);
-        if ((st = pinned(net, bt + 2 * bi)) != MM_OK) return st;
-        MM_CK(net, cudaMemcpyAsync(net->pin, net->spk_t, bt, cudaMemcpyDeviceToHost, net->stream));
-        MM_CK(net, cudaMemcpyAsync(net->pin + bt, net->spk_nrn, bi, cudaMemcpyDeviceToHost, net->stream));
-        MM_CK(net, cudaMemcpyAsync(net->pin + bt + bi, net->spk_comp, bi, cudaMemcpyDeviceToHost, net->stream));
-        MM_CK(net, cudaStreamSynchronize(net->stream));
-        tt = (const double *)net->pin;
-        nr = (const int32_t *)(net->pin + bt);
-        cp = (const int32_t *)(net->pin + bt + bi);
+        if (held > pre) {
+            if ((st = pinned(net, bt + 2 * bi)) != MM_OK) return st;
+            pin_off = 0;
+            MM_CK(net, cudaMemcpyAsync(net->pin, net->spk_t, bt, cudaMemcpyDeviceToHost, net->stream));
+            MM_CK(net, cudaMemcpyAsync(net->pin + bt, net->spk_nrn, bi, cudaMemcpyDeviceToHost, net->stream));
+            MM_CK(net, cudaMemcpyAsync(net->pin + bt + bi, net->spk_comp, bi, cudaMemcpyDeviceToHost, net->stream));
+            MM_CK(net, cudaStreamSynchronize(net->stream));
+            tt = (const double *)net->pin;
+            nr = (const int32_t *)(net->pin + bt);
+            cp = (const int32_t *)(net->pin + bt + bi);
+        } else {
+            const size_t pt = (size_t)pre * sizeof(double), pi = (size_t)pre * sizeof(int32_t);
+            tt = (const double *)(net->pin + pin_off);
+            nr = (const int32_t *)(net->pin + pin_off + pt);
+            cp = (const int32_t *)(net->pin + pin_off + pt + pi);
+        }
     }
     // order by (t, neuron, comp) as two unsigned keys: the bits of t mapped
     // to an order-preserving integer, then neuron and compartment
@@ -1058,6 +1068,44 @@ mm_status mm_read_spike_points(mm_net *net, int32_t *neuron, int32_t *comp, doub
     if (overflow) return fail(net, MM_EOVERFLOW, "spike buffer overflowed; raise mm_options.spike_capacity or read more often");
     if (w < held) return fail(net, MM_EOVERFLOW, "caller's spike arrays are smaller than the spike count");
     return MM_OK;
+}
+}  // namespace
+
+mm_status mm_read_spike_points(mm_net *net, int32_t *neuron, int32_t *comp, double *t_ms, int64_t cap,
+                               int64_t *n_out)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    if (!n_out || cap < 0 || (cap > 0 && (!neuron || !t_ms))) return fail(net, MM_EINVAL, "bad spike output arguments");
+    if ((st = check_device(net)) != MM_OK) return st;
+    return drain_spikes(net, *net->pin_ctl, 0, 0, neuron, comp, t_ms, cap, n_out);
+}
+
+mm_status mm_read_outputs(mm_net *net, double *soma, int64_t soma_cap, int32_t *neuron, int32_t *comp,
+                          double *t_ms, int64_t cap, int64_t *n_out)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    if (!soma || soma_cap < net->N) return fail(net, MM_EINVAL, "output buffer too small");
+    if (!n_out || cap < 0 || (cap > 0 && (!neuron || !t_ms))) return fail(net, MM_EINVAL, "bad spike output arguments");
+    // one batch: soma voltages, the first records of the spike buffer, the
+    // control block; one synchronisation
+    const size_t bs = (size_t)net->N * sizeof(double);
+    const int64_t pre = std::min<int64_t>(kSpikePrefetch, net->spk_cap);
+    const size_t soff = (bs + 15) / 16 * 16;
+    const size_t pt = (size_t)pre * sizeof(double), pi = (size_t)pre * sizeof(int32_t);
+    if ((st = pinned(net, soff + pt + 2 * pi)) != MM_OK) return st;
+    if (net->precision == MM_FP64)
+        MM_CKI(net, mmk_launch_gather_f64(net->V, net->soma_of_user, net->scratch, net->N, net->stream));
+    else
+        MM_CKI(net, mmk_launch_gather_f64(net->Vsoma, net->internal_of64, net->scratch, net->N, net->stream));
+    MM_CK(net, cudaMemcpyAsync(net->pin, net->scratch, bs, cudaMemcpyDeviceToHost, net->stream));
+    MM_CK(net, cudaMemcpyAsync(net->pin + soff, net->spk_t, pt, cudaMemcpyDeviceToHost, net->stream));
+    MM_CK(net, cudaMemcpyAsync(net->pin + soff + pt, net->spk_nrn, pi, cudaMemcpyDeviceToHost, net->stream));
+    MM_CK(net, cudaMemcpyAsync(net->pin + soff + pt + pi, net->spk_comp, pi, cudaMemcpyDeviceToHost, net->stream));
+    if ((st = check_device(net)) != MM_OK) return st;
+    std::memcpy(soma, net->pin, bs);
+    return drain_spikes(net, *net->pin_ctl, soff, pre, neuron, comp, t_ms, cap, n_out);
 }
 
 mm_status mm_read_spikes(mm_net *net, int32_t *neuron, double *t_ms, int64_t cap, int64_t *n_out)

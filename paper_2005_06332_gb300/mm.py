@@ -113,6 +113,9 @@ def load(build_if_missing: bool = False):
         L.mm_read_spikes.argtypes = [net_p, P(C.c_int32), P(C.c_double), C.c_int64, P(C.c_int64)]
         L.mm_read_spike_points.argtypes = [net_p, P(C.c_int32), P(C.c_int32), P(C.c_double), C.c_int64,
                                            P(C.c_int64)]
+        L.mm_read_outputs.argtypes = [net_p, P(C.c_double), C.c_int64, P(C.c_int32), P(C.c_int32), P(C.c_double),
+                                      C.c_int64, P(C.c_int64)]
+        L.mm_read_outputs.restype = C.c_int
         L.mm_train_schedule.argtypes = [P(Morphologies), P(ChannelParams), P(C.c_double), P(Options), C.c_int32,
                                         C.c_int32, C.c_int32, C.c_float, C.c_uint64, P(C.c_float), C.c_int64,
                                         C.c_void_p]
@@ -525,6 +528,23 @@ class Network:
                                           cap, C.byref(n))
         self._check(st, "mm_read_spike_points")
         return nr[:n.value].copy(), cp[:n.value].copy(), tt[:n.value].copy()
+
+    @property
+    def spike_capacity(self) -> int:
+        """Spike records the device buffer holds between two drains."""
+        return self._spk_cap
+
+    def read_outputs(self, soma: Optional[np.ndarray] = None):
+        """One round trip per step: the soma voltages and the spikes drained
+        since the last call, (soma, (neuron, compartment, t_ms))."""
+        if soma is None:
+            soma = np.empty(self.n_neurons, np.float64)
+        nr, cp, tt, cap = self._spike_arrays(None)
+        n = C.c_int64()
+        st = self._L.mm_read_outputs(self._h, _ptr(soma, C.c_double), soma.size, _ptr(nr, C.c_int32),
+                                     _ptr(cp, C.c_int32), _ptr(tt, C.c_double), cap, C.byref(n))
+        self._check(st, "mm_read_outputs")
+        return soma, (nr[:n.value].copy(), cp[:n.value].copy(), tt[:n.value].copy())
 
     def read_spikes(self, cap: Optional[int] = None, allow_overflow: bool = False):
         """(neuron, t_ms) drained since the last call, ordered by (t, neuron)."""

@@ -156,3 +156,27 @@ def test_source_compartment_out_of_range_is_rejected():
     with pytest.raises(mm.MMError) as e:
         mm.Network(net, precision="fp32c", detect="points")
     assert e.value.status == mm.MM_EINVAL
+
+
+def test_read_outputs_matches_the_separate_reads():
+    """mm_read_outputs (soma voltages and the spike drain in one round trip,
+    with more pending spikes than it prefetches) gives what
+    mm_read_soma_voltages and mm_read_spike_points give."""
+    net = netgen.make_network(200, size_dist=("loguniform", 20, 300), p_branch=0.1, syn_per_neuron=60, seed=47,
+                              stim_nA=(0.5, 0.9), src_points=True)
+    steps = 400
+    with mm.Network(net, precision="fp32c", detect="points", deterministic=True) as a, \
+            mm.Network(net, precision="fp32c", detect="points", deterministic=True) as b:
+        seen = 0
+        for k in range(steps // 80):
+            a.step(80)
+            b.step(80)
+            soma_a, (na, ca, ta) = a.read_outputs()
+            soma_b = b.read_soma()
+            nb, cb, tb = b.read_spike_points()
+            np.testing.assert_array_equal(soma_a, soma_b)
+            np.testing.assert_array_equal(na, nb)
+            np.testing.assert_array_equal(ca, cb)
+            np.testing.assert_array_equal(ta, tb)
+            seen = max(seen, len(na))
+    assert seen > 4096          # the drain went beyond the prefetched records at least once
