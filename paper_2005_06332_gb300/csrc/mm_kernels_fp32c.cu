@@ -200,6 +200,10 @@ constexpr int kGateChunk = 64;
 // together before the step's dependent chain).
 constexpr int kSweepChunk = 8;
 
+// Paths of at least this many compartments are swept by a whole warp
+// (chunks per lane combined by warp scans) instead of by one lane.
+constexpr int kWarpPath = 96;
+
 __device__ __forceinline__ void gate_chunks(const StepArgs32 &a, int64_t pc0, int pn, int *next, int lane)
 {
     for (;;) {
@@ -417,10 +421,39 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         //    their slots, summed in fold-list order once the level is done.
         //    The elimination leaves the substitution coefficients
         //    x_j = f_j x_{j-1} + c_j.
+        // the head of path pi once its interior is eliminated (dh, rh: the
+        // head's diagonal and rhs): for the path from a soma its dV, else the
+        // head link to the parent compartment assembled here (gh the
+        // implicit share of its coupling, ge all of it) and the head
+        // eliminated into the parent
+        auto eliminate_head = [&](int pi, const PathQ &P, float dh, float rh) {
+            const int h = P.head;
+            const float gh = sg[h], vt = svt[pi];
+            if (P.parent < 0) {  // soma: the stimulus, then its dV
+                rh += vt;
+                sy[2 * h + 1] = rh * rcp_approx(dh);
+                return;
+            }
+            const float ge = a.gimp < 1.f ? 2.f * gh : gh;
+            dh += gh;
+            rh = fmaf(ge, vt, rh);
+            const float inv = rcp_approx(dh);
+            const float f = gh * inv;
+            sdr[h] = make_float2(f, rh * inv);
+            const float cd = fmaf(-f, gh, gh), cr = fmaf(f, rh, -ge * vt);
+            if (P.nflag & kPathAlone) {
+                float2 v = sdr[P.parent];
+                v.x += cd;
+                v.y += cr;
+                sdr[P.parent] = v;
+            } else {
+                scd[pi] = cd;
+                scr[pi] = cr;
+            }
+        };
         auto eliminate_path = [&](int pi) {
             const PathQ P = paths[pi];
             const int h = P.head;
-            const float gh = sg[h], vt = svt[pi];
             int j = P.end - 1;
             const float2 v0 = sdr[j];
             float db = v0.x, rb = v0.y;
@@ -451,30 +484,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                     }
                 }
             }
-            if (P.parent < 0) {  // soma: the stimulus, then its dV
-                rh += vt;
-                sy[2 * h + 1] = rh * rcp_approx(dh);
-                return;
-            }
-            // the head link to the parent compartment: assembled here (gh
-            // the implicit share of its coupling, ge all of it), the head
-            // eliminated into the parent
-            const float ge = a.gimp < 1.f ? 2.f * gh : gh;
-            dh += gh;
-            rh = fmaf(ge, vt, rh);
-            const float inv = rcp_approx(dh);
-            const float f = gh * inv;
-            sdr[h] = make_float2(f, rh * inv);
-            const float cd = fmaf(-f, gh, gh), cr = fmaf(f, rh, -ge * vt);
-            if (P.nflag & kPathAlone) {
-                float2 v = sdr[P.parent];
-                v.x += cd;
-                v.y += cr;
-                sdr[P.parent] = v;
-            } else {
-                scd[pi] = cd;
-                scr[pi] = cr;
-            }
+            eliminate_head(pi, P, dh, rh);
         };
         // contributions of the level's paths that share a parent compartment
         // (fold entries e0 .. e1-1); a lane takes the entries that start a run
@@ -504,8 +514,10 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         //    (a path's head needs its parent, on a path of the level
         //    before); the path from a soma runs the FP64 soma accumulator and
         //    the spike test
-        auto substitute_path = [&](int pi) {
-            const PathQ P = paths[pi];
+        // dV of the head of path pi: from its parent's, or for the path from
+        // a soma its own, which also advances the FP64 soma accumulator and
+        // runs the spike test
+        auto substitute_head = [&](int pi, const PathQ &P) -> float {
             const int h = P.head;
             float x;
             const float2 vh = sdr[h];
@@ -525,6 +537,12 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                                      (double)n * a.dt64 + a.dt64 * (a.threshold - v0) / (v1 - v0), n);
                 }
             }
+            return x;
+        };
+        auto substitute_path = [&](int pi) {
+            const PathQ P = paths[pi];
+            const int h = P.head;
+            float x = substitute_head(pi, P);
             const float xh = x;
             // down the path, each compartment's parent is the one before
             // it: x_j = f_j x_{j-1} + c_j with the coefficients the
@@ -549,6 +567,155 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             if (P.parent >= 0) sy[2 * h + 1] = xh;  // read by the next level only
         };
 
+        // Paths of at least kWarpPath compartments are eliminated and
+        // substituted by a whole warp.  The path's interior is cut into 32
+        // chunks, one per lane.  The elimination's diagonal recurrence
+        // d'_{j-1} = d_{j-1} - g_j^2 / d'_j is the action of the 2x2 matrix
+        // [[d_{j-1}, -g_j^2], [1, 0]] on (d', 1) up to scale, and its rhs
+        // recurrence r'_{j-1} = r_{j-1} + (g_j / d'_j) r'_j and the
+        // substitution x_j = f_j x_{j-1} + c_j are affine maps: each lane
+        // composes its chunk, an inclusive warp scan combines the chunks,
+        // and each lane runs the recurrences through its chunk from the
+        // values the chunks before it leave (the same operations as the
+        // serial sweep, started from scanned values).
+        const int lane = tid & 31;
+        auto eliminate_path_warp = [&](int pi) {
+            const PathQ P = paths[pi];
+            const int h = P.head, e = P.end;
+            const int m = e - 1 - h;  // interior elements, t = 0 .. m-1 <-> j = e-1-t
+            const int cs = (m + 31) >> 5;
+            const int t0 = min(lane * cs, m), t1 = min(t0 + cs, m);
+            const float2 leaf = sdr[e - 1];
+            // the chunk's matrix product, rescaled as it goes (only ratios matter)
+            float m00 = 1.f, m01 = 0.f, m10 = 0.f, m11 = 1.f;
+            for (int tt = t0; tt < t1; ++tt) {
+                const int j = e - 1 - tt;
+                const float g = sg[j], g2 = g * g, dn = sdr[j - 1].x;
+                const float n00 = fmaf(dn, m00, -g2 * m10), n01 = fmaf(dn, m01, -g2 * m11);
+                m10 = m00;
+                m11 = m01;
+                const float s = rcp_approx(fabsf(n00) + fabsf(n01));
+                m00 = n00 * s;
+                m01 = n01 * s;
+                m10 *= s;
+                m11 *= s;
+            }
+            for (int off = 1; off < 32; off <<= 1) {
+                const float a00 = __shfl_up_sync(0xFFFFFFFFu, m00, off), a01 = __shfl_up_sync(0xFFFFFFFFu, m01, off);
+                const float a10 = __shfl_up_sync(0xFFFFFFFFu, m10, off), a11 = __shfl_up_sync(0xFFFFFFFFu, m11, off);
+                if (lane >= off) {  // this lane's chunks act after the earlier ones
+                    const float n00 = fmaf(m00, a00, m01 * a10), n01 = fmaf(m00, a01, m01 * a11);
+                    const float n10 = fmaf(m10, a00, m11 * a10), n11 = fmaf(m10, a01, m11 * a11);
+                    const float s = rcp_approx(fabsf(n00) + fabsf(n01) + fabsf(n10) + fabsf(n11));
+                    m00 = n00 * s;
+                    m01 = n01 * s;
+                    m10 = n10 * s;
+                    m11 = n11 * s;
+                }
+            }
+            float e00 = __shfl_up_sync(0xFFFFFFFFu, m00, 1), e01 = __shfl_up_sync(0xFFFFFFFFu, m01, 1);
+            float e10 = __shfl_up_sync(0xFFFFFFFFu, m10, 1), e11 = __shfl_up_sync(0xFFFFFFFFu, m11, 1);
+            if (lane == 0) {
+                e00 = 1.f;
+                e01 = 0.f;
+                e10 = 0.f;
+                e11 = 1.f;
+            }
+            const float db0 = fmaf(e00, leaf.x, e01) / fmaf(e10, leaf.x, e11);
+            // pass 1 (reads only): the diagonal through the chunk and the
+            // chunk's affine map of the rhs recurrence; the element after
+            // the chunk is kept for pass 2, whose writes it may see
+            float db = db0, A = 1.f, B = 0.f;
+            float2 nb = make_float2(0.f, 0.f);
+            for (int tt = t0; tt < t1; ++tt) {
+                const int j = e - 1 - tt;
+                const float g = sg[j];
+                const float2 w = sdr[j - 1];
+                const float inv = rcp_approx(db);
+                const float f = g * inv;
+                A *= f;
+                B = fmaf(f, B, w.y);
+                db = fmaf(-g * g, inv, w.x);
+                nb = w;
+            }
+            for (int off = 1; off < 32; off <<= 1) {
+                const float pa = __shfl_up_sync(0xFFFFFFFFu, A, off), pb = __shfl_up_sync(0xFFFFFFFFu, B, off);
+                if (lane >= off) {
+                    B = fmaf(A, pb, B);
+                    A *= pa;
+                }
+            }
+            float ea = __shfl_up_sync(0xFFFFFFFFu, A, 1), eb = __shfl_up_sync(0xFFFFFFFFu, B, 1);
+            if (lane == 0) {
+                ea = 1.f;
+                eb = 0.f;
+            }
+            // pass 2: the substitution coefficients (f_j, c_j) of the chunk
+            __syncwarp();
+            db = db0;
+            float rb = fmaf(ea, leaf.y, eb);
+            for (int tt = t0; tt < t1; ++tt) {
+                const int j = e - 1 - tt;
+                const float g = sg[j];
+                const float2 w = tt + 1 < t1 ? sdr[j - 1] : nb;
+                const float inv = rcp_approx(db);
+                const float f = g * inv;
+                sdr[j] = make_float2(f, rb * inv);
+                rb = fmaf(f, rb, w.y);
+                db = fmaf(-g * g, inv, w.x);
+            }
+            // the head, from the lane whose chunk ends at it
+            const int lastl = (m - 1) / cs;
+            const float dh = __shfl_sync(0xFFFFFFFFu, db, lastl), rh = __shfl_sync(0xFFFFFFFFu, rb, lastl);
+            __syncwarp();
+            if (lane == 0) eliminate_head(pi, P, dh, rh);
+            __syncwarp();
+        };
+        auto substitute_path_warp = [&](int pi) {
+            const PathQ P = paths[pi];
+            const int h = P.head, e = P.end;
+            float x = 0.f;
+            if (lane == 0) x = substitute_head(pi, P);
+            x = __shfl_sync(0xFFFFFFFFu, x, 0);
+            const int m = e - 1 - h;  // t = 0 .. m-1 <-> j = h+1+t
+            const int cs = (m + 31) >> 5;
+            const int t0 = min(lane * cs, m), t1 = min(t0 + cs, m);
+            float A = 1.f, B = 0.f;
+            for (int tt = t0; tt < t1; ++tt) {
+                const float2 w = sdr[h + 1 + tt];
+                A *= w.x;
+                B = fmaf(w.x, B, w.y);
+            }
+            for (int off = 1; off < 32; off <<= 1) {
+                const float pa = __shfl_up_sync(0xFFFFFFFFu, A, off), pb = __shfl_up_sync(0xFFFFFFFFu, B, off);
+                if (lane >= off) {
+                    B = fmaf(A, pb, B);
+                    A *= pa;
+                }
+            }
+            float ea = __shfl_up_sync(0xFFFFFFFFu, A, 1), eb = __shfl_up_sync(0xFFFFFFFFu, B, 1);
+            if (lane == 0) {
+                ea = 1.f;
+                eb = 0.f;
+            }
+            float xs = fmaf(ea, x, eb);
+            for (int tt = t0; tt < t1; ++tt) {
+                const int j = h + 1 + tt;
+                const float2 w = sdr[j];
+                xs = fmaf(w.x, xs, w.y);
+                sy[2 * j + 1] = xs;
+            }
+            __syncwarp();
+            if (lane == 0 && P.parent >= 0) sy[2 * h + 1] = x;  // read by the next level only
+        };
+        // the number of paths at the start of a level (paths run longest
+        // first) that a whole warp takes
+        auto warp_paths = [&](int pb, int pe) {
+            int nw = 0;
+            while (pb + nw < pe && paths[pb + nw].end - paths[pb + nw].head >= kWarpPath) ++nw;
+            return nw;
+        };
+
         // B from the deepest level up, then F from the soma down; a level's
         // paths go to the team's lanes longest first.  Then gate chunks of
         // the previous item (when timing items, the gates wait until after
@@ -559,7 +726,9 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             const int16_t *mc = mcnt + Nk.loff0;
             for (int l = Nk.nlevel - 1; l >= 0; --l) {
                 const int pb = lo[l], pe = lo[l + 1];
-                for (int pi = pb + tl; pi < pe; pi += TL) eliminate_path(pi);
+                const int nw = warp_paths(pb, pe);
+                for (int q = tl >> 5; q < nw; q += T) eliminate_path_warp(pb + q);
+                for (int pi = pb + nw + tl; pi < pe; pi += TL) eliminate_path(pi);
                 team_sync();
                 if (mc[l] > 0) {
                     fold_shared(pb, pb + mc[l]);
@@ -567,8 +736,10 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                 }
             }
             for (int l = 0; l < Nk.nlevel; ++l) {
-                const int pe = lo[l + 1];
-                for (int pi = lo[l] + tl; pi < pe; pi += TL) substitute_path(pi);
+                const int pb = lo[l], pe = lo[l + 1];
+                const int nw = warp_paths(pb, pe);
+                for (int q = tl >> 5; q < nw; q += T) substitute_path_warp(pb + q);
+                for (int pi = pb + nw + tl; pi < pe; pi += TL) substitute_path(pi);
                 team_sync();
             }
         }
