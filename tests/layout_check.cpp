@@ -11,9 +11,17 @@
 // comparing with the elimination of Algorithm 1 in double over the same
 // parent array.
 //
-// Usage: layout_check <network file> <group_comps> <regular smem limit> <large smem limit>
+// Paths of at least <warp path> compartments (optional 5th argument, 0 =
+// none) are swept as the step kernel's whole warps sweep them: the path cut
+// into 32 chunks, chunk products of the elimination's 2x2 matrices and of the
+// affine rhs and substitution maps combined by inclusive scans round by
+// round, then the serial recurrences through each chunk from the scanned
+// values (the lanes emulated one after another).
+//
+// Usage: layout_check <network file> <group_comps> <regular smem limit> <large smem limit> [warp path]
 // Network file: int32 N | int64 C | int64 comp_offset[N+1] | int32 parent[C].
 // Prints "bad=<violations> maxrel=<largest relative error>"; exit 0 iff bad == 0.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -26,6 +34,125 @@
 using namespace mmk;
 
 namespace {
+
+// Inclusive scan over 32 lanes, round by round as with shuffles (lane k
+// combines with lane k - off); combine(own, earlier) returns the composition.
+template <class V, class F>
+void lane_scan(V *v, F combine)
+{
+    for (int off = 1; off < 32; off <<= 1) {
+        V nv[32];
+        for (int k = 0; k < 32; ++k) nv[k] = k >= off ? combine(v[k], v[k - off]) : v[k];
+        for (int k = 0; k < 32; ++k) v[k] = nv[k];
+    }
+}
+
+struct Mat {
+    float m00, m01, m10, m11;
+};
+struct Aff {
+    float a, b;
+};
+
+// The warp-swept elimination of the interior of the path [h, e): leaves
+// (f_j, c_j) in (sd, sr) for h < j < e and returns the head's (dh, rh).
+void warp_eliminate(int h, int e, std::vector<float> &sd, std::vector<float> &sr, const std::vector<float> &sg,
+                    float *dh, float *rh)
+{
+    const int m = e - 1 - h, cs = (m + 31) / 32;
+    const float leafd = sd[e - 1], leafr = sr[e - 1];
+    Mat M[32];
+    for (int ln = 0; ln < 32; ++ln) {
+        const int t0 = std::min(ln * cs, m), t1 = std::min(t0 + cs, m);
+        Mat q{1.f, 0.f, 0.f, 1.f};
+        for (int tt = t0; tt < t1; ++tt) {
+            const int j = e - 1 - tt;
+            const float g = sg[j], g2 = g * g, dn = sd[j - 1];
+            const float n00 = std::fma(dn, q.m00, -g2 * q.m10), n01 = std::fma(dn, q.m01, -g2 * q.m11);
+            q.m10 = q.m00;
+            q.m11 = q.m01;
+            const float s = 1.f / (std::fabs(n00) + std::fabs(n01));
+            q = {n00 * s, n01 * s, q.m10 * s, q.m11 * s};
+        }
+        M[ln] = q;
+    }
+    lane_scan(M, [](const Mat &o, const Mat &a) {
+        const float n00 = std::fma(o.m00, a.m00, o.m01 * a.m10), n01 = std::fma(o.m00, a.m01, o.m01 * a.m11);
+        const float n10 = std::fma(o.m10, a.m00, o.m11 * a.m10), n11 = std::fma(o.m10, a.m01, o.m11 * a.m11);
+        const float s = 1.f / (std::fabs(n00) + std::fabs(n01) + std::fabs(n10) + std::fabs(n11));
+        return Mat{n00 * s, n01 * s, n10 * s, n11 * s};
+    });
+    float db0[32];
+    Aff F[32];
+    float nbd[32], nbr[32];
+    for (int ln = 0; ln < 32; ++ln) {
+        const Mat x = ln ? M[ln - 1] : Mat{1.f, 0.f, 0.f, 1.f};
+        db0[ln] = std::fma(x.m00, leafd, x.m01) / std::fma(x.m10, leafd, x.m11);
+        const int t0 = std::min(ln * cs, m), t1 = std::min(t0 + cs, m);
+        float db = db0[ln], A = 1.f, B = 0.f;
+        nbd[ln] = nbr[ln] = 0.f;
+        for (int tt = t0; tt < t1; ++tt) {
+            const int j = e - 1 - tt;
+            const float g = sg[j], inv = 1.f / db, f = g * inv;
+            A *= f;
+            B = std::fma(f, B, sr[j - 1]);
+            db = std::fma(-g * g, inv, sd[j - 1]);
+            nbd[ln] = sd[j - 1];
+            nbr[ln] = sr[j - 1];
+        }
+        F[ln] = {A, B};
+    }
+    lane_scan(F, [](const Aff &o, const Aff &a) { return Aff{o.a * a.a, std::fma(o.a, a.b, o.b)}; });
+    const int lastl = (m - 1) / cs;
+    for (int ln = 0; ln < 32; ++ln) {
+        const Aff x = ln ? F[ln - 1] : Aff{1.f, 0.f};
+        const int t0 = std::min(ln * cs, m), t1 = std::min(t0 + cs, m);
+        float db = db0[ln], rb = std::fma(x.a, leafr, x.b);
+        for (int tt = t0; tt < t1; ++tt) {
+            const int j = e - 1 - tt;
+            const float g = sg[j];
+            const float wd = tt + 1 < t1 ? sd[j - 1] : nbd[ln], wr = tt + 1 < t1 ? sr[j - 1] : nbr[ln];
+            const float inv = 1.f / db, f = g * inv;
+            sd[j] = f;
+            sr[j] = rb * inv;
+            rb = std::fma(f, rb, wr);
+            db = std::fma(-g * g, inv, wd);
+        }
+        if (ln == lastl) {
+            *dh = db;
+            *rh = rb;
+        }
+    }
+}
+
+// The warp-swept substitution x_j = f_j x_{j-1} + c_j for h < j < e from the
+// head's x.
+void warp_substitute(int h, int e, float xh, const std::vector<float> &sd, std::vector<float> &sr)
+{
+    const int m = e - 1 - h, cs = (m + 31) / 32;
+    Aff F[32];
+    for (int ln = 0; ln < 32; ++ln) {
+        const int t0 = std::min(ln * cs, m), t1 = std::min(t0 + cs, m);
+        float A = 1.f, B = 0.f;
+        for (int tt = t0; tt < t1; ++tt) {
+            const int j = h + 1 + tt;
+            A *= sd[j];
+            B = std::fma(sd[j], B, sr[j]);
+        }
+        F[ln] = {A, B};
+    }
+    lane_scan(F, [](const Aff &o, const Aff &a) { return Aff{o.a * a.a, std::fma(o.a, a.b, o.b)}; });
+    for (int ln = 0; ln < 32; ++ln) {
+        const Aff x = ln ? F[ln - 1] : Aff{1.f, 0.f};
+        const int t0 = std::min(ln * cs, m), t1 = std::min(t0 + cs, m);
+        float xs = std::fma(x.a, xh, x.b);
+        for (int tt = t0; tt < t1; ++tt) {
+            const int j = h + 1 + tt;
+            xs = std::fma(sd[j], xs, sr[j]);
+            sr[j] = xs;
+        }
+    }
+}
 
 struct Tables {  // an item's tables widened to int
     std::vector<int> nrn;    // 4 per sweep bundle: path0, npath, nlevel, loff0
@@ -109,6 +236,8 @@ int main(int argc, char **argv)
     in.big_smem_limit = std::atoi(argv[4]);
     in.path_items = true;
     in.smem_per_path = 12;
+    const int warp_min = argc > 5 ? std::atoi(argv[5]) : 0;
+    long long nwarp_paths = 0;
     mmh::Layout lay;
     bool invalid = false;
     const std::string err = mmh::build_layout(in, lay, &invalid);
@@ -256,12 +385,17 @@ int main(int argc, char **argv)
                     const int h = H(p);
                     int j = E(p) - 1;
                     float db = sd[j], rb = sr[j];
-                    for (; j > h; --j) {
-                        const float inv = 1.f / db, fj = sg[j] * inv;
-                        sd[j] = fj;
-                        sr[j] = rb * inv;
-                        rb = std::fma(fj, rb, sr[j - 1]);
-                        db = std::fma(-sg[j] * sg[j], inv, sd[j - 1]);
+                    if (warp_min > 0 && E(p) - h >= warp_min) {
+                        warp_eliminate(h, E(p), sd, sr, sg, &db, &rb);
+                        ++nwarp_paths;
+                    } else {
+                        for (; j > h; --j) {
+                            const float inv = 1.f / db, fj = sg[j] * inv;
+                            sd[j] = fj;
+                            sr[j] = rb * inv;
+                            rb = std::fma(fj, rb, sr[j - 1]);
+                            db = std::fma(-sg[j] * sg[j], inv, sd[j - 1]);
+                        }
                     }
                     if (Pa(p) < 0) { sr[h] = rb / db; continue; }
                     db += sg[h];
@@ -286,13 +420,16 @@ int main(int argc, char **argv)
                     const int h = H(p);
                     float xx = Pa(p) >= 0 ? std::fma(sd[h], sr[Pa(p)], sr[h]) : sr[h];
                     sr[h] = xx;
-                    for (int j = h + 1; j < E(p); ++j) { xx = std::fma(sd[j], xx, sr[j]); sr[j] = xx; }
+                    if (warp_min > 0 && E(p) - h >= warp_min)
+                        warp_substitute(h, E(p), xx, sd, sr);
+                    else
+                        for (int j = h + 1; j < E(p); ++j) { xx = std::fma(sd[j], xx, sr[j]); sr[j] = xx; }
                 }
         }
         for (int j = 0; j < G.ncomp; ++j) maxrel = std::max(maxrel, std::fabs(sr[j] - x[j]) / (std::fabs(x[j]) + 1e-3));
     }
     if (gcomps != lay.giant_comps || gpaths != lay.giant_paths || covered != C) ++bad;
-    std::printf("items=%d small=%d large=%d giant=%d bad=%lld maxrel=%.3e\n", nitems, lay.n_small, lay.n_big,
-                nitems - lay.n_small - lay.n_big, bad, maxrel);
+    std::printf("items=%d small=%d large=%d giant=%d warp_paths=%lld bad=%lld maxrel=%.3e\n", nitems, lay.n_small,
+                lay.n_big, nitems - lay.n_small - lay.n_big, nwarp_paths, bad, maxrel);
     return bad ? 1 : 0;
 }
