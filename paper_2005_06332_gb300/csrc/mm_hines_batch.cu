@@ -8,8 +8,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
-
 #include "mm.h"
 
 // Scratch of mm_hines_solve_noalloc: a fixed device array in this library
@@ -21,17 +19,23 @@ static __device__ __align__(256) double g_noalloc_scratch[32 + MM_NOALLOC_MAX_CO
 
 namespace {
 
-// status word: 0 = ok, 1 = a tree violates parent[0] = -1, 0 <= parent[i] < i
-__global__ void hines_batch_kernel(int32_t n_trees, const int64_t *__restrict__ off,
+// status word: 0 = ok, 1 = a tree violates parent[0] = -1, 0 <= parent[i] < i,
+// or its entry range tree_offset[t] .. tree_offset[t+1]-1 is not inside
+// [0, n_comp) (such a tree is skipped before any of its entries is touched)
+__global__ void hines_batch_kernel(int32_t n_trees, int64_t n_comp, const int64_t *__restrict__ off,
                                    const int32_t *__restrict__ parent, const double *__restrict__ a,
                                    const double *__restrict__ b, const double *__restrict__ c,
                                    const double *__restrict__ rhs, double *__restrict__ x,
                                    double *__restrict__ work, int *__restrict__ status)
 {
     for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_trees; t += gridDim.x * blockDim.x) {
-        const int64_t base = off[t];
-        const int64_t n = off[t + 1] - base;
-        if (n <= 0) continue;
+        const int64_t base = off[t], end = off[t + 1];
+        if (base < 0 || end < base || end > n_comp) {
+            atomicOr(status, 1);
+            continue;
+        }
+        const int64_t n = end - base;
+        if (n == 0) continue;
         const int32_t *p = parent + base;
         bool ok = p[0] == -1;
         for (int64_t i = 1; ok && i < n; ++i) ok = p[i] >= 0 && p[i] < i;
@@ -69,7 +73,7 @@ mm_status run_batch(int32_t n_trees, int64_t n_comp, const int64_t *off, const i
         const int threads = 128;
         int blocks = (int)((n_trees + threads - 1) / threads);
         if (blocks > 152 * 16) blocks = 152 * 16;
-        hines_batch_kernel<<<blocks, threads, 0, s>>>(n_trees, off, parent, a, b, c, rhs, x, work, status);
+        hines_batch_kernel<<<blocks, threads, 0, s>>>(n_trees, n_comp, off, parent, a, b, c, rhs, x, work, status);
         if (cudaGetLastError() != cudaSuccess) return MM_ECUDA;
     }
     int h = 0;
@@ -109,33 +113,20 @@ extern "C" mm_status mm_hines_solve(int32_t n_trees, int64_t n_comp, const int64
     return st;
 }
 
-// Device address of g_noalloc_scratch on each device.  In host code the
-// array's name is only a host-side stand-in, so the address is asked for
-// once per device, with that device current, on the first call there.
-static std::mutex g_noalloc_mu;
-static void *g_noalloc_ptr[128];
-
+// The device address of g_noalloc_scratch is looked up on every call, with
+// the caller's device current: in host code the array's name is only a
+// host-side stand-in, and a cached address could outlive the module it
+// points into (a cudaDeviceReset reloads it).  The lookup allocates nothing.
 extern "C" mm_status mm_hines_solve_noalloc(int32_t n_trees, int64_t n_comp, const int64_t *tree_offset,
                                             const int32_t *parent, const double *a, const double *b,
                                             const double *c, const double *rhs, double *x, void *cuda_stream)
 {
     if (!args_ok(n_trees, n_comp, tree_offset, parent, a, b, c, rhs, x)) return MM_EINVAL;
     if (n_comp > MM_NOALLOC_MAX_COMPS) return MM_EINVAL;
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return MM_ECUDA;
-    if (dev >= 128) return MM_ENOTSUP;
     void *base = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-                cudaGetLastError();
-                return MM_ECUDA;
-            }
-            g_noalloc_ptr[dev] = p;
-        }
-        base = g_noalloc_ptr[dev];
+    if (cudaGetSymbolAddress(&base, g_noalloc_scratch) != cudaSuccess || !base) {
+        cudaGetLastError();
+        return MM_ECUDA;
     }
     int *status = (int *)base;                       // cleared by run_batch before the kernel
     double *work = (double *)((char *)base + 256);   // fully written before it is read

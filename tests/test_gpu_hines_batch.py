@@ -52,3 +52,37 @@ def test_batch_solve_rejects_bad_parent():
     with pytest.raises(mm.MMError) as e:
         _gpu(off, par, a, b, c, r)
     assert e.value.status == mm.MM_EINVAL
+
+
+def _raw_call(fn, off, par, a, b, c, r, n_comp):
+    """Call an entry point through the C-ABI with an explicit n_comp (the
+    device buffers hold every entry of the offsets, whatever n_comp says)."""
+    import ctypes as C
+    import torch
+    dev = torch.device("cuda", 0)
+    t = [torch.as_tensor(v, dtype=dt, device=dev)
+         for v, dt in zip((off, par, a, b, c, r), (torch.int64, torch.int32) + (torch.float64,) * 4)]
+    x = torch.full_like(t[5], float("nan"))
+    st = fn(len(off) - 1, int(n_comp), t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr(), t[3].data_ptr(),
+            t[4].data_ptr(), t[5].data_ptr(), x.data_ptr(), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    return st, x.cpu().numpy()
+
+
+def test_batch_solve_rejects_offsets_outside_n_comp():
+    """A tree whose entry range reaches past n_comp (or runs backwards) is
+    rejected with MM_EINVAL before any of its entries is touched; the other
+    trees are still solved."""
+    L = mm.load()
+    off, par, a, b, c, r = _batch(5, 6, 12)
+    st, x = _raw_call(L.mm_hines_solve, off, par, a, b, c, r, off[-1] - 1)
+    assert st == mm.MM_EINVAL
+    for k in range(5):
+        s, e = off[k], off[k + 1]
+        np.testing.assert_allclose(x[s:e], oracle.hines_solve(a[s:e], b[s:e], c[s:e], r[s:e], par[s:e]),
+                                   rtol=1e-12, atol=1e-14)
+    assert np.all(np.isnan(x[off[5]:]))  # the rejected tree was not written
+    bad = off.copy()
+    bad[2], bad[3] = off[3], off[2]  # tree 1 takes in tree 2's root; tree 2 runs backwards
+    st, _ = _raw_call(L.mm_hines_solve, bad, par, a, b, c, r, off[-1])
+    assert st == mm.MM_EINVAL

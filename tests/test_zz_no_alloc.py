@@ -66,3 +66,25 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     t = _device(_inputs(13, 2, 4))
     x = torch.empty_like(t[5])
     assert _call(L.mm_hines_solve_noalloc, t, MAX_COMPS + 1, x) == mm.MM_EINVAL
+
+
+def test_noalloc_rejects_bad_trees_and_leaves_no_stale_error():
+    """A tree that breaks the parent rule, or whose offsets reach past n_comp,
+    is rejected with MM_EINVAL through the no-allocation path; the next valid
+    call on the same stream returns MM_OK (the shared status word starts at
+    zero on every call) and matches the allocating solve."""
+    import torch
+    L = mm.load(build_if_missing=True)
+    off, par, a, b, c, r = _inputs(14, 8, 30)
+    bad_par = par.copy()
+    bad_par[off[3]] = 0  # the root of tree 3 gets a parent
+    t_bad = _device((off, bad_par, a, b, c, r))
+    x = torch.empty_like(t_bad[5])
+    assert _call(L.mm_hines_solve_noalloc, t_bad, t_bad[5].numel(), x) == mm.MM_EINVAL
+    t = _device((off, par, a, b, c, r))
+    assert _call(L.mm_hines_solve_noalloc, t, t[5].numel() - 1, x) == mm.MM_EINVAL  # last tree past n_comp
+    x_ref = torch.empty_like(t[5])
+    x_new = torch.full_like(t[5], float("nan"))
+    assert _call(L.mm_hines_solve, t, t[5].numel(), x_ref) == mm.MM_OK
+    assert _call(L.mm_hines_solve_noalloc, t, t[5].numel(), x_new) == mm.MM_OK
+    np.testing.assert_allclose(x_new.cpu().numpy(), x_ref.cpu().numpy(), rtol=1e-12, atol=1e-14)
