@@ -274,8 +274,10 @@ mm_status mm_read_kernel_timing(mm_net *net, mm_kernel_times *out, int32_t reset
  * modified.  Runs on cuda_stream (NULL: the legacy default stream) and
  * returns after the solve has finished.  Allocates a device scratch of
  * n_comp doubles for the duration of the call.
- * Errors: MM_EINVAL (negative sizes, NULL arrays, or a tree that violates
- * the parent rule: its entries of x are then undefined), MM_ENOMEM, MM_ECUDA. */
+ * Errors: MM_EINVAL (negative sizes, NULL arrays, a tree whose offsets do
+ * not lie within [0, n_comp] in ascending order, or a tree that violates the
+ * parent rule: such a tree is skipped and its entries of x are undefined,
+ * the other trees are solved), MM_ENOMEM, MM_ECUDA. */
 mm_status mm_hines_solve(int32_t n_trees, int64_t n_comp, const int64_t *tree_offset, const int32_t *parent,
                          const double *a, const double *b, const double *c, const double *rhs, double *x,
                          void *cuda_stream);
@@ -289,9 +291,11 @@ mm_status mm_hines_solve(int32_t n_trees, int64_t n_comp, const int64_t *tree_of
  * passes every input and the output x.  The scratch is a fixed 8 MiB
  * device array inside this library (loaded on every GPU that loads the
  * library, until the process ends), so n_comp must not exceed 1,048,576
- * (MM_EINVAL otherwise).  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress, with that device current) and
- * should come before any stream capture.  Every call on a device shares
+ * (MM_EINVAL otherwise).  Every call looks up that array's device address
+ * (cudaGetSymbolAddress, with the caller's device current; the first call on
+ * a device also loads the module there and should come before any stream
+ * capture).  A failed call leaves no error behind: the status word is
+ * cleared at the start of every call.  Every call on a device shares
  * the same scratch: calls whose work overlaps on the GPU race, so callers
  * order them (one stream, or wait for the previous call to return).
  * Calls no cudaMalloc, cudaFree or allocating library routine. */

@@ -17,6 +17,7 @@ namespace {
 
 constexpr int kStepThreads = 256;
 constexpr int kDefaultGroupComps = 4096;
+constexpr int kDefaultGroupComps32 = 2048;  // FP32c: 28 B of shared memory per compartment
 constexpr int kMaxGroupComps = 8192;
 constexpr int kMaxGroupComps32 = 1 << 30;
 constexpr int kGiantSmemLimit = 110 * 1024;  // FP32c regular class: two blocks per SM
@@ -85,8 +86,9 @@ struct mm_net {
     int32_t *Vq = nullptr;
     uint32_t *mq = nullptr, *hq = nullptr, *nq = nullptr;
     double *Vsoma = nullptr;
-    float *area32 = nullptr, *gax32 = nullptr, *gsyn32 = nullptr;
+    float2 *area2 = nullptr, *gax2 = nullptr, *dp2 = nullptr, *gsyn2 = nullptr;
     float2 *dr = nullptr;
+    float *drl = nullptr;
     float4 *pq = nullptr;
     int64_t *soma_internal = nullptr, *internal_of64 = nullptr;
     // both
@@ -412,6 +414,69 @@ void release_all(mm_net *net)
     net->stream = nullptr;
 }
 
+float2 split_pair(double x)
+{
+    const float hi = (float)x;
+    return make_float2(hi, (float)(x - (double)hi));
+}
+
+std::vector<float2> split_pairs(const std::vector<double> &v)
+{
+    std::vector<float2> out(v.size());
+    for (size_t i = 0; i < v.size(); ++i) out[i] = split_pair(v[i]);
+    return out;
+}
+
+// FP32c constants per compartment (internal order), computed in FP64 from
+// the cylinders: area (cm^2), the axial conductance g to the parent (uS;
+// 1 / the sum of the two half-cylinder resistances, 0 at a soma) with the
+// sign bit of its high word set at path heads and somata, and the passive
+// diagonal d0' of Algorithm 1's elimination (uS): d0_i = C_i/dt + the leak
+// conductance (backward Euler only: Eq. 2 as printed keeps the membrane
+// current explicit) + the implicit share of every coupling at i, then
+// d0'_p -= (w g_i)^2 / d0'_i over the children i of p, leaves first (w the
+// implicit share: 1, or 1/2 for Eq. 2 as printed).
+void passive_constants(const mmh::Layout &L, const mm_channel_params &ch, double dt, bool cn,
+                       std::vector<float2> &area2, std::vector<float2> &gax2, std::vector<float2> &dp2)
+{
+    const size_t C = (size_t)L.C;
+    const double pi = 3.141592653589793, w = cn ? 0.5 : 1.0;
+    std::vector<double> area(C), g(C, 0.0), d(C);
+    auto rhalf = [&](size_t i) {
+        const double rad = 0.5e-4 * L.D[i];
+        return ch.Ra * (0.5e-4 * L.L[i]) / (pi * rad * rad) * 1e-6;
+    };
+    for (size_t i = 0; i < C; ++i) {
+        area[i] = pi * L.D[i] * L.L[i] * 1e-8;
+        d[i] = ch.Cm * area[i] * 1e3 / dt + (cn ? 0.0 : ch.gL * area[i] * 1e3);
+    }
+    for (size_t i = 0; i < C; ++i) {
+        const int32_t pd = std::abs(L.pdist[i]);
+        if (pd == 0) continue;
+        const size_t q = i - (size_t)pd;
+        g[i] = 1.0 / (rhalf(i) + rhalf(q));
+        d[i] += w * g[i];
+        d[q] += w * g[i];
+    }
+    // parents precede their children in internal order: children first
+    for (size_t i = C; i-- > 0;) {
+        const int32_t pd = std::abs(L.pdist[i]);
+        if (pd == 0) continue;
+        const double wg = w * g[i];
+        d[i - (size_t)pd] -= wg * wg / d[i];
+    }
+    area2.resize(C);
+    gax2.resize(C);
+    dp2.resize(C);
+    for (size_t i = 0; i < C; ++i) {
+        area2[i] = split_pair(area[i]);
+        float2 gp = split_pair(g[i]);
+        if (L.pdist[i] <= 0) gp.x = -gp.x;  // path head or soma (-0.0 at a soma)
+        gax2[i] = gp;
+        dp2[i] = split_pair(d[i]);
+    }
+}
+
 mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_params *chan, const mm_synapses *syn,
                 const double *stim_nA, const mm_options *opt)
 {
@@ -466,15 +531,20 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     li.stim = stim_nA;
     li.cost = opt->schedule == MM_SCHED_COST ? opt->cost : nullptr;
     li.dt = opt->dt_ms;
-    li.group_comps = opt->group_comps > 0 ? opt->group_comps : kDefaultGroupComps;
+    li.group_comps = opt->group_comps > 0 ? opt->group_comps
+                   : (opt->precision == MM_FP64 ? kDefaultGroupComps : kDefaultGroupComps32);
     li.max_group_comps = opt->precision == MM_FP64 ? kMaxGroupComps : kMaxGroupComps32;
     // shared memory per item: FP64 d and rhs per compartment (16 B); FP32c
     // d, rhs and |g| per compartment (12 B) and per path its contribution
     // to the parent (d, rhs) and the potential across its head link (12 B)
-    li.smem_per_comp = opt->precision == MM_FP64 ? 16 : 12;
+    // FP32c (active conductance, rhs) pair, the rhs's low word, the implicit
+    // coupling and the passive diagonal as pairs (28 B per compartment) and
+    // per path two words (the head link's current, then the contribution to
+    // the parent)
+    li.smem_per_comp = opt->precision == MM_FP64 ? 16 : 28;
     li.smem_per_seg = 0;
     li.path_items = opt->precision != MM_FP64;
-    li.smem_per_path = opt->precision == MM_FP64 ? 0 : 12;
+    li.smem_per_path = opt->precision == MM_FP64 ? 0 : 8;
     li.giant_smem_limit = opt->precision == MM_FP64 ? 0 : kGiantSmemLimit;
     li.big_smem_limit = opt->precision == MM_FP64 ? 0 : kBigSmemLimit;
     mmh::Layout L;
@@ -528,11 +598,21 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         ZR(net->mq, C);
         ZR(net->hq, C);
         ZR(net->nq, C);
-        ZR(net->area32, C);
-        ZR(net->gax32, C);
+        {
+            // constants of the FP32c path as float pairs, computed here in
+            // FP64 in internal order: membrane area, axial conductance to the
+            // parent (sign bit of the high word at path heads and somata) and
+            // the passive diagonal after the elimination of Algorithm 1
+            std::vector<float2> area2, gax2, dp2;
+            passive_constants(L, *chan, opt->dt_ms, opt->scheme == MM_SCHEME_CN, area2, gax2, dp2);
+            UP(net->area2, area2.data(), C);
+            UP(net->gax2, gax2.data(), C);
+            UP(net->dp2, dp2.data(), C);
+        }
         ZR(net->Vsoma, N);
-        ZR(net->gsyn32, (size_t)std::max<int64_t>(net->nsite, 1));
+        ZR(net->gsyn2, (size_t)std::max<int64_t>(net->nsite, 1));
         ZR(net->dr, (size_t)std::max<int64_t>(L.giant_comps, 1));
+        ZR(net->drl, (size_t)std::max<int64_t>(L.giant_comps, 1));
         ZR(net->pq, (size_t)std::max<int64_t>(L.giant_paths, 1));
         std::vector<int64_t> soma_int(N), int_of(N);
         for (size_t k = 0; k < N; ++k) soma_int[k] = L.noff[k];
@@ -553,7 +633,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     int64_t *din_off = nullptr;
     int32_t *din_src = nullptr, *din_ds = nullptr;
     double *din_w = nullptr;
-    float *din_w32 = nullptr;
+    float2 *din_w2 = nullptr;
     if (opt->deterministic_delivery) {
         net->ordered = true;
         net->fired_words = std::max(1, (net->n_src + 31) / 32);
@@ -564,8 +644,8 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         if (f64) {
             UP(din_w, L.in_w.data(), std::max<size_t>(L.in_w.size(), 1));
         } else {
-            std::vector<float> w32(L.in_w.begin(), L.in_w.end());
-            UP(din_w32, w32.data(), std::max<size_t>(w32.size(), 1));
+            const std::vector<float2> w2 = split_pairs(L.in_w);
+            UP(din_w2, w2.data(), std::max<size_t>(w2.size(), 1));
         }
     }
     if (li.points) {
@@ -587,15 +667,15 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     int64_t *dout_off = nullptr;
     int32_t *dout_site = nullptr, *dout_ds = nullptr, *ddclass = nullptr;
     double *dout_w = nullptr;
-    float *dout_w32 = nullptr;
+    float2 *dout_w2 = nullptr;
     UP(dout_off, L.out_off.data(), L.out_off.size());
     UP(dout_site, L.out_site.data(), std::max<size_t>(L.out_site.size(), 1));
     UP(dout_ds, L.out_dsteps.data(), std::max<size_t>(L.out_dsteps.size(), 1));
     if (f64) {
         UP(dout_w, L.out_w.data(), std::max<size_t>(L.out_w.size(), 1));
     } else {
-        std::vector<float> w32(L.out_w.begin(), L.out_w.end());
-        UP(dout_w32, w32.data(), std::max<size_t>(w32.size(), 1));
+        const std::vector<float2> w2 = split_pairs(L.out_w);
+        UP(dout_w2, w2.data(), std::max<size_t>(w2.size(), 1));
     }
     UP(ddclass, L.dclass.data(), std::max<size_t>(L.dclass.size(), 1));
 #undef UP
@@ -622,8 +702,6 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         ia.mq = net->mq;
         ia.hq = net->hq;
         ia.nq = net->nq;
-        ia.area32 = net->area32;
-        ia.gax32 = net->gax32;
         MM_CKI(net, mmk_launch_init_fp32c(ia, net->stream));
         MM_CKI(net, mmk_launch_fill_f64(net->Vsoma, chan->v_init, (int64_t)N, net->stream));
     }
@@ -693,9 +771,11 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.hq = net->hq;
         a.nq = net->nq;
         a.Vsoma = net->Vsoma;
-        a.area = net->area32;
-        a.gax = net->gax32;
+        a.area = net->area2;
+        a.gax = net->gax2;
+        a.dp = net->dp2;
         a.dr = net->dr;
+        a.drl = net->drl;
         a.pq = net->pq;
         if (opt->time_items) {
             if ((st = zeros(net, &net->item_ns, L.groups.size())) != MM_OK) return st;
@@ -711,7 +791,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.meta = dmeta;
         a.smem_meta = L.max_meta;
         a.site_comp = dsite;
-        a.gsyn = net->gsyn32;
+        a.gsyn = net->gsyn2;
         a.ring_nrn = net->ring_nrn;
         a.ring_cnt = net->ring_cnt;
         a.R = net->R;
@@ -730,19 +810,19 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.ctl = net->ctl;
         a.smem_comps = smem_comps;
         a.smem_segs = smem_segs;
-        a.gNa = (float)chan->gNa;
-        a.gK = (float)chan->gK;
-        a.gL = (float)chan->gL;
+        // channel densities (mS/cm^2) times 1e3: conductance in uS per cm^2 of membrane
+        a.gNa = split_pair(chan->gNa * 1e3);
+        a.gK = split_pair(chan->gK * 1e3);
+        a.gL = split_pair(chan->gL * 1e3);
         a.ENa = pot(chan->ENa);
         a.EK = pot(chan->EK);
         a.EL = pot(chan->EL);
         a.Esyn = pot(syn ? syn->e_rev_mV : 0.0);
-        a.cm_dt = (float)(chan->Cm * 1e3 / opt->dt_ms);
         a.gimp = opt->scheme == MM_SCHEME_CN ? 0.5f : 1.0f;
         a.g_implicit = opt->scheme == MM_SCHEME_CN ? 0 : 1;
         a.dt = (float)opt->dt_ms;
         a.dt_lo = (float)(opt->dt_ms - (double)a.dt);
-        a.decay = (float)decay;
+        a.decay = split_pair(decay);
         a.threshold = chan->threshold_mV;
         {
             const double q = std::ceil(chan->threshold_mV * mmk::kVScaleD);
@@ -777,13 +857,13 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     }
     d.gsyn = net->gsyn;
     d.ctl = net->ctl;
-    d.gsyn32 = net->gsyn32;
-    d.out_w32 = dout_w32;
+    d.gsyn2 = net->gsyn2;
+    d.out_w2 = dout_w2;
     d.in_off = din_off;
     d.in_src = din_src;
     d.in_dsteps = din_ds;
     d.in_w = din_w;
-    d.in_w32 = din_w32;
+    d.in_w2 = din_w2;
     d.fired = net->fired;
     d.fired_words = net->fired_words;
     d.nsite = net->nsite;
@@ -975,7 +1055,7 @@ mm_status mm_read_state(mm_net *net, int32_t which, double *out, int64_t cap)
         case MM_STATE_N: MM_CKI(net, mmk_launch_gq_to_f64(net->nq, dense, net->C, net->stream)); break;
         default:
             MM_CKI(net, mmk_launch_fill_f64(dense, 0.0, net->C, net->stream));
-            MM_CKI(net, mmk_launch_scatter_f32_to_f64(net->gsyn32, net->site_internal, dense, net->nsite, net->stream));
+            MM_CKI(net, mmk_launch_scatter_f2_to_f64(net->gsyn2, net->site_internal, dense, net->nsite, net->stream));
         }
         src = dense;
     }
@@ -1163,7 +1243,7 @@ std::vector<std::pair<void *, size_t>> ckpt_regions(mm_net *net)
         r.push_back({net->hq, C * sizeof(uint32_t)});
         r.push_back({net->nq, C * sizeof(uint32_t)});
         r.push_back({net->Vsoma, N * sizeof(double)});
-        r.push_back({net->gsyn32, ns * sizeof(float)});
+        r.push_back({net->gsyn2, ns * sizeof(float2)});
     }
     r.push_back({net->stim, N * sizeof(double)});
     r.push_back({net->ring_cnt, (size_t)net->R * sizeof(int32_t)});

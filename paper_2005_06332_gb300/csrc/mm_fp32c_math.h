@@ -9,11 +9,21 @@
 // Precision plan:
 //   * the state is fixed point: V = Vq * 2^-23 mV (int32), gates q * 2^-32
 //     (uint32); increments are rounded once and added exactly;
-//   * potential differences are taken in integers before rounding;
+//   * potential differences are taken in integers and carried exactly as
+//     float pairs;
+//   * the membrane and axial currents, the synaptic conductance and every
+//     constant of the model (areas, axial conductances, channel densities,
+//     the stimulus, the decay factor) are float pairs ("double-float", about
+//     44 bits): a constant rounded to FP32 would perturb the model the same
+//     way in every step, and the rhs is a sum of large terms that cancel in
+//     a steady state, where FP32 rounding repeats from step to step;
 //   * the rate functions, steady states and relaxation factors are computed
-//     as unevaluated float pairs ("double-float", about 44 bits), since
-//     their rounding biases the gate trajectories every cycle;
-//   * the rest (conductances, currents, the tree solve) is plain FP32.
+//     as float pairs, since their rounding biases the gate trajectories every
+//     cycle;
+//   * the Hines solve is FP32 on the rhs rounded once, with the diagonal split
+//     into its passive part (eliminated once in FP64 at set-up, kept as a
+//     pair) and the step's active conductance, eliminated in FP32 as a
+//     perturbation of it.
 #pragma once
 #include <stdint.h>
 
@@ -163,6 +173,7 @@ constexpr float kLN2_hi = (float)kLn2D;
 constexpr float kLN2_lo = (float)(kLn2D - (double)kLN2_hi);
 // Taylor coefficients of 2^f: (ln 2)^k / k!
 constexpr float kP2 = (float)(kLn2D * kLn2D / 2.0);
+constexpr float kP2_lo = (float)(kLn2D * kLn2D / 2.0 - (double)kP2);
 constexpr float kP3 = (float)(kLn2D * kLn2D * kLn2D / 6.0);
 constexpr float kP4 = (float)(kLn2D * kLn2D * kLn2D * kLn2D / 24.0);
 constexpr float kP5 = (float)(kLn2D * kLn2D * kLn2D * kLn2D * kLn2D / 120.0);
@@ -171,10 +182,11 @@ constexpr float kP7 = (float)(kLn2D * kLn2D * kLn2D * kLn2D * kLn2D * kLn2D * kL
 constexpr float kP8 = (float)(kLn2D * kLn2D * kLn2D * kLn2D * kLn2D * kLn2D * kLn2D * kLn2D / 40320.0);
 
 // e^(x.hi + x.lo) as a double-float, |x| < 80.  x log2(e) = n + f with n an
-// integer and |f| <= 1/2; 2^f = 1 + f (ln2 + f q(f)) by its Taylor series
-// (truncation below 3e-10 relative).  q is evaluated in float (its rounding
-// enters scaled by f^2 <= 1/4); u = ln2 + f q and 1 + f u are carried as
-// float pairs, and the low part of f enters through d(2^f)/df = ln2 2^f.
+// integer and |f| <= 1/2; 2^f = 1 + f (ln2 + P2 f + f^2 q(f)) by its Taylor
+// series (truncation below 3e-10 relative).  q is evaluated in float (its
+// rounding enters scaled by |f|^3 <= 1/8); u = ln2 + P2 f + f^2 q and 1 + f u
+// are carried as float pairs, and the low part of f enters through
+// d(2^f)/df = ln2 2^f.
 MMF_HD F2 exp_df(F2 x)
 {
     const float t_hi = x.hi * kL2E_hi;
@@ -187,10 +199,13 @@ MMF_HD F2 exp_df(F2 x)
     q = fmaf(q, f, kP5);
     q = fmaf(q, f, kP4);
     q = fmaf(q, f, kP3);
-    q = fmaf(q, f, kP2);
-    // u = ln2 + f q as a pair (ln2_hi - u_hi is exact)
-    const float u_hi = fmaf(q, f, kLN2_hi);
-    const float u_lo = fmaf(q, f, kLN2_hi - u_hi) + kLN2_lo;
+    // u = ln2 + f (P2 + f q) as a pair, with P2 (as a pair) times f exact:
+    // P2 f^2 is the largest term after the linear one, so its coefficient
+    // must not be rounded to FP32
+    const F2 p2f = add_f(two_prod(kP2, f), kP2_lo * f);
+    const F2 u = add(F2{kLN2_hi, kLN2_lo}, add_f(p2f, f * f * q));
+    const float u_hi = u.hi;
+    const float u_lo = u.lo;
     // p = 1 + f u as a pair (1 - p_hi is exact)
     const float p_hi = fmaf(u_hi, f, 1.0f);
     float p_lo = fmaf(u_hi, f, 1.0f - p_hi) + u_lo * f;
@@ -252,6 +267,28 @@ MMF_HD F2 scaled_diff(int32_t a, int32_t b, float ch, float cl)
     return {xh, fmaf(dh, ch, -xh) + fmaf(dh, cl, dl * ch)};
 }
 
+// (a - b) * 2^-23 exactly, as a float pair (|a - b| < 2^31).
+MMF_HD F2 vdiff_df(int32_t a, int32_t b)
+{
+    const int32_t d = a - b;
+    const float dh = (float)d;
+    const float dl = (float)(d - (int32_t)dh);
+    return {dh * kV2F, dl * kV2F};
+}
+
+// (vq * 2^-23) - E for E = eq * 2^-23 + eres, as a float pair.
+MMF_HD F2 vminus_df(int32_t vq, int32_t eq, float eres)
+{
+    return add_f(vdiff_df(vq, eq), -eres);
+}
+
+// a double split into a float pair (hi the nearest float)
+MMF_HD F2 split_d(double x)
+{
+    const float hi = (float)x;
+    return {hi, (float)(x - (double)hi)};
+}
+
 // exact value of a uint32 fixed-point gate as a double-float
 MMF_HD F2 gate_df(uint32_t q)
 {
@@ -262,13 +299,14 @@ MMF_HD F2 gate_df(uint32_t q)
 
 MMF_HD float gate_f(uint32_t q) { return (float)q * (1.0f / 4294967296.0f); }
 
-// q + dx * 2^32, rounded in steps of 2 units, clamped to [0, 2^32 - 1]
+// q + dx * 2^32 rounded to the nearest unit (dx * 2^31 first taken in
+// whole units, then the rest in half units), clamped to [0, 2^32 - 1]
 MMF_HD uint32_t gate_add(uint32_t q, F2 dx)
 {
     const float a = dx.hi * 2147483648.0f;
     const int32_t k1 = f2i_rn(a);
-    const int32_t k2 = f2i_rn((a - (float)k1) + dx.lo * 2147483648.0f);
-    const long long nq = (long long)q + 2 * ((long long)k1 + (long long)k2);
+    const int32_t k2 = f2i_rn(((a - (float)k1) + dx.lo * 2147483648.0f) * 2.0f);
+    const long long nq = (long long)q + 2 * (long long)k1 + (long long)k2;
     return (uint32_t)(nq < 0 ? 0 : (nq > 4294967295LL ? 4294967295LL : nq));
 }
 
@@ -339,104 +377,6 @@ MMF_HD bool v_add(int32_t vq, float dv, int32_t *out)
     if (nv > 120LL * 8388608LL || nv < -120LL * 8388608LL) return false;
     *out = (int32_t)nv;
     return true;
-}
-
-// ------------------------------------------------------- single-float path
-
-// e^x in float (about 1 ulp): the same reduction and series as exp_df,
-// without the low words.
-MMF_HD float exp_f(float x)
-{
-    const float t = x * kL2E_hi;
-    const float n = rint_f(t);
-    const float f = fmaf(x, kL2E_hi, -n) + x * kL2E_lo;
-    float q = kP8;
-    q = fmaf(q, f, kP7);
-    q = fmaf(q, f, kP6);
-    q = fmaf(q, f, kP5);
-    q = fmaf(q, f, kP4);
-    q = fmaf(q, f, kP3);
-    q = fmaf(q, f, kP2);
-    q = fmaf(q, f, kLN2_hi);
-    const float p = fmaf(q, f, 1.0f);
-    int32_t ni = (int32_t)n;
-    ni = ni < -120 ? -120 : (ni > 120 ? 120 : ni);
-    return p * pow2i(ni);
-}
-
-struct RatesF {
-    float am, bm, ah, bh, an, bn;
-};
-
-MMF_HD float xexpm1_given_f(float x, float ex)
-{
-    if (fabsf(x) < 0.125f) {
-        const float x2 = x * x;
-        float s = fmaf(x2, -1.0f / 1209600.0f, 1.0f / 30240.0f);
-        s = fmaf(x2, s, -1.0f / 720.0f);
-        s = fmaf(x2, s, 1.0f / 12.0f);
-        return fmaf(s, x2, fmaf(-0.5f, x, 1.0f));
-    }
-    return x * rcp_rn(ex - 1.0f);
-}
-
-MMF_HD RatesF hh_rates_f(int32_t vq)
-{
-    RatesF r;
-    const float u = (float)(kQm65 - vq) * kV2F;    // -(V + 65)
-    const float E10 = exp_f(u * 0.1f), E18 = exp_f(u * (1.0f / 18.0f)), E80 = exp_f(u * 0.0125f);
-    float E20 = E80 * E80;
-    E20 = E20 * E20;
-    r.am = xexpm1_given_f((float)(kQm40 - vq) * (kV2F * 0.1f), E10 * kE25_h);
-    r.bm = 4.0f * E18;
-    r.ah = 0.07f * E20;
-    r.bh = rcp_rn(fmaf(E10, kE3_h, 1.0f));
-    r.an = 0.1f * xexpm1_given_f((float)(kQm55 - vq) * (kV2F * 0.1f), E10 * kE1_h);
-    r.bn = 0.125f * E80;
-    return r;
-}
-
-MMF_HD uint32_t gate_step_f(uint32_t q, float a, float b, float dt)
-{
-    const float s = a + b;
-    const float y = s * dt;
-    float E;
-    if (y < 0.125f) {
-        float r = fmaf(y, -1.0f / 5040.0f, 1.0f / 720.0f);
-        r = fmaf(-y, r, 1.0f / 120.0f);
-        r = fmaf(-y, r, 1.0f / 24.0f);
-        r = fmaf(-y, r, 1.0f / 6.0f);
-        r = fmaf(-y, r, 0.5f);
-        E = fmaf(-r * y, y, y);
-    } else {
-        E = 1.0f - exp_f(-y);
-    }
-    const F2 x = gate_df(q);
-    // dx = (a/s - x) E = (a - s x) E / s, with s x formed exactly
-    const F2 sx = mul_f(x, s);
-    const float num = (a - sx.hi) - sx.lo;
-    return gate_add(q, F2{num * E * rcp_rn(s), 0.0f});
-}
-
-// Mixed: double-float rates and steady state, float relaxation factor.
-MMF_HD uint32_t gate_step_mixed(uint32_t q, F2 a, F2 b, float dt)
-{
-    const F2 s = add(a, b);
-    const F2 xinf = div(a, s);
-    const float y = s.hi * dt;
-    float E;
-    if (y < 0.125f) {
-        float r = fmaf(y, -1.0f / 5040.0f, 1.0f / 720.0f);
-        r = fmaf(-y, r, 1.0f / 120.0f);
-        r = fmaf(-y, r, 1.0f / 24.0f);
-        r = fmaf(-y, r, 1.0f / 6.0f);
-        r = fmaf(-y, r, 0.5f);
-        E = fmaf(-r * y, y, y);
-    } else {
-        E = 1.0f - exp_f(-y);
-    }
-    const F2 d = add(xinf, neg(gate_df(q)));
-    return gate_add(q, mul_f(d, E));
 }
 
 }  // namespace mmf

@@ -210,17 +210,25 @@ struct FxPot {
     float res;
 };
 
-// Arguments of the FP32c step kernel.
+// Arguments of the FP32c step kernel.  Float pairs (float2: .x the nearest
+// float, .y the rest) carry every model constant and the synaptic
+// conductances to about 44 bits.
 struct StepArgs32 {
     int32_t *Vq;                      // [C]
     uint32_t *mq, *hq, *nq;           // [C]
     double *Vsoma;                    // [N] FP64 soma voltage accumulator
-    const float *area;                // cm^2 [C]
-    const float *gax;                 // uS [C], sign bit set at path heads (somata included): their
-                                      // link to the parent is assembled in the sweep
-    float2 *dr;                       // scratch for giant items: Hines diagonal and rhs per compartment
-    float4 *pq;                       // scratch for giant items: per path its contribution (d, rhs) and
-                                      // the potential across its head link
+    const float2 *area;               // cm^2 [C]
+    const float2 *gax;                // axial conductance to the parent, uS [C]; the sign bit of .x is set
+                                      // at path heads (somata included): their link to the parent is
+                                      // assembled per path
+    const float2 *dp;                 // passive diagonal after the elimination of Algorithm 1 with the
+                                      // membrane conductance left out (C/dt, leak, implicit axial
+                                      // couplings), uS [C]
+    float2 *dr;                       // scratch for giant items per compartment: (active conductance, rhs),
+                                      // then the substitution coefficients (f, c), then (f, dV)
+    float *drl;                       // scratch for giant items: low word of the rhs per compartment
+    float4 *pq;                       // scratch for giant items per path: its contribution to the parent
+                                      // (active conductance, rhs) and the current across its head link (pair)
     const int64_t *gchunk0;           // giant items: first compartment chunk of each [item1 - item0 + 1]
     unsigned long long *item_ns;      // per work item solve time (ns, summed over steps) or nullptr
     const double *stim;               // nA [N]
@@ -234,7 +242,7 @@ struct StepArgs32 {
     int32_t smem_bytes;               // dynamic shared memory of the launch (largest item need)
     unsigned int *queue;              // its work-queue counter (in ctl, reset by the delivery kernel)
     const int32_t *site_comp;
-    float *gsyn;                      // per site, uS
+    float2 *gsyn;                     // per site, uS (pair)
     int32_t *ring_nrn;
     int32_t *ring_cnt;
     int32_t R, N;
@@ -251,10 +259,10 @@ struct StepArgs32 {
     uint32_t *fired;
     DevCtl *ctl;
     int32_t smem_comps, smem_segs;
-    float gNa, gK, gL;
+    float2 gNa, gK, gL;               // channel densities times 1e3 (uS per cm^2 of membrane), pairs
     FxPot ENa, EK, EL, Esyn;
-    float cm_dt;                      // Cm * 1e3 / dt
-    float dt, dt_lo, decay;           // dt as a float pair (dt + dt_lo)
+    float2 decay;                     // exp(-dt / tau_syn), pair
+    float dt, dt_lo;                  // dt as a float pair (dt + dt_lo)
     int64_t C;                        // compartments (gate kernel)
     double threshold, dt64;
     float gimp;                       // implicit share of each axial coupling: 1 or 1/2 (as in StepArgs)
@@ -337,15 +345,15 @@ struct DeliverArgs {
     const int32_t *in_src;
     const int32_t *in_dsteps;
     const double *in_w;               // FP64 weights
-    const float *in_w32;              // FP32c weights
+    const float2 *in_w2;              // FP32c weights (float pairs)
     uint32_t *fired;                  // [R * fired_words]
     int32_t fired_words;
     int64_t nsite;
     int32_t step_offset;
     double *gsyn;
     DevCtl *ctl;
-    float *gsyn32;                    // FP32c: per-site conductance (gsyn unused)
-    const float *out_w32;             // FP32c: weights
+    float2 *gsyn2;                    // FP32c: per-site conductance as a float pair (gsyn unused)
+    const float2 *out_w2;             // FP32c: weights as float pairs
 };
 
 struct InitArgs {
@@ -355,10 +363,10 @@ struct InitArgs {
     double *area, *gax;
     double *V, *m, *h, *n;
     double Ra, v_init;
-    // FP32c outputs (used when Vq != nullptr; the FP64 pointers are then unused)
+    // FP32c outputs (used when Vq != nullptr; the FP64 pointers are then
+    // unused; the FP32c constants are computed on the host)
     int32_t *Vq;
     uint32_t *mq, *hq, *nq;
-    float *area32, *gax32;
 };
 
 }  // namespace mmk
@@ -382,7 +390,7 @@ int mmk_launch_deliver_ordered(const mmk::DeliverArgs &a, int blocks, void *stre
 int mmk_launch_deliver_ordered_fp32c(const mmk::DeliverArgs &a, int blocks, void *stream);
 int mmk_launch_vq_to_f64(const int32_t *vq, double *dst, int64_t n, void *stream);
 int mmk_launch_gq_to_f64(const uint32_t *q, double *dst, int64_t n, void *stream);
-int mmk_launch_scatter_f32_to_f64(const float *src, const int64_t *idx, double *dst, int64_t n, void *stream);
+int mmk_launch_scatter_f2_to_f64(const float2 *src, const int64_t *idx, double *dst, int64_t n, void *stream);
 int mmk_launch_advance(mmk::DevCtl *ctl, int steps, void *stream);
 int mmk_launch_gather_f64(const double *src, const int64_t *idx, double *dst, int64_t n, void *stream);
 int mmk_launch_scatter_f64(const double *src, const int64_t *idx, double *dst, int64_t n, void *stream);

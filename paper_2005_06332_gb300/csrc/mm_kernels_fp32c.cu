@@ -2,15 +2,25 @@
 //
 // Same step as the FP64 kernel (HH currents, Hines assembly of Eq. 2,
 // Algorithm 1 in shared memory, exponential-Euler gates, synaptic decay, soma
-// threshold test), computed in FP32 with the state kept exact between steps:
+// threshold test), computed in FP32 with the state kept exact between steps
+// and every error that would repeat from step to step removed:
 //   * V is an int32 fixed-point number (2^-23 mV) and each gate a uint32
 //     fixed-point number (2^-32); every step adds an FP32 increment rounded
 //     once, so rounding never accumulates in the state itself;
 //   * differences of potentials (V - E, V_parent - V_child, V + c in the rate
-//     arguments) are taken exactly in integers before the single rounding;
+//     arguments) are taken exactly in integers and carried as float pairs;
+//   * the membrane, axial and synaptic currents are summed as float pairs
+//     (mm_fp32c_math.h) from constants stored as float pairs (areas, axial
+//     conductances, channel densities, weights, the decay factor), and the
+//     rhs is rounded to FP32 once;
+//   * the Hines diagonal is split into its passive part, eliminated once at
+//     set-up in FP64 and stored as a pair, and the step's active membrane
+//     and synaptic conductance, which the FP32 elimination carries as a
+//     perturbation of it (the passive part alone would lose most of the
+//     active conductance's digits to the capacitive and axial terms);
 //   * the rate functions, steady states and relaxation factors are computed
-//     as float pairs (mm_fp32c_math.h: an FMA-only exponential, two per
-//     compartment, shared by the six rates);
+//     as float pairs (an FMA-only exponential, two per compartment, shared
+//     by the six rates);
 //   * the soma voltage is also accumulated in FP64 and the spike crossing
 //     time is computed in FP64.
 #include <cuda_runtime.h>
@@ -25,36 +35,20 @@ using namespace mmk;
 
 namespace {
 
-constexpr double kPiD = 3.141592653589793;
-
-__device__ __forceinline__ float vminus(int32_t vq, FxPot E) { return mmf::vdiff(vq, E.q) - E.res; }
+__device__ __forceinline__ mmf::F2 f2(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ float2 tof2(mmf::F2 v) { return make_float2(v.hi, v.lo); }
+// V - E as a float pair
+__device__ __forceinline__ mmf::F2 vminus(int32_t vq, FxPot E) { return mmf::vminus_df(vq, E.q, E.res); }
 
 // ------------------------------------------------------------------ init
 
-__device__ __forceinline__ double half_cyl_resistance_d(double Ra, double L_um, double d_um)
-{
-    const double rad = 0.5e-4 * d_um;
-    return Ra * (0.5e-4 * L_um) / (kPiD * rad * rad) * 1e-6;
-}
-
 __device__ __forceinline__ double xexpm1_d(double x) { return fabs(x) < 1e-6 ? 1.0 - 0.5 * x : x / expm1(x); }
 
+// The resting state: V = v_init and every gate at its steady state there.
 __global__ void init_fp32c_kernel(InitArgs a)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.C;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double L = a.L[i], d = a.diam[i];
-        a.area32[i] = (float)(kPiD * d * L * 1e-8);
-        const int32_t pd = a.parent_dist[i];
-        const int32_t pa = abs(pd);
-        double g = 0.0;
-        if (pa > 0) {
-            const int64_t q = i - pa;
-            g = 1.0 / (half_cyl_resistance_d(a.Ra, L, d) + half_cyl_resistance_d(a.Ra, a.L[q], a.diam[q]));
-        }
-        // path heads (and somata) carry the sign bit: phase A assembles only
-        // the links inside paths, the sweep the links of the heads
-        a.gax32[i] = pd > 0 ? (float)g : -(float)g;
         const double v = a.v_init;
         a.Vq[i] = (int32_t)llrint(v * kVScaleD);
         const double am = xexpm1_d(-(v + 40.0) * 0.1), bm = 4.0 * exp(-(v + 65.0) / 18.0);
@@ -125,13 +119,23 @@ __global__ void __launch_bounds__(256) deliver_fp32c_kernel(DeliverArgs a)
             b = l;
             e = l2;
         }
-        for (long long q = b + lane; q < e; q += GL) atomicAdd(&a.gsyn32[a.out_site[q]], a.out_w32[q]);
+        // the weight's high word into the site's high word; the rounding
+        // error of that addition (exact, by TwoSum from the value the atomic
+        // returns: the atomic rounds as the same float addition does) and
+        // the weight's low word into the site's low word, so that the pair's
+        // sum is every arrived weight to about 44 bits, in any order
+        for (long long q = b + lane; q < e; q += GL) {
+            float2 *g = a.gsyn2 + a.out_site[q];
+            const float2 w = a.out_w2[q];
+            const float old = atomicAdd(&g->x, w.x);
+            atomicAdd(&g->y, mmf::two_sum(old, w.x).lo + w.y);
+        }
     }
 }
 
 // Deterministic delivery, FP32c conductances (as deliver_ordered_kernel of
 // the FP64 path: each site adds its arrived weights in ascending synapse
-// id, one thread per site, plus the per-step resets).
+// id, one thread per site, as float pairs, plus the per-step resets).
 __global__ void __launch_bounds__(256) deliver_ordered_fp32c_kernel(DeliverArgs a)
 {
     const long long n = (long long)a.ctl->step_base + a.step_offset;
@@ -148,18 +152,19 @@ __global__ void __launch_bounds__(256) deliver_ordered_fp32c_kernel(DeliverArgs 
     for (long long st = gt; st < a.nsite; st += nt) {
         const long long e0 = a.in_off[st], e1 = a.in_off[st + 1];
         if (e0 == e1) continue;
-        float g = a.gsyn32[st];
+        const float2 g0 = a.gsyn2[st];
+        mmf::F2 g = mmf::two_sum(g0.x, g0.y);
         bool hit = false;
         for (long long e = e0; e < e1; ++e) {
             const long long m = n - 1 - a.in_dsteps[e];
             if (m < 0) continue;
             const int src = a.in_src[e];
             if ((a.fired[(m % a.R) * a.fired_words + (src >> 5)] >> (src & 31)) & 1u) {
-                g += a.in_w32[e];
+                g = mmf::add(g, f2(a.in_w2[e]));
                 hit = true;
             }
         }
-        if (hit) a.gsyn32[st] = g;
+        if (hit) a.gsyn2[st] = tof2(g);
     }
 }
 
@@ -170,6 +175,17 @@ __device__ __forceinline__ float rcp_approx(float x)
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+
+// 1/x to within rounding: the approximate reciprocal and one Newton step
+// (its error is squared).  The Hines factors use it: their diagonals change
+// little from step to step, so the approximate reciprocal's error, which
+// depends on the operand's bits, would repeat in every step and bias the
+// solution the same way each time.
+__device__ __forceinline__ float rcp_nr(float x)
+{
+    const float r = rcp_approx(x);
+    return fmaf(r, fmaf(-x, r, 1.f), r);
 }
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -223,13 +239,15 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
 {
     // Shared memory of one work item, carved from the item's own sizes: its
     // tree blob (staged by one bulk copy), then per compartment the pair
-    // (diagonal, rhs) -- after elimination the substitution coefficients
-    // (f, c), after substitution (f, dV) -- and |g_axial| (staged by phase A,
-    // so that the sweeps touch only shared memory), then per path its
-    // contribution to its parent compartment (diagonal, rhs) and the exact
-    // potential difference across its head link (for the path from a soma:
-    // the stimulus current).  The launch provides the largest need
-    // over its items.
+    // (active conductance, rhs) -- after elimination the substitution
+    // coefficients (f, c), after substitution (f, dV) --, the implicit axial
+    // coupling to the parent and the passive eliminated diagonal (float
+    // pairs, staged by phase A so that the sweeps touch only shared memory)
+    // and the low word of the rhs; then per path two words: the current
+    // across its head link (a pair), later its contribution to its parent
+    // compartment (active conductance, rhs) -- for the path from a soma the
+    // FP64 soma voltage.  The launch provides the largest need over its
+    // items.
     //
     // Warp roles: all warps run the streaming phases (A, S, C) of an item.
     // In the sweeps teams of 1, 2 or 4 warps take whole sweep bundles of the
@@ -284,52 +302,52 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         const GroupRec G = a.groups[gi];
         const int64_t c0 = G.comp0;
         const int32_t *Vq = a.Vq + c0;
-        float2 *sdr = (float2 *)(smem_raw + G.meta_bytes);  // (d, rhs), then (f, c), then (f, dV)
+        float2 *sdr = (float2 *)(smem_raw + G.meta_bytes);  // (e, rhs), then (f, c), then (f, dV)
         float *sy = (float *)sdr;                            // sy[2 i + 1]: the second member of sdr[i]
-        float *sg = (float *)(sdr + G.ncomp);
-        float *scd = sg + G.ncomp;
+        float2 *sgp = sdr + G.ncomp;                         // implicit coupling to the parent (pair)
+        float2 *sdp = sgp + G.ncomp;                         // passive eliminated diagonal (pair)
+        float *srl = (float *)(sdp + G.ncomp);               // low word of the rhs
+        float *scd = srl + G.ncomp;
         float *scr = scd + G.npath;
-        float *svt = scr + G.npath;
 
         // A. membrane conductance and current at (V^n, gates^n), plus the
-        //    axial terms of every link inside a path (both ends; a link
-        //    (i-1, i) is inside a path when g_axial[i] has no sign bit).
-        //    Stage |g_axial| for the sweeps.  All reads go through the
-        //    read-only path (nothing here is written by this launch before
-        //    it is read), so that the loads of two iterations overlap.
+        //    axial currents of every link inside a path (both ends; a link
+        //    (i-1, i) is inside a path when g_axial[i] has no sign bit), the
+        //    rhs summed as a float pair; the active conductance (FP32) is the
+        //    diagonal's share that changes from step to step.  Stage the
+        //    couplings and the passive diagonal for the sweeps.  All reads
+        //    go through the read-only path (nothing here is written by this
+        //    launch before it is read), so that the loads of two iterations
+        //    overlap.
 #pragma unroll 2
         for (int i = tid; i < G.ncomp; i += NS) {
             const int32_t vq = __ldg(Vq + i);
-            const float gs = __ldg(a.gax + c0 + i);
-            const float g = fabsf(gs);
-            sg[i] = a.gimp * g;  // the implicit coupling, used by the sweeps
-            const float m = mmf::gate_f(__ldg(a.mq + c0 + i)), h = mmf::gate_f(__ldg(a.hq + c0 + i)),
-                        nn = mmf::gate_f(__ldg(a.nq + c0 + i));
-            const float ar = __ldg(a.area + c0 + i);
-            const float s = ar * 1e3f;
-            const float gna = a.gNa * s * (m * m * m * h);
-            const float n2 = nn * nn;
-            const float gk = a.gK * s * (n2 * n2);
-            const float gl = a.gL * s;
-            // the membrane conductance is implicit except in Eq. 2 as
-            // printed; of each axial coupling the share gimp enters the
-            // diagonal, all of it the explicit rhs
-            float d = fmaf(ar, a.cm_dt, a.g_implicit ? gna + gk + gl : 0.f);
-            float r = -fmaf(gna, vminus(vq, a.ENa), fmaf(gk, vminus(vq, a.EK), gl * vminus(vq, a.EL)));
-            if (!signbit(gs)) {  // link to the parent i-1
-                d = fmaf(a.gimp, g, d);
-                r = fmaf(g, mmf::vdiff(__ldg(Vq + i - 1), vq), r);
-            }
+            const float2 gs = __ldg(a.gax + c0 + i);
+            const float gh = fabsf(gs.x);
+            sgp[i] = make_float2(a.gimp * gh, a.gimp * gs.y);
+            sdp[i] = __ldg(a.dp + c0 + i);
+            const mmf::F2 ar = f2(__ldg(a.area + c0 + i));
+            const mmf::F2 m = mmf::gate_df(__ldg(a.mq + c0 + i)), h = mmf::gate_df(__ldg(a.hq + c0 + i)),
+                          nn = mmf::gate_df(__ldg(a.nq + c0 + i));
+            const mmf::F2 gna = mmf::mul(mmf::mul(f2(a.gNa), ar), mmf::mul(mmf::mul(mmf::mul(m, m), m), h));
+            const mmf::F2 n2 = mmf::mul(nn, nn);
+            const mmf::F2 gk = mmf::mul(mmf::mul(f2(a.gK), ar), mmf::mul(n2, n2));
+            const mmf::F2 gl = mmf::mul(f2(a.gL), ar);
+            mmf::F2 r = mmf::add(mmf::mul(gna, vminus(vq, a.ENa)),
+                                 mmf::add(mmf::mul(gk, vminus(vq, a.EK)), mmf::mul(gl, vminus(vq, a.EL))));
+            r = mmf::neg(r);
+            if (!signbit(gs.x))  // link to the parent i-1
+                r = mmf::add(r, mmf::mul(mmf::F2{gh, gs.y}, mmf::vdiff_df(__ldg(Vq + i - 1), vq)));
             if (i + 1 < G.ncomp) {
-                const float gc = __ldg(a.gax + c0 + i + 1);
-                if (!signbit(gc)) {  // link to the child i+1
-                    d = fmaf(a.gimp, gc, d);
-                    r = fmaf(gc, mmf::vdiff(__ldg(Vq + i + 1), vq), r);
-                }
+                const float2 gc = __ldg(a.gax + c0 + i + 1);
+                if (!signbit(gc.x))  // link to the child i+1
+                    r = mmf::add(r, mmf::mul(f2(gc), mmf::vdiff_df(__ldg(Vq + i + 1), vq)));
             }
-            sdr[i] = make_float2(d, r);
+            // the membrane conductance is implicit except in Eq. 2 as printed
+            sdr[i] = make_float2(a.g_implicit ? gna.hi + gk.hi : 0.f, r.hi);
+            srl[i] = r.lo;
         }
-        // the tree blob must have landed before the sweeps
+        // the tree blob must have landed before the per-path work
         if (!mbar_wait_bounded(&bar, parity)) s_abort = 1;
         parity ^= 1u;
         __syncthreads();
@@ -343,53 +361,81 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         const int16_t *loffs = (const int16_t *)(smeta + G.loffs_off);
         const int16_t *mcnt = (const int16_t *)(smeta + G.mcnt_off);
 
-        // S. synaptic sites, then decay (sites are distinct compartments).
-        //    Per path: the exact potential difference across its head link,
-        //    V_parent - V_head (for the path from a soma: the stimulus
-        //    current), which the elimination needs; the path from a soma
-        //    also fetches the FP64 soma voltage into its (otherwise unused)
-        //    contribution slot, as two 32-bit halves.
+        // S. synaptic sites (their conductance and current, then the
+        //    conductance's decay; sites are distinct compartments), then per
+        //    path the current across its head link into its head (for the
+        //    path from a soma: the stimulus; that path also fetches the FP64
+        //    soma voltage into its slots, as two 32-bit halves), then the
+        //    same currents out of the parent compartments, summed per parent
+        //    in fold-list order.  Each rhs stays a float pair until then.
         for (int t = tid; t < G.nsite; t += NS) {
             const int st = G.site0 + t;
             const int c = a.site_comp[st];
-            const float g = a.gsyn[st];
+            const float2 g0 = a.gsyn[st];
+            const mmf::F2 g = mmf::two_sum(g0.x, g0.y);
             float2 v = sdr[c];
-            if (a.g_implicit) v.x += g;
-            v.y = fmaf(-g, vminus(Vq[c], a.Esyn), v.y);
+            if (a.g_implicit) v.x += g.hi;
+            const mmf::F2 r = mmf::add(mmf::F2{v.y, srl[c]}, mmf::neg(mmf::mul(g, vminus(Vq[c], a.Esyn))));
+            v.y = r.hi;
             sdr[c] = v;
-            a.gsyn[st] = g * a.decay;
+            srl[c] = r.lo;
+            a.gsyn[st] = tof2(mmf::mul(g, f2(a.decay)));
         }
+        __syncthreads();
         for (int pi = tid; pi < G.npath; pi += NS) {
             const PathQ P = paths[pi];
+            mmf::F2 t;
             if (P.parent >= 0) {
-                svt[pi] = mmf::vdiff(Vq[P.parent], Vq[P.head]);
+                const float2 gs = __ldg(a.gax + c0 + P.head);
+                t = mmf::mul(mmf::F2{fabsf(gs.x), gs.y}, mmf::vdiff_df(Vq[P.parent], Vq[P.head]));
+                scd[pi] = t.hi;
+                scr[pi] = t.lo;
             } else {
                 const int nrn = G.neuron0 + (P.nflag & kPathNeuron);
-                svt[pi] = (float)a.stim[nrn];
+                t = mmf::split_d(a.stim[nrn]);
                 const double v0 = a.Vsoma[nrn];
                 scd[pi] = __int_as_float(__double2hiint(v0));
                 scr[pi] = __int_as_float(__double2loint(v0));
             }
+            const mmf::F2 r = mmf::add(mmf::F2{sdr[P.head].y, srl[P.head]}, t);
+            sdr[P.head].y = r.hi;
+            srl[P.head] = r.lo;
+        }
+        __syncthreads();
+        for (int e = tid; e < G.npath; e += NS) {
+            const int att = (int)(fold[e] >> 16);
+            if (att >= G.ncomp) continue;  // a path from a soma (no parent)
+            if (e > 0 && (int)(fold[e - 1] >> 16) == att) continue;  // not the first path of its parent
+            mmf::F2 t{0.f, 0.f};
+            for (int z = e; z < G.npath && (int)(fold[z] >> 16) == att; ++z) {
+                const int c = (int)(fold[z] & 0xFFFFu);
+                t = mmf::add(t, mmf::F2{scd[c], scr[c]});
+            }
+            const mmf::F2 r = mmf::add(mmf::F2{sdr[att].y, srl[att]}, mmf::neg(t));
+            sdr[att].y = r.hi;
+            srl[att] = r.lo;
         }
         __syncthreads();
 
-        // The next item's per-compartment streams (V, gates, area, g_axial)
-        // into L2, one 128-byte line per prefetch, while the sweeps run.
+        // The next item's per-compartment streams (V, gates, constants) into
+        // L2, one 128-byte line per prefetch, while the sweeps run.
         {
             const int ni = s_next;
             if (ni < a.item1) {
-                const int64_t b0 = a.groups[ni].comp0 * 4, b1 = b0 + a.groups[ni].ncomp * (int64_t)4;
-                const int64_t l0 = b0 >> 7, nl = ((b1 + 127) >> 7) - l0;  // bytes of any 4-byte stream
-                auto pull = [&](const void *p) {
+                const int64_t nc0 = a.groups[ni].comp0, ncn = a.groups[ni].ncomp;
+                auto pull = [&](const void *p, int64_t esz) {
+                    const int64_t b0 = nc0 * esz, b1 = b0 + ncn * esz;
+                    const int64_t l0 = b0 >> 7, nl = ((b1 + 127) >> 7) - l0;
                     for (int64_t x = tid; x < nl; x += NS)
                         asm volatile("prefetch.global.L2 [%0];" ::"l"((const char *)p + max((l0 + x) << 7, b0)));
                 };
-                pull(a.Vq);
-                pull(a.mq);
-                pull(a.hq);
-                pull(a.nq);
-                pull(a.area);
-                pull(a.gax);
+                pull(a.Vq, 4);
+                pull(a.mq, 4);
+                pull(a.hq, 4);
+                pull(a.nq, 4);
+                pull(a.area, 8);
+                pull(a.gax, 8);
+                pull(a.dp, 8);
             }
         }
 
@@ -412,42 +458,41 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         // B. leaves-to-root elimination (Algorithm 1) path by path, from the
         //    deepest level up: every compartment of a path has the one
         //    before it as its parent, so a path is one chain from its leaf
-        //    up to its head (links inside a path are assembled: a = c = -g),
-        //    kSweepChunk compartments at a time with their operands loaded before
-        //    any of their stores (indices past the head are clamped and their
-        //    results dropped).  The head is then eliminated into its parent
-        //    compartment: a path alone on that compartment adds its
-        //    contribution there itself; paths sharing one leave theirs in
-        //    their slots, summed in fold-list order once the level is done.
-        //    The elimination leaves the substitution coefficients
-        //    x_j = f_j x_{j-1} + c_j.
-        // the head of path pi once its interior is eliminated (dh, rh: the
-        // head's diagonal and rhs): for the path from a soma its dV, else the
-        // head link to the parent compartment assembled here (gh the
-        // implicit share of its coupling, ge all of it) and the head
-        // eliminated into the parent
-        auto eliminate_head = [&](int pi, const PathQ &P, float dh, float rh) {
+        //    up to its head (links inside a path are assembled: a = c = -g).
+        //    The diagonal of compartment j after the elimination of its
+        //    subtree is d'_j = d0'_j + e_j, with d0'_j the passive one
+        //    (eliminated at set-up) and e_j the active conductance carried
+        //    up the tree: e_{p} += (g/d0'_j) (g/d'_j) e_j, the exact
+        //    difference of the two eliminations.  kSweepChunk compartments
+        //    at a time with their operands loaded before any of their stores
+        //    (indices past the head are clamped and their results dropped).
+        //    The head is then eliminated into its parent compartment: a path
+        //    alone on that compartment adds its contribution there itself;
+        //    paths sharing one leave theirs in their slots, summed in
+        //    fold-list order once the level is done.  The elimination leaves
+        //    the substitution coefficients x_j = f_j x_{j-1} + c_j.
+        // the head of path pi once its interior is eliminated (eh, rh: the
+        // head's active conductance and rhs): for the path from a soma its
+        // dV, else the head eliminated into the parent
+        auto eliminate_head = [&](int pi, const PathQ &P, float eh, float rh) {
             const int h = P.head;
-            const float gh = sg[h], vt = svt[pi];
-            if (P.parent < 0) {  // soma: the stimulus, then its dV
-                rh += vt;
-                sy[2 * h + 1] = rh * rcp_approx(dh);
+            const float2 dq = sdp[h];
+            const float inv = rcp_nr(dq.x + (dq.y + eh));
+            if (P.parent < 0) {  // soma: its dV
+                sy[2 * h + 1] = rh * inv;
                 return;
             }
-            const float ge = a.gimp < 1.f ? 2.f * gh : gh;
-            dh += gh;
-            rh = fmaf(ge, vt, rh);
-            const float inv = rcp_approx(dh);
-            const float f = gh * inv;
+            const float2 gq = sgp[h];
+            const float f = fmaf(gq.x, inv, gq.y * inv);
             sdr[h] = make_float2(f, rh * inv);
-            const float cd = fmaf(-f, gh, gh), cr = fmaf(f, rh, -ge * vt);
+            const float ce = gq.x * rcp_nr(dq.x) * f * eh, cr = f * rh;
             if (P.nflag & kPathAlone) {
                 float2 v = sdr[P.parent];
-                v.x += cd;
+                v.x += ce;
                 v.y += cr;
                 sdr[P.parent] = v;
             } else {
-                scd[pi] = cd;
+                scd[pi] = ce;
                 scr[pi] = cr;
             }
         };
@@ -456,35 +501,39 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             const int h = P.head;
             int j = P.end - 1;
             const float2 v0 = sdr[j];
-            float db = v0.x, rb = v0.y;
-            float dh = db, rh = rb;
+            float eb = v0.x, rb = v0.y;
+            float eh = eb, rh = rb;
             for (; j > h; j -= kSweepChunk) {
                 const int cnt = j - h;
-                float g[kSweepChunk], g2[kSweepChunk], dp[kSweepChunk], rp[kSweepChunk];
+                float gh[kSweepChunk], gl[kSweepChunk], dh[kSweepChunk], dl[kSweepChunk], f0[kSweepChunk];
+                float ep[kSweepChunk], rp[kSweepChunk];
 #pragma unroll
                 for (int k = 0; k < kSweepChunk; ++k) {
                     const int q = max(j - k, h + 1);
-                    g[k] = sg[q];
-                    const float2 w = sdr[q - 1];
-                    dp[k] = w.x;
+                    const float2 gq = sgp[q], dq = sdp[q], w = sdr[q - 1];
+                    gh[k] = gq.x;
+                    gl[k] = gq.y;
+                    dh[k] = dq.x;
+                    dl[k] = dq.y;
+                    f0[k] = gq.x * rcp_nr(dq.x);
+                    ep[k] = w.x;
                     rp[k] = w.y;
-                    g2[k] = g[k] * g[k];
                 }
 #pragma unroll
                 for (int k = 0; k < kSweepChunk; ++k) {
-                    const float inv = rcp_approx(db);
-                    const float f = g[k] * inv;
+                    const float inv = rcp_nr(dh[k] + (dl[k] + eb));
+                    const float f = fmaf(gh[k], inv, gl[k] * inv);
                     const float c = rb * inv;
                     if (k < cnt) sdr[j - k] = make_float2(f, c);
                     rb = fmaf(f, rb, rp[k]);
-                    db = fmaf(-g2[k], inv, dp[k]);
+                    eb = fmaf(f0[k] * f, eb, ep[k]);
                     if (k == cnt - 1) {
-                        dh = db;
+                        eh = eb;
                         rh = rb;
                     }
                 }
             }
-            eliminate_head(pi, P, dh, rh);
+            eliminate_head(pi, P, eh, rh);
         };
         // contributions of the level's paths that share a parent compartment
         // (fold entries e0 .. e1-1); a lane takes the entries that start a run
@@ -569,10 +618,12 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
 
         // Paths of at least kWarpPath compartments are eliminated and
         // substituted by a whole warp.  The path's interior is cut into 32
-        // chunks, one per lane.  The elimination's diagonal recurrence
-        // d'_{j-1} = d_{j-1} - g_j^2 / d'_j is the action of the 2x2 matrix
-        // [[d_{j-1}, -g_j^2], [1, 0]] on (d', 1) up to scale, and its rhs
-        // recurrence r'_{j-1} = r_{j-1} + (g_j / d'_j) r'_j and the
+        // chunks, one per lane.  The recurrence of the active conductance,
+        // e_{j-1} = E_{j-1} + (g_j / D_j) g_j e_j / (D_j + e_j) (E the
+        // compartment's own share, D the passive diagonal), is the action of
+        // the 2x2 matrix [[E_{j-1} + g_j^2 / D_j, E_{j-1} D_j], [1, D_j]] on
+        // (e_j, 1) up to scale (all entries positive: no cancellation), and
+        // the rhs recurrence r'_{j-1} = r_{j-1} + f_j r'_j and the
         // substitution x_j = f_j x_{j-1} + c_j are affine maps: each lane
         // composes its chunk, an inclusive warp scan combines the chunks,
         // and each lane runs the recurrences through its chunk from the
@@ -590,15 +641,16 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             float m00 = 1.f, m01 = 0.f, m10 = 0.f, m11 = 1.f;
             for (int tt = t0; tt < t1; ++tt) {
                 const int j = e - 1 - tt;
-                const float g = sg[j], g2 = g * g, dn = sdr[j - 1].x;
-                const float n00 = fmaf(dn, m00, -g2 * m10), n01 = fmaf(dn, m01, -g2 * m11);
-                m10 = m00;
-                m11 = m01;
-                const float s = rcp_approx(fabsf(n00) + fabsf(n01));
+                const float2 gq = sgp[j], dq = sdp[j];
+                const float D = dq.x + dq.y, En = sdr[j - 1].x;
+                const float A = fmaf(gq.x * rcp_nr(D), gq.x, En), B = En * D;
+                const float n00 = fmaf(A, m00, B * m10), n01 = fmaf(A, m01, B * m11);
+                const float n10 = fmaf(D, m10, m00), n11 = fmaf(D, m11, m01);
+                const float s = rcp_approx(n00 + n01 + n10 + n11);
                 m00 = n00 * s;
                 m01 = n01 * s;
-                m10 *= s;
-                m11 *= s;
+                m10 = n10 * s;
+                m11 = n11 * s;
             }
             for (int off = 1; off < 32; off <<= 1) {
                 const float a00 = __shfl_up_sync(0xFFFFFFFFu, m00, off), a01 = __shfl_up_sync(0xFFFFFFFFu, m01, off);
@@ -621,21 +673,20 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                 e10 = 0.f;
                 e11 = 1.f;
             }
-            const float db0 = fmaf(e00, leaf.x, e01) / fmaf(e10, leaf.x, e11);
-            // pass 1 (reads only): the diagonal through the chunk and the
-            // chunk's affine map of the rhs recurrence; the element after
-            // the chunk is kept for pass 2, whose writes it may see
-            float db = db0, A = 1.f, B = 0.f;
+            const float eb0 = fmaf(e00, leaf.x, e01) / fmaf(e10, leaf.x, e11);
+            // pass 1 (reads only): the active conductance through the chunk
+            // and the chunk's affine map of the rhs recurrence; the element
+            // after the chunk is kept for pass 2, whose writes it may see
+            float eb = eb0, A = 1.f, B = 0.f;
             float2 nb = make_float2(0.f, 0.f);
             for (int tt = t0; tt < t1; ++tt) {
                 const int j = e - 1 - tt;
-                const float g = sg[j];
-                const float2 w = sdr[j - 1];
-                const float inv = rcp_approx(db);
-                const float f = g * inv;
+                const float2 gq = sgp[j], dq = sdp[j], w = sdr[j - 1];
+                const float inv = rcp_nr(dq.x + (dq.y + eb));
+                const float f = fmaf(gq.x, inv, gq.y * inv);
                 A *= f;
                 B = fmaf(f, B, w.y);
-                db = fmaf(-g * g, inv, w.x);
+                eb = fmaf(gq.x * rcp_nr(dq.x) * f, eb, w.x);
                 nb = w;
             }
             for (int off = 1; off < 32; off <<= 1) {
@@ -645,30 +696,30 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                     A *= pa;
                 }
             }
-            float ea = __shfl_up_sync(0xFFFFFFFFu, A, 1), eb = __shfl_up_sync(0xFFFFFFFFu, B, 1);
+            float ea = __shfl_up_sync(0xFFFFFFFFu, A, 1), ebs = __shfl_up_sync(0xFFFFFFFFu, B, 1);
             if (lane == 0) {
                 ea = 1.f;
-                eb = 0.f;
+                ebs = 0.f;
             }
             // pass 2: the substitution coefficients (f_j, c_j) of the chunk
             __syncwarp();
-            db = db0;
-            float rb = fmaf(ea, leaf.y, eb);
+            eb = eb0;
+            float rb = fmaf(ea, leaf.y, ebs);
             for (int tt = t0; tt < t1; ++tt) {
                 const int j = e - 1 - tt;
-                const float g = sg[j];
+                const float2 gq = sgp[j], dq = sdp[j];
                 const float2 w = tt + 1 < t1 ? sdr[j - 1] : nb;
-                const float inv = rcp_approx(db);
-                const float f = g * inv;
+                const float inv = rcp_nr(dq.x + (dq.y + eb));
+                const float f = fmaf(gq.x, inv, gq.y * inv);
                 sdr[j] = make_float2(f, rb * inv);
                 rb = fmaf(f, rb, w.y);
-                db = fmaf(-g * g, inv, w.x);
+                eb = fmaf(gq.x * rcp_nr(dq.x) * f, eb, w.x);
             }
             // the head, from the lane whose chunk ends at it
             const int lastl = (m - 1) / cs;
-            const float dh = __shfl_sync(0xFFFFFFFFu, db, lastl), rh = __shfl_sync(0xFFFFFFFFu, rb, lastl);
+            const float eh = __shfl_sync(0xFFFFFFFFu, eb, lastl), rh = __shfl_sync(0xFFFFFFFFu, rb, lastl);
             __syncwarp();
-            if (lane == 0) eliminate_head(pi, P, dh, rh);
+            if (lane == 0) eliminate_head(pi, P, eh, rh);
             __syncwarp();
         };
         auto substitute_path_warp = [&](int pi) {
@@ -796,14 +847,14 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
     // int32 index range): the same path-by-path solve as step_fp32c_kernel
     // with the whole block as one team, between giant_assemble_kernel
     // (phase A of every giant compartment, spread over many blocks) and
-    // giant_update_kernel (phase C and the gates, likewise).  The Hines
-    // diagonal and rhs of each compartment (after elimination f and c,
-    // after substitution dV) live in a global float2 scratch and the
-    // per-path slots in a global float4 scratch (contribution d, rhs;
-    // potential across the head link), so they stay in L2.  The tables are
-    // read from the item's blob in global memory (32-bit records); each lane
-    // loads the next eight compartments of its path while it eliminates (or
-    // substitutes) the current eight.
+    // giant_update_kernel (phase C and the gates, likewise).  The active
+    // conductance and rhs of each compartment (after elimination f and c,
+    // after substitution dV) live in a global float2 scratch, the rhs's low
+    // word in a float scratch and the per-path slots in a global float4
+    // scratch, so they stay in L2.  The tables are read from the item's
+    // blob in global memory (32-bit records); each lane loads the next eight
+    // compartments of its path while it eliminates (or substitutes) the
+    // current eight.
     __shared__ int s_item;
 
     const long long n = (long long)a.ctl->step_base + a.step_offset;
@@ -819,8 +870,10 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
         const GroupRec G = a.groups[gi];
         const int64_t c0 = G.comp0;
         const int32_t *Vq = a.Vq + c0;
-        const float *gax = a.gax + c0;
+        const float2 *gax = a.gax + c0;
+        const float2 *dpp = a.dp + c0;
         float2 *dr = a.dr + G.scratch0;
+        float *drl = a.drl + G.scratch0;
         float4 *pq = a.pq + G.pscratch0;
         const unsigned char *blob = a.meta + G.meta_off;
         const NrnG *nrns = (const NrnG *)blob;
@@ -829,95 +882,131 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
         const int32_t *loffs = (const int32_t *)(blob + G.loffs_off);
         const int32_t *mcnt = (const int32_t *)(blob + G.mcnt_off);
 
-        // S. synaptic sites, then decay (sites are distinct compartments);
-        //    per path the exact potential difference across its head link
-        //    (for the path from a soma: the stimulus current)
+        // S. synaptic sites (then their decay; sites are distinct
+        //    compartments), the current across each path's head link into
+        //    its head (for the path from a soma: the stimulus), then out of
+        //    the parent compartments, summed per parent in fold-list order
+        //    (as in step_fp32c_kernel)
         for (int t = tid; t < G.nsite; t += NT) {
             const int st = G.site0 + t;
             const int c = a.site_comp[st];
-            const float g = a.gsyn[st];
+            const float2 g0 = a.gsyn[st];
+            const mmf::F2 g = mmf::two_sum(g0.x, g0.y);
             float2 v = dr[c];
-            if (a.g_implicit) v.x += g;
-            v.y = fmaf(-g, vminus(Vq[c], a.Esyn), v.y);
+            if (a.g_implicit) v.x += g.hi;
+            const mmf::F2 r = mmf::add(mmf::F2{v.y, drl[c]}, mmf::neg(mmf::mul(g, vminus(Vq[c], a.Esyn))));
+            v.y = r.hi;
             dr[c] = v;
-            a.gsyn[st] = g * a.decay;
+            drl[c] = r.lo;
+            a.gsyn[st] = tof2(mmf::mul(g, f2(a.decay)));
         }
+        __syncthreads();
         for (int pi = tid; pi < G.npath; pi += NT) {
             const PathG P = paths[pi];
-            pq[pi].z = P.parent >= 0 ? mmf::vdiff(Vq[P.parent], Vq[P.head])
-                                     : (float)a.stim[G.neuron0 + (P.nflag & kPathNeuronG)];
+            mmf::F2 t;
+            if (P.parent >= 0) {
+                const float2 gs = gax[P.head];
+                t = mmf::mul(mmf::F2{fabsf(gs.x), gs.y}, mmf::vdiff_df(Vq[P.parent], Vq[P.head]));
+                pq[pi].z = t.hi;
+                pq[pi].w = t.lo;
+            } else {
+                t = mmf::split_d(a.stim[G.neuron0 + (P.nflag & kPathNeuronG)]);
+            }
+            const mmf::F2 r = mmf::add(mmf::F2{dr[P.head].y, drl[P.head]}, t);
+            dr[P.head].y = r.hi;
+            drl[P.head] = r.lo;
+        }
+        __syncthreads();
+        for (int e = tid; e < G.npath; e += NT) {
+            const int att = fold[e].y;
+            if (att < 0) continue;  // a path from a soma (no parent)
+            if (e > 0 && fold[e - 1].y == att) continue;  // not the first path of its parent
+            mmf::F2 t{0.f, 0.f};
+            for (int z = e; z < G.npath && fold[z].y == att; ++z) {
+                const float4 q = pq[fold[z].x];
+                t = mmf::add(t, mmf::F2{q.z, q.w});
+            }
+            const mmf::F2 r = mmf::add(mmf::F2{dr[att].y, drl[att]}, mmf::neg(t));
+            dr[att].y = r.hi;
+            drl[att] = r.lo;
         }
         __syncthreads();
 
         // B. leaves-to-root elimination path by path, from the deepest level
-        //    up (as in step_fp32c_kernel)
+        //    up (as in step_fp32c_kernel: passive diagonal plus the active
+        //    conductance carried up the tree)
         auto eliminate_path = [&](int pi) {
             const PathG P = paths[pi];
             const int h = P.head;
-            const float ge = fabsf(gax[h]), gh = a.gimp * ge, vt = pq[pi].z;
             int j = P.end - 1;
             const float2 v0 = dr[j];
-            float db = v0.x, rb = v0.y, dh = db, rh = rb;
-            float g0[8], d0[8], r0[8], g1[8], d1[8], r1[8];
-            auto load = [&](int jj, float *g, float *d, float *r) {
+            float eb = v0.x, rb = v0.y, eh = eb, rh = rb;
+            float g0[8], l0[8], d0[8], q0[8], e0[8], r0[8];
+            float g1[8], l1[8], d1[8], q1[8], e1[8], r1[8];
+            auto load = [&](int jj, float *g, float *l, float *d, float *q, float *ee, float *r) {
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    const int q = max(jj - k, h + 1);
-                    g[k] = a.gimp * fabsf(gax[q]);
-                    const float2 w = dr[q - 1];
-                    d[k] = w.x;
+                    const int x = max(jj - k, h + 1);
+                    const float2 gs = gax[x], dq = dpp[x], w = dr[x - 1];
+                    g[k] = a.gimp * fabsf(gs.x);
+                    l[k] = a.gimp * gs.y;
+                    d[k] = dq.x;
+                    q[k] = dq.y;
+                    ee[k] = w.x;
                     r[k] = w.y;
                 }
             };
-            auto chain = [&](int jj, const float *g, const float *d, const float *r) {
+            auto chain = [&](int jj, const float *g, const float *l, const float *d, const float *q,
+                             const float *ee, const float *r) {
                 const int cnt = jj - h;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    const float inv = rcp_approx(db);
-                    const float f = g[k] * inv;
+                    const float inv = rcp_nr(d[k] + (q[k] + eb));
+                    const float f = fmaf(g[k], inv, l[k] * inv);
                     if (k < cnt) dr[jj - k] = make_float2(f, rb * inv);
                     rb = fmaf(f, rb, r[k]);
-                    db = fmaf(-g[k] * g[k], inv, d[k]);
+                    eb = fmaf(g[k] * rcp_nr(d[k]) * f, eb, ee[k]);
                     if (k == cnt - 1) {
-                        dh = db;
+                        eh = eb;
                         rh = rb;
                     }
                 }
             };
             if (j > h) {
-                load(j, g0, d0, r0);
+                load(j, g0, l0, d0, q0, e0, r0);
                 for (;;) {
                     int jn = j - 8;
                     bool more = jn > h;
-                    if (more) load(jn, g1, d1, r1);
-                    chain(j, g0, d0, r0);
+                    if (more) load(jn, g1, l1, d1, q1, e1, r1);
+                    chain(j, g0, l0, d0, q0, e0, r0);
                     j = jn;
                     if (!more) break;
                     jn = j - 8;
                     more = jn > h;
-                    if (more) load(jn, g0, d0, r0);
-                    chain(j, g1, d1, r1);
+                    if (more) load(jn, g0, l0, d0, q0, e0, r0);
+                    chain(j, g1, l1, d1, q1, e1, r1);
                     j = jn;
                     if (!more) break;
                 }
             }
-            if (P.parent < 0) {  // soma: the stimulus, then its dV
-                dr[h].y = (rh + vt) * rcp_approx(dh);
+            const float2 dq = dpp[h];
+            const float inv = rcp_nr(dq.x + (dq.y + eh));
+            if (P.parent < 0) {  // soma: its dV
+                dr[h].y = rh * inv;
                 return;
             }
-            dh += gh;
-            rh = fmaf(ge, vt, rh);
-            const float inv = rcp_approx(dh);
-            const float f = gh * inv;
+            const float2 gs = gax[h];
+            const float gh = a.gimp * fabsf(gs.x), gl = a.gimp * gs.y;
+            const float f = fmaf(gh, inv, gl * inv);
             dr[h] = make_float2(f, rh * inv);
-            const float cd = fmaf(-f, gh, gh), cr = fmaf(f, rh, -ge * vt);
+            const float ce = gh * rcp_nr(dq.x) * f * eh, cr = f * rh;
             if (P.nflag & kPathAloneG) {
                 float2 v = dr[P.parent];
-                v.x += cd;
+                v.x += ce;
                 v.y += cr;
                 dr[P.parent] = v;
             } else {
-                pq[pi].x = cd;
+                pq[pi].x = ce;
                 pq[pi].y = cr;
             }
         };
@@ -1041,7 +1130,7 @@ __device__ __forceinline__ int giant_of_chunk(const StepArgs32 &a, int64_t ch)
 }
 
 // Phase A of every giant compartment (as in step_fp32c_kernel), into the
-// global scratch.
+// global scratch (the rhs's low word into its own array).
 __global__ void __launch_bounds__(256) giant_assemble_kernel(StepArgs32 a)
 {
     const int64_t nch = a.gchunk0[a.item1 - a.item0];
@@ -1050,34 +1139,32 @@ __global__ void __launch_bounds__(256) giant_assemble_kernel(StepArgs32 a)
         const GroupRec &G = a.groups[a.item0 + k];
         const int64_t c0 = G.comp0;
         const int32_t *Vq = a.Vq + c0;
-        const float *gax = a.gax + c0;
+        const float2 *gax = a.gax + c0;
         float2 *dr = a.dr + G.scratch0;
+        float *drl = a.drl + G.scratch0;
         const int i0 = (int)(ch - a.gchunk0[k]) * kGiantChunk, i1 = min(i0 + kGiantChunk, G.ncomp);
         for (int i = i0 + (int)threadIdx.x; i < i1; i += 256) {
             const int32_t vq = Vq[i];
-            const float gs = gax[i];
-            const float m = mmf::gate_f(a.mq[c0 + i]), h = mmf::gate_f(a.hq[c0 + i]), nn = mmf::gate_f(a.nq[c0 + i]);
-            const float ar = a.area[c0 + i];
-            const float s = ar * 1e3f;
-            const float gna = a.gNa * s * (m * m * m * h);
-            const float n2 = nn * nn;
-            const float gk = a.gK * s * (n2 * n2);
-            const float gl = a.gL * s;
-            float d = fmaf(ar, a.cm_dt, a.g_implicit ? gna + gk + gl : 0.f);
-            float r = -fmaf(gna, vminus(vq, a.ENa), fmaf(gk, vminus(vq, a.EK), gl * vminus(vq, a.EL)));
-            if (!signbit(gs)) {  // link to the parent i-1
-                const float g = fabsf(gs);
-                d = fmaf(a.gimp, g, d);
-                r = fmaf(g, mmf::vdiff(Vq[i - 1], vq), r);
-            }
+            const float2 gs = gax[i];
+            const mmf::F2 ar = f2(a.area[c0 + i]);
+            const mmf::F2 m = mmf::gate_df(a.mq[c0 + i]), h = mmf::gate_df(a.hq[c0 + i]),
+                          nn = mmf::gate_df(a.nq[c0 + i]);
+            const mmf::F2 gna = mmf::mul(mmf::mul(f2(a.gNa), ar), mmf::mul(mmf::mul(mmf::mul(m, m), m), h));
+            const mmf::F2 n2 = mmf::mul(nn, nn);
+            const mmf::F2 gk = mmf::mul(mmf::mul(f2(a.gK), ar), mmf::mul(n2, n2));
+            const mmf::F2 gl = mmf::mul(f2(a.gL), ar);
+            mmf::F2 r = mmf::add(mmf::mul(gna, vminus(vq, a.ENa)),
+                                 mmf::add(mmf::mul(gk, vminus(vq, a.EK)), mmf::mul(gl, vminus(vq, a.EL))));
+            r = mmf::neg(r);
+            if (!signbit(gs.x))  // link to the parent i-1
+                r = mmf::add(r, mmf::mul(mmf::F2{fabsf(gs.x), gs.y}, mmf::vdiff_df(Vq[i - 1], vq)));
             if (i + 1 < G.ncomp) {
-                const float gc = gax[i + 1];
-                if (!signbit(gc)) {  // link to the child i+1
-                    d = fmaf(a.gimp, gc, d);
-                    r = fmaf(gc, mmf::vdiff(Vq[i + 1], vq), r);
-                }
+                const float2 gc = gax[i + 1];
+                if (!signbit(gc.x))  // link to the child i+1
+                    r = mmf::add(r, mmf::mul(f2(gc), mmf::vdiff_df(Vq[i + 1], vq)));
             }
-            dr[i] = make_float2(d, r);
+            dr[i] = make_float2(a.g_implicit ? gna.hi + gk.hi : 0.f, r.hi);
+            drl[i] = r.lo;
         }
     }
 }
@@ -1123,10 +1210,10 @@ __global__ void gq_to_f64_kernel(const uint32_t *q, double *dst, int64_t n)
         dst[i] = (double)q[i] / kGScaleD;
 }
 
-__global__ void scatter_f32_to_f64_kernel(const float *src, const int64_t *idx, double *dst, int64_t n)
+__global__ void scatter_f2_to_f64_kernel(const float2 *src, const int64_t *idx, double *dst, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[idx[i]] = (double)src[i];
+        dst[idx[i]] = (double)src[i].x + (double)src[i].y;
 }
 
 int grid32(int64_t n, int threads)
@@ -1228,9 +1315,9 @@ int mmk_launch_gq_to_f64(const uint32_t *q, double *dst, int64_t n, void *stream
     return (int)cudaGetLastError();
 }
 
-int mmk_launch_scatter_f32_to_f64(const float *src, const int64_t *idx, double *dst, int64_t n, void *stream)
+int mmk_launch_scatter_f2_to_f64(const float2 *src, const int64_t *idx, double *dst, int64_t n, void *stream)
 {
     if (n <= 0) return 0;
-    scatter_f32_to_f64_kernel<<<grid32(n, 256), 256, 0, (cudaStream_t)stream>>>(src, idx, dst, n);
+    scatter_f2_to_f64_kernel<<<grid32(n, 256), 256, 0, (cudaStream_t)stream>>>(src, idx, dst, n);
     return (int)cudaGetLastError();
 }

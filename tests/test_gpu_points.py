@@ -62,7 +62,7 @@ def _three_class_network():
     and small ones, all driven to fire."""
     parts = [netgen.make_network(1, size_dist=("mono", 20000), p_branch=0.05, syn_per_neuron=0, seed=31,
                                  stim_nA=(2.0, 2.0)),
-             netgen.make_network(1, size_dist=("mono", 9000), p_branch=0.05, syn_per_neuron=0, seed=33,
+             netgen.make_network(1, size_dist=("mono", 6000), p_branch=0.05, syn_per_neuron=0, seed=33,
                                  stim_nA=(2.0, 2.0)),
              netgen.make_network(12, size_dist=("loguniform", 20, 400), p_branch=0.1, syn_per_neuron=0, seed=32,
                                  stim_nA=(0.3, 0.8))]
