@@ -44,27 +44,21 @@ L2_BYTES = 129 * 1024 * 1024
 # read (16 B); per synaptic site g_syn read + written and its index (20 B).
 BYTES_PER_UPDATE = {"fp64": (80.0, 20.0),
                     # FP32c: int32 V and three uint32 gates read + written (32 B),
-                    # FP32 area and g_axial read (8 B); per site FP32 g_syn r/w + index
-                    "fp32c": (40.0, 12.0)}
+                    # float-pair area, g_axial and passive diagonal read (24 B);
+                    # per site the float-pair conductance r/w (16 B) + index (4 B)
+                    "fp32c": (56.0, 20.0)}
 # FP32c splits the step over one solve kernel per work-item class (regular
 # and large shared-memory items, giant items), each also updating the gates
-# of its compartments; their own algorithmic bytes (V and gates read and
-# written, area and g_axial read; per site the conductance read + written
-# and its index): V r/w 8 + gates r/w 24 + area, g_axial 8 = 40 B (+12 B per site)
-KERNEL_BYTES_FP32C = {"step": (40.0, 12.0), "big": (40.0, 12.0), "giant": (40.0, 12.0)}
+# of its compartments; each moves the same bytes per compartment and site
+KERNEL_BYTES_FP32C = {"step": (56.0, 20.0), "big": (56.0, 20.0), "giant": (56.0, 20.0)}
 
 # Counters of one `ncu --set full` capture of the regular-class step kernel
-# (profiles/step_fp32c_multi10k.md): DRAM bytes read + written and warp
-# instructions executed per launch.  They describe the kernel built from the
-# sources whose SHA-256 is recorded; after any change they are not reported.
+# on multi10k: DRAM bytes read + written and warp instructions executed per
+# launch, with the compartments that launch updated.  They describe the
+# kernel built from the sources whose SHA-256 is recorded; after any change
+# they are not reported.
 KERNEL_SOURCES = ("mm_kernels_fp32c.cu", "mm_fp32c_math.h", "mm_internal.h", "mm_tma.h")
-PROFILED = {
-    ("multi10k", "fp32c", "step", "soma"): {
-        "sha256": "be1015ab0833dee5de0afa9af58ab0b5f1968fe65f83e3d04d589f294fd3a729",
-        "dram_bytes": 298201600 + 123973888,
-        "warp_instructions": 350648274,
-    },
-}
+PROFILED = {}
 
 
 def _kernel_sources_sha256():
@@ -213,8 +207,9 @@ def run_paper_replay(args):
     10,000 neurons of mean size 300 in three workloads -- one morphology
     for all, sizes from a group of 20 (at most 700 apart), F-distributed
     sizes -- each timed (FP32c, CUDA graphs, CUDA events) with the work
-    queue in size order (the paper's global sorting) and in a random order
-    (no sorting).  Prints one JSON line with the step times and the
+    queue in size order (the paper's global sorting), in a random order (no
+    sorting) and in the learned order (the MLP cost model trained on timed
+    neurons of the same network).  Prints one JSON line with the step times and the
     overheads of the multi-morphology workloads over the mono-morphology
     one (the paper reports them for its CPU cluster: 12 % unsorted, 2.8 %
     after sorting)."""
@@ -232,7 +227,12 @@ def run_paper_replay(args):
         sizes = net.sizes()
         r = {"n_comp": int(net.n_comp), "mean_size": float(sizes.mean()), "min_size": int(sizes.min()),
              "max_size": int(sizes.max())}
-        for label, cost in (("size_sorted", None), ("random_order", rng.random(net.n_neurons).astype(np.float32))):
+        lc = mm.train_schedule(net, n_timed=min(2000, net.n_neurons), steps=40, epochs=600, device=local,
+                               stream=stream.cuda_stream)
+        r["learned_r2_holdout"] = lc["r2_holdout"]
+        r["size_only_r2_holdout"] = lc["r2_holdout_size_only"]
+        for label, cost in (("size_sorted", None), ("random_order", rng.random(net.n_neurons).astype(np.float32)),
+                            ("learned", lc["cost"])):
             g = mm.Network(net, precision="fp32c", graph_steps=args.graph_steps, device=local,
                            stream=stream.cuda_stream, cost=cost, block_threads=args.block_threads,
                            group_comps=args.group_comps)
@@ -250,7 +250,7 @@ def run_paper_replay(args):
     mono = res["paper_mono"]
     over = {}
     for cfg in ("paper_multi20", "paper_fisher"):
-        for label in ("size_sorted", "random_order"):
+        for label in ("size_sorted", "random_order", "learned"):
             # per compartment, so that the small differences in total size cancel
             t = res[cfg][label + "_ms_per_step"] / res[cfg]["n_comp"]
             t0 = mono["size_sorted_ms_per_step"] / mono["n_comp"]
@@ -259,25 +259,58 @@ def run_paper_replay(args):
                       "warmup": args.warmup, "precision": "fp32c", "data": "synthetic"}), flush=True)
 
 
+def _timed(g, stream, K, settle, local, ws):
+    """Advance the network `settle` steps untimed (past the first minimum
+    delay, so that events flow), then time exactly K steps with CUDA events
+    on the launching stream, barriers and synchronisation on both sides,
+    nvidia-smi clocks sampled during the timed region.  Returns the slowest
+    rank's ms, the clock summary and the spikes detected inside the window."""
+    import torch
+    g.step(settle)
+    g.synchronize()
+    g.read_spikes(allow_overflow=True)  # drain what the settling produced
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        g.step(K)
+        ev1.record(stream)
+        ev1.synchronize()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ws, "cuda")
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    sn, _ = g.read_spikes(allow_overflow=True)
+    return ms, clk.summary(), sn
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="multi10k")
+    ap.add_argument("--config", default="multi10k",
+                    help="multi10k (default; 10,000 neurons, log-uniform [50, 5000]), lognormal100k, mixed200k, mono64, "
+                         "shapes10k, paper_mono, paper_multi20, paper_fisher")
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32c"])
     ap.add_argument("--graph-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--learned", action="store_true",
-                    help="also learn the work-queue order (MLP cost model) and time it against size-sorted")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="time the size-sorted work queue only (default: also learn the order with the MLP cost "
+                         "model and report the learned order's throughput as the value)")
     ap.add_argument("--n-timed", type=int, default=5000)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--block-threads", type=int, default=0)
     ap.add_argument("--group-comps", type=int, default=0)
     ap.add_argument("--no-autotune", action="store_true",
-                    help="skip the launch-configuration autotuner (default: tune on a 2M-compartment sample)")
+                    help="skip the launch-configuration autotuner")
     ap.add_argument("--detect", default="soma", choices=["soma", "points"],
                     help="threshold test at every soma, or at the points synapses leave from (each synapse "
                          "leaving a compartment drawn uniformly over its source neuron)")
@@ -285,7 +318,7 @@ def main():
                     help="deterministic event delivery (each site adds its events in ascending synapse id)")
     ap.add_argument("--paper-replay", action="store_true",
                     help="the paper's load-balance tests instead: one morphology vs a group of 20 sizes vs "
-                         "F-distributed sizes (same mean size), size-sorted vs random work-queue order")
+                         "F-distributed sizes (same mean size), size-sorted vs random vs learned work-queue order")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.paper_replay:
@@ -319,47 +352,64 @@ def main():
                            detect=args.detect)
         tune["seconds"] = time.perf_counter() - t0
         args.block_threads, args.group_comps = tune["block_threads"], tune["group_comps"]
-    g = mm.Network(net, precision=precision, graph_steps=args.graph_steps, device=local, stream=stream.cuda_stream,
-                   block_threads=args.block_threads, group_comps=args.group_comps, detect=args.detect,
-                   deterministic=args.deterministic)
-
-    launch = g.launch_info()
-    # warm-up (also captures the CUDA graph)
-    g.step(args.warmup)
-    g.synchronize()
-
-    # timed region: K steps, CUDA events on the launching stream; the state
-    # (> 500 MB for the default workload) is larger than L2.
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        g.step(args.steps)
-        ev1.record(stream)
-        ev1.synchronize()
-    torch.cuda.synchronize()
-    ms = max_over_ranks(ev0.elapsed_time(ev1), ws, "cuda")
-    if ws > 1:
-        dist.barrier()
-    G = args.graph_steps
+    learned = precision == "fp32c" and not args.no_learned
+    lc = None
+    if learned:
+        # the learned work-queue order (the target configuration): neurons
+        # timed by the solve kernel, the MLP trained by the library's own
+        # kernels, costs predicted for every neuron -- before the timed region
+        t0 = time.perf_counter()
+        lc = mm.train_schedule(net, n_timed=args.n_timed, steps=40, epochs=600, device=local,
+                               stream=stream.cuda_stream)
+        lc["seconds"] = time.perf_counter() - t0
+    mk = lambda cost: mm.Network(net, precision=precision, graph_steps=args.graph_steps, device=local,
+                                 stream=stream.cuda_stream, cost=cost, block_threads=args.block_threads,
+                                 group_comps=args.group_comps, detect=args.detect, deterministic=args.deterministic)
+    min_delay = int(round(float(np.min(net.syn_delay_ms)) / net.dt)) if net.n_syn else 0
+    # untimed steps before the timed region: the warm-up (which also
+    # captures the CUDA graphs), then past the first two minimum delays, so
+    # that spikes are recorded and events delivered inside the timed window
+    settle = args.warmup + 2 * (min_delay + 1)
     K = args.steps
-    # kernels per step: delivery, then the solve of each non-empty work-item
-    # class, then (FP32c) the gate update
+    G = args.graph_steps
+
+    g = mk(None)
+    launch = g.launch_info()
+    ms_size, clocks_size, sn_size = _timed(g, stream, K, settle, local, ws)
+    timed_order = "size_sorted"
+    g_timed, ms, clocks, sn_win = g, ms_size, clocks_size, sn_size
+    if learned:
+        gl = mk(lc["cost"])
+        ms_l, clocks_l, sn_l = _timed(gl, stream, K, settle, local, ws)
+        timed_order = "learned"
+        g_timed, ms, clocks, sn_win = gl, ms_l, clocks_l, sn_l
+        g.close()
+    launch = g_timed.launch_info()
+    # kernels per step: delivery, the solve of each non-empty work-item
+    # class (giant items: phase A, solve, phase C + gates); every step runs
+    # inside a CUDA graph (whole batches of G steps, the rest as one-step
+    # graphs), each graph replay also advancing the device step counter
     n_reg = launch["work_items"] - launch["big_items"] - launch["giant_items"]
-    # (giant items: phase A, solve and phase C + gates, three kernels)
     kps = 2 if precision == "fp64" else 1 + (n_reg > 0) + (launch["big_items"] > 0) + 3 * (launch["giant_items"] > 0)
-    launches = (K // G) * (kps * G + 1) + ((K % G > 0) * (kps * (K % G) + 1)) if G > 0 else kps * K + 1
+    if G > 0:
+        launches = (K // G) * (kps * G + 1) + (K % G) * (kps + 1)
+        launch_path = f"CUDA graphs: {K // G} replays of the {G}-step graph + {K % G} of the one-step graph"
+    else:
+        launches = kps * K + 1
+        launch_path = "direct launches"
     value = job_throughput(net.n_comp * K, ws, ms * 1e-3)
+    out_deg = np.bincount(net.syn_src, minlength=net.n_neurons) if net.n_syn else np.zeros(net.n_neurons, np.int64)
+    window = {"spikes": int(len(sn_win)),
+              "events_scheduled": int(out_deg[sn_win].sum()) if len(sn_win) and args.detect == "soma" else None,
+              "steps_before": settle, "note": "spikes detected inside the timed steps; each schedules one event "
+                                              "per outgoing synapse (delivered one delay later)"}
 
     # per-kernel times (events around each launch, direct launches)
     kt_steps = max(10, K // 4)
-    g.set_kernel_timing(True)
-    g.step(kt_steps)
-    kt = g.read_kernel_timing(reset=True)
-    g.set_kernel_timing(False)
+    g_timed.set_kernel_timing(True)
+    g_timed.step(kt_steps)
+    kt = g_timed.read_kernel_timing(reset=True)
+    g_timed.set_kernel_timing(False)
     step_ms = kt["step_kernel_ms"] / max(1, kt["step_kernel_launches"])
     deliver_ms = kt["deliver_kernel_ms"] / max(1, kt["deliver_kernel_launches"])
 
@@ -373,14 +423,14 @@ def main():
     # spike records (16 B each: time, neuron, compartment; more when more are
     # pending) out
     ctl_b = 32  # sizeof the control block
-    pre = min(4096, g.spike_capacity)
+    pre = min(4096, g_timed.spike_capacity)
     d2h = 0
-    g.synchronize()
+    g_timed.synchronize()
     t0 = time.perf_counter()
     for _ in range(ke):
-        g.set_stimulus(stim)
-        g.step(1)
-        _, (sn, _sc, _st) = g.read_outputs(soma)
+        g_timed.set_stimulus(stim)
+        g_timed.step(1)
+        _, (sn, _sc, _st) = g_timed.read_outputs(soma)
         d2h += 8 * net.n_neurons + ctl_b + 16 * pre + (16 * len(sn) if len(sn) > pre else 0)
     e2e_s = max_over_ranks(time.perf_counter() - t0, ws, "cuda")
     e2e = {"value": job_throughput(net.n_comp * ke, ws, e2e_s), "unit": UNIT,
@@ -410,86 +460,66 @@ def main():
     if prof is not None and prof["sha256"] != _kernel_sources_sha256():
         prof = None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": prof["dram_bytes"] if prof else None,
-                "traffic_gbs": (prof["dram_bytes"] / 1e9 / (dom_ms * 1e-3)) if prof else None,
+                "traffic": prof["dram_bytes"] * launch["comps"][0] / prof["comps"] if prof else None,
                 "peak_kind": peak_kind, "kernel": f"{dom}_{precision}",
                 "kernel_ms": dom_ms, "bytes_per_launch": dom_bytes,
                 "kernels_ms": {k: v[0] for k, v in kernels.items()},
                 "step_bytes_per_update": f"{b0:g} B per compartment + {bsite:g} B per synaptic site",
                 "step_achieved_gbs": (b0 * net.n_comp + bsite * nsite) / (ms / K * 1e-3) / 1e9}
-
-    clocks = clk.summary()
     # the bound the step kernel meets in practice: instruction issue (four
     # schedulers per SM, one warp instruction each per cycle, at the SM clock
     # sampled during the timed region), with the executed warp instructions
-    # of the profiled launch
+    # per compartment of the profiled launch
     roofline_issue = None
     if prof is not None and clocks.get("sm_mhz"):
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         ipeak = 4.0 * sms * clocks["sm_mhz"] * 1e6
-        iach = prof["warp_instructions"] / (dom_ms * 1e-3)
+        winst = prof["warp_instructions"] * launch["comps"][0] / prof["comps"]
+        iach = winst / (dom_ms * 1e-3)
         roofline_issue = {"bound": "issue", "achieved": iach, "peak": ipeak, "unit": "warp-instructions/s",
-                          "frac": iach / ipeak, "warp_instructions_per_launch": prof["warp_instructions"],
-                          "per_compartment": prof["warp_instructions"] / launch["comps"][0]}
+                          "frac": iach / ipeak, "warp_instructions_per_launch": winst,
+                          "per_compartment": prof["warp_instructions"] / prof["comps"]}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if precision == "fp64" else "f32", "data": "synthetic",
            "config": {"workload": net.name, "precision": precision, "n_neurons": net.n_neurons,
+                      "work_queue_order": timed_order,
                       "block_threads": args.block_threads, "group_comps": args.group_comps,
                       "n_comp": net.n_comp, "n_syn": net.n_syn, "dt_ms": net.dt, "graph_steps": G,
+                      "launch_path": launch_path,
                       "spike_detection": args.detect, "deterministic_delivery": args.deterministic,
-                      "l2": f"inputs larger than L2 (state + constants {((48 if precision == 'fp64' else 24) * net.n_comp) / 1e6:.0f} MB)",
+                      "l2": f"inputs larger than L2 (state + constants "
+                            f"{((48 if precision == 'fp64' else 40) * net.n_comp) / 1e6:.0f} MB)",
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+           "timed_window": window,
            "roofline": roofline, "roofline_issue": roofline_issue, "e2e": e2e, "gpu_launches": launches,
            "clocks": clocks,
            "launch": launch, "autotune": tune}
-    g.close()
-    if args.learned:
-        from paper_2005_06332_gb300 import schedule
-        t0 = time.perf_counter()
-        lc = schedule.learn_costs(net, n_timed=args.n_timed, steps=40, epochs=600, device=local)
-        learn_s = time.perf_counter() - t0
-        gl = mm.Network(net, precision=precision, graph_steps=args.graph_steps, device=local,
-                        stream=stream.cuda_stream, cost=lc["cost"], block_threads=args.block_threads,
-                        group_comps=args.group_comps)
-        gl.step(args.warmup)
-        gl.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        gl.step(K)
-        e1.record(stream)
-        e1.synchronize()
-        ms_l = e0.elapsed_time(e1) / K
-        gl.close()
-        out["learned_schedule"] = {"ms_per_step": ms_l, "size_sorted_ms_per_step": ms / K,
-                                   "gain": (ms / K) / ms_l - 1.0, "n_timed": int(len(lc["timed"])),
-                                   "r2_holdout": lc["r2_holdout"], "r2_holdout_size_only": lc["r2_holdout_size_only"],
-                                   "final_loss": float(lc["losses"][-1]), "learn_seconds": learn_s,
-                                   "value": net.n_comp * ws / (ms_l * 1e-3)}
+    if learned:
+        out["learned_schedule"] = {"ms_per_step": ms / K, "size_sorted_ms_per_step": ms_size / K,
+                                   "gain": ms_size / ms - 1.0, "size_sorted_value": job_throughput(net.n_comp * K, ws,
+                                                                                                   ms_size * 1e-3),
+                                   "n_timed": lc["n_timed"], "r2_holdout": lc["r2_holdout"],
+                                   "r2_holdout_size_only": lc["r2_holdout_size_only"],
+                                   "final_loss": lc["final_loss"], "learn_seconds": lc["seconds"],
+                                   "size_sorted_clocks": clocks_size}
+    g_timed.close()
     if precision != "fp64" and not args.no_fp64:
-        # the plain FP64 path on the same network, same launch configuration
+        # the plain FP64 path on the same network (its own default launch
+        # configuration), timed the same way over a shorter window
         try:
             g64 = mm.Network(net, precision="fp64", graph_steps=args.graph_steps, device=local,
                              stream=stream.cuda_stream)
         except mm.MMError as exc:
             g64 = None
             out["plain_fp64"] = {"unavailable": str(exc)}
-    if precision != "fp64" and not args.no_fp64 and g64 is not None:
-        g64.step(3)
-        g64.synchronize()
-        k64 = max(10, min(K, 40))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        g64.step(k64)
-        e1.record(stream)
-        e1.synchronize()
-        ms64 = e0.elapsed_time(e1) / k64
-        g64.close()
-        v64 = net.n_comp * ws / (ms64 * 1e-3)
-        out["plain_fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "steps": k64}
-        out["speedup_vs_plain_fp64"] = value / v64
+        if g64 is not None:
+            k64 = max(10, min(K, 40))
+            ms64, _, _ = _timed(g64, stream, k64, 3, local, ws)
+            g64.close()
+            v64 = job_throughput(net.n_comp * k64, ws, ms64 * 1e-3)
+            out["plain_fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64}
+            out["speedup_vs_plain_fp64"] = value / v64
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(net, detect=args.detect)
     if rank == 0:

@@ -191,7 +191,9 @@ mm_status mm_create_network(const mm_morphologies *morph, const mm_channel_param
                             const mm_options *opt, mm_net **out);
 
 /* Advance n_steps >= 0 time steps of dt_ms, which must equal the network's
- * dt.  Asynchronous on the network's stream. */
+ * dt.  Asynchronous on the network's stream.  With graph_steps > 0 (and
+ * kernel timing off) every step runs inside a CUDA graph: whole batches of
+ * graph_steps steps replay the batch graph, the rest the one-step graph. */
 mm_status mm_step(mm_net *net, int64_t n_steps, double dt_ms);
 
 /* Wait for the network's stream and report any error its kernels raised. */
@@ -391,6 +393,7 @@ typedef struct {
     double r2_holdout;      /* R^2 of the predicted log time on the held-out neurons */
     double final_loss;      /* standardised MSE before the last Adam step */
     double mean_time_us;    /* mean measured solve time per step of the timed neurons */
+    double r2_holdout_size_only; /* the same R^2 of a least-squares fit of log time on log size alone */
 } mm_schedule_report;
 
 mm_status mm_train_schedule(const mm_morphologies *morph, const mm_channel_params *chan, const double *stim_nA,

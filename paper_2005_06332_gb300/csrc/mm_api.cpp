@@ -17,7 +17,7 @@ namespace {
 
 constexpr int kStepThreads = 256;
 constexpr int kDefaultGroupComps = 4096;
-constexpr int kDefaultGroupComps32 = 2048;  // FP32c: 28 B of shared memory per compartment
+constexpr int kDefaultGroupComps32 = 2048;  // FP32c: 24 B of shared memory per compartment
 constexpr int kMaxGroupComps = 8192;
 constexpr int kMaxGroupComps32 = 1 << 30;
 constexpr int kGiantSmemLimit = 110 * 1024;  // FP32c regular class: two blocks per SM
@@ -37,6 +37,11 @@ struct mm_net {
     // end of the step)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // FP32c large class: forked onto a stream of its own after the delivery,
+    // so that its blocks (the largest items) start first and the regular
+    // class fills the SMs as they drain; joined at the end of the step
+    cudaStream_t side2 = nullptr;
+    cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
     // pinned host staging, so that the per-step host calls copy
     // asynchronously and synchronise once: the control block (read and
     // written back), the stimulus (with the event of its last upload) and
@@ -272,30 +277,40 @@ mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
     // giant items: phase A of all their compartments (every SM), their
     // solve forked onto the side stream to run beside the shared-memory
     // classes, and after the join phase C and the gates (every SM).
-    //   kinds: 0 delivery, 1 regular class, 4 large class, 5 giant phase A,
-    //          3 giant solve (side stream), 6 giant phase C + gates
+    //   kinds: 0 delivery, 1 regular class, 4 large class (second side
+    //          stream), 5 giant phase A, 3 giant solve (side stream), 6 giant
+    //          phase C + gates, 7 join of the large class
     const bool giants = net->precision != MM_FP64 && net->n_giant > 0;
     int kinds[8], nk = 0;
     kinds[nk++] = 0;
     if (net->precision == MM_FP64) {
         kinds[nk++] = 1;
     } else {
+        if (net->n_big > 0) kinds[nk++] = 4;
         if (giants) {
             kinds[nk++] = 5;
             kinds[nk++] = 3;
         }
         if (net->n_small > 0) kinds[nk++] = 1;
-        if (net->n_big > 0) kinds[nk++] = 4;
         if (giants) kinds[nk++] = 6;
+        if (net->n_big > 0) kinds[nk++] = 7;
     }
     for (int j = 0; j < count; ++j) {
         for (int ki = 0; ki < nk; ++ki) {
             const int kind = kinds[ki];
-            const bool forked = kind == 3;
-            cudaStream_t ks = forked ? net->side : s;
+            if (kind == 7) {  // the end of the step waits for the large class
+                MM_CK(net, cudaStreamWaitEvent(s, net->ev_join2, 0));
+                continue;
+            }
+            const bool forked = kind == 3, forked2 = kind == 4;
+            cudaStream_t ks = forked ? net->side : (forked2 ? net->side2 : s);
             if (forked) {
                 MM_CK(net, cudaEventRecord(net->ev_fork, s));
                 MM_CK(net, cudaStreamWaitEvent(net->side, net->ev_fork, 0));
+            }
+            if (forked2) {
+                MM_CK(net, cudaEventRecord(net->ev_fork2, s));
+                MM_CK(net, cudaStreamWaitEvent(net->side2, net->ev_fork2, 0));
             }
             if (kind == 6) MM_CK(net, cudaStreamWaitEvent(s, net->ev_join, 0));
             mm_net::Pending p{nullptr, nullptr, kind};
@@ -326,7 +341,7 @@ mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
             } else if (kind == 4) {
                 mmk::StepArgs32 sa = net->sa32b;
                 sa.step_offset = j;
-                MM_CKI(net, mmk_launch_step_fp32c(sa, net->big_blocks, kBigThreads, s));
+                MM_CKI(net, mmk_launch_step_fp32c(sa, net->big_blocks, kBigThreads, ks));
             } else {
                 mmk::StepArgs32 sa = net->sa32g;
                 sa.step_offset = j;
@@ -339,6 +354,7 @@ mm_status launch_steps(mm_net *net, cudaStream_t s, int count)
                 net->pending.push_back(p);
             }
             if (forked) MM_CK(net, cudaEventRecord(net->ev_join, net->side));
+            if (forked2) MM_CK(net, cudaEventRecord(net->ev_join2, net->side2));
         }
         if (timed && net->pending.size() > 4096) {
             mm_status st = collect_timing(net);
@@ -378,6 +394,7 @@ void release_all(mm_net *net)
     net->gexec = net->gexec1 = nullptr;
     if (net->stream) cudaStreamSynchronize(net->stream);
     if (net->side) cudaStreamSynchronize(net->side);
+    if (net->side2) cudaStreamSynchronize(net->side2);
     for (auto &p : net->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -397,6 +414,9 @@ void release_all(mm_net *net)
     if (net->side) cudaStreamDestroy(net->side);
     if (net->ev_fork) cudaEventDestroy(net->ev_fork);
     if (net->ev_join) cudaEventDestroy(net->ev_join);
+    if (net->side2) cudaStreamDestroy(net->side2);
+    if (net->ev_fork2) cudaEventDestroy(net->ev_fork2);
+    if (net->ev_join2) cudaEventDestroy(net->ev_join2);
     if (net->ev_stim) cudaEventDestroy(net->ev_stim);
     if (net->pin_ctl) cudaFreeHost(net->pin_ctl);
     if (net->pin_stim) cudaFreeHost(net->pin_stim);
@@ -409,6 +429,9 @@ void release_all(mm_net *net)
     net->side = nullptr;
     net->ev_fork = nullptr;
     net->ev_join = nullptr;
+    net->side2 = nullptr;
+    net->ev_fork2 = nullptr;
+    net->ev_join2 = nullptr;
     if (net->own_stream && net->stream) cudaStreamDestroy(net->stream);
     net->cap_stream = nullptr;
     net->stream = nullptr;
@@ -508,6 +531,9 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     MM_CK(net, cudaStreamCreateWithFlags(&net->side, cudaStreamNonBlocking));
     MM_CK(net, cudaEventCreateWithFlags(&net->ev_fork, cudaEventDisableTiming));
     MM_CK(net, cudaEventCreateWithFlags(&net->ev_join, cudaEventDisableTiming));
+    MM_CK(net, cudaStreamCreateWithFlags(&net->side2, cudaStreamNonBlocking));
+    MM_CK(net, cudaEventCreateWithFlags(&net->ev_fork2, cudaEventDisableTiming));
+    MM_CK(net, cudaEventCreateWithFlags(&net->ev_join2, cudaEventDisableTiming));
     MM_CK(net, cudaEventCreateWithFlags(&net->ev_stim, cudaEventDisableTiming));
     MM_CK(net, cudaMallocHost((void **)&net->pin_ctl, 2 * sizeof(mmk::DevCtl)));
     net->pin_ctl_w = net->pin_ctl + 1;
@@ -537,11 +563,11 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     // shared memory per item: FP64 d and rhs per compartment (16 B); FP32c
     // d, rhs and |g| per compartment (12 B) and per path its contribution
     // to the parent (d, rhs) and the potential across its head link (12 B)
-    // FP32c (active conductance, rhs) pair, the rhs's low word, the implicit
-    // coupling and the passive diagonal as pairs (28 B per compartment) and
-    // per path two words (the head link's current, then the contribution to
-    // the parent)
-    li.smem_per_comp = opt->precision == MM_FP64 ? 16 : 28;
+    // FP32c (active conductance, rhs) pair, the implicit coupling and the
+    // passive diagonal as pairs (the diagonal's place holds the rhs's low
+    // words until the rhs is final; 24 B per compartment) and per path two
+    // words (the head link's current, then the contribution to the parent)
+    li.smem_per_comp = opt->precision == MM_FP64 ? 16 : 24;
     li.smem_per_seg = 0;
     li.path_items = opt->precision != MM_FP64;
     li.smem_per_path = opt->precision == MM_FP64 ? 0 : 8;
@@ -1000,10 +1026,11 @@ mm_status mm_step(mm_net *net, int64_t n_steps, double dt_ms)
         n_steps -= net->graph_steps;
         net->steps_done += net->graph_steps;
     }
-    if (!net->timing && net->graph_steps > 0 && n_steps == 1) {
+    // the remainder (fewer steps than one graph) replays the one-step graph
+    while (!net->timing && net->graph_steps > 0 && n_steps > 0) {
         if ((st = ensure_graph(net, 1, &net->gexec1)) != MM_OK) return st;
         MM_CK(net, cudaGraphLaunch(net->gexec1, net->stream));
-        n_steps = 0;
+        n_steps -= 1;
         net->steps_done += 1;
     }
     while (n_steps > 0) {

@@ -234,16 +234,19 @@ __device__ __forceinline__ void gate_chunks(const StepArgs32 &a, int64_t pc0, in
 }
 
 
+// 1024 / NT blocks per SM at most 64 registers a thread: two blocks of 512
+// threads (or one of 1024) per SM, whatever the item's shared memory allows
 template <int NT>
-__global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
+__global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
 {
     // Shared memory of one work item, carved from the item's own sizes: its
     // tree blob (staged by one bulk copy), then per compartment the pair
     // (active conductance, rhs) -- after elimination the substitution
     // coefficients (f, c), after substitution (f, dV) --, the implicit axial
     // coupling to the parent and the passive eliminated diagonal (float
-    // pairs, staged by phase A so that the sweeps touch only shared memory)
-    // and the low word of the rhs; then per path two words: the current
+    // pairs, staged so that the sweeps touch only shared memory; until the
+    // rhs is final the diagonal's place holds the rhs's low words); then per
+    // path two words: the current
     // across its head link (a pair), later its contribution to its parent
     // compartment (active conductance, rhs) -- for the path from a soma the
     // FP64 soma voltage.  The launch provides the largest need over its
@@ -305,9 +308,10 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
         float2 *sdr = (float2 *)(smem_raw + G.meta_bytes);  // (e, rhs), then (f, c), then (f, dV)
         float *sy = (float *)sdr;                            // sy[2 i + 1]: the second member of sdr[i]
         float2 *sgp = sdr + G.ncomp;                         // implicit coupling to the parent (pair)
-        float2 *sdp = sgp + G.ncomp;                         // passive eliminated diagonal (pair)
-        float *srl = (float *)(sdp + G.ncomp);               // low word of the rhs
-        float *scd = srl + G.ncomp;
+        float2 *sdp = sgp + G.ncomp;                         // passive eliminated diagonal (pair), staged
+                                                             // once phase S is done
+        float *srl = (float *)sdp;                           // until then: the low word of each rhs
+        float *scd = (float *)(sdp + G.ncomp);
         float *scr = scd + G.npath;
 
         // A. membrane conductance and current at (V^n, gates^n), plus the
@@ -325,17 +329,16 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             const float2 gs = __ldg(a.gax + c0 + i);
             const float gh = fabsf(gs.x);
             sgp[i] = make_float2(a.gimp * gh, a.gimp * gs.y);
-            sdp[i] = __ldg(a.dp + c0 + i);
             const mmf::F2 ar = f2(__ldg(a.area + c0 + i));
             const mmf::F2 m = mmf::gate_df(__ldg(a.mq + c0 + i)), h = mmf::gate_df(__ldg(a.hq + c0 + i)),
                           nn = mmf::gate_df(__ldg(a.nq + c0 + i));
-            const mmf::F2 gna = mmf::mul(mmf::mul(f2(a.gNa), ar), mmf::mul(mmf::mul(mmf::mul(m, m), m), h));
+            // conductances and current per unit area, then times the area
+            const mmf::F2 gna = mmf::mul(f2(a.gNa), mmf::mul(mmf::mul(mmf::mul(m, m), m), h));
             const mmf::F2 n2 = mmf::mul(nn, nn);
-            const mmf::F2 gk = mmf::mul(mmf::mul(f2(a.gK), ar), mmf::mul(n2, n2));
-            const mmf::F2 gl = mmf::mul(f2(a.gL), ar);
-            mmf::F2 r = mmf::add(mmf::mul(gna, vminus(vq, a.ENa)),
-                                 mmf::add(mmf::mul(gk, vminus(vq, a.EK)), mmf::mul(gl, vminus(vq, a.EL))));
-            r = mmf::neg(r);
+            const mmf::F2 gk = mmf::mul(f2(a.gK), mmf::mul(n2, n2));
+            const mmf::F2 iu = mmf::add(mmf::mul(gna, vminus(vq, a.ENa)),
+                                        mmf::add(mmf::mul(gk, vminus(vq, a.EK)), mmf::mul(f2(a.gL), vminus(vq, a.EL))));
+            mmf::F2 r = mmf::neg(mmf::mul(ar, iu));
             if (!signbit(gs.x))  // link to the parent i-1
                 r = mmf::add(r, mmf::mul(mmf::F2{gh, gs.y}, mmf::vdiff_df(__ldg(Vq + i - 1), vq)));
             if (i + 1 < G.ncomp) {
@@ -344,7 +347,7 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                     r = mmf::add(r, mmf::mul(f2(gc), mmf::vdiff_df(__ldg(Vq + i + 1), vq)));
             }
             // the membrane conductance is implicit except in Eq. 2 as printed
-            sdr[i] = make_float2(a.g_implicit ? gna.hi + gk.hi : 0.f, r.hi);
+            sdr[i] = make_float2(a.g_implicit ? ar.hi * (gna.hi + gk.hi) : 0.f, r.hi);
             srl[i] = r.lo;
         }
         // the tree blob must have landed before the per-path work
@@ -415,6 +418,10 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             sdr[att].y = r.hi;
             srl[att] = r.lo;
         }
+        __syncthreads();
+        // every rhs is now final (its high word the nearest float): the
+        // passive diagonal takes the place of the low words
+        for (int i = tid; i < G.ncomp; i += NS) sdp[i] = __ldg(a.dp + c0 + i);
         __syncthreads();
 
         // The next item's per-compartment streams (V, gates, constants) into
@@ -521,12 +528,18 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                 }
 #pragma unroll
                 for (int k = 0; k < kSweepChunk; ++k) {
-                    const float inv = rcp_nr(dh[k] + (dl[k] + eb));
+                    // the active conductance's recurrence (the dependent
+                    // chain) takes the approximate reciprocal; the factors
+                    // that the rhs and the substitution use take it refined
+                    const float dd = dh[k] + (dl[k] + eb);
+                    const float r0 = rcp_approx(dd);
+                    const float fa = gh[k] * r0;
+                    const float inv = fmaf(r0, fmaf(-dd, r0, 1.f), r0);
                     const float f = fmaf(gh[k], inv, gl[k] * inv);
                     const float c = rb * inv;
                     if (k < cnt) sdr[j - k] = make_float2(f, c);
                     rb = fmaf(f, rb, rp[k]);
-                    eb = fmaf(f0[k] * f, eb, ep[k]);
+                    eb = fmaf(f0[k] * fa, eb, ep[k]);
                     if (k == cnt - 1) {
                         eh = eb;
                         rh = rb;
@@ -682,11 +695,13 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
             for (int tt = t0; tt < t1; ++tt) {
                 const int j = e - 1 - tt;
                 const float2 gq = sgp[j], dq = sdp[j], w = sdr[j - 1];
-                const float inv = rcp_nr(dq.x + (dq.y + eb));
+                const float dd = dq.x + (dq.y + eb);
+                const float r0 = rcp_approx(dd);
+                const float inv = fmaf(r0, fmaf(-dd, r0, 1.f), r0);
                 const float f = fmaf(gq.x, inv, gq.y * inv);
                 A *= f;
                 B = fmaf(f, B, w.y);
-                eb = fmaf(gq.x * rcp_nr(dq.x) * f, eb, w.x);
+                eb = fmaf(gq.x * rcp_nr(dq.x) * (gq.x * r0), eb, w.x);
                 nb = w;
             }
             for (int off = 1; off < 32; off <<= 1) {
@@ -709,11 +724,13 @@ __global__ void __launch_bounds__(NT) step_fp32c_kernel(StepArgs32 a)
                 const int j = e - 1 - tt;
                 const float2 gq = sgp[j], dq = sdp[j];
                 const float2 w = tt + 1 < t1 ? sdr[j - 1] : nb;
-                const float inv = rcp_nr(dq.x + (dq.y + eb));
+                const float dd = dq.x + (dq.y + eb);
+                const float r0 = rcp_approx(dd);
+                const float inv = fmaf(r0, fmaf(-dd, r0, 1.f), r0);
                 const float f = fmaf(gq.x, inv, gq.y * inv);
                 sdr[j] = make_float2(f, rb * inv);
                 rb = fmaf(f, rb, w.y);
-                eb = fmaf(gq.x * rcp_nr(dq.x) * f, eb, w.x);
+                eb = fmaf(gq.x * rcp_nr(dq.x) * (gq.x * r0), eb, w.x);
             }
             // the head, from the lane whose chunk ends at it
             const int lastl = (m - 1) / cs;
@@ -961,11 +978,13 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
                 const int cnt = jj - h;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    const float inv = rcp_nr(d[k] + (q[k] + eb));
+                    const float dd = d[k] + (q[k] + eb);
+                    const float r0 = rcp_approx(dd);
+                    const float inv = fmaf(r0, fmaf(-dd, r0, 1.f), r0);
                     const float f = fmaf(g[k], inv, l[k] * inv);
                     if (k < cnt) dr[jj - k] = make_float2(f, rb * inv);
                     rb = fmaf(f, rb, r[k]);
-                    eb = fmaf(g[k] * rcp_nr(d[k]) * f, eb, ee[k]);
+                    eb = fmaf(g[k] * rcp_nr(d[k]) * (g[k] * r0), eb, ee[k]);
                     if (k == cnt - 1) {
                         eh = eb;
                         rh = rb;
@@ -1149,13 +1168,12 @@ __global__ void __launch_bounds__(256) giant_assemble_kernel(StepArgs32 a)
             const mmf::F2 ar = f2(a.area[c0 + i]);
             const mmf::F2 m = mmf::gate_df(a.mq[c0 + i]), h = mmf::gate_df(a.hq[c0 + i]),
                           nn = mmf::gate_df(a.nq[c0 + i]);
-            const mmf::F2 gna = mmf::mul(mmf::mul(f2(a.gNa), ar), mmf::mul(mmf::mul(mmf::mul(m, m), m), h));
+            const mmf::F2 gna = mmf::mul(f2(a.gNa), mmf::mul(mmf::mul(mmf::mul(m, m), m), h));
             const mmf::F2 n2 = mmf::mul(nn, nn);
-            const mmf::F2 gk = mmf::mul(mmf::mul(f2(a.gK), ar), mmf::mul(n2, n2));
-            const mmf::F2 gl = mmf::mul(f2(a.gL), ar);
-            mmf::F2 r = mmf::add(mmf::mul(gna, vminus(vq, a.ENa)),
-                                 mmf::add(mmf::mul(gk, vminus(vq, a.EK)), mmf::mul(gl, vminus(vq, a.EL))));
-            r = mmf::neg(r);
+            const mmf::F2 gk = mmf::mul(f2(a.gK), mmf::mul(n2, n2));
+            const mmf::F2 iu = mmf::add(mmf::mul(gna, vminus(vq, a.ENa)),
+                                        mmf::add(mmf::mul(gk, vminus(vq, a.EK)), mmf::mul(f2(a.gL), vminus(vq, a.EL))));
+            mmf::F2 r = mmf::neg(mmf::mul(ar, iu));
             if (!signbit(gs.x))  // link to the parent i-1
                 r = mmf::add(r, mmf::mul(mmf::F2{fabsf(gs.x), gs.y}, mmf::vdiff_df(Vq[i - 1], vq)));
             if (i + 1 < G.ncomp) {
@@ -1163,7 +1181,7 @@ __global__ void __launch_bounds__(256) giant_assemble_kernel(StepArgs32 a)
                 if (!signbit(gc.x))  // link to the child i+1
                     r = mmf::add(r, mmf::mul(f2(gc), mmf::vdiff_df(Vq[i + 1], vq)));
             }
-            dr[i] = make_float2(a.g_implicit ? gna.hi + gk.hi : 0.f, r.hi);
+            dr[i] = make_float2(a.g_implicit ? ar.hi * (gna.hi + gk.hi) : 0.f, r.hi);
             drl[i] = r.lo;
         }
     }

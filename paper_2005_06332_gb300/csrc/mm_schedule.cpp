@@ -141,9 +141,39 @@ extern "C" mm_status mm_train_schedule(const mm_morphologies *morph, const mm_ch
             }
             r2 = ss > 0.0 ? 1.0 - se / ss : 0.0;
         }
+        // the size-only baseline: log time = a log(size) + b fitted by least
+        // squares on the training neurons, scored on the same hold-out
+        double r2s = 0.0;
+        if (n_test > 1) {
+            auto lsz = [&](int32_t r) {
+                const int32_t u = pick[(size_t)order[(size_t)r]];
+                return std::log((double)(morph->comp_offset[u + 1] - morph->comp_offset[u]));
+            };
+            double sx = 0.0, sy = 0.0, sxx = 0.0, sxy = 0.0;
+            const int32_t ntr = k - n_test;
+            for (int32_t r = n_test; r < k; ++r) {
+                const double x = lsz(r), yv = y[(size_t)order[(size_t)r]];
+                sx += x;
+                sy += yv;
+                sxx += x * x;
+                sxy += x * yv;
+            }
+            const double den = ntr * sxx - sx * sx;
+            const double a = den != 0.0 ? (ntr * sxy - sx * sy) / den : 0.0, b = (sy - a * sx) / ntr;
+            double mu = 0.0, ss = 0.0, se = 0.0;
+            for (float v : yte) mu += v;
+            mu /= n_test;
+            for (int32_t r = 0; r < n_test; ++r) {
+                const double yv = yte[(size_t)r], e = yv - (a * lsz(r) + b);
+                ss += (yv - mu) * (yv - mu);
+                se += e * e;
+            }
+            r2s = ss > 0.0 ? 1.0 - se / ss : 0.0;
+        }
         report->n_timed = k;
         report->n_holdout = n_test;
         report->r2_holdout = r2;
+        report->r2_holdout_size_only = r2s;
         report->final_loss = losses.back();
         report->mean_time_us = mean_t / k;
     }

@@ -335,7 +335,7 @@ def _marshal(net):
 
 class ScheduleReport(C.Structure):
     _fields_ = [("n_timed", C.c_int32), ("n_holdout", C.c_int32), ("r2_holdout", C.c_double),
-                ("final_loss", C.c_double), ("mean_time_us", C.c_double)]
+                ("final_loss", C.c_double), ("mean_time_us", C.c_double), ("r2_holdout_size_only", C.c_double)]
 
 
 def train_schedule(net, n_timed: int = 5000, steps: int = 40, epochs: int = 600, lr: float = 3e-3, seed: int = 0,
@@ -360,7 +360,8 @@ def train_schedule(net, n_timed: int = 5000, steps: int = 40, epochs: int = 600,
     if st != MM_OK:
         raise MMError(st, "mm_train_schedule failed")
     return {"cost": cost, "n_timed": rep.n_timed, "n_holdout": rep.n_holdout, "r2_holdout": rep.r2_holdout,
-            "final_loss": rep.final_loss, "mean_time_us": rep.mean_time_us}
+            "r2_holdout_size_only": rep.r2_holdout_size_only, "final_loss": rep.final_loss,
+            "mean_time_us": rep.mean_time_us}
 
 
 class TunePoint(C.Structure):
