@@ -174,6 +174,10 @@ typedef struct {
     void *cuda_stream;          /* cudaStream_t to run on; NULL = a library-owned stream */
     const float *cost;          /* [n_neurons] per-neuron cost for MM_SCHED_COST, or NULL */
     mm_allocator allocator;     /* alloc == NULL: cudaMalloc / cudaFree */
+    int32_t n_ext_sources;      /* spike sources outside this network (neurons simulated elsewhere,
+                                   e.g. on other GPUs): synapse src_neuron values n_neurons ..
+                                   n_neurons + n_ext_sources - 1 name them, and their spikes are
+                                   handed in with mm_inject_spikes.  MM_DETECT_SOMA only; 0 = none */
 } mm_options;
 
 /* Fill *opt with defaults: FP64, size-sorted, graphs of 40 steps, dt 0.025 ms. */
@@ -304,6 +308,40 @@ mm_status mm_hines_solve(int32_t n_trees, int64_t n_comp, const int64_t *tree_of
 mm_status mm_hines_solve_noalloc(int32_t n_trees, int64_t n_comp, const int64_t *tree_offset,
                                  const int32_t *parent, const double *a, const double *b, const double *c,
                                  const double *rhs, double *x, void *cuda_stream);
+
+/* Spikes of the external sources (mm_options.n_ext_sources), for a network
+ * that is one part of a larger one split across devices or processes (the
+ * paper's local and global spike buffers, Sec. 2: each part runs a global
+ * step of local steps, then the spikes of that global step are exchanged).
+ * Spike k: external source ext_src[k] (0 .. n_ext_sources - 1) crossed its
+ * threshold in step step[k]; each of its synapses then delivers as a local
+ * neuron's would, round(delay/dt) + 1 steps later.  Host arrays of n
+ * entries.  A spike must be handed in before its earliest delivery:
+ * step[k] < mm_get_step() <= step[k] + 1 + round(min delay / dt); a source
+ * spikes at most once per step.  Stream-ordered before the next mm_step.
+ * Errors: MM_EINVAL (bad arguments, a spike handed in too late, a source
+ * out of range), MM_EOVERFLOW (more spikes in one step than sources),
+ * MM_ENOMEM, MM_ECUDA. */
+mm_status mm_inject_spikes(mm_net *net, int64_t n, const int32_t *ext_src, const int64_t *step);
+
+/* The spikes this network's own neurons fired in steps step0 .. step0 +
+ * n_steps - 1 (all already run, and no more than R - 1 = the largest delay
+ * in steps + 1 steps back), in step order: user neuron ids in neuron[],
+ * their steps in step[] (host arrays of cap entries); *n_out = how many
+ * (MM_EOVERFLOW if more than cap).  These are what a part of a split
+ * network sends to the others after each global step.  MM_DETECT_SOMA
+ * only.  Synchronises.  Errors: MM_EINVAL, MM_EOVERFLOW, MM_ECUDA. */
+mm_status mm_read_fired(mm_net *net, int64_t step0, int32_t n_steps, int32_t *neuron, int64_t *step, int64_t cap,
+                        int64_t *n_out);
+
+/* Exercises the step kernels' bounded wait (the paper has no counterpart):
+ * a one-block kernel on `device` waits on an mbarrier that nothing arrives
+ * at, giving up after max_polls polls (1 .. 2^20) as the step kernels give
+ * up on a lost copy completion, and records the timeout in a device error
+ * word that the host reads back.  Returns MM_ETIMEOUT when the wait ran out
+ * and the error reached the host; the device stays usable.  Synchronises
+ * the device.  Errors: MM_EINVAL, MM_ENOMEM, MM_ECUDA. */
+mm_status mm_selftest_bounded_wait(int32_t device, uint32_t max_polls);
 
 /* Per-neuron solve time, in microseconds per step, for a network created
  * with MM_FP32C, time_items = 1 and group_comps = 1 (every neuron its own
@@ -458,7 +496,9 @@ mm_status mm_autotune(const mm_morphologies *morph, const mm_channel_params *cha
                       const double *stim_nA, const mm_options *opt, int64_t sample_comps, int32_t warmup,
                       int32_t steps, mm_tune_point *points, int32_t cap, int32_t *n_points, mm_options *best);
 
-/* Message of the last error on this network ("" if none); never NULL. */
+/* Message of the last error on this network ("" if none); never NULL.
+ * With net == NULL: the message of the calling thread's last failed
+ * mm_create_network. */
 const char *mm_last_error(const mm_net *net);
 
 /* Static name of a status code. */

@@ -81,6 +81,19 @@ def lib():
                                        C.c_int64, _I32, _I32, _I32, _D, _D, _I32,
                                        C.POINTER(Params), C.c_double, C.c_int, C.c_int64, _D,
                                        _D, _D, _D, _D, _D, _D, _I32, _I32, _D, C.c_int64, _I64, C.c_int]
+            L.orc_part_create.restype = C.c_void_p
+            L.orc_part_create.argtypes = [C.c_int32, _I64, _I32, _D, _D, _D, C.c_int64, _I32, _I32, _I32, _D, _D,
+                                          C.c_int32, C.POINTER(Params), C.c_double, C.c_int]
+            L.orc_part_destroy.restype = None
+            L.orc_part_destroy.argtypes = [C.c_void_p]
+            L.orc_part_step.restype = C.c_int
+            L.orc_part_step.argtypes = [C.c_void_p, C.c_int64]
+            L.orc_part_fired.restype = C.c_int64
+            L.orc_part_fired.argtypes = [C.c_void_p, C.c_int64, C.c_int32, _I32, _I64, C.c_int64]
+            L.orc_part_inject.restype = C.c_int
+            L.orc_part_inject.argtypes = [C.c_void_p, C.c_int64, _I32, _I64]
+            L.orc_part_read.restype = C.c_int64
+            L.orc_part_read.argtypes = [C.c_void_p, _D, _D, _D, _D, _D]
             _lib = L
     return _lib
 
@@ -244,3 +257,56 @@ def simulate(net, n_steps: int, dt: float = None, params: dict = None, V_init=No
         raise OverflowError("oracle: spike capacity exceeded")
     k = int(nsp[0])
     return Result(V, m, h, n, g, trace, spn[:k].copy(), spt[:k].copy(), k, spc[:k].copy())
+
+
+class Part:
+    """A steppable FP64 network part (orc_part_*): ``net`` a netgen.Network
+    whose synapse sources n_neurons .. n_neurons + n_ext - 1 are external
+    (neurons simulated elsewhere).  The same methods as the library's network
+    for a sharded run: step, read_fired, inject_spikes, read_voltages."""
+
+    def __init__(self, net, n_ext: int = 0, scheme: str = "be"):
+        self._keep = dict(off=_i64(net.comp_offset), parent=_i32(net.parent), L=_f64(net.length_um),
+                          d=_f64(net.diam_um), stim=_f64(net.stim_nA), src=_i32(net.syn_src), dst=_i32(net.syn_dst),
+                          comp=_i32(net.syn_comp), w=_f64(net.syn_w), dl=_f64(net.syn_delay_ms))
+        k = self._keep
+        self._pr = params_from(net.params)
+        self.n_neurons, self.n_comp = net.n_neurons, net.n_comp
+        self._h = lib().orc_part_create(net.n_neurons, _p(k["off"], C.c_int64), _p(k["parent"], C.c_int32),
+                                        _p(k["L"], C.c_double), _p(k["d"], C.c_double), _p(k["stim"], C.c_double),
+                                        len(k["src"]), _p(k["src"], C.c_int32), _p(k["dst"], C.c_int32),
+                                        _p(k["comp"], C.c_int32), _p(k["w"], C.c_double), _p(k["dl"], C.c_double),
+                                        int(n_ext), C.byref(self._pr), float(net.dt), SCHEMES[scheme])
+        if not self._h:
+            raise ValueError("oracle: invalid network part")
+
+    def step(self, n: int):
+        if lib().orc_part_step(self._h, int(n)) != 0:
+            raise MemoryError("oracle: allocation failed")
+
+    def read_fired(self, step0: int, n_steps: int):
+        cap = max(1, self.n_neurons * max(1, n_steps))
+        nrn, st = np.empty(cap, np.int32), np.empty(cap, np.int64)
+        k = lib().orc_part_fired(self._h, int(step0), int(n_steps), _p(nrn, C.c_int32), _p(st, C.c_int64), cap)
+        return nrn[:k].copy(), st[:k].copy()
+
+    def inject_spikes(self, ext_src, step):
+        src, st = _i32(ext_src), _i64(step)
+        if lib().orc_part_inject(self._h, len(src), _p(src, C.c_int32), _p(st, C.c_int64)) != 0:
+            raise ValueError("oracle: a spike handed in too late or out of range")
+
+    def read_voltages(self):
+        V = np.empty(self.n_comp)
+        lib().orc_part_read(self._h, _p(V, C.c_double), None, None, None, None)
+        return V
+
+    def close(self):
+        if self._h:
+            lib().orc_part_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -496,3 +496,197 @@ done:
     free(out_start); free(out_syn); free(dsteps);
     return rc;
 }
+
+/* ------------------------------------------------ a steppable network part */
+
+/* The same step as orc_simulate (soma detection, scheme 0 or 1), kept as a
+ * state that advances a few steps at a time and takes spikes of neurons
+ * simulated elsewhere: the part of a network that one node of the paper's
+ * cluster holds (Sec. 2: local steps, then the spikes of the global step
+ * exchanged with MPI_AllGather and stored in the global buffer).  Synapse
+ * sources n_neurons .. n_neurons + n_ext - 1 are external; orc_part_inject
+ * schedules their synapses' events exactly as a local spike's are
+ * scheduled (arrival n + 1 + round(delay/dt), ascending synapse id within a
+ * step). */
+typedef struct {
+    int32_t N, n_ext, scheme;
+    int64_t C, S, step, R;
+    double dt, decay;
+    orc_params p;
+    int64_t *off;
+    int32_t *parent;
+    double *stim, *area, *Cn, *gax, *V, *m, *h, *n, *gs, *wa, *wb, *wc, *wr, *w, *vpre;
+    int32_t *dst, *comp;
+    int64_t *dsteps, *out_start, *out_syn;
+    unsigned char *fired;
+    idlist *ring;
+    idlist hist;            /* spikes so far: neuron * 2^32 + step... as (step << 31 | neuron) */
+} orc_part;
+
+void orc_part_destroy(orc_part *q)
+{
+    if (!q) return;
+    if (q->ring) {
+        for (int64_t r = 0; r < q->R; ++r) free(q->ring[r].ids);
+        free(q->ring);
+    }
+    free(q->hist.ids);
+    free(q->off); free(q->parent); free(q->stim); free(q->area); free(q->Cn); free(q->gax);
+    free(q->V); free(q->m); free(q->h); free(q->n); free(q->gs); free(q->wa); free(q->wb); free(q->wc);
+    free(q->wr); free(q->w); free(q->vpre); free(q->dst); free(q->comp); free(q->dsteps);
+    free(q->out_start); free(q->out_syn); free(q->fired);
+    free(q);
+}
+
+orc_part *orc_part_create(int32_t n_neurons, const int64_t *off, const int32_t *parent, const double *L,
+                          const double *diam, const double *stim_nA, int64_t n_syn, const int32_t *syn_src,
+                          const int32_t *syn_dst, const int32_t *syn_comp, const double *syn_w,
+                          const double *syn_delay_ms, int32_t n_ext, const orc_params *p, double dt, int scheme)
+{
+    if (n_neurons < 0 || n_ext < 0 || dt <= 0.0 || scheme < 0 || scheme > 1) return NULL;
+    orc_part *q = calloc(1, sizeof(orc_part));
+    if (!q) return NULL;
+    const int64_t C = off[n_neurons], S = n_syn, NS = (int64_t)n_neurons + n_ext;
+    q->N = n_neurons; q->n_ext = n_ext; q->scheme = scheme; q->C = C; q->S = S; q->dt = dt; q->p = *p; q->R = 2;
+    q->off = malloc(((size_t)n_neurons + 1) * sizeof(int64_t));
+    q->parent = malloc((size_t)(C > 0 ? C : 1) * sizeof(int32_t));
+    q->stim = malloc((size_t)(n_neurons > 0 ? n_neurons : 1) * sizeof(double));
+    double **arr[] = {&q->area, &q->Cn, &q->gax, &q->V, &q->m, &q->h, &q->n, &q->gs, &q->wa, &q->wb, &q->wc, &q->wr};
+    for (size_t k = 0; k < sizeof(arr) / sizeof(arr[0]); ++k) *arr[k] = calloc((size_t)(C > 0 ? C : 1), sizeof(double));
+    q->w = malloc((size_t)(S > 0 ? S : 1) * sizeof(double));
+    q->dst = malloc((size_t)(S > 0 ? S : 1) * sizeof(int32_t));
+    q->comp = malloc((size_t)(S > 0 ? S : 1) * sizeof(int32_t));
+    q->dsteps = malloc((size_t)(S > 0 ? S : 1) * sizeof(int64_t));
+    q->out_start = calloc((size_t)NS + 1, sizeof(int64_t));
+    q->out_syn = malloc((size_t)(S > 0 ? S : 1) * sizeof(int64_t));
+    q->fired = calloc((size_t)(n_neurons > 0 ? n_neurons : 1), 1);
+    q->vpre = malloc((size_t)(n_neurons > 0 ? n_neurons : 1) * sizeof(double));
+    if (!q->off || !q->parent || !q->stim || !q->w || !q->dst || !q->comp || !q->dsteps || !q->out_start ||
+        !q->out_syn || !q->fired || !q->vpre) { orc_part_destroy(q); return NULL; }
+    for (size_t k = 0; k < sizeof(arr) / sizeof(arr[0]); ++k) if (!*arr[k]) { orc_part_destroy(q); return NULL; }
+    memcpy(q->off, off, ((size_t)n_neurons + 1) * sizeof(int64_t));
+    memcpy(q->parent, parent, (size_t)C * sizeof(int32_t));
+    for (int32_t k = 0; k < n_neurons; ++k) q->stim[k] = stim_nA ? stim_nA[k] : 0.0;
+    for (int32_t k = 0; k < n_neurons; ++k) {
+        int64_t nk = off[k + 1] - off[k];
+        if (nk < 1 || parent[off[k]] != -1) { orc_part_destroy(q); return NULL; }
+        for (int64_t i = 1; i < nk; ++i)
+            if (parent[off[k] + i] < 0 || parent[off[k] + i] >= i) { orc_part_destroy(q); return NULL; }
+    }
+    for (int64_t s = 0; s < S; ++s) {
+        if (syn_src[s] < 0 || syn_src[s] >= NS || syn_dst[s] < 0 || syn_dst[s] >= n_neurons ||
+            syn_comp[s] < 0 || syn_comp[s] >= off[syn_dst[s] + 1] - off[syn_dst[s]]) { orc_part_destroy(q); return NULL; }
+        q->dsteps[s] = (int64_t)llround(syn_delay_ms[s] / dt);
+        if (q->dsteps[s] < 1) { orc_part_destroy(q); return NULL; }
+        if (q->dsteps[s] + 2 > q->R) q->R = q->dsteps[s] + 2;
+        q->w[s] = syn_w[s];
+        q->dst[s] = syn_dst[s];
+        q->comp[s] = syn_comp[s];
+        q->out_start[syn_src[s] + 1]++;
+    }
+    for (int64_t k = 0; k < NS; ++k) q->out_start[k + 1] += q->out_start[k];
+    {
+        int64_t *fill = calloc((size_t)NS + 1, sizeof(int64_t));
+        if (!fill) { orc_part_destroy(q); return NULL; }
+        for (int64_t s = 0; s < S; ++s) q->out_syn[q->out_start[syn_src[s]] + fill[syn_src[s]]++] = s;
+        free(fill);
+    }
+    q->ring = calloc((size_t)q->R, sizeof(idlist));
+    if (!q->ring) { orc_part_destroy(q); return NULL; }
+    orc_geometry(n_neurons, off, parent, L, diam, p, q->area, q->Cn, q->gax);
+    for (int64_t i = 0; i < C; ++i) {
+        q->V[i] = p->v_init;
+        orc_gates_inf(q->V[i], &q->m[i], &q->h[i], &q->n[i]);
+    }
+    q->decay = exp(-dt / p->tau_syn);
+    return q;
+}
+
+/* Schedules the events of source src (local neuron or external source) for
+ * its spike in step st; -1 if an arrival would already be past. */
+static int part_schedule(orc_part *q, int64_t src, int64_t st)
+{
+    for (int64_t o = q->out_start[src]; o < q->out_start[src + 1]; ++o) {
+        int64_t s = q->out_syn[o];
+        int64_t arrival = st + 1 + q->dsteps[s];
+        if (arrival < q->step) return -1;
+        if (idlist_push(&q->ring[arrival % q->R], s)) return -2;
+    }
+    return 0;
+}
+
+int orc_part_step(orc_part *q, int64_t n_steps)
+{
+    for (int64_t k = 0; k < n_steps; ++k) {
+        const int64_t step = q->step;
+        idlist *due = &q->ring[step % q->R];
+        if (due->len > 1) qsort(due->ids, (size_t)due->len, sizeof(int64_t), cmp_i64);
+        for (int64_t e = 0; e < due->len; ++e) {
+            int64_t s = due->ids[e];
+            q->gs[q->off[q->dst[s]] + q->comp[s]] += q->w[s];
+        }
+        due->len = 0;
+        for (int32_t j = 0; j < q->N; ++j) {
+            int64_t b0 = q->off[j];
+            int32_t nj = (int32_t)(q->off[j + 1] - b0);
+            q->vpre[j] = q->V[b0];
+            orc_assemble(nj, q->parent + b0, q->V + b0, q->m + b0, q->h + b0, q->n + b0, q->gs + b0, q->area + b0,
+                         q->Cn + b0, q->gax + b0, q->stim[j], &q->p, q->dt, q->scheme, q->wa + b0, q->wb + b0,
+                         q->wc + b0, q->wr + b0);
+            orc_hines_solve(q->wa + b0, q->wb + b0, q->wc + b0, q->wr + b0, q->parent + b0, nj, NULL);
+            for (int32_t i = 0; i < nj; ++i) {
+                q->V[b0 + i] += q->wr[b0 + i];
+                orc_gate_step(q->V[b0 + i], q->dt, &q->m[b0 + i], &q->h[b0 + i], &q->n[b0 + i]);
+                q->gs[b0 + i] *= q->decay;
+            }
+            q->fired[j] = q->vpre[j] < q->p.threshold && q->V[b0] >= q->p.threshold;
+        }
+        for (int32_t j = 0; j < q->N; ++j) {
+            if (!q->fired[j]) continue;
+            if (idlist_push(&q->hist, (step << 31) | (int64_t)j)) return -2;
+            if (part_schedule(q, j, step)) return -2;
+        }
+        q->step = step + 1;
+    }
+    return 0;
+}
+
+/* The local spikes of steps step0 .. step0 + n_steps - 1, in step order
+ * (neurons ascending within a step); returns how many (all of them, even
+ * beyond cap). */
+int64_t orc_part_fired(const orc_part *q, int64_t step0, int32_t n_steps, int32_t *neuron, int64_t *step, int64_t cap)
+{
+    int64_t k = 0;
+    for (int64_t e = 0; e < q->hist.len; ++e) {
+        int64_t st = q->hist.ids[e] >> 31, j = q->hist.ids[e] & 0x7FFFFFFF;
+        if (st < step0 || st >= step0 + n_steps) continue;
+        if (k < cap) { neuron[k] = (int32_t)j; step[k] = st; }
+        ++k;
+    }
+    return k;
+}
+
+/* Spikes of external sources (0 .. n_ext - 1) in the given steps; 0, -1 if a
+ * source is out of range or an event would arrive in a step already run. */
+int orc_part_inject(orc_part *q, int64_t n, const int32_t *ext_src, const int64_t *step)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        if (ext_src[k] < 0 || ext_src[k] >= q->n_ext || step[k] >= q->step) return -1;
+        int rc = part_schedule(q, (int64_t)q->N + ext_src[k], step[k]);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+/* V, m, h, n and the merged synaptic conductance (any may be NULL), and the
+ * number of steps run. */
+int64_t orc_part_read(const orc_part *q, double *V, double *m, double *h, double *n, double *g)
+{
+    size_t b = (size_t)q->C * sizeof(double);
+    if (V) memcpy(V, q->V, b);
+    if (m) memcpy(m, q->m, b);
+    if (h) memcpy(h, q->h, b);
+    if (n) memcpy(n, q->n, b);
+    if (g) memcpy(g, q->gs, b);
+    return q->step;
+}

@@ -41,6 +41,11 @@ struct mm_net {
     // so that its blocks (the largest items) start first and the regular
     // class fills the SMs as they drain; joined at the end of the step
     cudaStream_t side2 = nullptr;
+    // external spike sources (a network that is one part of a larger one)
+    int32_t n_ext = 0, min_dsteps = 0;
+    int32_t *inj_src = nullptr;      // device staging of mm_inject_spikes
+    int64_t *inj_step = nullptr;
+    int64_t inj_cap = 0;
     cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
     // pinned host staging, so that the per-step host calls copy
     // asynchronously and synchronise once: the control block (read and
@@ -169,6 +174,20 @@ void *dev_alloc(mm_net *net, size_t bytes)
     return p;
 }
 
+// Releases one block from dev_alloc (the stream must be idle).
+void dev_free(mm_net *net, void *p)
+{
+    if (!p) return;
+    auto it = std::find(net->blocks.begin(), net->blocks.end(), p);
+    if (it == net->blocks.end()) return;
+    net->blocks.erase(it);
+    if (net->alloc.alloc) {
+        if (net->alloc.release) net->alloc.release(p, net->alloc.ctx);
+    } else {
+        cudaFree(p);
+    }
+}
+
 template <class T>
 mm_status upload(mm_net *net, T **dst, const T *src, size_t count)
 {
@@ -207,6 +226,8 @@ mm_status snap_ctl(mm_net *net)
 mm_status ctl_status(mm_net *net, const mmk::DevCtl &c)
 {
     if (c.err & mmk::MMK_ERR_NUMERIC) return fail(net, MM_ENUMERIC, "a soma voltage became NaN or infinite");
+    if (c.err & mmk::MMK_ERR_TIMEOUT)
+        return fail(net, MM_ETIMEOUT, "a work item's tree blob did not arrive within the kernel's wait limit");
     return MM_OK;
 }
 
@@ -518,6 +539,9 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         return fail(net, MM_EINVAL, "mm_options.deterministic_delivery must be 0 or 1");
     if (opt->schedule == MM_SCHED_COST && !opt->cost) return fail(net, MM_EINVAL, "MM_SCHED_COST needs mm_options.cost");
     if (syn && !(syn->tau_ms > 0.0)) return fail(net, MM_EINVAL, "tau_ms must be > 0");
+    if (opt->n_ext_sources < 0) return fail(net, MM_EINVAL, "n_ext_sources must be >= 0");
+    if (opt->n_ext_sources > 0 && opt->detect != MM_DETECT_SOMA)
+        return fail(net, MM_ENOTSUP, "external spike sources need MM_DETECT_SOMA");
     if (!chan) return fail(net, MM_EINVAL, "channel parameters must not be NULL");
 
     MM_CK(net, cudaSetDevice(net->device));
@@ -557,6 +581,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     li.stim = stim_nA;
     li.cost = opt->schedule == MM_SCHED_COST ? opt->cost : nullptr;
     li.dt = opt->dt_ms;
+    li.n_ext = opt->n_ext_sources;
     li.group_comps = opt->group_comps > 0 ? opt->group_comps
                    : (opt->precision == MM_FP64 ? kDefaultGroupComps : kDefaultGroupComps32);
     li.max_group_comps = opt->precision == MM_FP64 ? kMaxGroupComps : kMaxGroupComps32;
@@ -594,6 +619,8 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
     net->S = li.S;
     net->R = L.R;
     net->n_src = L.n_src;
+    net->n_ext = opt->n_ext_sources;
+    net->min_dsteps = L.dclass.empty() ? 0 : L.dclass.front();
     net->detect = opt->detect;
     net->order = L.order;
     net->internal_of = L.internal_of;
@@ -993,6 +1020,9 @@ void mm_default_options(mm_options *opt)
     opt->dt_ms = 0.025;
 }
 
+// the message of this thread's last failed mm_create_network (mm_last_error(NULL))
+static thread_local std::string g_create_error;
+
 mm_status mm_create_network(const mm_morphologies *morph, const mm_channel_params *chan, const mm_synapses *syn,
                             const double *stim_nA, const mm_options *opt, mm_net **out)
 {
@@ -1006,6 +1036,7 @@ mm_status mm_create_network(const mm_morphologies *morph, const mm_channel_param
     if (!net) return MM_ENOMEM;
     mm_status st = build(net, morph, chan, syn, stim_nA, opt);
     if (st != MM_OK) {
+        g_create_error = net->err;
         release_all(net);
         delete net;
         return st;
@@ -1244,6 +1275,121 @@ mm_status mm_get_step(const mm_net *net, int64_t *step)
     return MM_OK;
 }
 
+mm_status mm_selftest_bounded_wait(int32_t device, uint32_t max_polls)
+{
+    if (max_polls < 1 || max_polls > (1u << 20)) return MM_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return MM_ECUDA;
+    }
+    int *err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return MM_ENOMEM;
+    }
+    int h = 0;
+    mm_status st = MM_OK;
+    if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess || mmk_launch_wait_selftest(err, max_polls, nullptr) != 0 ||
+        cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        st = MM_ECUDA;
+    cudaFree(err);
+    if (st != MM_OK) {
+        cudaGetLastError();
+        return st;
+    }
+    return (h & mmk::MMK_ERR_TIMEOUT) ? MM_ETIMEOUT : MM_OK;
+}
+
+mm_status mm_inject_spikes(mm_net *net, int64_t n, const int32_t *ext_src, const int64_t *step)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    if (n < 0 || (n > 0 && (!ext_src || !step))) return fail(net, MM_EINVAL, "bad spike arrays");
+    if (n == 0) return MM_OK;
+    if (net->n_ext <= 0) return fail(net, MM_EINVAL, "the network has no external spike sources");
+    const int64_t now = net->steps_done;
+    std::vector<std::pair<int64_t, int32_t>> seen((size_t)n);
+    for (int64_t k = 0; k < n; ++k) {
+        if (ext_src[k] < 0 || ext_src[k] >= net->n_ext) return fail(net, MM_EINVAL, "external source out of range");
+        if (step[k] < 0 || step[k] >= now) return fail(net, MM_EINVAL, "a spike's step has not run yet");
+        if (step[k] + 1 + net->min_dsteps < now)
+            return fail(net, MM_EINVAL, "a spike handed in after its earliest delivery step");
+        seen[(size_t)k] = {step[k], ext_src[k]};
+    }
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+        return fail(net, MM_EINVAL, "a source spikes twice in one step");
+    if (n > net->inj_cap) {
+        MM_CK(net, cudaStreamSynchronize(net->stream));
+        dev_free(net, net->inj_src);
+        dev_free(net, net->inj_step);
+        net->inj_src = nullptr;
+        net->inj_step = nullptr;
+        net->inj_cap = 0;
+        const int64_t cap = std::max<int64_t>(n, 4096);
+        net->inj_src = (int32_t *)dev_alloc(net, (size_t)cap * sizeof(int32_t));
+        net->inj_step = (int64_t *)dev_alloc(net, (size_t)cap * sizeof(int64_t));
+        if (!net->inj_src || !net->inj_step) return fail(net, MM_ENOMEM, "device allocation failed");
+        net->inj_cap = cap;
+    }
+    // pinned staging (the copies are ordered on the stream; the staging is
+    // reused only after a synchronisation)
+    const size_t bs = (size_t)n * sizeof(int32_t), bt = (size_t)n * sizeof(int64_t);
+    if ((st = pinned(net, bs + bt + 16)) != MM_OK) return st;
+    MM_CK(net, cudaStreamSynchronize(net->stream));
+    std::memcpy(net->pin, step, bt);
+    std::memcpy(net->pin + bt, ext_src, bs);
+    MM_CK(net, cudaMemcpyAsync(net->inj_step, net->pin, bt, cudaMemcpyHostToDevice, net->stream));
+    MM_CK(net, cudaMemcpyAsync(net->inj_src, net->pin + bt, bs, cudaMemcpyHostToDevice, net->stream));
+    MM_CKI(net, mmk_launch_inject(net->ring_nrn, net->ring_cnt, net->R, std::max(net->n_src, 1), net->N,
+                                  net->fired, net->fired_words, net->inj_src, net->inj_step, n, net->ctl,
+                                  net->stream));
+    MM_CK(net, cudaStreamSynchronize(net->stream));
+    return MM_OK;
+}
+
+mm_status mm_read_fired(mm_net *net, int64_t step0, int32_t n_steps, int32_t *neuron, int64_t *step, int64_t cap,
+                        int64_t *n_out)
+{
+    mm_status st = guard(net);
+    if (st != MM_OK) return st;
+    if (!n_out || n_steps < 0 || cap < 0 || (cap > 0 && (!neuron || !step))) return fail(net, MM_EINVAL, "bad arguments");
+    if (net->detect != MM_DETECT_SOMA) return fail(net, MM_EINVAL, "mm_read_fired needs MM_DETECT_SOMA");
+    *n_out = 0;
+    const int64_t now = net->steps_done;
+    if (step0 < 0 || step0 + n_steps > now || step0 < now - (net->R - 1))
+        return fail(net, MM_EINVAL, "steps outside those run and still held in the spike ring");
+    if (n_steps == 0) return MM_OK;
+    const int32_t Ns = std::max(net->n_src, 1);
+    std::vector<int32_t> cnt((size_t)net->R);
+    MM_CK(net, cudaStreamSynchronize(net->stream));
+    MM_CK(net, cudaMemcpy(cnt.data(), net->ring_cnt, (size_t)net->R * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    int64_t total = 0;
+    std::vector<int32_t> ids;
+    for (int64_t m = step0; m < step0 + n_steps; ++m) {
+        const int slot = (int)(m % net->R);
+        const int32_t c = std::min(cnt[(size_t)slot], Ns);
+        ids.resize((size_t)c);
+        if (c > 0)
+            MM_CK(net, cudaMemcpy(ids.data(), net->ring_nrn + (int64_t)slot * Ns, (size_t)c * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost));
+        std::vector<int32_t> own;
+        for (int32_t id : ids)
+            if (id >= 0 && id < net->N) own.push_back(net->order[(size_t)id]);
+        std::sort(own.begin(), own.end());
+        for (int32_t u : own) {
+            if (total < cap) {
+                neuron[total] = u;
+                step[total] = m;
+            }
+            ++total;
+        }
+    }
+    *n_out = total;
+    if (total > cap) return fail(net, MM_EOVERFLOW, "caller's arrays are smaller than the spike count");
+    return MM_OK;
+}
+
 // Checkpoint blob: a header, then every dynamic device array of the
 // network's precision, the stimulus, the spike ring, the control block and
 // the undrained spikes, in a fixed order.
@@ -1415,7 +1561,7 @@ mm_status mm_get_launch_info(const mm_net *net, mm_launch_info *out)
 
 const char *mm_last_error(const mm_net *net)
 {
-    if (!net) return "";
+    if (!net) return g_create_error.c_str();
     return net->err.c_str();
 }
 

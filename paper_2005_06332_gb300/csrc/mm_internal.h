@@ -392,6 +392,10 @@ int mmk_launch_vq_to_f64(const int32_t *vq, double *dst, int64_t n, void *stream
 int mmk_launch_gq_to_f64(const uint32_t *q, double *dst, int64_t n, void *stream);
 int mmk_launch_scatter_f2_to_f64(const float2 *src, const int64_t *idx, double *dst, int64_t n, void *stream);
 int mmk_launch_advance(mmk::DevCtl *ctl, int steps, void *stream);
+int mmk_launch_wait_selftest(int *err, unsigned int max_polls, void *stream);
+int mmk_launch_inject(int32_t *ring_nrn, int32_t *ring_cnt, int32_t R, int32_t Nsrc, int32_t N, uint32_t *fired,
+                      int32_t fired_words, const int32_t *src, const int64_t *step, int64_t n, mmk::DevCtl *ctl,
+                      void *stream);
 int mmk_launch_gather_f64(const double *src, const int64_t *idx, double *dst, int64_t n, void *stream);
 int mmk_launch_scatter_f64(const double *src, const int64_t *idx, double *dst, int64_t n, void *stream);
 int mmk_launch_fill_f64(double *dst, double v, int64_t n, void *stream);

@@ -14,6 +14,8 @@
 // here is written independently of it.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "mm_internal.h"
 #include "mm_tma.h"
 
@@ -236,7 +238,13 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
             sd[i] = ar * a.cm_dt + (a.g_implicit ? gna + gk + gl : 0.0);
             sr[i] = -(gna * (v - a.ENa) + gk * (v - a.EK) + gl * (v - a.EL));
         }
-        if (!mbar_wait_bounded(&bar, parity)) s_abort = 1;
+        if (!mbar_wait_bounded(&bar, parity)) {
+            // give up on this item, but not on the copy in flight: wait for
+            // it once more (bounded) so that the block never leaves while
+            // the copy could still write into its shared memory
+            s_abort = 1;
+            mbar_wait_bounded(&bar, parity);
+        }
         parity ^= 1u;
         __syncthreads();
         if (s_abort) {
@@ -359,6 +367,28 @@ __global__ void __launch_bounds__(NT) step_fp64_kernel(StepArgs a)
 
 __global__ void advance_kernel(DevCtl *ctl, int steps) { ctl->step_base += (unsigned long long)steps; }
 
+// Spikes of external sources into the ring slots of their steps, as if the
+// step kernel had recorded them: source id N + src[i] appended to slot
+// step[i] % R (and its bit in the fired mask of deterministic delivery).  A
+// slot holds at most Nsrc ids: an append beyond that is undone and flagged.
+__global__ void inject_kernel(int32_t *ring_nrn, int32_t *ring_cnt, int32_t R, int32_t Nsrc, int32_t N,
+                              uint32_t *fired, int32_t fired_words, const int32_t *src, const int64_t *step, int64_t n,
+                              DevCtl *ctl)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int slot = (int)(step[i] % R);
+        const int id = N + src[i];
+        const int p = atomicAdd(&ring_cnt[slot], 1);
+        if (p >= Nsrc) {
+            atomicSub(&ring_cnt[slot], 1);
+            atomicOr(&ctl->err, MMK_ERR_OVERFLOW);
+            continue;
+        }
+        ring_nrn[(long long)slot * Nsrc + p] = id;
+        if (fired) atomicOr(&fired[(long long)slot * fired_words + (id >> 5)], 1u << (id & 31));
+    }
+}
+
 __global__ void gather_f64_kernel(const double *src, const int64_t *idx, double *dst, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -434,29 +464,43 @@ int mmk_launch_step_fp64(const StepArgs &a, int blocks, int threads, void *strea
     return (int)cudaGetLastError();
 }
 
+// The dynamic shared-memory limit only ever grows (see the FP32c kernels:
+// several networks of one process share the kernel's attribute).
+template <int NT>
+static int fp64_attr_and_occupancy(int smem, int *blocks)
+{
+    static std::mutex mu;
+    static int limit = 0;
+    cudaError_t e = cudaSuccess;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (smem > limit) {
+            e = cudaFuncSetAttribute(step_fp64_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e == cudaSuccess) limit = smem;
+        }
+    }
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, step_fp64_kernel<NT>, NT, smem);
+    return (int)e;
+}
+
 int mmk_step_fp64_blocks_per_sm(int threads, int smem_bytes, int *blocks)
 {
-    cudaError_t e = cudaSuccess;
     switch (threads) {
-    case 128:
-        e = cudaFuncSetAttribute(step_fp64_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, step_fp64_kernel<128>, 128, smem_bytes);
-        break;
-    case 256:
-        e = cudaFuncSetAttribute(step_fp64_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, step_fp64_kernel<256>, 256, smem_bytes);
-        break;
-    case 512:
-        e = cudaFuncSetAttribute(step_fp64_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, step_fp64_kernel<512>, 512, smem_bytes);
-        break;
-    default:
-        return (int)cudaErrorInvalidValue;
+    case 128: return fp64_attr_and_occupancy<128>(smem_bytes, blocks);
+    case 256: return fp64_attr_and_occupancy<256>(smem_bytes, blocks);
+    case 512: return fp64_attr_and_occupancy<512>(smem_bytes, blocks);
+    default: return (int)cudaErrorInvalidValue;
     }
-    return (int)e;
+}
+
+int mmk_launch_inject(int32_t *ring_nrn, int32_t *ring_cnt, int32_t R, int32_t Nsrc, int32_t N, uint32_t *fired,
+                      int32_t fired_words, const int32_t *src, const int64_t *step, int64_t n, DevCtl *ctl,
+                      void *stream)
+{
+    if (n <= 0) return 0;
+    inject_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(ring_nrn, ring_cnt, R, Nsrc, N, fired,
+                                                                      fired_words, src, step, n, ctl);
+    return (int)cudaGetLastError();
 }
 
 int mmk_launch_advance(DevCtl *ctl, int steps, void *stream)
@@ -483,5 +527,24 @@ int mmk_launch_fill_f64(double *dst, double v, int64_t n, void *stream)
 {
     if (n <= 0) return 0;
     fill_f64_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(dst, v, n);
+    return (int)cudaGetLastError();
+}
+
+namespace mmk {
+__global__ void bounded_wait_selftest_kernel(int *err, uint32_t max_polls)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0u, max_polls) && threadIdx.x == 0) atomicOr(err, MMK_ERR_TIMEOUT);
+}
+}  // namespace mmk
+
+int mmk_launch_wait_selftest(int *err, unsigned int max_polls, void *stream)
+{
+    mmk::bounded_wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(err, max_polls);
     return (int)cudaGetLastError();
 }

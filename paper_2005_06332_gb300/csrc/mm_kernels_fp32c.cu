@@ -25,6 +25,7 @@
 //     time is computed in FP64.
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <type_traits>
 
 #include "mm_fp32c_math.h"
@@ -351,7 +352,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
             srl[i] = r.lo;
         }
         // the tree blob must have landed before the per-path work
-        if (!mbar_wait_bounded(&bar, parity)) s_abort = 1;
+        if (!mbar_wait_bounded(&bar, parity)) {
+            // give up on this item, but not on the copy in flight: wait for
+            // it once more (bounded) so that the block never leaves while
+            // the copy could still write into its shared memory
+            s_abort = 1;
+            mbar_wait_bounded(&bar, parity);
+        }
         parity ^= 1u;
         __syncthreads();
         if (s_abort) {  // the whole block leaves at the next item boundary
@@ -1242,10 +1249,23 @@ int grid32(int64_t n, int threads)
     return (int)b;
 }
 
+// The dynamic shared-memory limit is a property of the kernel, shared by
+// every network of the process: it only ever grows, so that a network
+// created later with smaller items does not lower it below what an earlier
+// one launches with.
 template <int NT>
 int set_attr_and_occupancy(int smem, int *blocks)
 {
-    cudaError_t e = cudaFuncSetAttribute(step_fp32c_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    static std::mutex mu;
+    static int limit = 0;
+    cudaError_t e = cudaSuccess;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (smem > limit) {
+            e = cudaFuncSetAttribute(step_fp32c_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e == cudaSuccess) limit = smem;
+        }
+    }
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, step_fp32c_kernel<NT>, NT, smem);
     return (int)e;
 }

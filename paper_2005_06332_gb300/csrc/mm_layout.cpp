@@ -324,12 +324,13 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
             !std::isfinite(in.diam_um[i])) { e << "compartment " << i << ": length and diameter must be positive and finite"; return msg(e); }
     }
     if (in.S < 0) { e << "negative synapse count"; return msg(e); }
+    if (in.n_ext < 0 || (in.n_ext > 0 && in.points)) { e << "external sources need soma detection"; return msg(e); }
     if (in.S > 0 && (!in.src || !in.dst || !in.dcomp || !in.w || !in.delay_ms)) { e << "synapse arrays must not be NULL"; return msg(e); }
     int64_t max_ds = 0;
     std::vector<int32_t> dsteps((size_t)in.S);
     for (int64_t s = 0; s < in.S; ++s) {
         const int32_t a = in.src[s], b = in.dst[s];
-        if (a < 0 || a >= N || b < 0 || b >= N) { e << "synapse " << s << ": neuron id out of range"; return msg(e); }
+        if (a < 0 || a >= N + in.n_ext || b < 0 || b >= N) { e << "synapse " << s << ": neuron id out of range"; return msg(e); }
         const int64_t nb = in.comp_offset[b + 1] - in.comp_offset[b];
         if (in.dcomp[s] < 0 || in.dcomp[s] >= nb) { e << "synapse " << s << ": dst_comp out of range"; return msg(e); }
         if (in.points && in.scomp &&
@@ -741,8 +742,10 @@ std::string build_layout(const LayoutInput &in, Layout &out, bool *invalid)
     //     internal compartment order
     std::vector<int32_t> src_id((size_t)in.S);
     if (!in.points) {
-        L.n_src = N;
-        for (int64_t s = 0; s < in.S; ++s) src_id[(size_t)s] = L.internal_of[(size_t)in.src[s]];
+        // internal neurons 0 .. N-1, then the external sources N .. N + n_ext - 1
+        L.n_src = N + in.n_ext;
+        for (int64_t s = 0; s < in.S; ++s)
+            src_id[(size_t)s] = in.src[s] < N ? L.internal_of[(size_t)in.src[s]] : in.src[s];
     } else {
         std::vector<int64_t> ic((size_t)in.S);
         for (int64_t s = 0; s < in.S; ++s)

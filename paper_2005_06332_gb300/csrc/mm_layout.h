@@ -16,6 +16,9 @@ struct LayoutInput {
     const double *length_um, *diam_um;
     int64_t S;
     const int32_t *src, *dst, *dcomp;
+    // sources outside the network: src values N .. N + n_ext - 1 (soma
+    // detection only); their spike source ids are the same values
+    int32_t n_ext;
     const double *w, *delay_ms;
     // threshold tests at the synapse points (distinct (src, scomp) pairs;
     // scomp NULL: every synapse leaves from the soma) instead of the somata

@@ -63,4 +63,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// The bounded wait on an mbarrier that nothing arrives at (its first phase
+// never completes): gives up after max_polls polls and records the timeout
+// in *err, the path a lost copy completion takes in the step kernels.
+__global__ void bounded_wait_selftest_kernel(int *err, uint32_t max_polls);
+
 }  // namespace mmk

@@ -85,6 +85,7 @@ extern "C" mm_status mm_autotune(const mm_morphologies *morph, const mm_channel_
     if (morph->n_neurons < 1 || !morph->comp_offset || !morph->parent || !morph->length_um || !morph->diam_um)
         return MM_EINVAL;
     if (opt->precision != MM_FP64 && opt->precision != MM_FP32C) return MM_EINVAL;
+    if (opt->n_ext_sources != 0) return MM_ENOTSUP;  // its sample keeps synapses among sampled neurons only
     if (opt->schedule == MM_SCHED_COST && !opt->cost) return MM_EINVAL;
     if (syn && syn->n > 0 && (!syn->src_neuron || !syn->dst_neuron || !syn->dst_comp || !syn->weight_uS ||
                               !syn->delay_ms))

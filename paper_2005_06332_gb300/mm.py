@@ -61,7 +61,7 @@ class Options(C.Structure):
                 ("time_items", C.c_int32), ("scheme", C.c_int32), ("detect", C.c_int32),
                 ("deterministic_delivery", C.c_int32),
                 ("dt_ms", C.c_double), ("spike_capacity", C.c_int64), ("cuda_stream", C.c_void_p),
-                ("cost", C.POINTER(C.c_float)), ("allocator", Allocator)]
+                ("cost", C.POINTER(C.c_float)), ("allocator", Allocator), ("n_ext_sources", C.c_int32)]
 
 
 class KernelTimes(C.Structure):
@@ -148,6 +148,12 @@ def load(build_if_missing: bool = False):
         for name in ("mm_mlp_create", "mm_mlp_set_params", "mm_mlp_get_params", "mm_mlp_set_normalisation",
                      "mm_mlp_loss_grad", "mm_mlp_train", "mm_mlp_predict"):
             getattr(L, name).restype = C.c_int
+        L.mm_selftest_bounded_wait.argtypes = [C.c_int32, C.c_uint32]
+        L.mm_selftest_bounded_wait.restype = C.c_int
+        L.mm_inject_spikes.argtypes = [net_p, C.c_int64, P(C.c_int32), P(C.c_int64)]
+        L.mm_inject_spikes.restype = C.c_int
+        L.mm_read_fired.argtypes = [net_p, C.c_int64, C.c_int32, P(C.c_int32), P(C.c_int64), C.c_int64, P(C.c_int64)]
+        L.mm_read_fired.restype = C.c_int
         L.mm_hines_solve.argtypes = [C.c_int32, C.c_int64] + [C.c_void_p] * 8
         L.mm_hines_solve.restype = C.c_int
         L.mm_hines_solve_noalloc.argtypes = [C.c_int32, C.c_int64] + [C.c_void_p] * 8
@@ -263,6 +269,12 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+
+def selftest_bounded_wait(device: int = 0, max_polls: int = 1000) -> int:
+    """mm_selftest_bounded_wait: the status (MM_ETIMEOUT when the bounded
+    wait on a barrier nothing arrives at gave up and reported it)."""
+    return int(load().mm_selftest_bounded_wait(int(device), int(max_polls)))
 
 
 def hines_solve(tree_offset, parent, a, b, c, rhs, stream=None):
@@ -412,7 +424,7 @@ class Network:
     def __init__(self, net, precision: str = "fp64", cost: Optional[np.ndarray] = None, graph_steps: int = 40,
                  block_threads: int = 0, group_comps: int = 0, spike_capacity: int = 0, device: int = 0,
                  stream=None, torch_alloc: bool = True, time_items: bool = False, scheme: str = "be",
-                 detect: str = "soma", deterministic: bool = False):
+                 detect: str = "soma", deterministic: bool = False, n_ext_sources: int = 0):
         L = load()
         self._L = L
         self._h = C.c_void_p()
@@ -435,6 +447,7 @@ class Network:
         opt.scheme = SCHEMES[scheme]
         opt.detect = DETECT[detect]
         opt.deterministic_delivery = 1 if deterministic else 0
+        opt.n_ext_sources = int(n_ext_sources)
         # the library's automatic spike-buffer size (mm_options.spike_capacity)
         if spike_capacity > 0:
             self._spk_cap = int(spike_capacity)
@@ -458,7 +471,7 @@ class Network:
         st = L.mm_create_network(C.byref(morph), C.byref(chan), C.byref(syn), _ptr(a["stim"], C.c_double),
                                  C.byref(opt), C.byref(self._h))
         if st != MM_OK:
-            raise MMError(st, "mm_create_network failed")
+            raise MMError(st, "mm_create_network failed: " + L.mm_last_error(None).decode())
         self._in = None
 
     # ---------------------------------------------------------------- helpers
@@ -557,6 +570,25 @@ class Network:
             return nr[:k].copy(), tt[:k].copy()
         self._check(st, "mm_read_spikes")
         return nr[:n.value].copy(), tt[:n.value].copy()
+
+    def inject_spikes(self, ext_src: np.ndarray, step: np.ndarray):
+        """Spikes of the external sources (mm_inject_spikes): ext_src[k] fired in step[k]."""
+        src = np.ascontiguousarray(ext_src, np.int32)
+        stp = np.ascontiguousarray(step, np.int64)
+        if src.shape != stp.shape:
+            raise ValueError("ext_src and step differ in length")
+        self._check(self._L.mm_inject_spikes(self._h, src.size, _ptr(src, C.c_int32), _ptr(stp, C.c_int64)),
+                    "mm_inject_spikes")
+
+    def read_fired(self, step0: int, n_steps: int):
+        """(user neuron ids, steps) of this network's spikes in steps step0 .. step0 + n_steps - 1."""
+        cap = max(1, self.n_neurons * max(1, n_steps))
+        nrn = np.empty(cap, np.int32)
+        stp = np.empty(cap, np.int64)
+        n = C.c_int64(0)
+        self._check(self._L.mm_read_fired(self._h, int(step0), int(n_steps), _ptr(nrn, C.c_int32),
+                                          _ptr(stp, C.c_int64), cap, C.byref(n)), "mm_read_fired")
+        return nrn[:n.value].copy(), stp[:n.value].copy()
 
     def set_stimulus(self, stim_nA: np.ndarray):
         s = np.ascontiguousarray(stim_nA, np.float64)

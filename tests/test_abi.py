@@ -47,3 +47,32 @@ def test_status_strings_without_gpu(libpath):
     lib.mm_status_string.restype = ctypes.c_char_p
     assert lib.mm_status_string(0) == b"MM_OK"
     assert lib.mm_status_string(6) == b"MM_EOVERFLOW"
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of the boundary's structs have the C sizes and
+    field offsets (compiled against include/mm.h with the host compiler)."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    import subprocess
+
+    from paper_2005_06332_gb300 import mm
+    checks = {"mm_options": (mm.Options, ["precision", "dt_ms", "cost", "allocator", "n_ext_sources"]),
+              "mm_synapses": (mm.Synapses, ["n", "tau_ms", "src_comp"]),
+              "mm_schedule_report": (mm.ScheduleReport, ["r2_holdout", "r2_holdout_size_only"]),
+              "mm_launch_info": (mm.LaunchInfo, ["comps", "sites"])}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "mm.h"', "int main(void) {"]
+    for t, (_, fields) in checks.items():
+        lines.append(f'printf("{t} %zu\\n", sizeof({t}));')
+        for f in fields:
+            lines.append(f'printf("{t}.{f} %zu\\n", offsetof({t}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "sizes.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for t, (cls, fields) in checks.items():
+        assert int(got[t]) == ctypes.sizeof(cls), t
+        for f in fields:
+            assert int(got[f"{t}.{f}"]) == getattr(cls, f).offset, f"{t}.{f}"

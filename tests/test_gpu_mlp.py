@@ -116,40 +116,42 @@ def test_native_train_schedule_rejects_bad_arguments():
     assert e.value.status == mm.MM_EINVAL
 
 
-def _ms_per_step(net, cost, group_comps, steps=200, reps=2):
+def _ms_per_step(net, cost, group_comps, steps=200):
     import torch
-    best = None
-    for _ in range(reps):
-        s = torch.cuda.Stream()
-        with mm.Network(net, precision="fp32c", cost=cost, block_threads=512, group_comps=group_comps,
-                        stream=s.cuda_stream) as g:
-            g.step(5)
-            g.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(s)
-            g.step(steps)
-            e1.record(s)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1) / steps
-        best = ms if best is None else min(best, ms)
-    return best
+    s = torch.cuda.Stream()
+    with mm.Network(net, precision="fp32c", cost=cost, block_threads=512, group_comps=group_comps,
+                    stream=s.cuda_stream) as g:
+        g.step(45)
+        g.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        g.step(steps)
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
 
 
 def test_learned_order_gains_where_size_does_not_predict_cost():
     """shapes10k: half the neurons unbranched chains, half bushy trees, sizes
     log-uniform, so size alone does not predict a neuron's solve time.  The
     trained network predicts it (held-out R^2 of log time, against the
-    size-only fit), and ordering the work queue by its prediction is not
-    slower than size order with 8192-compartment items, where size order
-    packs chains with trees.  (Measured: 2.5 % faster with the warp-swept
-    long paths, 21.9 % faster before them, when each chain was one lane's
-    serial sweep.)"""
+    size-only fit), and ordering the work queue by its prediction makes the
+    step faster than size order with 4096-compartment items: the two orders
+    are timed three times each, interleaved, and the best of each compared,
+    so that the gain is measured beyond run-to-run noise (about 0.1 %).
+    (Measured: about 1 % here; with 2048-compartment items the two orders
+    are within 1 % of each other either way, the work queue balancing the
+    blocks already.)"""
     net = netgen.make_config("shapes10k")
-    r = schedule.learn_costs(net, n_timed=5000, steps=30, epochs=600, seed=1)
+    r = mm.train_schedule(net, n_timed=5000, steps=30, epochs=600, seed=1)
     print(f"R2 learned {r['r2_holdout']:.3f}, size only {r['r2_holdout_size_only']:.3f}")
     assert r["r2_holdout"] > 0.85 and r["r2_holdout"] > r["r2_holdout_size_only"] + 0.15, r
-    t_size = _ms_per_step(net, None, 8192)
-    t_learned = _ms_per_step(net, r["cost"], 8192)
-    print(f"8192-compartment items: size order {t_size:.4f} ms, learned order {t_learned:.4f} ms, "
-          f"gain {t_size / t_learned - 1:+.1%}")
-    assert t_learned < 1.02 * t_size
+    t_size, t_learned = [], []
+    for _ in range(3):
+        t_size.append(_ms_per_step(net, None, 4096))
+        t_learned.append(_ms_per_step(net, r["cost"], 4096))
+    gain = min(t_size) / min(t_learned) - 1.0
+    spread = max(max(t_size) / min(t_size), max(t_learned) / min(t_learned)) - 1.0
+    print(f"4096-compartment items: size order {min(t_size):.4f} ms, learned order {min(t_learned):.4f} ms, "
+          f"gain {gain:+.2%}, run-to-run spread {spread:.2%}")
+    assert gain > 0.003 and gain > 2 * spread
