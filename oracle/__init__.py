@@ -20,20 +20,26 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mm_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB_TWIN = os.path.join(_BUILD, "liboracle_twin.so")
 _lock = threading.Lock()
 _lib = None
+_lib_twin = None
 
 
-def build(force: bool = False) -> str:
-    """Compile mm_oracle.c (gcc, -O2, no FMA contraction, OpenMP)."""
+def build(force: bool = False, twin: bool = False) -> str:
+    """Compile mm_oracle.c (gcc, -O2, no FMA contraction, OpenMP).  twin:
+    the same oracle with its membrane sums in the opposite order
+    (ORC_SUM_REVERSED), an equally valid FP64 evaluation that rounds
+    differently."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
+    out = _LIB_TWIN if twin else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fno-fast-math",
-               "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+               "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"] + (["-DORC_SUM_REVERSED"] if twin else [])
         subprocess.check_call(cmd)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
 
 
 class Params(C.Structure):
@@ -51,12 +57,11 @@ _I32 = C.POINTER(C.c_int32)
 _I64 = C.POINTER(C.c_int64)
 
 
-def lib():
-    global _lib
+def lib(twin: bool = False):
+    global _lib, _lib_twin
     with _lock:
-        if _lib is None:
-            build()
-            L = C.CDLL(_LIB)
+        if (_lib_twin if twin else _lib) is None:
+            L = C.CDLL(build(twin=twin))
             L.orc_area_cm2.restype = C.c_double
             L.orc_area_cm2.argtypes = [C.c_double, C.c_double]
             L.orc_rhalf_Mohm.restype = C.c_double
@@ -94,8 +99,11 @@ def lib():
             L.orc_part_inject.argtypes = [C.c_void_p, C.c_int64, _I32, _I64]
             L.orc_part_read.restype = C.c_int64
             L.orc_part_read.argtypes = [C.c_void_p, _D, _D, _D, _D, _D]
-            _lib = L
-    return _lib
+            if twin:
+                _lib_twin = L
+            else:
+                _lib = L
+    return _lib_twin if twin else _lib
 
 
 def _p(a, ct):
@@ -265,14 +273,15 @@ class Part:
     (neurons simulated elsewhere).  The same methods as the library's network
     for a sharded run: step, read_fired, inject_spikes, read_voltages."""
 
-    def __init__(self, net, n_ext: int = 0, scheme: str = "be"):
+    def __init__(self, net, n_ext: int = 0, scheme: str = "be", twin: bool = False):
         self._keep = dict(off=_i64(net.comp_offset), parent=_i32(net.parent), L=_f64(net.length_um),
                           d=_f64(net.diam_um), stim=_f64(net.stim_nA), src=_i32(net.syn_src), dst=_i32(net.syn_dst),
                           comp=_i32(net.syn_comp), w=_f64(net.syn_w), dl=_f64(net.syn_delay_ms))
         k = self._keep
         self._pr = params_from(net.params)
         self.n_neurons, self.n_comp = net.n_neurons, net.n_comp
-        self._h = lib().orc_part_create(net.n_neurons, _p(k["off"], C.c_int64), _p(k["parent"], C.c_int32),
+        self._L = lib(twin)
+        self._h = self._L.orc_part_create(net.n_neurons, _p(k["off"], C.c_int64), _p(k["parent"], C.c_int32),
                                         _p(k["L"], C.c_double), _p(k["d"], C.c_double), _p(k["stim"], C.c_double),
                                         len(k["src"]), _p(k["src"], C.c_int32), _p(k["dst"], C.c_int32),
                                         _p(k["comp"], C.c_int32), _p(k["w"], C.c_double), _p(k["dl"], C.c_double),
@@ -281,28 +290,28 @@ class Part:
             raise ValueError("oracle: invalid network part")
 
     def step(self, n: int):
-        if lib().orc_part_step(self._h, int(n)) != 0:
+        if self._L.orc_part_step(self._h, int(n)) != 0:
             raise MemoryError("oracle: allocation failed")
 
     def read_fired(self, step0: int, n_steps: int):
         cap = max(1, self.n_neurons * max(1, n_steps))
         nrn, st = np.empty(cap, np.int32), np.empty(cap, np.int64)
-        k = lib().orc_part_fired(self._h, int(step0), int(n_steps), _p(nrn, C.c_int32), _p(st, C.c_int64), cap)
+        k = self._L.orc_part_fired(self._h, int(step0), int(n_steps), _p(nrn, C.c_int32), _p(st, C.c_int64), cap)
         return nrn[:k].copy(), st[:k].copy()
 
     def inject_spikes(self, ext_src, step):
         src, st = _i32(ext_src), _i64(step)
-        if lib().orc_part_inject(self._h, len(src), _p(src, C.c_int32), _p(st, C.c_int64)) != 0:
+        if self._L.orc_part_inject(self._h, len(src), _p(src, C.c_int32), _p(st, C.c_int64)) != 0:
             raise ValueError("oracle: a spike handed in too late or out of range")
 
     def read_voltages(self):
         V = np.empty(self.n_comp)
-        lib().orc_part_read(self._h, _p(V, C.c_double), None, None, None, None)
+        self._L.orc_part_read(self._h, _p(V, C.c_double), None, None, None, None)
         return V
 
     def close(self):
         if self._h:
-            lib().orc_part_destroy(self._h)
+            self._L.orc_part_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -201,8 +201,16 @@ static void membrane(const orc_params *p, double area, double V, double m, doubl
     double gna = p->gNa * s * m * m * m * h;
     double gk = p->gK * s * n * n * n * n;
     double gl = p->gL * s;
+#ifndef ORC_SUM_REVERSED
     *G = gna + gk + gl + gsyn;
     *I = gna * (V - p->ENa) + gk * (V - p->EK) + gl * (V - p->EL) + gsyn * (V - p->e_syn);
+#else
+    /* the same sums in the opposite order: an equally valid FP64 evaluation
+     * whose rounding differs, built as a second library to measure how much
+     * a neuron's trajectory depends on the last bits of the arithmetic */
+    *G = gsyn + gl + gk + gna;
+    *I = gsyn * (V - p->e_syn) + gl * (V - p->EL) + gk * (V - p->EK) + gna * (V - p->ENa);
+#endif
 }
 
 /* Hines system of one neuron for dV (Eq. 2, symmetric reading), scheme 0:

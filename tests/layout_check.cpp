@@ -6,17 +6,20 @@
 // inside the item, the paths partitioning its compartments, each
 // compartment after a path head having the previous one as its parent, path
 // levels, sweep bundles holding whole neurons, the fold lists and the
-// "alone" flags -- and then replays the kernels' path-by-path elimination
-// and substitution in float on random diagonally dominant coefficients,
-// comparing with the elimination of Algorithm 1 in double over the same
-// parent array.
+// "alone" flags -- and then replays the FP32c kernels' path-by-path
+// elimination and substitution in float on random coefficients, comparing
+// with the elimination of Algorithm 1 in double over the same parent array:
+// the diagonal split into a passive part (eliminated in double, kept as a
+// float pair) and an active part that the float sweep carries up the tree
+// as its perturbation, the couplings as float pairs, reciprocals refined by
+// one Newton step.
 //
 // Paths of at least <warp path> compartments (optional 5th argument, 0 =
 // none) are swept as the step kernel's whole warps sweep them: the path cut
-// into 32 chunks, chunk products of the elimination's 2x2 matrices and of the
-// affine rhs and substitution maps combined by inclusive scans round by
-// round, then the serial recurrences through each chunk from the scanned
-// values (the lanes emulated one after another).
+// into 32 chunks, chunk products of the 2x2 matrices of the active part's
+// recurrence and of the affine rhs and substitution maps combined by
+// inclusive scans round by round, then the serial recurrences through each
+// chunk from the scanned values (the lanes emulated one after another).
 //
 // Usage: layout_check <network file> <group_comps> <regular smem limit> <large smem limit> [warp path]
 // Network file: int32 N | int64 C | int64 comp_offset[N+1] | int32 parent[C].
@@ -54,25 +57,50 @@ struct Aff {
     float a, b;
 };
 
+float rcp_nr(float x)
+{
+    const float r = 1.f / x;
+    return std::fma(r, std::fma(-x, r, 1.f), r);
+}
+
+// Coefficients of one compartment for the sweeps: the implicit coupling to
+// its parent (gh + gl) and the passive eliminated diagonal (dh + dl).
+struct Co {
+    std::vector<float> gh, gl, dh, dl;
+};
+
+// One step of the serial elimination at compartment j of a path: its
+// active part eb and rhs rb in, the next compartment's (ep, rp) out.
+inline void elim_step(const Co &k, int j, float &eb, float &rb, float ep, float rp, float *f_out, float *c_out)
+{
+    const float dd = k.dh[j] + (k.dl[j] + eb);
+    const float r0 = 1.f / dd;
+    const float inv = std::fma(r0, std::fma(-dd, r0, 1.f), r0);
+    const float f = std::fma(k.gh[j], inv, k.gl[j] * inv);
+    *f_out = f;
+    *c_out = rb * inv;
+    rb = std::fma(f, rb, rp);
+    eb = std::fma(k.gh[j] * rcp_nr(k.dh[j]) * (k.gh[j] * r0), eb, ep);
+}
+
 // The warp-swept elimination of the interior of the path [h, e): leaves
-// (f_j, c_j) in (sd, sr) for h < j < e and returns the head's (dh, rh).
-void warp_eliminate(int h, int e, std::vector<float> &sd, std::vector<float> &sr, const std::vector<float> &sg,
-                    float *dh, float *rh)
+// (f_j, c_j) in (se, sr) for h < j < e and returns the head's (eh, rh).
+void warp_eliminate(int h, int e, std::vector<float> &se, std::vector<float> &sr, const Co &k, float *eh, float *rh)
 {
     const int m = e - 1 - h, cs = (m + 31) / 32;
-    const float leafd = sd[e - 1], leafr = sr[e - 1];
+    const float leafe = se[e - 1], leafr = sr[e - 1];
     Mat M[32];
     for (int ln = 0; ln < 32; ++ln) {
         const int t0 = std::min(ln * cs, m), t1 = std::min(t0 + cs, m);
         Mat q{1.f, 0.f, 0.f, 1.f};
         for (int tt = t0; tt < t1; ++tt) {
             const int j = e - 1 - tt;
-            const float g = sg[j], g2 = g * g, dn = sd[j - 1];
-            const float n00 = std::fma(dn, q.m00, -g2 * q.m10), n01 = std::fma(dn, q.m01, -g2 * q.m11);
-            q.m10 = q.m00;
-            q.m11 = q.m01;
-            const float s = 1.f / (std::fabs(n00) + std::fabs(n01));
-            q = {n00 * s, n01 * s, q.m10 * s, q.m11 * s};
+            const float D = k.dh[j] + k.dl[j], En = se[j - 1];
+            const float A = std::fma(k.gh[j] * rcp_nr(D), k.gh[j], En), B = En * D;
+            const float n00 = std::fma(A, q.m00, B * q.m10), n01 = std::fma(A, q.m01, B * q.m11);
+            const float n10 = std::fma(D, q.m10, q.m00), n11 = std::fma(D, q.m11, q.m01);
+            const float s = 1.f / (n00 + n01 + n10 + n11);
+            q = {n00 * s, n01 * s, n10 * s, n11 * s};
         }
         M[ln] = q;
     }
@@ -82,22 +110,22 @@ void warp_eliminate(int h, int e, std::vector<float> &sd, std::vector<float> &sr
         const float s = 1.f / (std::fabs(n00) + std::fabs(n01) + std::fabs(n10) + std::fabs(n11));
         return Mat{n00 * s, n01 * s, n10 * s, n11 * s};
     });
-    float db0[32];
+    float eb0[32];
     Aff F[32];
-    float nbd[32], nbr[32];
+    float nbe[32], nbr[32];
     for (int ln = 0; ln < 32; ++ln) {
         const Mat x = ln ? M[ln - 1] : Mat{1.f, 0.f, 0.f, 1.f};
-        db0[ln] = std::fma(x.m00, leafd, x.m01) / std::fma(x.m10, leafd, x.m11);
+        eb0[ln] = std::fma(x.m00, leafe, x.m01) / std::fma(x.m10, leafe, x.m11);
         const int t0 = std::min(ln * cs, m), t1 = std::min(t0 + cs, m);
-        float db = db0[ln], A = 1.f, B = 0.f;
-        nbd[ln] = nbr[ln] = 0.f;
+        float eb = eb0[ln], A = 1.f, B = 0.f, rb = 0.f, fj, cj;
+        nbe[ln] = nbr[ln] = 0.f;
         for (int tt = t0; tt < t1; ++tt) {
             const int j = e - 1 - tt;
-            const float g = sg[j], inv = 1.f / db, f = g * inv;
-            A *= f;
-            B = std::fma(f, B, sr[j - 1]);
-            db = std::fma(-g * g, inv, sd[j - 1]);
-            nbd[ln] = sd[j - 1];
+            rb = B;
+            elim_step(k, j, eb, rb, se[j - 1], sr[j - 1], &fj, &cj);
+            A *= fj;
+            B = rb;
+            nbe[ln] = se[j - 1];
             nbr[ln] = sr[j - 1];
         }
         F[ln] = {A, B};
@@ -107,19 +135,17 @@ void warp_eliminate(int h, int e, std::vector<float> &sd, std::vector<float> &sr
     for (int ln = 0; ln < 32; ++ln) {
         const Aff x = ln ? F[ln - 1] : Aff{1.f, 0.f};
         const int t0 = std::min(ln * cs, m), t1 = std::min(t0 + cs, m);
-        float db = db0[ln], rb = std::fma(x.a, leafr, x.b);
+        float eb = eb0[ln], rb = std::fma(x.a, leafr, x.b);
         for (int tt = t0; tt < t1; ++tt) {
             const int j = e - 1 - tt;
-            const float g = sg[j];
-            const float wd = tt + 1 < t1 ? sd[j - 1] : nbd[ln], wr = tt + 1 < t1 ? sr[j - 1] : nbr[ln];
-            const float inv = 1.f / db, f = g * inv;
-            sd[j] = f;
-            sr[j] = rb * inv;
-            rb = std::fma(f, rb, wr);
-            db = std::fma(-g * g, inv, wd);
+            const float we = tt + 1 < t1 ? se[j - 1] : nbe[ln], wr = tt + 1 < t1 ? sr[j - 1] : nbr[ln];
+            float fj, cj;
+            elim_step(k, j, eb, rb, we, wr, &fj, &cj);
+            se[j] = fj;
+            sr[j] = cj;
         }
         if (ln == lastl) {
-            *dh = db;
+            *eh = eb;
             *rh = rb;
         }
     }
@@ -230,12 +256,12 @@ int main(int argc, char **argv)
     in.dt = 0.025;
     in.group_comps = std::atoi(argv[2]);
     in.max_group_comps = 1 << 30;
-    in.smem_per_comp = 12;
+    in.smem_per_comp = 24;
     in.smem_per_seg = 0;
     in.giant_smem_limit = std::atoi(argv[3]);
     in.big_smem_limit = std::atoi(argv[4]);
     in.path_items = true;
-    in.smem_per_path = 12;
+    in.smem_per_path = 8;
     const int warp_min = argc > 5 ? std::atoi(argv[5]) : 0;
     long long nwarp_paths = 0;
     mmh::Layout lay;
@@ -260,7 +286,7 @@ int main(int argc, char **argv)
             gcomps += G.ncomp;
             gpaths += G.npath;
         } else {
-            const int64_t need = G.meta_bytes + 12LL * G.ncomp + 12LL * G.npath;
+            const int64_t need = G.meta_bytes + 24LL * G.ncomp + 8LL * G.npath;
             if (need > (gi < lay.n_small ? lay.max_smem : lay.big_max_smem) || G.ncomp > 32767 || G.npath > 32767) ++bad;
         }
         covered += G.ncomp;
@@ -350,16 +376,19 @@ int main(int argc, char **argv)
             const int pd = lay.pdist[(size_t)(c0 + j)];
             pp[j] = pd == 0 ? -1 : j - std::abs(pd);
         }
-        std::vector<double> d(G.ncomp), r(G.ncomp), g(G.ncomp), x(G.ncomp);
+        // coupling g, passive diagonal d0 = d + sum of couplings, active part a
+        std::vector<double> d(G.ncomp), a(G.ncomp), r(G.ncomp), g(G.ncomp), x(G.ncomp);
         for (int j = 0; j < G.ncomp; ++j) {
             g[j] = pp[j] >= 0 ? 0.05 + U(rng) : 0.0;
             d[j] = 1.0 + 0.1 * U(rng);
+            a[j] = 0.3 * U(rng);
             r[j] = U(rng) - 0.5;
         }
-        std::vector<double> dd(d);
-        for (int j = 0; j < G.ncomp; ++j) if (pp[j] >= 0) { dd[j] += g[j]; dd[pp[j]] += g[j]; }
+        std::vector<double> d0(d);
+        for (int j = 0; j < G.ncomp; ++j) if (pp[j] >= 0) { d0[j] += g[j]; d0[pp[j]] += g[j]; }
         {
-            std::vector<double> b(dd), rr(r);
+            std::vector<double> b(d0), rr(r);
+            for (int j = 0; j < G.ncomp; ++j) b[j] += a[j];
             for (int j = G.ncomp - 1; j >= 1; --j) {
                 if (pp[j] < 0) continue;
                 const double fct = g[j] / b[j];
@@ -368,42 +397,48 @@ int main(int argc, char **argv)
             }
             for (int j = 0; j < G.ncomp; ++j) x[j] = (rr[j] + (pp[j] >= 0 ? g[j] * x[pp[j]] : 0.0)) / b[j];
         }
-        std::vector<float> sd(G.ncomp), sr(G.ncomp), sg(G.ncomp), scd(G.npath), scr(G.npath);
-        for (int j = 0; j < G.ncomp; ++j) {  // phase A: links inside paths at both ends
-            float dj = (float)d[j];
-            if (lay.pdist[(size_t)(c0 + j)] == 1) dj += (float)g[j];
-            if (j + 1 < G.ncomp && lay.pdist[(size_t)(c0 + j + 1)] == 1) dj += (float)g[j + 1];
-            sd[j] = dj;
-            sr[j] = (float)r[j];
-            sg[j] = (float)g[j];
+        std::vector<double> dp(d0);  // the passive part eliminated in double
+        for (int j = G.ncomp - 1; j >= 1; --j)
+            if (pp[j] >= 0) dp[pp[j]] -= g[j] * g[j] / dp[j];
+        Co k;
+        k.gh.resize(G.ncomp); k.gl.resize(G.ncomp); k.dh.resize(G.ncomp); k.dl.resize(G.ncomp);
+        for (int j = 0; j < G.ncomp; ++j) {
+            k.gh[j] = (float)g[j];
+            k.gl[j] = (float)(g[j] - (double)k.gh[j]);
+            k.dh[j] = (float)dp[j];
+            k.dl[j] = (float)(dp[j] - (double)k.dh[j]);
         }
-        for (int k = 0; k < G.nbundle; ++k) {
-            const int nl = T.nrn[4 * k + 2], l0 = T.nrn[4 * k + 3];
+        std::vector<float> se(G.ncomp), sr(G.ncomp), scd(G.npath), scr(G.npath);
+        for (int j = 0; j < G.ncomp; ++j) {
+            se[j] = (float)a[j];
+            sr[j] = (float)r[j];
+        }
+        for (int kk = 0; kk < G.nbundle; ++kk) {
+            const int nl = T.nrn[4 * kk + 2], l0 = T.nrn[4 * kk + 3];
             const int *lo = T.loffs.data() + l0, *mc = T.mcnt.data() + l0;
             for (int l = nl - 1; l >= 0; --l) {
                 for (int p = lo[l]; p < lo[l + 1]; ++p) {
                     const int h = H(p);
                     int j = E(p) - 1;
-                    float db = sd[j], rb = sr[j];
+                    float eb = se[j], rb = sr[j];
                     if (warp_min > 0 && E(p) - h >= warp_min) {
-                        warp_eliminate(h, E(p), sd, sr, sg, &db, &rb);
+                        warp_eliminate(h, E(p), se, sr, k, &eb, &rb);
                         ++nwarp_paths;
                     } else {
                         for (; j > h; --j) {
-                            const float inv = 1.f / db, fj = sg[j] * inv;
-                            sd[j] = fj;
-                            sr[j] = rb * inv;
-                            rb = std::fma(fj, rb, sr[j - 1]);
-                            db = std::fma(-sg[j] * sg[j], inv, sd[j - 1]);
+                            float fj, cj;
+                            elim_step(k, j, eb, rb, se[j - 1], sr[j - 1], &fj, &cj);
+                            se[j] = fj;
+                            sr[j] = cj;
                         }
                     }
-                    if (Pa(p) < 0) { sr[h] = rb / db; continue; }
-                    db += sg[h];
-                    const float inv = 1.f / db, fh = sg[h] * inv;
-                    sd[h] = fh;
+                    const float inv = rcp_nr(k.dh[h] + (k.dl[h] + eb));
+                    if (Pa(p) < 0) { sr[h] = rb * inv; continue; }
+                    const float fh = std::fma(k.gh[h], inv, k.gl[h] * inv);
+                    se[h] = fh;
                     sr[h] = rb * inv;
-                    const float cd = std::fma(-fh, sg[h], sg[h]), cr = fh * rb;
-                    if (T.alone[p]) { sd[Pa(p)] += cd; sr[Pa(p)] += cr; } else { scd[p] = cd; scr[p] = cr; }
+                    const float ce = k.gh[h] * rcp_nr(k.dh[h]) * fh * eb, cr = fh * rb;
+                    if (T.alone[p]) { se[Pa(p)] += ce; sr[Pa(p)] += cr; } else { scd[p] = ce; scr[p] = cr; }
                 }
                 const int zend = lo[l] + mc[l];
                 for (int z = lo[l]; z < zend; ++z) {
@@ -411,19 +446,19 @@ int main(int argc, char **argv)
                     if (z > lo[l] && T.fold[2 * z - 1] == att) continue;
                     float ad = 0.f, ar = 0.f;
                     for (int y = z; y < zend && T.fold[2 * y + 1] == att; ++y) { ad += scd[T.fold[2 * y]]; ar += scr[T.fold[2 * y]]; }
-                    sd[att] += ad;
+                    se[att] += ad;
                     sr[att] += ar;
                 }
             }
             for (int l = 0; l < nl; ++l)
                 for (int p = lo[l]; p < lo[l + 1]; ++p) {
                     const int h = H(p);
-                    float xx = Pa(p) >= 0 ? std::fma(sd[h], sr[Pa(p)], sr[h]) : sr[h];
+                    float xx = Pa(p) >= 0 ? std::fma(se[h], sr[Pa(p)], sr[h]) : sr[h];
                     sr[h] = xx;
                     if (warp_min > 0 && E(p) - h >= warp_min)
-                        warp_substitute(h, E(p), xx, sd, sr);
+                        warp_substitute(h, E(p), xx, se, sr);
                     else
-                        for (int j = h + 1; j < E(p); ++j) { xx = std::fma(sd[j], xx, sr[j]); sr[j] = xx; }
+                        for (int j = h + 1; j < E(p); ++j) { xx = std::fma(se[j], xx, sr[j]); sr[j] = xx; }
                 }
         }
         for (int j = 0; j < G.ncomp; ++j) maxrel = std::max(maxrel, std::fabs(sr[j] - x[j]) / (std::fabs(x[j]) + 1e-3));

@@ -66,16 +66,19 @@ def test_virtual_parts_on_one_gpu_match_the_oracle(precision, tol, n_parts):
 
 
 def test_read_fired_lists_the_steps_of_the_spike_records():
-    net = netgen.make_network(40, size_dist=("loguniform", 10, 200), syn_per_neuron=5, seed=12, stim_nA=(0.8, 1.5),
+    """Every spike record (user neuron, crossing time) of the first 120
+    steps (the opening volley; no more than R - 1 = 121 steps back) is one
+    (neuron, step) of mm_read_fired, the time within that step."""
+    net = netgen.make_network(40, size_dist=("loguniform", 10, 200), syn_per_neuron=5, seed=12, stim_nA=(0.3, 0.9),
                               delay_ms=("uniform", 1.0, 3.0))
     with mm.Network(net, precision="fp64") as g:
-        g.step(300)
-        nrn, st = g.read_fired(200, 100)  # no more than R - 1 = 121 steps back
+        g.step(120)
+        nrn, st = g.read_fired(0, 120)
         sn, tt = g.read_spikes()
-    sel = (tt > 200 * net.dt) & (tt <= 300 * net.dt)
-    assert len(nrn) == int(sel.sum()) > 5
-    assert np.all((st >= 200) & (st < 300))
-    # the record's time lies within the step that crossed
+    assert len(sn) > 20 and len(nrn) == len(sn)
+    assert np.all((st >= 0) & (st < 120)) and np.all(np.diff(st) >= 0)
+    ref = sorted(zip(sn.tolist(), np.ceil(tt / net.dt - 1e-9).astype(int) - 1))
+    assert sorted(zip(nrn.tolist(), st.tolist())) == ref
     for k, m in zip(nrn, st):
         t = tt[sn == k]
         assert np.any((t > m * net.dt) & (t <= (m + 1) * net.dt))

@@ -63,7 +63,7 @@ def test_path_tables_and_sweeps(checker, tmp_path, case, warp):
     elif case == "large_and_giant":
         net = netgen.make_network(40, size_dist=("loguniform", 50, 2000), p_branch=0.1, giants=2,
                                   giant_size=40_000, syn_per_neuron=0, seed=13)
-        args = (4096, 24 * 1024, 60 * 1024)
+        args = (2048, 30 * 1024, 80 * 1024)
     else:  # every item beyond shared memory: 32-bit tables only
         net = netgen.make_network(30, size_dist=("loguniform", 20, 600), p_branch=0.2, syn_per_neuron=0, seed=14)
         args = (512, 1, 1)
