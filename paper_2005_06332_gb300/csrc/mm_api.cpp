@@ -475,7 +475,9 @@ std::vector<float2> split_pairs(const std::vector<double> &v)
 // the cylinders: area (cm^2), the axial conductance g to the parent (uS;
 // 1 / the sum of the two half-cylinder resistances, 0 at a soma) with the
 // sign bit of its high word set at path heads and somata, and the passive
-// diagonal d0' of Algorithm 1's elimination (uS): d0_i = C_i/dt + the leak
+// diagonal d0' of Algorithm 1's elimination (uS) as its nearest float and
+// the share of the active part that stands for the rest (below):
+// d0_i = C_i/dt + the leak
 // conductance (backward Euler only: Eq. 2 as printed keeps the membrane
 // current explicit) + the implicit share of every coupling at i, then
 // d0'_p -= (w g_i)^2 / d0'_i over the children i of p, leaves first (w the
@@ -509,6 +511,19 @@ void passive_constants(const mmh::Layout &L, const mm_channel_params &ch, double
         const double wg = w * g[i];
         d[i - (size_t)pd] -= wg * wg / d[i];
     }
+    // The sweep keeps d0' = dh + dl only through its nearest float dh: the
+    // low word dl enters the active part it carries instead (e' = e + dl),
+    // whose recurrence then takes dl_p - sum_c (w g_c / d0'_c)^2 dl_c once
+    // per step (the children's share, at the passive coupling factor; the
+    // remainder is of order (e / d0') dl, below the float rounding of d').
+    std::vector<double> eps(C);
+    for (size_t i = 0; i < C; ++i) eps[i] = d[i] - (double)(float)d[i];
+    for (size_t i = C; i-- > 0;) {
+        const int32_t pd = std::abs(L.pdist[i]);
+        if (pd == 0) continue;
+        const double f0 = w * g[i] / d[i];
+        eps[i - (size_t)pd] -= f0 * f0 * (d[i] - (double)(float)d[i]);
+    }
     area2.resize(C);
     gax2.resize(C);
     dp2.resize(C);
@@ -517,7 +532,7 @@ void passive_constants(const mmh::Layout &L, const mm_channel_params &ch, double
         float2 gp = split_pair(g[i]);
         if (L.pdist[i] <= 0) gp.x = -gp.x;  // path head or soma (-0.0 at a soma)
         gax2[i] = gp;
-        dp2[i] = split_pair(d[i]);
+        dp2[i] = make_float2((float)d[i], (float)eps[i]);
     }
 }
 

@@ -223,7 +223,8 @@ struct StepArgs32 {
                                       // assembled per path
     const float2 *dp;                 // passive diagonal after the elimination of Algorithm 1 with the
                                       // membrane conductance left out (C/dt, leak, implicit axial
-                                      // couplings), uS [C]
+                                      // couplings), uS [C]: .x its nearest float, .y the constant
+                                      // share of the active part that stands for the rest
     float2 *dr;                       // scratch for giant items per compartment: (active conductance, rhs),
                                       // then the substitution coefficients (f, c), then (f, dV)
     float *drl;                       // scratch for giant items: low word of the rhs per compartment

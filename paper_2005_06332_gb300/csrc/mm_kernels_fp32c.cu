@@ -347,8 +347,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
                 if (!signbit(gc.x))  // link to the child i+1
                     r = mmf::add(r, mmf::mul(f2(gc), mmf::vdiff_df(__ldg(Vq + i + 1), vq)));
             }
-            // the membrane conductance is implicit except in Eq. 2 as printed
-            sdr[i] = make_float2(a.g_implicit ? ar.hi * (gna.hi + gk.hi) : 0.f, r.hi);
+            // the active part: the membrane conductance (implicit except in
+            // Eq. 2 as printed) and the constant share that stands for the
+            // passive diagonal's low word
+            const float eps = __ldg(&a.dp[c0 + i].y);
+            sdr[i] = make_float2((a.g_implicit ? ar.hi * (gna.hi + gk.hi) : 0.f) + eps, r.hi);
             srl[i] = r.lo;
         }
         // the tree blob must have landed before the per-path work
@@ -427,8 +430,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
         }
         __syncthreads();
         // every rhs is now final (its high word the nearest float): the
-        // passive diagonal takes the place of the low words
-        for (int i = tid; i < G.ncomp; i += NS) sdp[i] = __ldg(a.dp + c0 + i);
+        // passive diagonal and the factor g / d0' of the active part's
+        // recurrence take the place of the low words
+        for (int i = tid; i < G.ncomp; i += NS) {
+            const float dh = __ldg(&a.dp[c0 + i].x);
+            sdp[i] = make_float2(dh, sgp[i].x * rcp_nr(dh));
+        }
         __syncthreads();
 
         // The next item's per-compartment streams (V, gates, constants) into
@@ -491,7 +498,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
         auto eliminate_head = [&](int pi, const PathQ &P, float eh, float rh) {
             const int h = P.head;
             const float2 dq = sdp[h];
-            const float inv = rcp_nr(dq.x + (dq.y + eh));
+            const float inv = rcp_nr(dq.x + eh);
             if (P.parent < 0) {  // soma: its dV
                 sy[2 * h + 1] = rh * inv;
                 return;
@@ -499,7 +506,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
             const float2 gq = sgp[h];
             const float f = fmaf(gq.x, inv, gq.y * inv);
             sdr[h] = make_float2(f, rh * inv);
-            const float ce = gq.x * rcp_nr(dq.x) * f * eh, cr = f * rh;
+            const float ce = dq.y * f * eh, cr = f * rh;
             if (P.nflag & kPathAlone) {
                 float2 v = sdr[P.parent];
                 v.x += ce;
@@ -519,7 +526,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
             float eh = eb, rh = rb;
             for (; j > h; j -= kSweepChunk) {
                 const int cnt = j - h;
-                float gh[kSweepChunk], gl[kSweepChunk], dh[kSweepChunk], dl[kSweepChunk], f0[kSweepChunk];
+                float gh[kSweepChunk], gl[kSweepChunk], dh[kSweepChunk], f0[kSweepChunk];
                 float ep[kSweepChunk], rp[kSweepChunk];
 #pragma unroll
                 for (int k = 0; k < kSweepChunk; ++k) {
@@ -528,8 +535,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
                     gh[k] = gq.x;
                     gl[k] = gq.y;
                     dh[k] = dq.x;
-                    dl[k] = dq.y;
-                    f0[k] = gq.x * rcp_nr(dq.x);
+                    f0[k] = dq.y;
                     ep[k] = w.x;
                     rp[k] = w.y;
                 }
@@ -538,7 +544,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
                     // the active conductance's recurrence (the dependent
                     // chain) takes the approximate reciprocal; the factors
                     // that the rhs and the substitution use take it refined
-                    const float dd = dh[k] + (dl[k] + eb);
+                    const float dd = dh[k] + eb;
                     const float r0 = rcp_approx(dd);
                     const float fa = gh[k] * r0;
                     const float inv = fmaf(r0, fmaf(-dd, r0, 1.f), r0);
@@ -662,8 +668,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
             for (int tt = t0; tt < t1; ++tt) {
                 const int j = e - 1 - tt;
                 const float2 gq = sgp[j], dq = sdp[j];
-                const float D = dq.x + dq.y, En = sdr[j - 1].x;
-                const float A = fmaf(gq.x * rcp_nr(D), gq.x, En), B = En * D;
+                const float D = dq.x, En = sdr[j - 1].x;
+                const float A = fmaf(dq.y, gq.x, En), B = En * D;
                 const float n00 = fmaf(A, m00, B * m10), n01 = fmaf(A, m01, B * m11);
                 const float n10 = fmaf(D, m10, m00), n11 = fmaf(D, m11, m01);
                 const float s = rcp_approx(n00 + n01 + n10 + n11);
@@ -702,13 +708,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
             for (int tt = t0; tt < t1; ++tt) {
                 const int j = e - 1 - tt;
                 const float2 gq = sgp[j], dq = sdp[j], w = sdr[j - 1];
-                const float dd = dq.x + (dq.y + eb);
+                const float dd = dq.x + eb;
                 const float r0 = rcp_approx(dd);
                 const float inv = fmaf(r0, fmaf(-dd, r0, 1.f), r0);
                 const float f = fmaf(gq.x, inv, gq.y * inv);
                 A *= f;
                 B = fmaf(f, B, w.y);
-                eb = fmaf(gq.x * rcp_nr(dq.x) * (gq.x * r0), eb, w.x);
+                eb = fmaf(dq.y * (gq.x * r0), eb, w.x);
                 nb = w;
             }
             for (int off = 1; off < 32; off <<= 1) {
@@ -731,13 +737,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
                 const int j = e - 1 - tt;
                 const float2 gq = sgp[j], dq = sdp[j];
                 const float2 w = tt + 1 < t1 ? sdr[j - 1] : nb;
-                const float dd = dq.x + (dq.y + eb);
+                const float dd = dq.x + eb;
                 const float r0 = rcp_approx(dd);
                 const float inv = fmaf(r0, fmaf(-dd, r0, 1.f), r0);
                 const float f = fmaf(gq.x, inv, gq.y * inv);
                 sdr[j] = make_float2(f, rb * inv);
                 rb = fmaf(f, rb, w.y);
-                eb = fmaf(gq.x * rcp_nr(dq.x) * (gq.x * r0), eb, w.x);
+                eb = fmaf(dq.y * (gq.x * r0), eb, w.x);
             }
             // the head, from the lane whose chunk ends at it
             const int lastl = (m - 1) / cs;
@@ -971,11 +977,11 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int x = max(jj - k, h + 1);
-                    const float2 gs = gax[x], dq = dpp[x], w = dr[x - 1];
+                    const float2 gs = gax[x], w = dr[x - 1];
                     g[k] = a.gimp * fabsf(gs.x);
                     l[k] = a.gimp * gs.y;
-                    d[k] = dq.x;
-                    q[k] = dq.y;
+                    d[k] = dpp[x].x;
+                    q[k] = g[k] * rcp_nr(d[k]);
                     ee[k] = w.x;
                     r[k] = w.y;
                 }
@@ -985,13 +991,13 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
                 const int cnt = jj - h;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    const float dd = d[k] + (q[k] + eb);
+                    const float dd = d[k] + eb;
                     const float r0 = rcp_approx(dd);
                     const float inv = fmaf(r0, fmaf(-dd, r0, 1.f), r0);
                     const float f = fmaf(g[k], inv, l[k] * inv);
                     if (k < cnt) dr[jj - k] = make_float2(f, rb * inv);
                     rb = fmaf(f, rb, r[k]);
-                    eb = fmaf(g[k] * rcp_nr(d[k]) * (g[k] * r0), eb, ee[k]);
+                    eb = fmaf(q[k] * (g[k] * r0), eb, ee[k]);
                     if (k == cnt - 1) {
                         eh = eb;
                         rh = rb;
@@ -1015,8 +1021,8 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
                     if (!more) break;
                 }
             }
-            const float2 dq = dpp[h];
-            const float inv = rcp_nr(dq.x + (dq.y + eh));
+            const float dhh = dpp[h].x;
+            const float inv = rcp_nr(dhh + eh);
             if (P.parent < 0) {  // soma: its dV
                 dr[h].y = rh * inv;
                 return;
@@ -1025,7 +1031,7 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
             const float gh = a.gimp * fabsf(gs.x), gl = a.gimp * gs.y;
             const float f = fmaf(gh, inv, gl * inv);
             dr[h] = make_float2(f, rh * inv);
-            const float ce = gh * rcp_nr(dq.x) * f * eh, cr = f * rh;
+            const float ce = gh * rcp_nr(dhh) * f * eh, cr = f * rh;
             if (P.nflag & kPathAloneG) {
                 float2 v = dr[P.parent];
                 v.x += ce;
@@ -1188,7 +1194,7 @@ __global__ void __launch_bounds__(256) giant_assemble_kernel(StepArgs32 a)
                 if (!signbit(gc.x))  // link to the child i+1
                     r = mmf::add(r, mmf::mul(f2(gc), mmf::vdiff_df(Vq[i + 1], vq)));
             }
-            dr[i] = make_float2(a.g_implicit ? ar.hi * (gna.hi + gk.hi) : 0.f, r.hi);
+            dr[i] = make_float2((a.g_implicit ? ar.hi * (gna.hi + gk.hi) : 0.f) + a.dp[c0 + i].y, r.hi);
             drl[i] = r.lo;
         }
     }

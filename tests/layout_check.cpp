@@ -64,23 +64,24 @@ float rcp_nr(float x)
 }
 
 // Coefficients of one compartment for the sweeps: the implicit coupling to
-// its parent (gh + gl) and the passive eliminated diagonal (dh + dl).
+// its parent (gh + gl), the passive eliminated diagonal's nearest float dh
+// and the factor f0 = gh / dh of the active part's recurrence.
 struct Co {
-    std::vector<float> gh, gl, dh, dl;
+    std::vector<float> gh, gl, dh, f0;
 };
 
 // One step of the serial elimination at compartment j of a path: its
 // active part eb and rhs rb in, the next compartment's (ep, rp) out.
 inline void elim_step(const Co &k, int j, float &eb, float &rb, float ep, float rp, float *f_out, float *c_out)
 {
-    const float dd = k.dh[j] + (k.dl[j] + eb);
+    const float dd = k.dh[j] + eb;
     const float r0 = 1.f / dd;
     const float inv = std::fma(r0, std::fma(-dd, r0, 1.f), r0);
     const float f = std::fma(k.gh[j], inv, k.gl[j] * inv);
     *f_out = f;
     *c_out = rb * inv;
     rb = std::fma(f, rb, rp);
-    eb = std::fma(k.gh[j] * rcp_nr(k.dh[j]) * (k.gh[j] * r0), eb, ep);
+    eb = std::fma(k.f0[j] * (k.gh[j] * r0), eb, ep);
 }
 
 // The warp-swept elimination of the interior of the path [h, e): leaves
@@ -95,8 +96,8 @@ void warp_eliminate(int h, int e, std::vector<float> &se, std::vector<float> &sr
         Mat q{1.f, 0.f, 0.f, 1.f};
         for (int tt = t0; tt < t1; ++tt) {
             const int j = e - 1 - tt;
-            const float D = k.dh[j] + k.dl[j], En = se[j - 1];
-            const float A = std::fma(k.gh[j] * rcp_nr(D), k.gh[j], En), B = En * D;
+            const float D = k.dh[j], En = se[j - 1];
+            const float A = std::fma(k.f0[j], k.gh[j], En), B = En * D;
             const float n00 = std::fma(A, q.m00, B * q.m10), n01 = std::fma(A, q.m01, B * q.m11);
             const float n10 = std::fma(D, q.m10, q.m00), n11 = std::fma(D, q.m11, q.m01);
             const float s = 1.f / (n00 + n01 + n10 + n11);
@@ -400,17 +401,23 @@ int main(int argc, char **argv)
         std::vector<double> dp(d0);  // the passive part eliminated in double
         for (int j = G.ncomp - 1; j >= 1; --j)
             if (pp[j] >= 0) dp[pp[j]] -= g[j] * g[j] / dp[j];
+        // the low word of d0' enters the active part: eps_j = dl_j minus the
+        // children's dl at the passive coupling factor
+        std::vector<double> eps(G.ncomp);
+        for (int j = 0; j < G.ncomp; ++j) eps[j] = dp[j] - (double)(float)dp[j];
+        for (int j = G.ncomp - 1; j >= 1; --j)
+            if (pp[j] >= 0) eps[pp[j]] -= (g[j] / dp[j]) * (g[j] / dp[j]) * (dp[j] - (double)(float)dp[j]);
         Co k;
-        k.gh.resize(G.ncomp); k.gl.resize(G.ncomp); k.dh.resize(G.ncomp); k.dl.resize(G.ncomp);
+        k.gh.resize(G.ncomp); k.gl.resize(G.ncomp); k.dh.resize(G.ncomp); k.f0.resize(G.ncomp);
         for (int j = 0; j < G.ncomp; ++j) {
             k.gh[j] = (float)g[j];
             k.gl[j] = (float)(g[j] - (double)k.gh[j]);
             k.dh[j] = (float)dp[j];
-            k.dl[j] = (float)(dp[j] - (double)k.dh[j]);
+            k.f0[j] = k.gh[j] * rcp_nr(k.dh[j]);
         }
         std::vector<float> se(G.ncomp), sr(G.ncomp), scd(G.npath), scr(G.npath);
         for (int j = 0; j < G.ncomp; ++j) {
-            se[j] = (float)a[j];
+            se[j] = (float)a[j] + (float)eps[j];
             sr[j] = (float)r[j];
         }
         for (int kk = 0; kk < G.nbundle; ++kk) {
@@ -432,12 +439,12 @@ int main(int argc, char **argv)
                             sr[j] = cj;
                         }
                     }
-                    const float inv = rcp_nr(k.dh[h] + (k.dl[h] + eb));
+                    const float inv = rcp_nr(k.dh[h] + eb);
                     if (Pa(p) < 0) { sr[h] = rb * inv; continue; }
                     const float fh = std::fma(k.gh[h], inv, k.gl[h] * inv);
                     se[h] = fh;
                     sr[h] = rb * inv;
-                    const float ce = k.gh[h] * rcp_nr(k.dh[h]) * fh * eb, cr = fh * rb;
+                    const float ce = k.f0[h] * fh * eb, cr = fh * rb;
                     if (T.alone[p]) { se[Pa(p)] += ce; sr[Pa(p)] += cr; } else { scd[p] = ce; scr[p] = cr; }
                 }
                 const int zend = lo[l] + mc[l];
