@@ -57,8 +57,12 @@ typedef enum {
 enum {
     MM_FP64 = 0,   /* everything in FP64 */
     MM_FP32C = 1   /* FP32 increments on a fixed-point state (V in 2^-23 mV, gates
-                      in 2^-32), rate functions as float pairs; FP64 soma
-                      voltage and spike-crossing time */
+                      in 2^-32); model constants, currents and synaptic
+                      conductances as float pairs, the Hines solve in FP32 on
+                      the FP64-eliminated passive diagonal; FP64 soma voltage
+                      and spike-crossing time.  Voltages must stay within
+                      +-120 mV (the fixed-point range): a compartment driven
+                      beyond it stops the network with MM_ENUMERIC */
 };
 
 /* Time discretisation of the voltage equation (Eq. 1) -- the reading of
