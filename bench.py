@@ -58,7 +58,15 @@ KERNEL_BYTES_FP32C = {"step": (56.0, 20.0), "big": (56.0, 20.0), "giant": (56.0,
 # kernel built from the sources whose SHA-256 is recorded; after any change
 # they are not reported.
 KERNEL_SOURCES = ("mm_kernels_fp32c.cu", "mm_fp32c_math.h", "mm_internal.h", "mm_tma.h")
-PROFILED = {}
+PROFILED = {
+    # regular-class launch of the command in profiles/step_fp32c_multi10k.md
+    ("multi10k", "fp32c", "step", "soma"): {
+        "sha256": "aa4fd3c5b4bbcac51756344b3e29cab3255c0331b53c93ab5e35b8b3dfed9e27",
+        "dram_bytes": 510190848 + 121059072,
+        "warp_instructions": 404135077,
+        "comps": 9484756,
+    },
+}
 
 
 def _kernel_sources_sha256():
@@ -299,6 +307,9 @@ def main():
                     help="multi10k (default; 10,000 neurons, log-uniform [50, 5000]), lognormal100k, mixed200k, mono64, "
                          "shapes10k, paper_mono, paper_multi20, paper_fisher")
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32c"])
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the workload's neuron count (and giant sizes) by this factor, for small profiling "
+                         "cases of the same distributions")
     ap.add_argument("--graph-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -325,7 +336,7 @@ def main():
         run_paper_replay(args)
         return
 
-    net = netgen.make_config(args.config, src_points=args.detect == "points")
+    net = netgen.make_config(args.config, scale=args.scale, src_points=args.detect == "points")
     precision = args.precision or "fp32c"
     if args.impl == "reference":
         run_reference(args, net)
