@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "mm.h"
+#include "mm_gate_table.h"
 #include "mm_internal.h"
 #include "mm_layout.h"
 
@@ -100,6 +101,7 @@ struct mm_net {
     float2 *dr = nullptr;
     float *drl = nullptr;
     float4 *pq = nullptr;
+    float4 *gtab = nullptr;           // gate table for dt (mm_gate_table.h)
     int64_t *soma_internal = nullptr, *internal_of64 = nullptr;
     // both
     double *stim = nullptr;
@@ -677,6 +679,13 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
             UP(net->gax2, gax2.data(), C);
             UP(net->dp2, dp2.data(), C);
         }
+        {
+            // X(V) and E(V) of the three gates for this dt, per 0.5 mV
+            static_assert(sizeof(mmf::Tab4) == sizeof(float4), "table quads are float4");
+            std::vector<mmf::Tab4> tab((size_t)mmf::kTabQuads * mmf::kTabIntervals);
+            mmf::build_gate_table(opt->dt_ms, tab.data());
+            UP(net->gtab, reinterpret_cast<const float4 *>(tab.data()), tab.size());
+        }
         ZR(net->Vsoma, N);
         ZR(net->gsyn2, (size_t)std::max<int64_t>(net->nsite, 1));
         ZR(net->dr, (size_t)std::max<int64_t>(L.giant_comps, 1));
@@ -888,8 +897,7 @@ mm_status build(mm_net *net, const mm_morphologies *morph, const mm_channel_para
         a.Esyn = pot(syn ? syn->e_rev_mV : 0.0);
         a.gimp = opt->scheme == MM_SCHEME_CN ? 0.5f : 1.0f;
         a.g_implicit = opt->scheme == MM_SCHEME_CN ? 0 : 1;
-        a.dt = (float)opt->dt_ms;
-        a.dt_lo = (float)(opt->dt_ms - (double)a.dt);
+        a.gtab = net->gtab;
         a.decay = split_pair(decay);
         a.threshold = chan->threshold_mV;
         {

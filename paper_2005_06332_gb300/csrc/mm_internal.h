@@ -263,7 +263,7 @@ struct StepArgs32 {
     float2 gNa, gK, gL;               // channel densities times 1e3 (uS per cm^2 of membrane), pairs
     FxPot ENa, EK, EL, Esyn;
     float2 decay;                     // exp(-dt / tau_syn), pair
-    float dt, dt_lo;                  // dt as a float pair (dt + dt_lo)
+    const float4 *gtab;               // gate table for dt (mm_gate_table.h): 12 arrays of 481 float4
     int64_t C;                        // compartments (gate kernel)
     double threshold, dt64;
     float gimp;                       // implicit share of each axial coupling: 1 or 1/2 (as in StepArgs)

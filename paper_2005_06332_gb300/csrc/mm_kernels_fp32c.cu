@@ -18,9 +18,10 @@
 //     and synaptic conductance, which the FP32 elimination carries as a
 //     perturbation of it (the passive part alone would lose most of the
 //     active conductance's digits to the capacitive and axial terms);
-//   * the rate functions, steady states and relaxation factors are computed
-//     as float pairs (an FMA-only exponential, two per compartment, shared
-//     by the six rates);
+//   * each gate's steady state X(V) and relaxation factor E(V) for the
+//     step come from a table of degree-5 polynomials per 0.5 mV interval,
+//     built in FP64 for the network's dt, whose two leading terms are float
+//     pairs (mm_gate_table.h; within 1e-10 relative);
 //   * the soma voltage is also accumulated in FP64 and the spike crossing
 //     time is computed in FP64.
 #include <cuda_runtime.h>
@@ -29,6 +30,7 @@
 #include <type_traits>
 
 #include "mm_fp32c_math.h"
+#include "mm_gate_table.h"
 #include "mm_internal.h"
 #include "mm_tma.h"
 
@@ -197,15 +199,26 @@ __device__ __forceinline__ unsigned long long global_ns()
 }
 
 
+__device__ __forceinline__ mmf::Tab4 ld_tab(const float4 *p)
+{
+    const float4 v = __ldg(p);
+    return {v.x, v.y, v.z, v.w};
+}
+
 // Exponential-Euler gate update at V^{n+1} of one compartment (its V is
-// final for this step).
+// final for this step): X and E of each gate from the table interval of V.
 __device__ __forceinline__ void gate_update(const StepArgs32 &a, int64_t c)
 {
-    const mmf::F2 dt2{a.dt, a.dt_lo};
-    const mmf::Rates r = mmf::hh_rates(a.Vq[c]);
-    a.mq[c] = mmf::gate_step(a.mq[c], r.am, r.bm, dt2);
-    a.hq[c] = mmf::gate_step(a.hq[c], r.ah, r.bh, dt2);
-    a.nq[c] = mmf::gate_step(a.nq[c], r.an, r.bn, dt2);
+    const mmf::TabIndex t = mmf::tab_index(a.Vq[c]);
+    const float4 *f = a.gtab + t.i;
+    constexpr int I = mmf::kTabIntervals;
+    uint32_t *const q[3] = {a.mq + c, a.hq + c, a.nq + c};
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+        const mmf::Tab4 tg[4] = {ld_tab(f + (4 * g) * I), ld_tab(f + (4 * g + 1) * I), ld_tab(f + (4 * g + 2) * I),
+                                 ld_tab(f + (4 * g + 3) * I)};
+        *q[g] = mmf::tab_gate_step(*q[g], tg, t.u);
+    }
 }
 
 // Gate updates of the compartments pc0 .. pc0 + pn - 1, in chunks of
