@@ -57,13 +57,14 @@ KERNEL_BYTES_FP32C = {"step": (56.0, 20.0), "big": (56.0, 20.0), "giant": (56.0,
 # launch, with the compartments that launch updated.  They describe the
 # kernel built from the sources whose SHA-256 is recorded; after any change
 # they are not reported.
-KERNEL_SOURCES = ("mm_kernels_fp32c.cu", "mm_fp32c_math.h", "mm_internal.h", "mm_tma.h")
+KERNEL_SOURCES = ("mm_kernels_fp32c.cu", "mm_fp32c_math.h", "mm_gate_table.h", "mm_internal.h", "mm_tma.h")
 PROFILED = {
-    # regular-class launch of the command in profiles/step_fp32c_multi10k.md
+    # ncu counters of one regular-class launch of the step kernel (multi10k,
+    # 512 threads, 4096-compartment items, a step inside the timed window)
     ("multi10k", "fp32c", "step", "soma"): {
-        "sha256": "aa4fd3c5b4bbcac51756344b3e29cab3255c0331b53c93ab5e35b8b3dfed9e27",
-        "dram_bytes": 510190848 + 121059072,
-        "warp_instructions": 404135077,
+        "sha256": "291920e376904b9dc400d5ff1a48a00010d50ac170a273d6338c8bc839cfeadc",
+        "dram_bytes": 506971904 + 120907520,
+        "warp_instructions": 290835335,
         "comps": 9484756,
     },
 }
