@@ -443,11 +443,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
         }
         __syncthreads();
         // every rhs is now final (its high word the nearest float): the
-        // passive diagonal and the factor g / d0' of the active part's
-        // recurrence take the place of the low words
+        // passive diagonal and the factor g^2 / d0' of the active part's
+        // recurrence (taken as (g / d0') g) take the place of the low words
         for (int i = tid; i < G.ncomp; i += NS) {
             const float dh = __ldg(&a.dp[c0 + i].x);
-            sdp[i] = make_float2(dh, sgp[i].x * rcp_nr(dh));
+            sdp[i] = make_float2(dh, (sgp[i].x * rcp_nr(dh)) * sgp[i].x);
         }
         __syncthreads();
 
@@ -496,8 +496,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
         //    The diagonal of compartment j after the elimination of its
         //    subtree is d'_j = d0'_j + e_j, with d0'_j the passive one
         //    (eliminated at set-up) and e_j the active conductance carried
-        //    up the tree: e_{p} += (g/d0'_j) (g/d'_j) e_j, the exact
-        //    difference of the two eliminations.  kSweepChunk compartments
+        //    up the tree: e_{p} += (g^2/d0'_j) (1/d'_j) e_j, the exact
+        //    difference of the two eliminations (g^2/d0'_j staged per
+        //    compartment, so that the dependent chain is an add, the
+        //    approximate reciprocal, a multiply and an FMA).  kSweepChunk compartments
         //    at a time with their operands loaded before any of their stores
         //    (indices past the head are clamped and their results dropped).
         //    The head is then eliminated into its parent compartment: a path
@@ -519,7 +521,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
             const float2 gq = sgp[h];
             const float f = fmaf(gq.x, inv, gq.y * inv);
             sdr[h] = make_float2(f, rh * inv);
-            const float ce = dq.y * f * eh, cr = f * rh;
+            const float ce = gq.x * rcp_nr(dq.x) * f * eh, cr = f * rh;
             if (P.nflag & kPathAlone) {
                 float2 v = sdr[P.parent];
                 v.x += ce;
@@ -539,7 +541,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
             float eh = eb, rh = rb;
             for (; j > h; j -= kSweepChunk) {
                 const int cnt = j - h;
-                float gh[kSweepChunk], gl[kSweepChunk], dh[kSweepChunk], f0[kSweepChunk];
+                float gh[kSweepChunk], gl[kSweepChunk], dh[kSweepChunk], fg[kSweepChunk];
                 float ep[kSweepChunk], rp[kSweepChunk];
 #pragma unroll
                 for (int k = 0; k < kSweepChunk; ++k) {
@@ -548,7 +550,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
                     gh[k] = gq.x;
                     gl[k] = gq.y;
                     dh[k] = dq.x;
-                    f0[k] = dq.y;
+                    fg[k] = dq.y;
                     ep[k] = w.x;
                     rp[k] = w.y;
                 }
@@ -559,13 +561,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
                     // that the rhs and the substitution use take it refined
                     const float dd = dh[k] + eb;
                     const float r0 = rcp_approx(dd);
-                    const float fa = gh[k] * r0;
                     const float inv = fmaf(r0, fmaf(-dd, r0, 1.f), r0);
                     const float f = fmaf(gh[k], inv, gl[k] * inv);
                     const float c = rb * inv;
                     if (k < cnt) sdr[j - k] = make_float2(f, c);
                     rb = fmaf(f, rb, rp[k]);
-                    eb = fmaf(f0[k] * fa, eb, ep[k]);
+                    eb = fmaf(fg[k] * r0, eb, ep[k]);
                     if (k == cnt - 1) {
                         eh = eb;
                         rh = rb;
@@ -682,7 +683,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
                 const int j = e - 1 - tt;
                 const float2 gq = sgp[j], dq = sdp[j];
                 const float D = dq.x, En = sdr[j - 1].x;
-                const float A = fmaf(dq.y, gq.x, En), B = En * D;
+                const float A = dq.y + En, B = En * D;
                 const float n00 = fmaf(A, m00, B * m10), n01 = fmaf(A, m01, B * m11);
                 const float n10 = fmaf(D, m10, m00), n11 = fmaf(D, m11, m01);
                 const float s = rcp_approx(n00 + n01 + n10 + n11);
@@ -727,7 +728,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
                 const float f = fmaf(gq.x, inv, gq.y * inv);
                 A *= f;
                 B = fmaf(f, B, w.y);
-                eb = fmaf(dq.y * (gq.x * r0), eb, w.x);
+                eb = fmaf(dq.y * r0, eb, w.x);
                 nb = w;
             }
             for (int off = 1; off < 32; off <<= 1) {
@@ -756,7 +757,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) step_fp32c_kernel(StepArgs32 a)
                 const float f = fmaf(gq.x, inv, gq.y * inv);
                 sdr[j] = make_float2(f, rb * inv);
                 rb = fmaf(f, rb, w.y);
-                eb = fmaf(dq.y * (gq.x * r0), eb, w.x);
+                eb = fmaf(dq.y * r0, eb, w.x);
             }
             // the head, from the lane whose chunk ends at it
             const int lastl = (m - 1) / cs;
@@ -994,7 +995,7 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
                     g[k] = a.gimp * fabsf(gs.x);
                     l[k] = a.gimp * gs.y;
                     d[k] = dpp[x].x;
-                    q[k] = g[k] * rcp_nr(d[k]);
+                    q[k] = (g[k] * rcp_nr(d[k])) * g[k];
                     ee[k] = w.x;
                     r[k] = w.y;
                 }
@@ -1010,7 +1011,7 @@ __global__ void __launch_bounds__(NT) giant_fp32c_kernel(StepArgs32 a)
                     const float f = fmaf(g[k], inv, l[k] * inv);
                     if (k < cnt) dr[jj - k] = make_float2(f, rb * inv);
                     rb = fmaf(f, rb, r[k]);
-                    eb = fmaf(q[k] * (g[k] * r0), eb, ee[k]);
+                    eb = fmaf(q[k] * r0, eb, ee[k]);
                     if (k == cnt - 1) {
                         eh = eb;
                         rh = rb;

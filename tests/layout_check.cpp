@@ -64,10 +64,10 @@ float rcp_nr(float x)
 }
 
 // Coefficients of one compartment for the sweeps: the implicit coupling to
-// its parent (gh + gl), the passive eliminated diagonal's nearest float dh
-// and the factor f0 = gh / dh of the active part's recurrence.
+// its parent (gh + gl), the passive eliminated diagonal's nearest float dh,
+// f0 = gh / dh, and the factor fg = f0 gh of the active part's recurrence.
 struct Co {
-    std::vector<float> gh, gl, dh, f0;
+    std::vector<float> gh, gl, dh, f0, fg;
 };
 
 // One step of the serial elimination at compartment j of a path: its
@@ -81,7 +81,7 @@ inline void elim_step(const Co &k, int j, float &eb, float &rb, float ep, float 
     *f_out = f;
     *c_out = rb * inv;
     rb = std::fma(f, rb, rp);
-    eb = std::fma(k.f0[j] * (k.gh[j] * r0), eb, ep);
+    eb = std::fma(k.fg[j] * r0, eb, ep);
 }
 
 // The warp-swept elimination of the interior of the path [h, e): leaves
@@ -97,7 +97,7 @@ void warp_eliminate(int h, int e, std::vector<float> &se, std::vector<float> &sr
         for (int tt = t0; tt < t1; ++tt) {
             const int j = e - 1 - tt;
             const float D = k.dh[j], En = se[j - 1];
-            const float A = std::fma(k.f0[j], k.gh[j], En), B = En * D;
+            const float A = k.fg[j] + En, B = En * D;
             const float n00 = std::fma(A, q.m00, B * q.m10), n01 = std::fma(A, q.m01, B * q.m11);
             const float n10 = std::fma(D, q.m10, q.m00), n11 = std::fma(D, q.m11, q.m01);
             const float s = 1.f / (n00 + n01 + n10 + n11);
@@ -408,12 +408,13 @@ int main(int argc, char **argv)
         for (int j = G.ncomp - 1; j >= 1; --j)
             if (pp[j] >= 0) eps[pp[j]] -= (g[j] / dp[j]) * (g[j] / dp[j]) * (dp[j] - (double)(float)dp[j]);
         Co k;
-        k.gh.resize(G.ncomp); k.gl.resize(G.ncomp); k.dh.resize(G.ncomp); k.f0.resize(G.ncomp);
+        k.gh.resize(G.ncomp); k.gl.resize(G.ncomp); k.dh.resize(G.ncomp); k.f0.resize(G.ncomp); k.fg.resize(G.ncomp);
         for (int j = 0; j < G.ncomp; ++j) {
             k.gh[j] = (float)g[j];
             k.gl[j] = (float)(g[j] - (double)k.gh[j]);
             k.dh[j] = (float)dp[j];
             k.f0[j] = k.gh[j] * rcp_nr(k.dh[j]);
+            k.fg[j] = k.f0[j] * k.gh[j];
         }
         std::vector<float> se(G.ncomp), sr(G.ncomp), scd(G.npath), scr(G.npath);
         for (int j = 0; j < G.ncomp; ++j) {
