@@ -62,9 +62,9 @@ PROFILED = {
     # ncu counters of one regular-class launch of the step kernel (multi10k,
     # 512 threads, 4096-compartment items, a step inside the timed window)
     ("multi10k", "fp32c", "step", "soma"): {
-        "sha256": "291920e376904b9dc400d5ff1a48a00010d50ac170a273d6338c8bc839cfeadc",
-        "dram_bytes": 506971904 + 120907520,
-        "warp_instructions": 290835335,
+        "sha256": "af2bdc7c0dae0158d95e614e20bedf57bbfb47c8a4cd8494347cf39c14973a4c",
+        "dram_bytes": 507479552 + 121233664,
+        "warp_instructions": 289721058,
         "comps": 9484756,
     },
 }
