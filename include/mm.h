@@ -184,6 +184,9 @@ typedef struct {
                                    handed in with mm_inject_spikes.  MM_DETECT_SOMA only; 0 = none */
 } mm_options;
 
+/* The largest neuron (compartments) the MM_FP64 path holds. */
+#define MM_FP64_MAX_NEURON_COMPS 8192
+
 /* Fill *opt with defaults: FP64, size-sorted, graphs of 40 steps, dt 0.025 ms. */
 void mm_default_options(mm_options *opt);
 
@@ -193,7 +196,10 @@ void mm_default_options(mm_options *opt);
  * On success *out owns the network; on failure *out is NULL.
  * Errors: MM_EINVAL (bad sizes, parent[i] >= i, non-positive geometry,
  * dst_comp or src_comp out of range, delay < dt, dt <= 0, unknown scheme or
- * detection mode, deterministic_delivery not 0 or 1), MM_ENOMEM, MM_ECUDA, MM_ENOTSUP. */
+ * detection mode, deterministic_delivery not 0 or 1), MM_ENOMEM, MM_ECUDA,
+ * MM_ENOTSUP (e.g. MM_FP64 with a neuron of more than MM_FP64_MAX_NEURON_COMPS
+ * compartments: the FP64 kernel holds a whole neuron in one block's shared
+ * memory; MM_FP32C has no such limit). */
 mm_status mm_create_network(const mm_morphologies *morph, const mm_channel_params *chan,
                             const mm_synapses *syn, const double *stim_nA,
                             const mm_options *opt, mm_net **out);

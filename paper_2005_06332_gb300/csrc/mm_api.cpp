@@ -19,7 +19,7 @@ namespace {
 constexpr int kStepThreads = 256;
 constexpr int kDefaultGroupComps = 4096;
 constexpr int kDefaultGroupComps32 = 2048;  // FP32c: 24 B of shared memory per compartment
-constexpr int kMaxGroupComps = 8192;
+constexpr int kMaxGroupComps = MM_FP64_MAX_NEURON_COMPS;
 constexpr int kMaxGroupComps32 = 1 << 30;
 constexpr int kGiantSmemLimit = 110 * 1024;  // FP32c regular class: two blocks per SM
 constexpr int kBigSmemLimit = 224 * 1024;    // FP32c large class (one block per SM); above it: giant kernel
