@@ -180,9 +180,18 @@ def cpu_baseline(net, seconds_hint: float = 15.0, detect: str = "soma"):
     t0 = time.perf_counter()
     oracle.simulate(sub, steps, threads=cores, detect=detect)
     el = time.perf_counter() - t0
+    # the same oracle on one core, over a tenth of the sample's neurons
+    k1 = max(1, k // 10)
+    sub1 = net.subset(pick[:: max(1, k // k1)][:k1], keep_synapses=True)
+    steps1 = max(8, steps // 4)
+    t0 = time.perf_counter()
+    oracle.simulate(sub1, steps1, threads=1, detect=detect)
+    el1 = time.perf_counter() - t0
     return {"value": sub.n_comp * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{k} of {net.n_neurons} neurons ({sub.n_comp} compartments, synapses among them), "
-                      f"{steps} steps from rest, FP64 C oracle with OpenMP over neurons"}
+                      f"{steps} steps from rest, FP64 C oracle with OpenMP over neurons",
+            "one_core": {"value": sub1.n_comp * steps1 / el1, "unit": UNIT, "cores": 1,
+                         "sample": f"{sub1.n_neurons} of those neurons ({sub1.n_comp} compartments), {steps1} steps"}}
 
 
 def run_reference(args, net):
