@@ -76,6 +76,23 @@ def test_fp32c_short_horizon_parity():
     assert ref.n_spikes > 0
 
 
+@pytest.mark.parametrize("dt", [0.01, 0.05])
+def test_fp32c_other_time_steps(dt):
+    """The gate table and the passive elimination are built for the network's
+    dt: other steps than the default 0.025 ms, over 20 ms of spiking."""
+    net = netgen.make_network(30, size_dist=("loguniform", 2, 300), p_branch=("uniform", 0.02, 0.3),
+                              syn_per_neuron=10, seed=22, stim_nA=(0.2, 0.8))
+    net.dt = dt
+    steps = int(round(20.0 / dt))
+    ref = oracle.simulate(net, steps)
+    V, gates, sn, st, _ = _run(net, steps)
+    assert ref.n_spikes > 10
+    assert np.max(np.abs(V - ref.V)) <= TOL_V
+    for k, r in (("m", ref.m), ("h", ref.h), ("n", ref.n)):
+        assert np.max(np.abs(gates[k] - r)) <= 1e-4, k
+    assert _spike_match(net, sn, st, ref) is not None
+
+
 @pytest.mark.parametrize("dist", [("group", 20, 700, 300), ("fisher", 10, 40, 300, 10, 5000)])
 def test_fp32c_paper_size_distributions_parity(dist):
     """The size distributions of the paper's load-balance tests (a group of 20
