@@ -228,7 +228,7 @@ constexpr int kGateChunk = 64;
 
 // Compartments per step of a path sweep (their operands are loaded
 // together before the step's dependent chain).
-constexpr int kSweepChunk = 8;
+constexpr int kSweepChunk = 4;
 
 // Paths of at least this many compartments are swept by a whole warp
 // (chunks per lane combined by warp scans) instead of by one lane.
