@@ -63,9 +63,9 @@ PROFILED = {
     # ncu counters of one regular-class launch of the step kernel (multi10k,
     # 512 threads, 4096-compartment items, a step inside the timed window)
     ("multi10k", "fp32c", "step", "soma"): {
-        "sha256": "af2bdc7c0dae0158d95e614e20bedf57bbfb47c8a4cd8494347cf39c14973a4c",
-        "dram_bytes": 507479552 + 121233664,
-        "warp_instructions": 289721058,
+        "sha256": "f442347e16f327b6adfd673c0fa934f5e2714eac09b925479dac6083f08d09c0",
+        "dram_bytes": 495057920 + 111741184,
+        "warp_instructions": 285126986,
         "comps": 9484756,
     },
 }
