@@ -104,3 +104,16 @@ def test_planted_coefficient_error_is_caught(checker, tmp_path):
     F, _ = _run(exe, 0.025, vq, np.full((len(vq), 3), 1 << 31, np.int64))
     want = _hh(vq / VQ, 0.025)
     assert (np.abs(F - want) / np.abs(want)).max() > 2e-10
+
+
+def test_voltages_beyond_the_range_read_the_end_intervals(checker):
+    """V outside +-120 mV (which the step reports as MM_ENUMERIC) still reads
+    inside the table: the first or last interval at its end."""
+    lo, hi = -120 * VQ - VQ // 4, 120 * VQ + VQ // 4  # the table's outer edges
+    vq = np.array([lo - 5 * VQ, lo, -2**31 + 1, hi + 5 * VQ, hi - 1, 2**31 - 1], np.int64)
+    F, _ = _run(checker, 0.025, vq, np.full((len(vq), 3), 1 << 31, np.int64))
+    assert np.all(np.isfinite(F))
+    np.testing.assert_array_equal(F[0], F[1])
+    np.testing.assert_array_equal(F[0], F[2])
+    np.testing.assert_allclose(F[3], F[4], rtol=1e-7)  # one fixed-point unit apart
+    np.testing.assert_array_equal(F[3], F[5])
